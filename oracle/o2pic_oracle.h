@@ -1,0 +1,101 @@
+/*
+ * o2pic_oracle.h -- declarations of the plain FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle exists to check the GPU library
+ * against a slow, obviously correct restatement of the method of Bronold et
+ * al., "Radio-frequency discharges in Oxygen. Part 1: Modeling"
+ * (Sec. II, Sec. III, Eqs. 1-9, Table I).  Only tests/, the smoke check and
+ * the CPU-baseline leg of bench.py may load it.  It shares no code, header,
+ * constant or table generator with the CUDA library.
+ *
+ * Species: 0 = electron, 1 = O-, 2 = O2+.  All quantities SI unless a name
+ * says otherwise (_eV).
+ */
+#ifndef O2PIC_ORACLE_H
+#define O2PIC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double L;            /* electrode gap [m] (Sec. II) */
+    double p_Pa;         /* O2 reservoir pressure (Sec. II) */
+    double T_gas;        /* O2 temperature [K] */
+    double U_rf;         /* RF amplitude [V], driven electrode at x = 0 */
+    double f_rf;         /* RF frequency [Hz] */
+    double rf_phase;     /* U(t) = U_rf sin(2 pi f t + rf_phase); 0 in the paper */
+    double dt;           /* time step [s] */
+    double weight;       /* real particles per m^2 of electrode per superparticle */
+    double C_delta;      /* O2(a) / O2 density ratio (Sec. III C, "C") */
+    double T0_eV[3];     /* initial Maxwellian temperatures */
+    double ecap_eV[3];   /* energy cap used when bounding the collision frequency */
+    double numax_safety; /* multiplier on the bound (>= 1) */
+    double eedf_emax, iedf_emax, fm_emax;   /* histogram ranges [eV] */
+    long long n_init[3]; /* initial superparticles per species */
+    unsigned long long seed;
+    int n_cells;
+    int n1;              /* pair-reaction interval in steps (tau = n1 dt) */
+    int sort_interval;   /* cell sort interval in steps */
+    int diag_every;      /* 0 = no diagnostics */
+    int eedf_bins, iedf_bins, fm_bins;
+    int discharge;       /* discharge index, enters the random counter */
+    int cx_isotropic;    /* reaction (6): 0 = velocity swap, 1 = isotropic */
+} orc_cfg;
+
+typedef struct {
+    int reaction;          /* 4..19, numbering of Table I */
+    int sub;               /* vibrational level for reaction 7, else 0 */
+    int n;                 /* nodes */
+    const double *E_eV;    /* node energies, strictly increasing */
+    const double *sigma_m2;/* cross section at the nodes */
+    double threshold_eV;   /* sigma = 0 below; energy loss of the channel */
+} orc_xs;
+
+typedef struct orc_sim orc_sim;
+
+orc_sim *orc_create(const orc_cfg *cfg, const orc_xs *xs, int n_xs, int load);
+void orc_destroy(orc_sim *s);
+void orc_step(orc_sim *s, long long nsteps);
+long long orc_step_index(const orc_sim *s);
+long long orc_count(const orc_sim *s, int sp);
+void orc_get(const orc_sim *s, int sp, double *x, double *vx, double *vy,
+             double *vz, int *alive);
+int orc_set(orc_sim *s, int sp, long long n, const double *x, const double *vx,
+            const double *vy, const double *vz, const int *alive);
+void orc_set_step(orc_sim *s, long long step);
+double orc_numax(const orc_sim *s, int sp);
+void orc_fields(orc_sim *s, double *rho, double *phi, double *E);
+/* counters: absorbed[3][2], events[20], violations[2] (gas, pair), births[3] */
+void orc_counters(const orc_sim *s, long long *absorbed, long long *events,
+                  long long *violations, long long *births);
+/* diagnostics: dens_sum[3][N+1], phi_sum[N+1], eedf, iedf[2][bins], fm[N][bins] */
+long long orc_diag(const orc_sim *s, double *dens_sum, double *phi_sum,
+                   long long *eedf, long long *iedf, long long *fm);
+
+/* unit-level entry points used by the pins */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_sigma(const orc_sim *s, int table, double E_eV);
+void orc_poisson(int n_cells, double dx, double phi0, double phiN,
+                 const double *rho, double *phi);
+void orc_field(int n_cells, double dx, const double *rho, const double *phi,
+               double *E);
+/* one gas-target event of reaction r for a particle of species sp with
+ * velocity v against a gas molecule of velocity V; r4 = four uniforms of the
+ * second draw, r2 = two uniforms of the third draw.  Outputs the particle's new
+ * velocity, the products (up to 2: species + velocity), their count, and
+ * whether the particle survives. */
+int orc_gas_event(const orc_sim *s, int sp, int reaction, int table,
+                  const double v[3], const double V[3], const double r4[4],
+                  const double r2[2], double vout[3], int *alive_out,
+                  int *prod_sp, double *prod_v, double *Vout);
+/* reaction 19 pair event: electron v, O- target vt; returns e1 and e2 */
+void orc_pair19_event(const orc_sim *s, int table, const double v[3],
+                      const double vt[3], const double rc[2], const double r2[2],
+                      double v1[3], double v2[3], double Vo[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,517 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms printed in the paper (Eqs. 4, 8, 9),
+exact solutions of the discrete field equations, leapfrog trajectories,
+the cold-plasma dispersion relation, conservation laws of each reaction of
+Table I, the collision-rate algebra of the null-collision method and of
+Eq. 1, and a library solver.  Runs on the CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_0705_0495_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+AMU = 1.66053906660e-27
+KB = 1.380649e-23
+EPS0 = 8.8541878128e-12
+M_O = 16 * AMU
+M_O2 = 32 * AMU
+M_OM = M_O + ME
+M_OP = M_O2 - ME
+MASS = (ME, M_OM, M_OP)
+
+
+def _disch(**kw):
+    base = dict(L=1.0, n_cells=128, p_Pa=20.0, U_rf=0.0, n_op=0, n0_m3=0.0,
+                weight_override=0.0, n1=0, sort_interval=0, diag_every=0,
+                T0_eV=(0.0, 0.0, 0.0), dt_override=1e-10)
+    base.update(kw)
+    return inputs.Discharge(**base)
+
+
+def _flat(reaction, sigma, grid=inputs.E_GRID_E, th=0.0):
+    E = inputs.geometric_grid(*grid)
+    return dict(reaction=reaction, sub=0, E_eV=E, sigma_m2=np.full_like(E, sigma),
+                threshold_eV=th)
+
+
+def _table(reaction):
+    return [t for t in inputs.xs_tables() if t["reaction"] == reaction][0]
+
+
+def _empty_others(o, keep):
+    for s in range(3):
+        if s not in keep:
+            o.set(s, [], [], [], [])
+
+
+# ------------------------------------------------------------------ RNG
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        assert oracle.philox(v[0:4], v[4:6]) == v[6:10]
+
+
+def test_philox_uniformity_and_independence():
+    words = []
+    for i in range(4000):
+        words += oracle.philox([i, 7, 1 << 28, 0], [1, 0])
+    u = (np.array(words, dtype=np.float64) + 0.5) / 2**32
+    counts, _ = np.histogram(u, bins=40, range=(0, 1))
+    chi2, p = stats.chisquare(counts)
+    assert p > 1e-4
+    assert abs(np.corrcoef(u[:-1], u[1:])[0, 1]) < 0.03
+
+
+# ------------------------------------------------------- cross sections
+
+def test_closed_form_cross_sections_in_tables():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "cross_sections.txt"))
+            if l.strip() and not l.startswith("#")]
+    for r in rows:
+        reaction, E, s_cm2 = int(r[0]), float(r[1]), float(r[2])
+        t = _table(reaction)
+        o = oracle.Oracle(_disch(), [t])
+        got = o.sigma(0, E) * 1e4
+        assert got == pytest.approx(s_cm2, rel=2e-4), (reaction, E)
+
+
+def test_sigma_interpolation_rules():
+    E = np.array([0.1, 1.0, 10.0, 100.0])
+    t = dict(reaction=9, sub=0, E_eV=E, sigma_m2=np.array([0.0, 2.0, 4.0, 1.0]) * 1e-20,
+             threshold_eV=0.5)
+    o = oracle.Oracle(_disch(), [t])
+    assert o.sigma(0, 0.4) == 0.0                    # below threshold
+    assert o.sigma(0, 1.0) == pytest.approx(2e-20)   # at a node
+    assert o.sigma(0, 5.5) == pytest.approx(3e-20)   # linear in E
+    assert o.sigma(0, 1e4) == pytest.approx(1e-20)   # held above the last node (Sec. III)
+    t2 = dict(t, threshold_eV=0.0)
+    o2 = oracle.Oracle(_disch(), [t2])
+    assert o2.sigma(0, 0.01) == 0.0                  # held at the first node value
+
+
+def test_numax_for_flat_table():
+    sig = 1e-19
+    d = _disch(ecap_override=40.0)
+    o = oracle.Oracle(d, [_flat(4, sig)])
+    n = d.p_Pa / (KB * d.T_gas)
+    mu = ME * M_O2 / (ME + M_O2)
+    expect = d.numax_safety * n * sig * math.sqrt(2 * 40.0 * QE / mu)
+    assert o.numax(0) == pytest.approx(expect, rel=1e-12)
+    assert o.numax(1) == 0.0 and o.numax(2) == 0.0
+
+
+# ------------------------------------------------------------ Poisson
+
+def test_poisson_uniform_charge_parabola():
+    N, L, rho0, U = 64, 0.01, 1e-3, 50.0
+    dx = L / N
+    x = np.arange(N + 1) * dx
+    rho = np.full(N + 1, rho0)
+    phi = oracle.poisson(N, dx, U, 0.0, rho)
+    exact = rho0 * x * (L - x) / (2 * EPS0) + U * (1 - x / L)
+    assert np.max(np.abs(phi - exact)) < 1e-12 * np.max(np.abs(exact))
+    E = oracle.field(N, dx, rho, phi)
+    Eex = -rho0 * (L - 2 * x) / (2 * EPS0) + U / L
+    assert np.max(np.abs(E - Eex)) < 1e-9 * np.max(np.abs(Eex))
+
+
+def test_poisson_against_dense_solve():
+    rs = np.random.default_rng(3)
+    N, L = 200, 0.04
+    dx = L / N
+    rho = rs.normal(size=N + 1) * 1e-4
+    phi = oracle.poisson(N, dx, 123.0, 0.0, rho)
+    A = (np.diag(-2.0 * np.ones(N - 1)) + np.diag(np.ones(N - 2), 1)
+         + np.diag(np.ones(N - 2), -1))
+    b = -rho[1:N] * dx * dx / EPS0
+    b[0] -= 123.0
+    ref = np.linalg.solve(A, b)
+    assert np.max(np.abs(phi[1:N] - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_deposit_total_charge():
+    d = _disch(n_op=2000, n0_m3=1e15, weight_override=None, T0_eV=(1.0, 0.03, 0.03),
+               L=0.02)
+    o = oracle.Oracle(d, [])
+    rho, _, _ = o.fields()
+    N, dx = d.n_cells, d.L / d.n_cells
+    vol = np.full(N + 1, dx)
+    vol[0] = vol[-1] = dx / 2
+    q = QE * d.weight * (d.n_init[2] - d.n_init[0] - d.n_init[1])
+    assert np.sum(rho * vol) == pytest.approx(q, abs=1e-9 * QE * d.weight * d.n_op)
+
+
+# ------------------------------------------------------------- push
+
+def test_free_streaming_and_absorption():
+    d = _disch(L=0.01, dt_override=1e-11)
+    o = oracle.Oracle(d, [])
+    rs = np.random.default_rng(5)
+    n = 500
+    x0 = rs.uniform(0, d.L, n)
+    vx = rs.normal(0, 2e6, n)
+    o.set(0, x0, vx, np.zeros(n), np.zeros(n))
+    _empty_others(o, [0])
+    steps = 40
+    o.step(steps)
+    st = o.get(0)
+    k = np.arange(1, steps + 1)[None, :]
+    traj = x0[:, None] + k * vx[:, None] * d.dt
+    out = (traj < 0) | (traj >= d.L)
+    alive = ~out.any(axis=1)
+    assert np.array_equal(st["alive"], alive)
+    xe = x0 + steps * vx * d.dt
+    assert np.max(np.abs(st["x"][alive] - xe[alive])) < 1e-12 * d.L
+    first = np.where(out.any(axis=1), np.argmax(out, axis=1), -1)
+    lefts = np.sum((first >= 0) & (traj[np.arange(n), np.maximum(first, 0)] < 0))
+    ab = o.counters()["absorbed"]
+    assert ab[0, 0] == lefts and ab[0, 1] == np.sum(first >= 0) - lefts
+
+
+def test_uniform_field_leapfrog_parabola():
+    # f = 0 and phase pi/2: the driven electrode sits at U_rf; without space
+    # charge the potential is linear and E = U/L everywhere (Sec. II geometry)
+    U = 30.0
+    d = _disch(L=0.05, U_rf=U, f_rf=0.0, rf_phase=math.pi / 2, dt_override=2e-11)
+    o = oracle.Oracle(d, [])
+    n = 200
+    rs = np.random.default_rng(9)
+    x0 = rs.uniform(0.02, 0.03, n)
+    vh = rs.normal(0, 1e4, n)
+    o.set(2, x0, vh, np.zeros(n), np.zeros(n))   # O2+
+    o.set(0, x0, vh * 10, np.zeros(n), np.zeros(n))  # electrons
+    o.set(1, [], [], [], [])
+    steps = 30
+    o.step(steps)
+    for s, v in ((2, vh), (0, vh * 10)):
+        a = (1.0 if s == 2 else -1.0) * QE * U / (d.L * MASS[s])
+        st = o.get(s)
+        xn = x0 + steps * v * d.dt + a * d.dt**2 * steps * (steps + 1) / 2
+        vn = v + steps * a * d.dt
+        m = st["alive"]
+        assert m.sum() > n // 2
+        assert np.max(np.abs(st["x"][m] - xn[m])) < 1e-9 * d.L
+        assert np.max(np.abs(st["vx"][m] - vn[m])) < 1e-9 * np.max(np.abs(vn))
+
+
+def test_cold_plasma_oscillation_frequency():
+    # cold electrons displaced by xi sin(2 pi x / L) over a uniform ion
+    # background oscillate at the leapfrog frequency sin(w dt/2) = w_pe dt/2
+    N = 128
+    L = 0.02
+    npart = 64 * N
+    n0 = 1e15
+    w = n0 * L / npart
+    wpe = math.sqrt(n0 * QE**2 / (EPS0 * ME))
+    dt = 0.1 / wpe
+    d = _disch(L=L, n_cells=N, dt_override=dt, weight_override=w)
+    o = oracle.Oracle(d, [])
+    xb = (np.arange(npart) + 0.5) * L / npart
+    xi = 0.2 * (L / N) * np.sin(2 * np.pi * xb / L)
+    z = np.zeros(npart)
+    o.set(0, xb + xi, z, z, z)
+    o.set(2, xb, z, z, z)
+    o.set(1, [], [], [], [])
+    mode = np.sin(2 * np.pi * xb / L)
+    amp = []
+    for k in range(200):
+        amp.append(np.sum((o.get(0)["x"] - xb) * mode))
+        o.step(1)
+    amp = np.array(amp)
+    sgn = np.sign(amp)
+    idx = np.where(sgn[:-1] * sgn[1:] < 0)[0]
+    tz = idx + amp[idx] / (amp[idx] - amp[idx + 1])
+    period_steps = 2 * np.mean(np.diff(tz))
+    w_num = 2 * np.pi / (period_steps * dt)
+    w_exp = 2 / dt * math.asin(wpe * dt / 2)
+    assert w_num == pytest.approx(w_exp, rel=0.01)
+
+
+# ------------------------------------------------------------ gas MCC
+
+def test_null_collision_real_event_fraction():
+    sig, E0, cap = 1e-19, 10.0, 40.0
+    d = _disch(ecap_override=cap, dt_override=5e-11)
+    o = oracle.Oracle(d, [_flat(4, sig)])
+    n = 200000
+    rs = np.random.default_rng(11)
+    dirs = rs.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    v = math.sqrt(2 * E0 * QE / ME) * dirs
+    o.set(0, np.full(n, 0.5), v[:, 0], v[:, 1], v[:, 2])
+    _empty_others(o, [0])
+    o.step(1)
+    ev = o.counters()["events"][4]
+    ngas = d.p_Pa / (KB * d.T_gas)
+    mu = ME * M_O2 / (ME + M_O2)
+    numax = d.numax_safety * ngas * sig * math.sqrt(2 * cap * QE / mu)
+    nu = ngas * sig * math.sqrt(2 * E0 * QE / mu)  # gas motion is negligible here
+    p = (1 - math.exp(-numax * d.dt)) * nu / numax
+    assert abs(ev - n * p) < 4 * math.sqrt(n * p * (1 - p))
+
+
+def test_channel_shares_follow_cross_sections():
+    d = _disch(ecap_override=30.0, dt_override=1e-10)
+    tabs = [_flat(4, 1e-19), _flat(9, 3e-20, th=6.4)]
+    o = oracle.Oracle(d, tabs)
+    n = 100000
+    E0 = 20.0
+    rs = np.random.default_rng(12)
+    dirs = rs.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    v = math.sqrt(2 * E0 * QE / ME) * dirs
+    o.set(0, np.full(n, 0.5), v[:, 0], v[:, 1], v[:, 2])
+    _empty_others(o, [0])
+    o.step(1)
+    ev = o.counters()["events"]
+    tot = ev[4] + ev[9]
+    frac = 3e-20 / 1.3e-19
+    assert abs(ev[9] - tot * frac) < 4 * math.sqrt(tot * frac * (1 - frac))
+
+
+@pytest.mark.parametrize("T0", [0.0259, 1.0])
+def test_associative_detachment_decay_rate(T0):
+    # sigma_ad u is energy independent (Eq. 9), so O- decays as
+    # exp(-C n_O2 K_ad t) whatever its velocity distribution (Sec. IV)
+    d = _disch(n_op=0, T0_eV=(0.0, T0, 0.0), dt_override=1e-7, ecap_override=5.0)
+    o = oracle.Oracle(d, [_table(17)])
+    n = 40000
+    rs = np.random.default_rng(13)
+    vt = math.sqrt(T0 * QE / M_OM)
+    v = rs.normal(0, vt, size=(n, 3))
+    o.set(1, rs.uniform(0.45, 0.55, n), v[:, 0], v[:, 1], v[:, 2])
+    _empty_others(o, [1])
+    steps = 100
+    o.step(steps)
+    mu = M_OM * M_O2 / (M_OM + M_O2)
+    kad = 5.96e-16 * 1e-4 * math.sqrt(2 * QE / mu)
+    nu = d.C_delta * d.p_Pa / (KB * d.T_gas) * kad
+    surv = math.exp(-nu * steps * d.dt)
+    alive = o.get(1)["alive"].sum()
+    c = o.counters()
+    assert abs(alive - n * surv) < 4 * math.sqrt(n * surv * (1 - surv))
+    assert c["events"][17] == n - alive
+    assert c["births"][0] == c["events"][17] and o.count(0) == c["births"][0]
+
+
+@pytest.mark.parametrize("species,reaction", [(2, 6), (1, 5)])
+def test_ion_relaxes_to_gas_maxwellian(species, reaction):
+    # (6) and (5) conserve the pair's momentum and energy, so the ion
+    # distribution relaxes to a Maxwellian at the gas temperature
+    d = _disch(n_op=0, dt_override=2e-8 if reaction == 6 else 4e-8, ecap_override=5.0)
+    o = oracle.Oracle(d, [_table(reaction)])
+    n = 20000
+    rs = np.random.default_rng(14)
+    m = MASS[species]
+    v = rs.normal(0, math.sqrt(0.5 * QE / m), size=(n, 3))
+    o.set(species, rs.uniform(0.45, 0.55, n), v[:, 0], v[:, 1], v[:, 2])
+    _empty_others(o, [species])
+    o.step(400)
+    st = o.get(species)
+    assert st["alive"].all()
+    kT = KB * d.T_gas
+    ke = 0.5 * m * (st["vx"]**2 + st["vy"]**2 + st["vz"]**2)
+    assert np.mean(ke) / (1.5 * kT) == pytest.approx(1.0, abs=0.03)
+    assert stats.kstest(st["vx"] / math.sqrt(kT / m), "norm").pvalue > 1e-3
+
+
+def _ke(m, v):
+    return 0.5 * m * float(np.dot(v, v))
+
+
+@pytest.mark.parametrize("reaction", [4, 5, 7, 8, 9, 10, 11, 12, 15, 16, 17, 18])
+def test_gas_event_conservation(reaction):
+    tabs = inputs.xs_tables()
+    idx = [i for i, t in enumerate(tabs) if t["reaction"] == reaction][0]
+    th = tabs[idx]["threshold_eV"]
+    sp = {5: 1, 16: 1, 17: 1}.get(reaction, 0)
+    o = oracle.Oracle(_disch(), tabs)
+    rs = np.random.default_rng(reaction)
+    for trial in range(20):
+        m = MASS[sp]
+        E = th + 1.0 + 30.0 * rs.random()
+        dirn = rs.normal(size=3)
+        dirn /= np.linalg.norm(dirn)
+        v = math.sqrt(2 * E * QE / m) * dirn * (1.05 if sp == 0 else 1.0)
+        V = rs.normal(0, 300.0, 3)
+        r4 = rs.random(4)
+        r2 = rs.random(2)
+        vo, alive, prods, Vo = o.gas_event(sp, idx, v, V, r4, r2)
+        p_in = m * v + M_O2 * V
+        k_in = _ke(m, v) + _ke(M_O2, V)
+        if reaction in (4, 5, 7, 8, 9, 10, 11, 12):
+            assert alive and not prods
+            assert np.allclose(m * vo + M_O2 * Vo, p_in, rtol=1e-12, atol=1e-12 * np.abs(p_in).max())
+            dk = k_in - _ke(m, vo) - _ke(M_O2, Vo)
+            assert dk == pytest.approx(th * QE, rel=1e-9, abs=1e-9 * k_in)
+        elif reaction == 15:
+            assert not alive and [p[0] for p in prods] == [1]
+            vom = prods[0][1]
+            vO = (p_in - M_OM * vom) / M_O
+            dk = k_in - _ke(M_OM, vom) - _ke(M_O, vO)
+            assert dk == pytest.approx(th * QE, rel=1e-9)
+        elif reaction == 16:
+            assert not alive and [p[0] for p in prods] == [0]
+            assert _ke(ME, prods[0][1]) == pytest.approx(_ke(M_OM, v) / 10, rel=1e-12)
+        elif reaction == 17:
+            assert not alive and [p[0] for p in prods] == [0]
+            vcm = p_in / (m + M_O2)
+            mu = m * M_O2 / (m + M_O2)
+            ecm = 0.5 * mu * float(np.dot(v - V, v - V))
+            w = np.linalg.norm(prods[0][1] - vcm)
+            assert w == pytest.approx(math.sqrt(2 * ecm / ME), rel=1e-12)
+        elif reaction == 18:
+            assert alive and [p[0] for p in prods] == [0, 2]
+            ve2, vop = prods[0][1], prods[1][1]
+            p_out = ME * vo + ME * ve2 + M_OP * vop
+            assert np.allclose(p_out, p_in, rtol=1e-10, atol=1e-10 * np.abs(p_in).max())
+            dk = k_in - _ke(ME, vo) - _ke(ME, ve2) - _ke(M_OP, vop)
+            assert dk == pytest.approx(th * QE, rel=1e-8)
+
+
+def test_charge_exchange_swaps_velocities():
+    tabs = inputs.xs_tables()
+    idx = [i for i, t in enumerate(tabs) if t["reaction"] == 6][0]
+    o = oracle.Oracle(_disch(), tabs)
+    v, V = np.array([1e3, -2e3, 5.0]), np.array([-300.0, 20.0, 110.0])
+    vo, alive, prods, Vo = o.gas_event(2, idx, v, V, [0.3, 0.2, 0.7, 0.1])
+    assert alive and not prods
+    assert np.array_equal(vo, V) and np.array_equal(Vo, v)
+
+
+def test_impact_detachment_event_conservation():
+    tabs = inputs.xs_tables()
+    idx = [i for i, t in enumerate(tabs) if t["reaction"] == 19][0]
+    th = tabs[idx]["threshold_eV"]
+    o = oracle.Oracle(_disch(), tabs)
+    rs = np.random.default_rng(19)
+    for _ in range(20):
+        v = rs.normal(0, 3e6, 3)
+        vt = rs.normal(0, 500, 3)
+        v1, v2, vO = o.pair19_event(idx, v, vt, rs.random(2), rs.random(2))
+        p_in = ME * v + M_OM * vt
+        p_out = ME * v1 + ME * v2 + M_O * vO
+        assert np.allclose(p_out, p_in, rtol=1e-10, atol=1e-10 * np.abs(p_in).max())
+        dk = _ke(ME, v) + _ke(M_OM, vt) - _ke(ME, v1) - _ke(ME, v2) - _ke(M_O, vO)
+        assert dk == pytest.approx(th * QE, rel=1e-8)
+
+
+# -------------------------------------------------------- bookkeeping
+
+def test_particle_and_charge_bookkeeping_full_step_loop():
+    d = inputs.cfg1(n_op=4000)
+    o = oracle.Oracle(d, inputs.xs_tables())
+    n0 = [o.count(s) for s in range(3)]
+    o.step(300)
+    c = o.counters()
+    ev, ab = c["events"], c["absorbed"].sum(axis=1)
+    live = [int(o.get(s)["alive"].sum()) for s in range(3)]
+    de = -ev[13] - ev[15] + ev[16] + ev[17] + ev[18] + ev[19] - ab[0]
+    dm = -ev[14] + ev[15] - ev[16] - ev[17] - ev[19] - ab[1]
+    dp = -ev[13] - ev[14] + ev[18] - ab[2]
+    assert live == [n0[0] + de, n0[1] + dm, n0[2] + dp]
+    assert ev[4] > 0 and ev[18] > 0 and c["violations"][0] == 0
+    q = live[2] - live[0] - live[1]
+    assert q == (n0[2] - n0[0] - n0[1]) - ab[2] + ab[0] + ab[1]
+
+
+def test_sort_is_stable_by_cell_and_drops_dead():
+    d = _disch(L=0.01, n_cells=32, sort_interval=1)
+    o = oracle.Oracle(d, [])
+    rs = np.random.default_rng(21)
+    n = 3000
+    x = rs.uniform(0, d.L, n)
+    vx = np.zeros(n)
+    vx[:50] = -1e9  # leave through x = 0 in the first step
+    tag = np.arange(n, dtype=float)  # carried in vy to follow each particle
+    o.set(0, x, vx, tag, np.zeros(n))
+    _empty_others(o, [0])
+    o.step(1)
+    st = o.get(0)
+    cell = np.floor(x[50:] / (d.L / d.n_cells))
+    order = np.argsort(cell, kind="stable") + 50
+    assert np.array_equal(st["vy"], tag[order])
+    assert st["alive"].all() and len(st["x"]) == n - 50
+
+
+# ----------------------------------------------------------- pair pass
+
+def test_neutralisation_rate_matches_eq1():
+    # all O- and O2+ in one cell, zero net charge, one pass of (14)
+    L, N = 0.064, 64
+    dx = L / N
+    n = 8000
+    dt = 1e-9
+    d = _disch(L=L, n_cells=N, n1=1, dt_override=dt, weight_override=2e14)
+    o = oracle.Oracle(d, [_table(14)])
+    rs = np.random.default_rng(31)
+    x = rs.uniform(10 * dx + 0.3 * dx, 10 * dx + 0.7 * dx, n)
+    vm = rs.normal(0, math.sqrt(KB * 300 / M_OM), (n, 3))
+    vp = rs.normal(0, math.sqrt(KB * 300 / M_OP), (n, 3))
+    o.set(1, x, vm[:, 0], vm[:, 1], vm[:, 2])
+    o.set(2, x, vp[:, 0], vp[:, 1], vp[:, 2])
+    o.set(0, [], [], [], [])
+    o.step(1)
+    ev = o.counters()["events"][14]
+    nT = n * d.weight / dx
+    mu = M_OM * M_OP / (M_OM + M_OP)
+    sub = rs.choice(n, 1500, replace=False)
+    g = vm[sub][:, None, :] - vp[None, :, :]
+    u = np.sqrt(np.sum(g * g, axis=2))
+    E = 0.5 * mu * u * u / QE
+    sig = 0.8 * (1 + 2.85 / E) * 1e-18
+    p = np.minimum(nT * sig * u * dt, 1.0).mean()
+    expect = n * p
+    assert 500 < expect < 4000
+    assert abs(ev - expect) < 4 * math.sqrt(expect) + 0.02 * expect
+
+
+def test_pair_pass_exhausts_targets_with_clamped_probability():
+    L, N = 0.064, 64
+    dx = L / N
+    # a huge cross section (not a weight, whose field would scatter the
+    # electrons) makes P = n sigma u tau >> 1 for every pair
+    d = _disch(L=L, n_cells=N, n1=1, dt_override=1e-9, weight_override=1e6)
+    o = oracle.Oracle(d, [_flat(13, 1e-2)])
+    rs = np.random.default_rng(33)
+    ne, nop = 300, 200
+    x = rs.uniform(5.2 * dx, 5.8 * dx, ne)
+    v = rs.normal(0, 1e3, (ne, 3))  # slow: everyone stays in cell 5
+    o.set(0, x, v[:, 0], v[:, 1], v[:, 2])
+    o.set(2, x[:nop], np.zeros(nop), np.zeros(nop), np.zeros(nop))
+    o.set(1, [], [], [], [])
+    o.step(1)
+    c = o.counters()
+    assert c["events"][13] == nop
+    assert c["violations"][1] == nop
+    assert o.get(2)["alive"].sum() == 0
+    assert o.get(0)["alive"].sum() == ne - nop
+
+
+# ------------------------------------------------------------- loading
+
+def test_initial_load_statistics():
+    d = inputs.cfg1(n_op=20000)
+    o = oracle.Oracle(d, [])
+    for s in range(3):
+        st = o.get(s)
+        assert len(st["x"]) == d.n_init[s]
+        assert stats.kstest(st["x"] / d.L, "uniform").pvalue > 1e-3
+        vt = math.sqrt(d.T0_eV[s] * QE / MASS[s])
+        for comp in ("vx", "vy", "vz"):
+            assert stats.kstest(st[comp] / vt, "norm").pvalue > 1e-3
