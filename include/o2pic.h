@@ -1,0 +1,238 @@
+/*
+ * o2pic.h -- C ABI of libo2pic.so, a GB300 (sm_103a) implementation of the
+ * per-time-step hot path of the particle-in-cell Monte-Carlo model of a
+ * capacitively coupled RF discharge in O2 of Bronold, Matyash, Tskhakaya,
+ * Schneider and Fehske, "Radio-frequency discharges in Oxygen. Part 1:
+ * Modeling" (cited below as "the paper").
+ *
+ * What one pic_step() advances (paper Sec. II, "Method of simulation", and
+ * Sec. III, "Scattering and reaction channels"):
+ *   1. linear (cloud-in-cell) charge assignment of e, O- and O2+ (Sec. II (i));
+ *   2. the 1D Poisson equation with the driven electrode x = 0 at
+ *      U(t) = U_rf sin(2 pi f_rf t) and the grounded electrode x = L (Sec. II);
+ *   3. linear force interpolation and the Newton (leapfrog) push (Sec. II (i));
+ *   4. absorption at both electrodes, no secondary emission (Sec. II);
+ *   5. collisions with the O2 reservoir n = p/(kT) for reactions (4)-(12) and
+ *      (15)-(18) of Table I by the null-collision method, with the kinematic
+ *      rules of Sec. III (Eq. 5, charge exchange, attachment, detachment,
+ *      ionisation) and O2(a) at density C n_O2 for (17) (Sec. III C);
+ *   6. births of new superparticles and removal of dead ones;
+ *   7. every sort_interval steps a stable counting sort by cell that drops
+ *      dead particles (Sec. II: particles are sorted into cells after the free
+ *      flight);
+ *   8. every n1 steps the per-cell particle-target reactions (13), (14), (19)
+ *      with probability P = n sigma u tau, tau = n1 dt (Eq. 1);
+ *   9. diagnostics: cycle-averaged densities and potential, the electron
+ *      energy distribution at L/2, the O- distribution f_-(E, x) (Sec. IV) and
+ *      the O2+ energy distribution at each electrode.
+ *
+ * Units are SI unless a field name says otherwise.  Species indices:
+ * 0 = electron, 1 = O-, 2 = O2+.  Several independent discharges can be
+ * advanced together ("batched"): every entry point that takes a discharge
+ * index refers to the order of the configurations given to pic_init().
+ *
+ * Memory: the caller allocates ONE device workspace of pic_workspace_size()
+ * bytes (256-byte aligned) and keeps it alive until pic_destroy().  The
+ * library never allocates device memory after pic_init(); host-side staging
+ * for state and diagnostics copies uses ordinary host memory.  All work is
+ * issued on the CUDA stream given to pic_init().
+ *
+ * Errors: every call returns a pic_status; nothing is thrown across the ABI.
+ * After an error the handle stays valid and may be destroyed; pic_last_error()
+ * returns a text.
+ */
+#ifndef O2PIC_H
+#define O2PIC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_EINVAL = 1,     /* invalid argument or configuration */
+    PIC_ENOMEM = 2,     /* workspace too small */
+    PIC_ECAPACITY = 3,  /* particle capacity or a birth buffer overflowed */
+    PIC_ETIMEOUT = 4,   /* a bounded device-side wait gave up */
+    PIC_ECUDA = 5,      /* a CUDA runtime call failed */
+    PIC_ENUMERIC = 6    /* collision-frequency bound or P <= 1 violated too often */
+} pic_status;
+
+typedef enum {
+    PIC_FP64 = 0,       /* every particle quantity and all arithmetic in FP64 */
+    PIC_FP32_MIXED = 1  /* particles and push/collisions in FP32; charge
+                           accumulation (exact fixed point), Poisson, field
+                           and diagnostics in FP64 */
+} pic_precision;
+
+/*
+ * One cross-section table (one channel of Table I).  Nodes E_eV[0..n-1] are
+ * strictly increasing; sigma is linear in E between nodes, equal to the first
+ * node value below E_eV[0], equal to the last value above E_eV[n-1] (paper
+ * Sec. III: the largest tabulated value is extended to higher energies), and
+ * zero below threshold_eV.  threshold_eV is also the energy lost in the
+ * inelastic channels (7)-(12), (15), (18), (19) (Eq. 5).  The energy argument
+ * is the centre-of-mass energy (1/2) mu u^2 of the colliding pair.
+ *
+ * reaction: 4..19 in the numbering of Table I.  The projectile is the
+ * electron for 4, 7-13, 15, 18, 19; O- for 5, 14, 16, 17; O2+ for 6.  The
+ * target is O2 gas except 13, 14 (O2+) and 19 (O-).  The gas channels of one
+ * projectile are tried in the order given here (null-collision walk) and must
+ * share one node grid, which must be geometric (E_k = E_0 r^k).
+ * sub: vibrational level for reaction 7 (informational), else 0.
+ * The tables are copied by pic_init(); the caller keeps ownership.
+ */
+typedef struct {
+    int reaction;
+    int sub;
+    int n;
+    const double *E_eV;
+    const double *sigma_m2;
+    double threshold_eV;
+} pic_xs_table;
+
+/*
+ * One discharge (paper Sec. II).  The driven electrode is x = 0.
+ *   weight_m2      real particles per m^2 of electrode per superparticle (the
+ *                  paper's lateral area A only enters through this number)
+ *   C_delta        O2(a1Delta_g)/O2 density ratio for reaction (17) (Sec. III C)
+ *   T0_eV          temperatures of the initial Maxwellian load per species
+ *   ecap_eV        centre-of-mass energy up to which the collision-frequency
+ *                  bound nu_max is taken (max of sum_j n_j sigma_j(E) u over
+ *                  table nodes below the cap and the cap, times numax_safety)
+ *   n_init         superparticles loaded uniformly in (0, L) per species
+ *   capacity       slots per species (>= n_init; births beyond it fail with
+ *                  PIC_ECAPACITY)
+ *   n1             interval of the particle-target reactions (tau = n1 dt);
+ *                  0 disables them
+ *   sort_interval  cell-sort interval in steps (a sort also runs on every
+ *                  particle-target step); 0 = only on those steps
+ *   diag_every     diagnostics sampling interval in steps; 0 = none
+ *   *_bins, *_emax histogram sizes and ranges [eV]; f_- uses fm_xbins equal
+ *                  regions of (0, L) and fm_bins signed-energy bins over
+ *                  (-fm_emax, fm_emax)
+ *   cx_isotropic   reaction (6): 0 = the ion takes the gas molecule's velocity
+ *                  (resonant exchange), 1 = isotropic elastic scattering
+ *   precision      pic_precision; all discharges of one handle share it
+ */
+typedef struct {
+    double L_m, p_Pa, T_gas_K, U_rf_V, f_rf_Hz, rf_phase, dt_s;
+    double weight_m2, C_delta;
+    double T0_eV[3];
+    double ecap_eV[3];
+    double numax_safety;
+    double eedf_emax_eV, iedf_emax_eV, fm_emax_eV;
+    long long n_init[3];
+    long long capacity[3];
+    unsigned long long seed;
+    int n_cells, n1, sort_interval, diag_every;
+    int eedf_bins, iedf_bins, fm_bins, fm_xbins;
+    int cx_isotropic;
+    int precision;
+} pic_config;
+
+typedef struct pic_handle pic_handle;
+
+/*
+ * Bytes of device workspace needed for the given discharges and tables.
+ * Returns 0 if the configuration is invalid (pic_last_error(NULL) says why).
+ */
+size_t pic_workspace_size(const pic_config *cfgs, int n_discharges,
+                          const pic_xs_table *xs, int n_xs);
+
+/*
+ * Validate, copy the tables to device look-up tables, compute nu_max per
+ * species and discharge, carve the caller's workspace, load the particles
+ * (uniform positions, Maxwellian velocities, counter-based Philox4x32-10 from
+ * `seed`, so the load is reproducible) and deposit the initial charge.
+ *   d_workspace  device pointer, >= pic_workspace_size() bytes, 256-aligned
+ *   cuda_stream  a cudaStream_t (NULL = legacy default stream)
+ *   out          receives the handle
+ * Synchronises the stream before returning.
+ */
+pic_status pic_init(const pic_config *cfgs, int n_discharges,
+                    const pic_xs_table *xs, int n_xs, void *d_workspace,
+                    size_t ws_bytes, void *cuda_stream, pic_handle **out);
+
+/*
+ * Advance every discharge by n_steps time steps (each of length dt_s).
+ * Work is queued on the handle's stream (replaying a captured CUDA graph of
+ * whole sort/diagnostic periods where possible); the call then synchronises
+ * and checks the device status word, returning PIC_ECAPACITY, PIC_ETIMEOUT or
+ * PIC_ENUMERIC if the device reported one.
+ */
+pic_status pic_step(pic_handle *h, long long n_steps);
+
+/*
+ * Diagnostics of one discharge, copied into caller-owned host arrays (any
+ * pointer may be NULL to skip it).  Sizes: N = n_cells.
+ *   dens_sum   [3][N+1]  sum over samples of the number density per species
+ *   phi_sum    [N+1]     sum over samples of the potential
+ *   eedf       [eedf_bins] electrons in the cell [L/2, L/2 + dx), E = m v^2/2
+ *   iedf       [2][iedf_bins] O2+ absorbed at x = 0 and x = L, E = M v^2/2
+ *   fm         [fm_xbins][fm_bins] O-, E = sign(vx) M vx^2 / 2
+ *   counters   [32]: 0-5 absorbed (species*2 + wall), 6-25 events per
+ *              reaction 0..19 (index 6 + reaction), 26 gas nu_max
+ *              violations, 27 pair P > 1 clamps, 28-30 live slots per species
+ *              (including dead slots not yet compacted), 31 steps taken
+ *   n_samples  number of diagnostic samples accumulated
+ * reset != 0 clears the sums and histograms after copying.
+ */
+pic_status pic_diagnostics(pic_handle *h, int discharge, double *dens_sum,
+                           double *phi_sum, long long *eedf, long long *iedf,
+                           long long *fm, long long *counters,
+                           long long *n_samples, int reset);
+
+/*
+ * Particle state of one discharge and species, as host arrays of length
+ * *n (slots in the device order, including not-yet-compacted dead slots):
+ * x [m], vx, vy, vz [m/s] and alive (1/0).  Pass NULL arrays with a valid n
+ * to query the count only; capacity_n is the length of the caller's arrays.
+ */
+pic_status pic_get_state(pic_handle *h, int discharge, int species,
+                         double *x, double *vx, double *vy, double *vz,
+                         int *alive, long long capacity_n, long long *n);
+
+/*
+ * Replace the particle state of one discharge and species (n slots, same
+ * layout as pic_get_state; alive may be NULL = all alive) and recompute the
+ * charge density of that discharge.  x must lie in [0, L) for live slots.
+ */
+pic_status pic_set_state(pic_handle *h, int discharge, int species, long long n,
+                         const double *x, const double *vx, const double *vy,
+                         const double *vz, const int *alive);
+
+/* Set the step counter (which drives U(t) and the random counters). */
+pic_status pic_set_step(pic_handle *h, long long step);
+
+/* Potential, field and charge density of one discharge at the current state
+ * (each [N+1], SI; NULL skips). */
+pic_status pic_fields(pic_handle *h, int discharge, double *rho, double *phi,
+                      double *E);
+
+/* nu_max [1/s] of one discharge and species (after pic_init). */
+double pic_numax(const pic_handle *h, int discharge, int species);
+
+/*
+ * Per-kernel timing: when on, pic_step launches kernels one by one with CUDA
+ * events around each particle push and accumulates their device time;
+ * pic_timing() returns (ms total of the push kernel, push launches, all
+ * kernel launches, algorithmic bytes moved by the push kernel) since the last
+ * reset.  Kernel launches are always counted.
+ */
+pic_status pic_set_timing(pic_handle *h, int on);
+pic_status pic_timing(pic_handle *h, double *push_ms, long long *push_launches,
+                      long long *launches, double *push_bytes, int reset);
+
+void pic_destroy(pic_handle *h);
+
+/* Text of the last error on this handle (or of the calling thread's last
+ * handle-less call when h == NULL). */
+const char *pic_last_error(const pic_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* O2PIC_H */

@@ -46,7 +46,8 @@ class _Cfg(C.Structure):
         ("n_init", C.c_longlong * 3), ("seed", C.c_ulonglong),
         ("n_cells", C.c_int), ("n1", C.c_int), ("sort_interval", C.c_int),
         ("diag_every", C.c_int), ("eedf_bins", C.c_int), ("iedf_bins", C.c_int),
-        ("fm_bins", C.c_int), ("discharge", C.c_int), ("cx_isotropic", C.c_int),
+        ("fm_bins", C.c_int), ("fm_xbins", C.c_int), ("discharge", C.c_int),
+        ("cx_isotropic", C.c_int),
     ]
 
 
@@ -148,6 +149,7 @@ class Oracle:
         cfg.n_cells, cfg.n1, cfg.sort_interval = d.n_cells, d.n1, d.sort_interval
         cfg.diag_every = d.diag_every
         cfg.eedf_bins, cfg.iedf_bins, cfg.fm_bins = d.eedf_bins, d.iedf_bins, d.fm_bins
+        cfg.fm_xbins = d.fm_xbins
         cfg.discharge = discharge
         cfg.cx_isotropic = int(d.cx_isotropic)
         self._keep = []
@@ -220,7 +222,7 @@ class Oracle:
         phi = np.zeros(N + 1)
         eedf = np.zeros(max(d.eedf_bins, 1), dtype=np.int64)
         iedf = np.zeros((2, max(d.iedf_bins, 1)), dtype=np.int64)
-        fm = np.zeros((N, max(d.fm_bins, 1)), dtype=np.int64)
+        fm = np.zeros((max(d.fm_xbins, 1), max(d.fm_bins, 1)), dtype=np.int64)
         lp = lambda a: a.ctypes.data_as(C.POINTER(C.c_longlong))
         ns = lib().orc_diag(self.h, _dp(dens), _dp(phi), lp(eedf), lp(iedf), lp(fm))
         return {"n_samples": ns, "dens_sum": dens, "phi_sum": phi, "eedf": eedf,

@@ -330,7 +330,8 @@ orc_sim *orc_create(const orc_cfg *cfg, const orc_xs *xs, int n_xs, int load)
     }
     s->eedf = calloc(cfg->eedf_bins > 0 ? cfg->eedf_bins : 1, sizeof(long long));
     s->iedf = calloc(cfg->iedf_bins > 0 ? 2 * cfg->iedf_bins : 1, sizeof(long long));
-    s->fm = calloc((size_t)N * (cfg->fm_bins > 0 ? cfg->fm_bins : 1), sizeof(long long));
+    s->fm = calloc((size_t)(cfg->fm_xbins > 0 ? cfg->fm_xbins : 1) * (cfg->fm_bins > 0 ? cfg->fm_bins : 1),
+                   sizeof(long long));
     if (load)
         for (int sp = 0; sp < 3; ++sp) load_species(s, sp);
     return s;
@@ -655,7 +656,9 @@ static void sample_histograms(orc_sim *s, int sp, double x, const double v[3])
         double E = 0.5 * MASS[SP_OM] * v[0] * v[0] / QE;
         if (v[0] < 0.0) E = -E;
         double b = floor((E + s->c.fm_emax) / (2.0 * s->c.fm_emax) * s->c.fm_bins);
-        if (b >= 0 && b < s->c.fm_bins) s->fm[(size_t)c * s->c.fm_bins + (int)b]++;
+        /* x binned into fm_xbins equal regions of the gap, by cell */
+        int xb = (int)(((long long)c * s->c.fm_xbins) / N);
+        if (b >= 0 && b < s->c.fm_bins) s->fm[(size_t)xb * s->c.fm_bins + (int)b]++;
     }
 }
 
@@ -977,6 +980,6 @@ long long orc_diag(const orc_sim *s, double *dens_sum, double *phi_sum,
     if (eedf && s->c.eedf_bins > 0) memcpy(eedf, s->eedf, s->c.eedf_bins * sizeof(long long));
     if (iedf && s->c.iedf_bins > 0) memcpy(iedf, s->iedf, 2 * s->c.iedf_bins * sizeof(long long));
     if (fm && s->c.fm_bins > 0)
-        memcpy(fm, s->fm, (size_t)N * s->c.fm_bins * sizeof(long long));
+        memcpy(fm, s->fm, (size_t)s->c.fm_xbins * s->c.fm_bins * sizeof(long long));
     return s->nsamp;
 }

@@ -40,6 +40,7 @@ typedef struct {
     int sort_interval;   /* cell sort interval in steps */
     int diag_every;      /* 0 = no diagnostics */
     int eedf_bins, iedf_bins, fm_bins;
+    int fm_xbins;        /* f_-(E, x): equal regions of (0, L) */
     int discharge;       /* discharge index, enters the random counter */
     int cx_isotropic;    /* reaction (6): 0 = velocity swap, 1 = isotropic */
 } orc_cfg;
@@ -70,7 +71,7 @@ void orc_fields(orc_sim *s, double *rho, double *phi, double *E);
 /* counters: absorbed[3][2], events[20], violations[2] (gas, pair), births[3] */
 void orc_counters(const orc_sim *s, long long *absorbed, long long *events,
                   long long *violations, long long *births);
-/* diagnostics: dens_sum[3][N+1], phi_sum[N+1], eedf, iedf[2][bins], fm[N][bins] */
+/* diagnostics: dens_sum[3][N+1], phi_sum[N+1], eedf, iedf[2][bins], fm[xbins][bins] */
 long long orc_diag(const orc_sim *s, double *dens_sum, double *phi_sum,
                    long long *eedf, long long *iedf, long long *fm);
 

@@ -1,0 +1,258 @@
+// o2pic_dev.cuh -- device data layout, constants and small device helpers of
+// libo2pic (GB300, sm_103a).  Shared by the kernels and the host driver of the
+// library; the CPU oracle does not use any of it.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace o2 {
+
+constexpr int NSP = 3;                 // 0 e, 1 O-, 2 O2+
+constexpr int CHUNK = 1024;            // slots per push chunk
+constexpr int PUSH_THREADS = 256;      // 4 consecutive slots per thread
+constexpr int BIRTH_CAP = 256;         // births staged per push chunk
+constexpr int SORT_WARPS = 4;          // warps per sort block
+constexpr int SORT_WARP_SLOTS = 4096;  // slots per sort warp
+constexpr int SORT_CHUNK = SORT_WARPS * SORT_WARP_SLOTS;
+constexpr int PAIR_BIRTH_CAP = 16;     // births of (19) per cell per pass
+constexpr int MAX_GAS_CH = 16;
+constexpr int FIELD_THREADS = 512;
+constexpr int FIX_BITS = 26;           // fixed-point deposit: weight * 2^26
+constexpr int MAX_DISCHARGES = 1024;
+constexpr long long SPIN_LIMIT = 1LL << 22;  // polls of a bounded wait
+
+enum : unsigned {
+    ST_CAPACITY = 1u,   // particle capacity exceeded
+    ST_TIMEOUT = 2u,    // look-back wait gave up
+    ST_BIRTHBUF = 4u,   // a per-chunk or per-cell birth buffer overflowed
+    ST_BADSTATE = 8u    // an impossible state was found (index out of range)
+};
+
+// Counters accumulated on the device (per discharge).
+enum {
+    C_ABS = 0,          // 6: absorbed (species*2 + wall)
+    C_EVENTS = 6,       // 20: events per reaction number 0..19
+    C_VIOL_GAS = 26,
+    C_VIOL_PAIR = 27,
+    C_SLOTS = 28,       // slots processed by the push (all species)
+    C_CANDS = 29,       // null-collision candidates
+    C_NCOUNT = 32
+};
+
+struct TableDesc {
+    int off;            // offset of the nodes in the LUT arrays
+    int n;              // nodes
+    int reaction;
+    int pad;
+    double th;          // threshold [eV]
+    double lnE0;        // log of the first node
+    double inv_dlog;    // (n-1) / log(E_last/E_0)
+};
+
+struct GasChan {
+    int table;          // index into the table descriptors
+    int reaction;
+    double coef;        // n_target * dx (normalised frequency per unit u_n * sigma)
+    double dloss;       // 2 dE / mu * (dt/dx)^2 (inelastic reduction of u_n^2)
+};
+
+struct SpeciesC {
+    double qm;          // (q/m) dt^2 / dx : normalised acceleration per V/m
+    double numax_n;     // nu_max * dt
+    double numax;       // nu_max [1/s]
+    double vgas_n;      // sqrt(kT/M_O2) * dt/dx
+    double Ek;          // (1/2) mu (dx/dt)^2 / e: E_cm[eV] = Ek * u_n^2
+    double mfrac;       // m/(m+M_O2)
+    double Mfrac;       // M_O2/(m+M_O2)
+    double ke_eV;       // (1/2) m (dx/dt)^2 / e: lab kinetic energy per u_n^2
+    double vscale;      // dx/dt: normalised -> m/s
+    unsigned int tnull; // null-collision threshold on a 32-bit word
+    int nch;
+    int table_lo;       // first table of the shared grid (for the index)
+    int pad;
+    GasChan ch[MAX_GAS_CH];
+};
+
+struct PairC {          // particle-target reaction of one discharge
+    int table;          // -1 = absent
+    int proj, targ;
+    int pad;
+    double coef;        // weight * n1: P = count * coef * sigma * u_n
+    double Ek;          // (1/2) mu (dx/dt)^2 / e
+    double mfrac, Mfrac;// m/(m+M), M/(m+M) of the pair
+    double dloss;       // 2 dE/mu (dt/dx)^2
+};
+
+struct Disc {
+    int N;                   // cells
+    int gbase;               // first node of this discharge in grid arrays
+    int pbase[NSP];          // first slot of each species in the particle pools
+    int cap[NSP];            // slots per species
+    int ccell_base;          // first entry in per-cell pair arrays
+    int sort_cbase[NSP];     // first entry of the sort count matrix per species
+    int sort_gmax[NSP];      // sort blocks available per species
+    int cs_base;             // first entry of cell_start arrays (3*(N+2) per discharge)
+    double dx, dt, L, weight;
+    double U_rf, omega, phase;
+    double vol_fix;          // density per accumulated unit (interior node)
+    double kE;               // dt^2/dx
+    double f15, mu2_15;      // reaction (15) product speed factor
+    double f16;              // (16): v_e = |v_Om| * f16
+    double f17;              // (17): w = sqrt(E_cm * f17)
+    double eedf_scale, iedf_scale, fm_scale, fm_emax;
+    int eedf_bins, iedf_bins, fm_bins, fm_xbins;
+    int diag_every, n1, sort_interval, pad;
+    int eedf_base, iedf_base, fm_base, pad2;
+    unsigned long long seed;
+    int discharge;
+    int cx_iso;
+    SpeciesC sp[NSP];
+    PairC pair[3];           // 13, 14, 19
+};
+
+struct Ctl {
+    unsigned long long step[2];   // step number, read by parity
+    unsigned int status;
+    int cur;                      // particle buffer holding the state (0/1)
+    unsigned int ticket;          // dynamic chunk counter of the push
+    int total_chunks;             // chunks in the current push
+    int D;                        // discharges
+    int pad;
+};
+
+// Per (discharge, species) dynamic counts.
+struct Counts {
+    int n;          // slots in use (live + dead not yet compacted)
+    int n_snap;     // slots at the start of the current push
+    int chunk0;     // first chunk of this (d, s) in the current push
+    int nchunk;
+};
+
+// Pointers to every array of the workspace (device addresses).
+template <typename Real>
+struct Pools {
+    int *cell[2];
+    Real *off[2], *vx[2], *vy[2], *vz[2];
+};
+
+struct WsPtrs {
+    Ctl *ctl;
+    Disc *disc;
+    Counts *cnt;              // [D*3]
+    int *chunk_ds;            // [D*3 + 1] first chunk per (d,s) (prefix), device copy
+    unsigned long long *lb;   // look-back status, [max_chunks * 3]
+    unsigned long long *acc_fix;  // [3 * total_nodes] fixed-point density accumulators
+    double *acc_dbl;          // [3 * total_nodes] FP64 accumulators
+    double *Efield;           // [total_nodes] E [V/m]
+    void *Ereal;              // [total_nodes] E as Real for the push
+    double *phi;              // [total_nodes]
+    double *rho;              // [total_nodes]
+    double *dens;             // [3 * total_nodes]
+    double *dens_sum;         // [3 * total_nodes]
+    double *phi_sum;          // [total_nodes]
+    unsigned long long *nsamp;// [D]
+    unsigned long long *counters; // [D * C_NCOUNT]
+    unsigned int *eedf, *iedf, *fm;
+    TableDesc *tables;
+    double *lutE, *lutS;      // FP64 nodes and values
+    float *lutEf, *lutSf;     // FP32 copies
+    int *sort_counts;         // count matrix
+    int *cell_start;          // [sum over d of 3*(N+2)]
+    int *sort_live;           // [D*3]
+    int *pair_bcount;         // [total cells] births of (19) per cell
+    int *cell_disc;           // [total cells] discharge of each global cell
+    void *pair_births;        // [total cells * PAIR_BIRTH_CAP] records
+    int total_nodes;
+    int total_cells;
+    int max_chunks;
+    int D;
+};
+
+// ---------------------------------------------------------------- Philox
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): each round
+// multiplies words 0 and 2 by the round multipliers, swaps the halves and
+// xors in the round key; the key advances by the Weyl increments between
+// rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        unsigned lo0 = 0xD2511F53u * c.x;
+        unsigned hi0 = __umulhi(0xD2511F53u, c.x);
+        unsigned lo1 = 0xCD9E8D57u * c.z;
+        unsigned hi1 = __umulhi(0xCD9E8D57u, c.z);
+        uint4 n;
+        n.x = hi1 ^ c.y ^ k.x;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k.y;
+        n.w = lo0;
+        c = n;
+    }
+    return c;
+}
+
+// Counter layout (identical to the oracle's contract): word 0 = step low 32
+// bits, word 1 = index, word 2 = stream<<28 | sub<<20 | draw, word 3 =
+// discharge<<16 | species<<8 | step bits 32..39; key = seed (low, high).
+__device__ __forceinline__ uint4 rng_block(unsigned long long seed, int disc, int sp,
+                                           int stream, int sub, unsigned draw,
+                                           unsigned long long step, unsigned index)
+{
+    uint4 c;
+    c.x = (unsigned)(step & 0xFFFFFFFFull);
+    c.y = index;
+    c.z = ((unsigned)stream << 28) | ((unsigned)sub << 20) | (draw & 0xFFFFFu);
+    c.w = ((unsigned)disc << 16) | ((unsigned)sp << 8) | (unsigned)((step >> 32) & 0xFF);
+    uint2 k = make_uint2((unsigned)(seed & 0xFFFFFFFFull), (unsigned)(seed >> 32));
+    return philox10(c, k);
+}
+
+template <typename Real> __device__ __forceinline__ Real unif(unsigned w);
+template <> __device__ __forceinline__ double unif<double>(unsigned w)
+{
+    return ((double)w + 0.5) * (1.0 / 4294967296.0);
+}
+// FP32: (2k+1) 2^-24 with k = w >> 9, exactly representable, inside (0, 1);
+// within 2^-24 of the FP64 value.
+template <> __device__ __forceinline__ float unif<float>(unsigned w)
+{
+    return (float)(w >> 9) * (1.0f / 8388608.0f) + (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
+__device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
+
+template <typename Real>
+__device__ __forceinline__ void box_muller(unsigned a, unsigned b, Real &n0, Real &n1)
+{
+    Real r = sqrt(Real(-2) * log(unif<Real>(a)));
+    Real s, c;
+    sincospi_(Real(2) * unif<Real>(b), &s, &c);
+    n0 = r * c;
+    n1 = r * s;
+}
+
+template <typename Real>
+__device__ __forceinline__ void iso_dir(Real r1, Real r2, Real n[3])
+{
+    Real cx = Real(1) - Real(2) * r1;
+    Real sx = Real(1) - cx * cx;
+    sx = sx > Real(0) ? sqrt(sx) : Real(0);
+    Real s, c;
+    sincospi_(Real(2) * r2, &s, &c);
+    n[0] = sx * c;
+    n[1] = sx * s;
+    n[2] = cx;
+}
+
+__device__ __forceinline__ void set_status(Ctl *ctl, unsigned bits)
+{
+    atomicOr(&ctl->status, bits);
+}
+
+} // namespace o2

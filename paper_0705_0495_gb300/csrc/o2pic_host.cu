@@ -1,0 +1,1030 @@
+// o2pic_host.cu -- the C ABI of libo2pic (declared in include/o2pic.h):
+// validation, device constants, workspace carving, the step schedule (CUDA
+// graph replay of whole periods), state and diagnostics copies.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/o2pic.h"
+#include "o2pic_launch.h"
+
+using namespace o2;
+
+namespace {
+
+constexpr double QE = 1.602176634e-19;
+constexpr double ME = 9.1093837015e-31;
+constexpr double AMU = 1.66053906660e-27;
+constexpr double KB = 1.380649e-23;
+constexpr double PI = 3.14159265358979323846;
+constexpr double M_O = 16.0 * AMU;
+constexpr double M_O2 = 32.0 * AMU;
+// O- carries the extra electron and O2+ lacks one, so that every reaction of
+// Table I conserves mass exactly.
+const double MASS[3] = {ME, M_O + ME, M_O2 - ME};
+const double CHARGE[3] = {-QE, -QE, QE};
+
+thread_local std::string g_err;
+
+int proj_of(int r)
+{
+    switch (r) {
+    case 5: case 14: case 16: case 17: return 1;
+    case 6: return 2;
+    default: return 0;
+    }
+}
+int targ_of(int r)
+{
+    if (r == 13 || r == 14) return 2;
+    if (r == 19) return 1;
+    return -1;
+}
+
+struct HostTable {
+    int reaction, sub, n;
+    std::vector<double> E, S;
+    double th;
+};
+
+// sigma(E): linear between nodes, end values held, zero below threshold
+double sigma_host(const HostTable &t, double E)
+{
+    if (E < t.th) return 0.0;
+    if (E <= t.E[0]) return t.S[0];
+    if (E >= t.E[t.n - 1]) return t.S[t.n - 1];
+    int k = int(std::upper_bound(t.E.begin(), t.E.end(), E) - t.E.begin()) - 1;
+    k = std::max(0, std::min(k, t.n - 2));
+    double f = (E - t.E[k]) / (t.E[k + 1] - t.E[k]);
+    return t.S[k] + f * (t.S[k + 1] - t.S[k]);
+}
+
+struct Bump {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        size_t o = (off + 255) & ~size_t(255);
+        off = o + bytes;
+        return o;
+    }
+};
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    size_t ctl, disc, cnt, lb, acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
+        counters, eedf, iedf, fm, tables, lutE, lutS, lutEf, lutSf, sort_counts, cell_start,
+        sort_live, pair_bcount, cell_disc, pair_births, sort_tab, ninit, vt;
+    size_t cell[2], off[2], vx[2], vy[2], vz[2];
+    size_t total;
+    int total_nodes, total_cells, max_chunks, total_cap, sort_blocks, n_lut, maxN, eedf_max, fm_max;
+    std::vector<int> pbase, capr, gbase, ccell, sort_cbase, sort_gmax, cs_base, eedf_base, iedf_base,
+        fm_base;
+};
+
+bool validate(const pic_config *c, int D, const pic_xs_table *xs, int n_xs, std::string &why)
+{
+    if (!c || D < 1 || D > MAX_DISCHARGES) {
+        why = "n_discharges must be in [1, 1024]";
+        return false;
+    }
+    for (int d = 0; d < D; ++d) {
+        const pic_config &q = c[d];
+        char b[256];
+        if (!(q.L_m > 0) || !(q.dt_s > 0) || q.n_cells < 2 || q.n_cells > 4096 || !(q.weight_m2 >= 0) ||
+            !(q.p_Pa >= 0) || !(q.T_gas_K > 0) || !(q.numax_safety >= 1.0)) {
+            snprintf(b, sizeof b, "discharge %d: need L > 0, dt > 0, 2 <= n_cells <= 4096, weight >= 0, "
+                                  "p >= 0, T > 0, numax_safety >= 1", d);
+            why = b;
+            return false;
+        }
+        if (q.precision != c[0].precision || q.diag_every != c[0].diag_every || q.n1 != c[0].n1 ||
+            q.sort_interval != c[0].sort_interval) {
+            why = "all discharges of one handle must share precision, diag_every, n1 and sort_interval";
+            return false;
+        }
+        if (q.precision != PIC_FP64 && q.precision != PIC_FP32_MIXED) {
+            why = "precision must be PIC_FP64 or PIC_FP32_MIXED";
+            return false;
+        }
+        if (q.n1 < 0 || q.sort_interval < 0 || q.diag_every < 0) {
+            why = "n1, sort_interval and diag_every must be >= 0";
+            return false;
+        }
+        if (q.eedf_bins < 0 || q.iedf_bins < 0 || q.fm_bins < 0 || q.eedf_bins > 4096 ||
+            q.iedf_bins > 4096 || (q.fm_bins > 0 && (q.fm_xbins < 1 || q.fm_xbins * q.fm_bins > 16384))) {
+            why = "histogram sizes out of range (eedf, iedf <= 4096; fm_xbins*fm_bins <= 16384)";
+            return false;
+        }
+        if ((q.eedf_bins > 0 && !(q.eedf_emax_eV > 0)) || (q.iedf_bins > 0 && !(q.iedf_emax_eV > 0)) ||
+            (q.fm_bins > 0 && !(q.fm_emax_eV > 0))) {
+            why = "histogram ranges must be > 0";
+            return false;
+        }
+        for (int s = 0; s < 3; ++s) {
+            if (q.n_init[s] < 0 || q.capacity[s] < q.n_init[s] || q.capacity[s] > (1LL << 30) ||
+                !(q.T0_eV[s] >= 0) || !(q.ecap_eV[s] > 0)) {
+                snprintf(b, sizeof b, "discharge %d species %d: need 0 <= n_init <= capacity <= 2^30, "
+                                      "T0 >= 0, ecap > 0", d, s);
+                why = b;
+                return false;
+            }
+        }
+    }
+    if (n_xs < 0 || (n_xs > 0 && !xs)) {
+        why = "bad table list";
+        return false;
+    }
+    int ngas[3] = {0, 0, 0}, npair[20] = {0};
+    int first[3] = {-1, -1, -1};
+    for (int i = 0; i < n_xs; ++i) {
+        const pic_xs_table &t = xs[i];
+        char b[256];
+        if (t.reaction < 4 || t.reaction > 19 || t.n < 2 || !t.E_eV || !t.sigma_m2 || !(t.threshold_eV >= 0)) {
+            snprintf(b, sizeof b, "table %d: reaction must be 4..19, n >= 2, threshold >= 0", i);
+            why = b;
+            return false;
+        }
+        if (!(t.E_eV[0] > 0)) {
+            snprintf(b, sizeof b, "table %d: first node must be > 0", i);
+            why = b;
+            return false;
+        }
+        for (int k = 0; k + 1 < t.n; ++k)
+            if (!(t.E_eV[k + 1] > t.E_eV[k])) {
+                snprintf(b, sizeof b, "table %d: nodes must increase strictly", i);
+                why = b;
+                return false;
+            }
+        // geometric grid (the device locates the segment by a logarithm)
+        const double r = std::log(t.E_eV[t.n - 1] / t.E_eV[0]) / (t.n - 1);
+        for (int k = 0; k < t.n; ++k)
+            if (std::fabs(std::log(t.E_eV[k] / t.E_eV[0]) - k * r) > 0.25 * r) {
+                snprintf(b, sizeof b, "table %d: nodes must be geometric", i);
+                why = b;
+                return false;
+            }
+        if (targ_of(t.reaction) >= 0) {
+            if (++npair[t.reaction] > 1) {
+                why = "at most one table per particle-target reaction";
+                return false;
+            }
+        } else {
+            const int s = proj_of(t.reaction);
+            if (++ngas[s] > MAX_GAS_CH) {
+                why = "too many gas channels for one projectile (max 16)";
+                return false;
+            }
+            if (first[s] < 0) {
+                first[s] = i;
+            } else {
+                const pic_xs_table &f = xs[first[s]];
+                bool same = f.n == t.n;
+                for (int k = 0; same && k < t.n; ++k)
+                    same = std::fabs(f.E_eV[k] - t.E_eV[k]) <= 1e-12 * f.E_eV[k];
+                if (!same) {
+                    snprintf(b, sizeof b, "table %d: gas channels of one projectile must share one grid", i);
+                    why = b;
+                    return false;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs, bool fp64)
+{
+    Layout L{};
+    const size_t R = fp64 ? 8 : 4;
+    int tn = 0, tc = 0, mc = 0, cap = 0, sb = 0, maxN = 0, em = 0, fmm = 0;
+    long long sortc = 0, csb = 0, eb = 0, ib = 0, fb = 0;
+    L.pbase.resize(3 * D);
+    L.capr.resize(3 * D);
+    L.sort_cbase.resize(3 * D);
+    L.sort_gmax.resize(3 * D);
+    for (int d = 0; d < D; ++d) {
+        const int N = c[d].n_cells;
+        L.gbase.push_back(tn);
+        L.ccell.push_back(tc);
+        L.cs_base.push_back((int)csb);
+        L.eedf_base.push_back((int)eb);
+        L.iedf_base.push_back((int)ib);
+        L.fm_base.push_back((int)fb);
+        tn += N + 1;
+        tc += N;
+        csb += 3LL * (N + 2);
+        eb += c[d].eedf_bins;
+        ib += 2LL * c[d].iedf_bins;
+        fb += (long long)c[d].fm_xbins * c[d].fm_bins;
+        maxN = std::max(maxN, N);
+        em = std::max(em, c[d].eedf_bins);
+        fmm = std::max(fmm, c[d].fm_xbins * c[d].fm_bins);
+        for (int s = 0; s < 3; ++s) {
+            const int cr = (int)round_up((size_t)std::max(1LL, c[d].capacity[s]), CHUNK);
+            L.pbase[3 * d + s] = cap;
+            L.capr[3 * d + s] = cr;
+            cap += cr;
+            mc += cr / CHUNK;
+            const int g = (cr + SORT_CHUNK - 1) / SORT_CHUNK;
+            L.sort_gmax[3 * d + s] = g;
+            L.sort_cbase[3 * d + s] = (int)sortc;
+            sortc += (long long)g * (N + 1);
+            sb += g;
+        }
+    }
+    int nl = 0;
+    for (int i = 0; i < n_xs; ++i) nl += xs[i].n;
+    L.total_nodes = tn;
+    L.total_cells = tc;
+    L.max_chunks = mc;
+    L.total_cap = cap;
+    L.sort_blocks = sb;
+    L.n_lut = nl;
+    L.maxN = maxN;
+    L.eedf_max = em;
+    L.fm_max = fmm;
+    Bump B;
+    L.ctl = B.take(sizeof(Ctl));
+    L.disc = B.take(sizeof(Disc) * D);
+    L.cnt = B.take(sizeof(Counts) * 3 * D);
+    L.lb = B.take(8ull * 3 * mc);
+    L.acc = B.take(8ull * 3 * tn);
+    L.Efield = B.take(8ull * tn);
+    L.Ereal = B.take(R * tn);
+    L.phi = B.take(8ull * tn);
+    L.rho = B.take(8ull * tn);
+    L.dens = B.take(8ull * 3 * tn);
+    L.dens_sum = B.take(8ull * 3 * tn);
+    L.phi_sum = B.take(8ull * tn);
+    L.nsamp = B.take(8ull * D);
+    L.counters = B.take(8ull * C_NCOUNT * D);
+    L.eedf = B.take(4ull * std::max(1LL, eb));
+    L.iedf = B.take(4ull * std::max(1LL, ib));
+    L.fm = B.take(4ull * std::max(1LL, fb));
+    L.tables = B.take(sizeof(TableDesc) * std::max(1, n_xs));
+    L.lutE = B.take(8ull * std::max(1, nl));
+    L.lutS = B.take(8ull * std::max(1, nl));
+    L.lutEf = B.take(4ull * std::max(1, nl));
+    L.lutSf = B.take(4ull * std::max(1, nl));
+    L.sort_counts = B.take(4ull * std::max(1LL, sortc));
+    L.cell_start = B.take(4ull * csb);
+    L.sort_live = B.take(4ull * 3 * D);
+    L.pair_bcount = B.take(4ull * tc);
+    L.cell_disc = B.take(4ull * tc);
+    L.pair_births = B.take((size_t)tc * PAIR_BIRTH_CAP * (8 + 4 * 8));
+    L.sort_tab = B.take(8ull * sb);
+    L.ninit = B.take(8ull * 3 * D);
+    L.vt = B.take(8ull * 3 * D);
+    for (int b = 0; b < 2; ++b) {
+        L.cell[b] = B.take(4ull * cap);
+        L.off[b] = B.take(R * cap);
+        L.vx[b] = B.take(R * cap);
+        L.vy[b] = B.take(R * cap);
+        L.vz[b] = B.take(R * cap);
+    }
+    L.total = round_up(B.off, 256);
+    return L;
+}
+
+} // namespace
+
+struct pic_handle {
+    int D = 0;
+    bool fp64 = false;
+    std::vector<pic_config> cfg;
+    std::vector<HostTable> tabs;
+    char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    Layout lay;
+    WsPtrs W{};
+    Pools<float> Pf{};
+    Pools<double> Pd{};
+    LaunchCfg L{};
+    int *sort_tab = nullptr;
+    long long step = 0;
+    std::vector<Disc> disc;
+    std::vector<double> numax;  // [D*3]
+    std::string err;
+    // graph of one period
+    cudaGraphExec_t gexec = nullptr;
+    long long period = 0;
+    long long graph_launches = 0;
+    bool graph_failed = false;
+    // timing
+    bool timing = false;
+    double push_ms = 0.0;
+    long long push_launches = 0, launches = 0;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    unsigned long long slots0 = 0, cands0 = 0;
+    const void *pools() const { return fp64 ? (const void *)&Pd : (const void *)&Pf; }
+};
+
+static pic_status fail(pic_handle *h, pic_status s, const std::string &m)
+{
+    if (h) h->err = m;
+    g_err = m;
+    return s;
+}
+
+static pic_status cuda_fail(pic_handle *h, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, PIC_ECUDA, m);
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);     \
+    } while (0)
+
+extern "C" size_t pic_workspace_size(const pic_config *cfgs, int n_discharges, const pic_xs_table *xs, int n_xs)
+{
+    std::string why;
+    if (!validate(cfgs, n_discharges, xs, n_xs, why)) {
+        g_err = why;
+        return 0;
+    }
+    return make_layout(cfgs, n_discharges, xs, n_xs, cfgs[0].precision == PIC_FP64).total;
+}
+
+static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by_sp_flat,
+                       const std::vector<int> &gas_count, const int pair_tab[20])
+{
+    const pic_config &q = h->cfg[d];
+    const Layout &L = h->lay;
+    Disc D{};
+    const int N = q.n_cells;
+    D.N = N;
+    D.gbase = L.gbase[d];
+    for (int s = 0; s < 3; ++s) {
+        D.pbase[s] = L.pbase[3 * d + s];
+        D.cap[s] = (int)q.capacity[s];
+        D.sort_cbase[s] = L.sort_cbase[3 * d + s];
+        D.sort_gmax[s] = L.sort_gmax[3 * d + s];
+    }
+    D.ccell_base = L.ccell[d];
+    D.cs_base = L.cs_base[d];
+    D.dx = q.L_m / N;
+    D.dt = q.dt_s;
+    D.L = q.L_m;
+    D.weight = q.weight_m2;
+    D.U_rf = q.U_rf_V;
+    D.omega = 2.0 * PI * q.f_rf_Hz;
+    D.phase = q.rf_phase;
+    const double tdx = q.dt_s / D.dx, xdt = D.dx / q.dt_s;
+    D.kE = q.dt_s * q.dt_s / D.dx;
+    const double mu2 = M_O * MASS[1] / (M_O + MASS[1]);
+    D.mu2_15 = mu2;
+    D.f15 = 2.0 * QE * mu2 / (MASS[1] * MASS[1]) * tdx * tdx;
+    D.f16 = std::sqrt(MASS[1] / (10.0 * ME));
+    D.f17 = 2.0 * QE / ME * tdx * tdx;
+    D.eedf_bins = q.eedf_bins;
+    D.iedf_bins = q.iedf_bins;
+    D.fm_bins = q.fm_bins;
+    D.fm_xbins = q.fm_bins > 0 ? q.fm_xbins : 0;
+    D.eedf_scale = q.eedf_bins > 0 ? q.eedf_bins / q.eedf_emax_eV : 0.0;
+    D.iedf_scale = q.iedf_bins > 0 ? q.iedf_bins / q.iedf_emax_eV : 0.0;
+    D.fm_scale = q.fm_bins > 0 ? q.fm_bins / (2.0 * q.fm_emax_eV) : 0.0;
+    D.fm_emax = q.fm_emax_eV;
+    D.eedf_base = L.eedf_base[d];
+    D.iedf_base = L.iedf_base[d];
+    D.fm_base = L.fm_base[d];
+    D.diag_every = q.diag_every;
+    D.n1 = q.n1;
+    D.sort_interval = q.sort_interval;
+    D.seed = q.seed;
+    D.discharge = d;
+    D.cx_iso = q.cx_isotropic;
+    const double ngas = q.p_Pa / (KB * q.T_gas_K);
+    for (int s = 0; s < 3; ++s) {
+        SpeciesC &S = D.sp[s];
+        const double m = MASS[s];
+        const double mu = m * M_O2 / (m + M_O2);
+        S.qm = CHARGE[s] / m * q.dt_s * q.dt_s / D.dx;
+        S.vgas_n = std::sqrt(KB * q.T_gas_K / M_O2) * tdx;
+        S.Ek = 0.5 * mu * xdt * xdt / QE;
+        S.ke_eV = 0.5 * m * xdt * xdt / QE;
+        S.mfrac = m / (m + M_O2);
+        S.Mfrac = M_O2 / (m + M_O2);
+        S.vscale = xdt;
+        S.nch = gas_count[s];
+        S.table_lo = S.nch > 0 ? gas_tabs_by_sp_flat[s * MAX_GAS_CH] : 0;
+        for (int j = 0; j < S.nch; ++j) {
+            const int ti = gas_tabs_by_sp_flat[s * MAX_GAS_CH + j];
+            const HostTable &t = h->tabs[ti];
+            S.ch[j].table = ti;
+            S.ch[j].reaction = t.reaction;
+            const double nj = (t.reaction == 17) ? q.C_delta * ngas : ngas;
+            S.ch[j].coef = nj * D.dx;
+            S.ch[j].dloss = 2.0 * t.th * QE / mu * tdx * tdx;
+        }
+        // nu_max: largest sum_j n_j sigma_j(E) sqrt(2E/mu) over the nodes up to
+        // the cap and the cap itself, times the safety factor
+        double best = 0.0;
+        const double capE = q.ecap_eV[s];
+        for (int a = 0; a < S.nch; ++a) {
+            const HostTable &ta = h->tabs[S.ch[a].table];
+            for (int k = 0; k <= ta.n; ++k) {
+                const double E = k < ta.n ? ta.E[k] : capE;
+                if (E > capE || E <= 0.0) continue;
+                const double u = std::sqrt(2.0 * E * QE / mu);
+                double nu = 0.0;
+                for (int b = 0; b < S.nch; ++b) {
+                    const HostTable &tb = h->tabs[S.ch[b].table];
+                    const double nj = (tb.reaction == 17) ? q.C_delta * ngas : ngas;
+                    nu += nj * sigma_host(tb, E) * u;
+                }
+                best = std::max(best, nu);
+            }
+        }
+        S.numax = best * q.numax_safety;
+        S.numax_n = S.numax * q.dt_s;
+        const double pnull = 1.0 - std::exp(-S.numax * q.dt_s);
+        const double thr = std::ceil(pnull * 4294967296.0 - 0.5);
+        S.tnull = thr <= 0.0 ? 0u : (thr >= 4294967295.0 ? 0xFFFFFFFFu : (unsigned)thr);
+        h->numax[3 * d + s] = S.numax;
+    }
+    const int rx[3] = {13, 14, 19};
+    for (int k = 0; k < 3; ++k) {
+        PairC &P = D.pair[k];
+        P.table = pair_tab[rx[k]];
+        P.proj = proj_of(rx[k]);
+        P.targ = targ_of(rx[k]);
+        const double mp = MASS[P.proj], mt = MASS[P.targ];
+        const double mu = mp * mt / (mp + mt);
+        P.coef = q.weight_m2 * q.n1;
+        P.Ek = 0.5 * mu * xdt * xdt / QE;
+        P.mfrac = mp / (mp + mt);
+        P.Mfrac = mt / (mp + mt);
+        P.dloss = P.table >= 0 ? 2.0 * h->tabs[P.table].th * QE / mu * tdx * tdx : 0.0;
+    }
+    h->disc[d] = D;
+}
+
+extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const pic_xs_table *xs, int n_xs,
+                               void *d_workspace, size_t ws_bytes, void *cuda_stream, pic_handle **out)
+{
+    if (!out) return fail(nullptr, PIC_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (!validate(cfgs, n_discharges, xs, n_xs, why)) return fail(nullptr, PIC_EINVAL, why);
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255))
+        return fail(nullptr, PIC_EINVAL, "workspace must be a 256-byte aligned device pointer");
+    pic_handle *h = new pic_handle();
+    h->D = n_discharges;
+    h->fp64 = cfgs[0].precision == PIC_FP64;
+    h->cfg.assign(cfgs, cfgs + n_discharges);
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->lay = make_layout(cfgs, n_discharges, xs, n_xs, h->fp64);
+    if (ws_bytes < h->lay.total) {
+        delete h;
+        return fail(nullptr, PIC_ENOMEM, "workspace smaller than pic_workspace_size()");
+    }
+    h->ws = static_cast<char *>(d_workspace);
+    for (int i = 0; i < n_xs; ++i) {
+        HostTable t;
+        t.reaction = xs[i].reaction;
+        t.sub = xs[i].sub;
+        t.n = xs[i].n;
+        t.E.assign(xs[i].E_eV, xs[i].E_eV + t.n);
+        t.S.assign(xs[i].sigma_m2, xs[i].sigma_m2 + t.n);
+        t.th = xs[i].threshold_eV;
+        h->tabs.push_back(t);
+    }
+    const Layout &L = h->lay;
+    char *b = h->ws;
+    WsPtrs &W = h->W;
+    W.ctl = reinterpret_cast<Ctl *>(b + L.ctl);
+    W.disc = reinterpret_cast<Disc *>(b + L.disc);
+    W.cnt = reinterpret_cast<Counts *>(b + L.cnt);
+    W.chunk_ds = nullptr;
+    W.lb = reinterpret_cast<unsigned long long *>(b + L.lb);
+    W.acc_fix = reinterpret_cast<unsigned long long *>(b + L.acc);
+    W.acc_dbl = reinterpret_cast<double *>(b + L.acc);
+    W.Efield = reinterpret_cast<double *>(b + L.Efield);
+    W.Ereal = b + L.Ereal;
+    W.phi = reinterpret_cast<double *>(b + L.phi);
+    W.rho = reinterpret_cast<double *>(b + L.rho);
+    W.dens = reinterpret_cast<double *>(b + L.dens);
+    W.dens_sum = reinterpret_cast<double *>(b + L.dens_sum);
+    W.phi_sum = reinterpret_cast<double *>(b + L.phi_sum);
+    W.nsamp = reinterpret_cast<unsigned long long *>(b + L.nsamp);
+    W.counters = reinterpret_cast<unsigned long long *>(b + L.counters);
+    W.eedf = reinterpret_cast<unsigned *>(b + L.eedf);
+    W.iedf = reinterpret_cast<unsigned *>(b + L.iedf);
+    W.fm = reinterpret_cast<unsigned *>(b + L.fm);
+    W.tables = reinterpret_cast<TableDesc *>(b + L.tables);
+    W.lutE = reinterpret_cast<double *>(b + L.lutE);
+    W.lutS = reinterpret_cast<double *>(b + L.lutS);
+    W.lutEf = reinterpret_cast<float *>(b + L.lutEf);
+    W.lutSf = reinterpret_cast<float *>(b + L.lutSf);
+    W.sort_counts = reinterpret_cast<int *>(b + L.sort_counts);
+    W.cell_start = reinterpret_cast<int *>(b + L.cell_start);
+    W.sort_live = reinterpret_cast<int *>(b + L.sort_live);
+    W.pair_bcount = reinterpret_cast<int *>(b + L.pair_bcount);
+    W.cell_disc = reinterpret_cast<int *>(b + L.cell_disc);
+    W.pair_births = b + L.pair_births;
+    W.total_nodes = L.total_nodes;
+    W.total_cells = L.total_cells;
+    W.max_chunks = L.max_chunks;
+    W.D = n_discharges;
+    for (int k = 0; k < 2; ++k) {
+        h->Pf.cell[k] = h->Pd.cell[k] = reinterpret_cast<int *>(b + L.cell[k]);
+        h->Pf.off[k] = reinterpret_cast<float *>(b + L.off[k]);
+        h->Pf.vx[k] = reinterpret_cast<float *>(b + L.vx[k]);
+        h->Pf.vy[k] = reinterpret_cast<float *>(b + L.vy[k]);
+        h->Pf.vz[k] = reinterpret_cast<float *>(b + L.vz[k]);
+        h->Pd.off[k] = reinterpret_cast<double *>(b + L.off[k]);
+        h->Pd.vx[k] = reinterpret_cast<double *>(b + L.vx[k]);
+        h->Pd.vy[k] = reinterpret_cast<double *>(b + L.vy[k]);
+        h->Pd.vz[k] = reinterpret_cast<double *>(b + L.vz[k]);
+    }
+    h->sort_tab = reinterpret_cast<int *>(b + L.sort_tab);
+
+    // tables: descriptors and LUTs
+    std::vector<TableDesc> td(n_xs);
+    std::vector<double> lE, lS;
+    std::vector<float> lEf, lSf;
+    std::vector<int> gas(3 * MAX_GAS_CH, 0), gcount(3, 0);
+    int pair_tab[20];
+    for (int r = 0; r < 20; ++r) pair_tab[r] = -1;
+    for (int i = 0; i < n_xs; ++i) {
+        const HostTable &t = h->tabs[i];
+        td[i].off = (int)lE.size();
+        td[i].n = t.n;
+        td[i].reaction = t.reaction;
+        td[i].th = t.th;
+        td[i].lnE0 = std::log(t.E[0]);
+        td[i].inv_dlog = (t.n - 1) / std::log(t.E[t.n - 1] / t.E[0]);
+        for (int k = 0; k < t.n; ++k) {
+            lE.push_back(t.E[k]);
+            lS.push_back(t.S[k]);
+            lEf.push_back((float)t.E[k]);
+            lSf.push_back((float)t.S[k]);
+        }
+        if (targ_of(t.reaction) >= 0) {
+            pair_tab[t.reaction] = i;
+        } else {
+            const int s = proj_of(t.reaction);
+            gas[s * MAX_GAS_CH + gcount[s]++] = i;
+        }
+    }
+    h->disc.resize(n_discharges);
+    h->numax.assign(3 * n_discharges, 0.0);
+    for (int d = 0; d < n_discharges; ++d) build_disc(h, d, gas, gcount, pair_tab);
+
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    h->L.maxN = L.maxN;
+    h->L.eedf_max = L.eedf_max;
+    h->L.fm_max = L.fm_max;
+    h->L.sort_blocks = L.sort_blocks;
+    CK(configure_kernels(h->fp64, h->L));
+    CK(push_configure(h->fp64, h->L, nsm));
+
+    // host-built small tables
+    std::vector<int> stab;
+    std::vector<int> cdisc(L.total_cells);
+    for (int d = 0; d < n_discharges; ++d) {
+        for (int s = 0; s < 3; ++s)
+            for (int g = 0; g < L.sort_gmax[3 * d + s]; ++g) {
+                stab.push_back(3 * d + s);
+                stab.push_back(g);
+            }
+        for (int c = 0; c < h->cfg[d].n_cells; ++c) cdisc[L.ccell[d] + c] = d;
+    }
+    std::vector<long long> ninit(3 * n_discharges);
+    std::vector<double> vt(3 * n_discharges);
+    std::vector<Counts> cnt(3 * n_discharges);
+    int max_n = 1;
+    for (int d = 0; d < n_discharges; ++d)
+        for (int s = 0; s < 3; ++s) {
+            ninit[3 * d + s] = h->cfg[d].n_init[s];
+            vt[3 * d + s] = std::sqrt(h->cfg[d].T0_eV[s] * QE / MASS[s]);
+            cnt[3 * d + s] = Counts{(int)h->cfg[d].n_init[s], 0, 0, 0};
+            max_n = std::max(max_n, (int)h->cfg[d].n_init[s]);
+        }
+    Ctl ctl{};
+    ctl.D = n_discharges;
+    cudaStream_t st = h->stream;
+    CK(cudaMemsetAsync(h->ws, 0, L.total, st));
+    CK(cudaMemcpyAsync(W.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(W.disc, h->disc.data(), sizeof(Disc) * n_discharges, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(W.cnt, cnt.data(), sizeof(Counts) * cnt.size(), cudaMemcpyHostToDevice, st));
+    if (n_xs > 0) {
+        CK(cudaMemcpyAsync(W.tables, td.data(), sizeof(TableDesc) * n_xs, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(W.lutE, lE.data(), 8 * lE.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(W.lutS, lS.data(), 8 * lS.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(W.lutEf, lEf.data(), 4 * lEf.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(W.lutSf, lSf.data(), 4 * lSf.size(), cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemcpyAsync(h->sort_tab, stab.data(), 4 * stab.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(W.cell_disc, cdisc.data(), 4 * cdisc.size(), cudaMemcpyHostToDevice, st));
+    long long *d_ninit = reinterpret_cast<long long *>(b + L.ninit);
+    double *d_vt = reinterpret_cast<double *>(b + L.vt);
+    CK(cudaMemcpyAsync(d_ninit, ninit.data(), 8 * ninit.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_vt, vt.data(), 8 * vt.size(), cudaMemcpyHostToDevice, st));
+    CK(launch_load(h->fp64, W, h->pools(), d_ninit, d_vt, max_n, st));
+    CK(launch_deposit_all(h->fp64, W, h->pools(), -1, max_n, st));
+    CK(cudaStreamSynchronize(st));
+    h->launches = 0;
+    *out = h;
+    return PIC_OK;
+}
+
+static long long lcm_ll(long long a, long long b) { return a / std::gcd(a, b) * b; }
+
+// Kernels of one step; returns the number launched.
+static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool time_push)
+{
+    const pic_config &q = h->cfg[0];
+    const int par = (int)(n & 1);
+    const bool diag = q.diag_every > 0 && (n % q.diag_every) == 0;
+    cudaStream_t st = h->stream;
+    cudaError_t e = launch_field(h->fp64, diag, 0, h->W, par, h->L, st);
+    if (e) return e;
+    ++nk;
+    if (time_push) {
+        if (h->ev_used + 2 > (int)h->ev.size()) return cudaErrorNotReady;
+        e = cudaEventRecord(h->ev[h->ev_used], st);
+        if (e) return e;
+    }
+    e = launch_push(h->fp64, diag, h->W, h->pools(), par, h->L, st);
+    if (e) return e;
+    ++nk;
+    if (time_push) {
+        e = cudaEventRecord(h->ev[h->ev_used + 1], st);
+        if (e) return e;
+        h->ev_used += 2;
+    }
+    const long long next = n + 1;
+    const bool pair = q.n1 > 0 && next % q.n1 == 0;
+    const bool sort = pair || (q.sort_interval > 0 && next % q.sort_interval == 0);
+    if (sort) {
+        e = launch_sort(h->fp64, h->W, h->pools(), h->sort_tab, h->L, st);
+        if (e) return e;
+        nk += kernels_per_sort();
+    }
+    if (pair) {
+        e = launch_pair(h->fp64, h->W, h->pools(), par, h->L, st);
+        if (e) return e;
+        nk += kernels_per_pair();
+    }
+    return cudaSuccess;
+}
+
+static pic_status harvest_events(pic_handle *h)
+{
+    if (h->ev_used == 0) return PIC_OK;
+    CK(cudaEventSynchronize(h->ev[h->ev_used - 1]));
+    for (int i = 0; i < h->ev_used; i += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
+        h->push_ms += ms;
+        h->push_launches += 1;
+    }
+    h->ev_used = 0;
+    return PIC_OK;
+}
+
+static pic_status check_status(pic_handle *h)
+{
+    unsigned status = 0;
+    CK(cudaMemcpyAsync(&status, &h->W.ctl->status, sizeof status, cudaMemcpyDeviceToHost, h->stream));
+    std::vector<unsigned long long> c((size_t)h->D * C_NCOUNT);
+    CK(cudaMemcpyAsync(c.data(), h->W.counters, 8 * c.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (status & ST_TIMEOUT) return fail(h, PIC_ETIMEOUT, "a bounded device wait (birth look-back) gave up");
+    if (status & (ST_CAPACITY | ST_BIRTHBUF))
+        return fail(h, PIC_ECAPACITY, (status & ST_CAPACITY) ? "particle capacity exceeded; births were dropped"
+                                                             : "a per-chunk or per-cell birth buffer overflowed");
+    if (status & ST_BADSTATE) return fail(h, PIC_EINVAL, "inconsistent device state");
+    for (int d = 0; d < h->D; ++d) {
+        const unsigned long long v = c[(size_t)d * C_NCOUNT + C_VIOL_GAS];
+        const unsigned long long cand = c[(size_t)d * C_NCOUNT + C_CANDS];
+        if (v > 10 && (double)v > 1e-6 * (double)cand)
+            return fail(h, PIC_ENUMERIC, "collision frequency above nu_max too often (raise ecap_eV)");
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_step(pic_handle *h, long long n_steps)
+{
+    if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
+    if (n_steps < 0) return fail(h, PIC_EINVAL, "n_steps < 0");
+    const pic_config &q = h->cfg[0];
+    if (h->period == 0) {
+        long long P = 2;
+        if (q.n1 > 0) P = lcm_ll(P, q.n1);
+        if (q.sort_interval > 0) P = lcm_ll(P, q.sort_interval);
+        if (q.diag_every > 0) P = lcm_ll(P, q.diag_every);
+        h->period = P;
+    }
+    long long left = n_steps;
+    while (left > 0) {
+        const bool aligned = (h->step % h->period) == 0;
+        if (!h->timing && !h->graph_failed && aligned && left >= h->period && h->period <= 4096) {
+            if (!h->gexec) {
+                cudaGraph_t g = nullptr;
+                cudaStream_t cs = nullptr;
+                CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+                bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                int nk = 0;
+                cudaStream_t keep = h->stream;
+                h->stream = cs;
+                for (long long k = 0; ok && k < h->period; ++k)
+                    ok = enqueue_step(h, h->step + k, nk, false) == cudaSuccess;
+                h->stream = keep;
+                cudaError_t ee = cudaStreamEndCapture(cs, &g);
+                ok = ok && ee == cudaSuccess && g;
+                if (ok) ok = cudaGraphInstantiate(&h->gexec, g, 0) == cudaSuccess;
+                if (g) cudaGraphDestroy(g);
+                cudaStreamDestroy(cs);
+                cudaGetLastError();
+                if (!ok) {
+                    h->gexec = nullptr;
+                    h->graph_failed = true;
+                    continue;
+                }
+                h->graph_launches = nk;
+            }
+            CK(cudaGraphLaunch(h->gexec, h->stream));
+            h->launches += h->graph_launches;
+            h->step += h->period;
+            left -= h->period;
+            continue;
+        }
+        int nk = 0;
+        if (h->timing && h->ev_used + 2 > (int)h->ev.size()) {
+            pic_status s = harvest_events(h);
+            if (s != PIC_OK) return s;
+        }
+        cudaError_t e = enqueue_step(h, h->step, nk, h->timing);
+        if (e) return cuda_fail(h, e, "kernel launch");
+        h->launches += nk;
+        h->step += 1;
+        left -= 1;
+    }
+    if (h->timing) {
+        pic_status s = harvest_events(h);
+        if (s != PIC_OK) return s;
+    }
+    return check_status(h);
+}
+
+extern "C" pic_status pic_set_step(pic_handle *h, long long step)
+{
+    if (!h || step < 0) return fail(h, PIC_EINVAL, "bad handle or step");
+    unsigned long long v = (unsigned long long)step;
+    CK(cudaMemcpyAsync(&h->W.ctl->step[step & 1], &v, 8, cudaMemcpyHostToDevice, h->stream));
+    // look-back words are tagged with the step; a step number can now repeat
+    CK(cudaMemsetAsync(h->W.lb, 0, 8ull * NSP * h->W.max_chunks, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->step = step;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_diagnostics(pic_handle *h, int d, double *dens_sum, double *phi_sum, long long *eedf,
+                                      long long *iedf, long long *fm, long long *counters, long long *n_samples,
+                                      int reset)
+{
+    if (!h || d < 0 || d >= h->D) return fail(h, PIC_EINVAL, "bad handle or discharge");
+    const pic_config &q = h->cfg[d];
+    const Disc &D = h->disc[d];
+    const int N = q.n_cells, tn = h->W.total_nodes;
+    cudaStream_t st = h->stream;
+    if (dens_sum)
+        for (int s = 0; s < 3; ++s)
+            CK(cudaMemcpyAsync(dens_sum + (size_t)s * (N + 1), h->W.dens_sum + (size_t)s * tn + D.gbase,
+                               8 * (N + 1), cudaMemcpyDeviceToHost, st));
+    if (phi_sum) CK(cudaMemcpyAsync(phi_sum, h->W.phi_sum + D.gbase, 8 * (N + 1), cudaMemcpyDeviceToHost, st));
+    std::vector<unsigned> e(std::max(1, q.eedf_bins)), i2(std::max(1, 2 * q.iedf_bins)),
+        f(std::max(1, D.fm_xbins * q.fm_bins));
+    if (q.eedf_bins)
+        CK(cudaMemcpyAsync(e.data(), h->W.eedf + D.eedf_base, 4 * q.eedf_bins, cudaMemcpyDeviceToHost, st));
+    if (q.iedf_bins)
+        CK(cudaMemcpyAsync(i2.data(), h->W.iedf + D.iedf_base, 8 * q.iedf_bins, cudaMemcpyDeviceToHost, st));
+    if (q.fm_bins)
+        CK(cudaMemcpyAsync(f.data(), h->W.fm + D.fm_base, 4 * (size_t)D.fm_xbins * q.fm_bins,
+                           cudaMemcpyDeviceToHost, st));
+    std::vector<unsigned long long> c(C_NCOUNT);
+    CK(cudaMemcpyAsync(c.data(), h->W.counters + (size_t)d * C_NCOUNT, 8 * C_NCOUNT, cudaMemcpyDeviceToHost, st));
+    unsigned long long ns = 0;
+    CK(cudaMemcpyAsync(&ns, h->W.nsamp + d, 8, cudaMemcpyDeviceToHost, st));
+    Counts cn[3];
+    CK(cudaMemcpyAsync(cn, h->W.cnt + 3 * d, sizeof cn, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (eedf) for (int k = 0; k < q.eedf_bins; ++k) eedf[k] = e[k];
+    if (iedf) for (int k = 0; k < 2 * q.iedf_bins; ++k) iedf[k] = i2[k];
+    if (fm) for (int k = 0; k < D.fm_xbins * q.fm_bins; ++k) fm[k] = f[k];
+    if (counters) {
+        for (int k = 0; k < 28; ++k) counters[k] = (long long)c[k];
+        for (int s = 0; s < 3; ++s) counters[28 + s] = cn[s].n;
+        counters[31] = h->step;
+    }
+    if (n_samples) *n_samples = (long long)ns;
+    if (reset) {
+        for (int s = 0; s < 3; ++s)
+            CK(cudaMemsetAsync(h->W.dens_sum + (size_t)s * tn + D.gbase, 0, 8 * (N + 1), st));
+        CK(cudaMemsetAsync(h->W.phi_sum + D.gbase, 0, 8 * (N + 1), st));
+        if (q.eedf_bins) CK(cudaMemsetAsync(h->W.eedf + D.eedf_base, 0, 4 * q.eedf_bins, st));
+        if (q.iedf_bins) CK(cudaMemsetAsync(h->W.iedf + D.iedf_base, 0, 8 * q.iedf_bins, st));
+        if (q.fm_bins) CK(cudaMemsetAsync(h->W.fm + D.fm_base, 0, 4 * (size_t)D.fm_xbins * q.fm_bins, st));
+        CK(cudaMemsetAsync(h->W.nsamp + d, 0, 8, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_get_state(pic_handle *h, int d, int s, double *x, double *vx, double *vy, double *vz,
+                                    int *alive, long long capacity_n, long long *n)
+{
+    if (!h || d < 0 || d >= h->D || s < 0 || s > 2) return fail(h, PIC_EINVAL, "bad handle, discharge or species");
+    Counts cn;
+    int cur = 0;
+    CK(cudaMemcpyAsync(&cn, h->W.cnt + 3 * d + s, sizeof cn, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&cur, &h->W.ctl->cur, sizeof cur, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (n) *n = cn.n;
+    if (!x && !vx && !vy && !vz && !alive) return PIC_OK;
+    if (capacity_n < cn.n) return fail(h, PIC_EINVAL, "host arrays shorter than the slot count");
+    const Disc &D = h->disc[d];
+    const size_t g = D.pbase[s], m = cn.n;
+    const size_t R = h->fp64 ? 8 : 4;
+    const char *base = h->ws;
+    const Layout &L = h->lay;
+    std::vector<int> cell(m);
+    std::vector<char> o(m * R), a(m * R), bb(m * R), cc(m * R);
+    if (m) {
+        CK(cudaMemcpyAsync(cell.data(), base + L.cell[cur] + 4 * g, 4 * m, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(o.data(), base + L.off[cur] + R * g, R * m, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(a.data(), base + L.vx[cur] + R * g, R * m, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(bb.data(), base + L.vy[cur] + R * g, R * m, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(cc.data(), base + L.vz[cur] + R * g, R * m, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    const double dx = D.dx, vs = D.dx / D.dt;
+    auto rd = [&](const std::vector<char> &v, size_t i) {
+        return h->fp64 ? reinterpret_cast<const double *>(v.data())[i]
+                       : (double)reinterpret_cast<const float *>(v.data())[i];
+    };
+    for (size_t i = 0; i < m; ++i) {
+        const bool al = cell[i] >= 0;
+        if (x) x[i] = al ? ((double)cell[i] + rd(o, i)) * dx : 0.0;
+        if (vx) vx[i] = rd(a, i) * vs;
+        if (vy) vy[i] = rd(bb, i) * vs;
+        if (vz) vz[i] = rd(cc, i) * vs;
+        if (alive) alive[i] = al ? 1 : 0;
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_state(pic_handle *h, int d, int s, long long n, const double *x, const double *vx,
+                                    const double *vy, const double *vz, const int *alive)
+{
+    if (!h || d < 0 || d >= h->D || s < 0 || s > 2) return fail(h, PIC_EINVAL, "bad handle, discharge or species");
+    if (n < 0 || n > h->cfg[d].capacity[s]) return fail(h, PIC_ECAPACITY, "n exceeds the species capacity");
+    if (n > 0 && (!x || !vx || !vy || !vz)) return fail(h, PIC_EINVAL, "NULL state array");
+    const Disc &D = h->disc[d];
+    const int N = D.N;
+    const size_t R = h->fp64 ? 8 : 4;
+    std::vector<int> cell(n);
+    std::vector<char> o(n * R), a(n * R), bb(n * R), cc(n * R);
+    const double tdx = D.dt / D.dx;
+    for (long long i = 0; i < n; ++i) {
+        const bool al = alive ? alive[i] != 0 : true;
+        const double xx = x[i] / D.dx;
+        int c = al ? (int)std::floor(xx) : -1;
+        if (al && (!(x[i] >= 0.0) || !(x[i] < D.L))) return fail(h, PIC_EINVAL, "live particle outside [0, L)");
+        if (c > N - 1) c = N - 1;
+        double off = al ? xx - c : 0.0;
+        if (h->fp64) {
+            reinterpret_cast<double *>(o.data())[i] = off;
+            reinterpret_cast<double *>(a.data())[i] = vx[i] * tdx;
+            reinterpret_cast<double *>(bb.data())[i] = vy[i] * tdx;
+            reinterpret_cast<double *>(cc.data())[i] = vz[i] * tdx;
+        } else {
+            float of = (float)off;
+            if (al && of >= 1.0f) {
+                if (c + 1 < N) {
+                    ++c;
+                    of = 0.0f;
+                } else {
+                    of = std::nextafter(1.0f, 0.0f);
+                }
+            }
+            reinterpret_cast<float *>(o.data())[i] = of;
+            reinterpret_cast<float *>(a.data())[i] = (float)(vx[i] * tdx);
+            reinterpret_cast<float *>(bb.data())[i] = (float)(vy[i] * tdx);
+            reinterpret_cast<float *>(cc.data())[i] = (float)(vz[i] * tdx);
+        }
+        cell[i] = c;
+    }
+    int cur = 0;
+    CK(cudaMemcpyAsync(&cur, &h->W.ctl->cur, sizeof cur, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const size_t g = D.pbase[s];
+    char *base = h->ws;
+    const Layout &L = h->lay;
+    if (n) {
+        CK(cudaMemcpyAsync(base + L.cell[cur] + 4 * g, cell.data(), 4 * n, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(base + L.off[cur] + R * g, o.data(), R * n, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(base + L.vx[cur] + R * g, a.data(), R * n, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(base + L.vy[cur] + R * g, bb.data(), R * n, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(base + L.vz[cur] + R * g, cc.data(), R * n, cudaMemcpyHostToDevice, h->stream));
+    }
+    Counts cn{(int)n, 0, 0, 0};
+    CK(cudaMemcpyAsync(h->W.cnt + 3 * d + s, &cn, sizeof cn, cudaMemcpyHostToDevice, h->stream));
+    const int tn = h->W.total_nodes;
+    for (int sp = 0; sp < 3; ++sp)
+        CK(cudaMemsetAsync(reinterpret_cast<char *>(h->W.acc_dbl) + 8 * ((size_t)sp * tn + D.gbase), 0,
+                           8 * (N + 1), h->stream));
+    int max_n = 1;
+    for (int sp = 0; sp < 3; ++sp) max_n = std::max(max_n, (int)h->cfg[d].capacity[sp]);
+    CK(launch_deposit_all(h->fp64, h->W, h->pools(), d, max_n, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_fields(pic_handle *h, int d, double *rho, double *phi, double *E)
+{
+    if (!h || d < 0 || d >= h->D) return fail(h, PIC_EINVAL, "bad handle or discharge");
+    CK(launch_field(h->fp64, false, 1, h->W, (int)(h->step & 1), h->L, h->stream));
+    const Disc &D = h->disc[d];
+    const int N = D.N;
+    if (rho) CK(cudaMemcpyAsync(rho, h->W.rho + D.gbase, 8 * (N + 1), cudaMemcpyDeviceToHost, h->stream));
+    if (phi) CK(cudaMemcpyAsync(phi, h->W.phi + D.gbase, 8 * (N + 1), cudaMemcpyDeviceToHost, h->stream));
+    if (E) CK(cudaMemcpyAsync(E, h->W.Efield + D.gbase, 8 * (N + 1), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+}
+
+extern "C" double pic_numax(const pic_handle *h, int d, int s)
+{
+    if (!h || d < 0 || d >= h->D || s < 0 || s > 2) return -1.0;
+    return h->numax[3 * d + s];
+}
+
+extern "C" pic_status pic_set_timing(pic_handle *h, int on)
+{
+    if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
+    if (on && h->ev.empty()) {
+        h->ev.resize(4096);
+        for (auto &e : h->ev) CK(cudaEventCreate(&e));
+    }
+    h->timing = on != 0;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_timing(pic_handle *h, double *push_ms, long long *push_launches, long long *launches,
+                                 double *push_bytes, int reset)
+{
+    if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
+    std::vector<unsigned long long> c((size_t)h->D * C_NCOUNT);
+    CK(cudaMemcpyAsync(c.data(), h->W.counters, 8 * c.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    unsigned long long slots = 0, cands = 0;
+    for (int d = 0; d < h->D; ++d) {
+        slots += c[(size_t)d * C_NCOUNT + C_SLOTS];
+        cands += c[(size_t)d * C_NCOUNT + C_CANDS];
+    }
+    // algorithmic bytes of the push: cell, offset and vx read and written for
+    // every slot; vy, vz read and written for null-collision candidates
+    const double R = h->fp64 ? 8.0 : 4.0;
+    const double bytes = (double)(slots - h->slots0) * 2.0 * (4.0 + 2.0 * R) +
+                         (double)(cands - h->cands0) * 2.0 * (2.0 * R);
+    if (push_ms) *push_ms = h->push_ms;
+    if (push_launches) *push_launches = h->push_launches;
+    if (launches) *launches = h->launches;
+    if (push_bytes) *push_bytes = bytes;
+    if (reset) {
+        h->push_ms = 0.0;
+        h->push_launches = 0;
+        h->launches = 0;
+        h->slots0 = slots;
+        h->cands0 = cands;
+    }
+    return PIC_OK;
+}
+
+extern "C" void pic_destroy(pic_handle *h)
+{
+    if (!h) return;
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (auto &e : h->ev) cudaEventDestroy(e);
+    delete h;
+}
+
+extern "C" const char *pic_last_error(const pic_handle *h)
+{
+    if (h) return h->err.c_str();
+    return g_err.c_str();
+}

@@ -1,0 +1,778 @@
+// o2pic_kernels.cu -- field solve, cell sort, particle-target pass, load and
+// deposit kernels of libo2pic (GB300, sm_103a).
+#include "o2pic_launch.h"
+
+namespace o2 {
+
+constexpr double QE_ = 1.602176634e-19;
+constexpr double EPS0_ = 8.8541878128e-12;
+
+// ------------------------------------------------------------ helpers
+
+template <typename Real> struct AccK;
+template <> struct AccK<float> {
+    using T = unsigned long long;
+    static __device__ __forceinline__ T *ptr(const WsPtrs &W) { return W.acc_fix; }
+};
+template <> struct AccK<double> {
+    using T = double;
+    static __device__ __forceinline__ T *ptr(const WsPtrs &W) { return W.acc_dbl; }
+};
+
+__device__ __forceinline__ void dep_global(unsigned long long *acc, int c, float off, int sign)
+{
+    unsigned w1 = __float2uint_rn(off * (float)(1 << FIX_BITS));
+    unsigned w0 = (1u << FIX_BITS) - w1;
+    unsigned long long a = w0, b = w1;
+    if (sign < 0) { a = 0ull - a; b = 0ull - b; }
+    atomicAdd(&acc[c], a);
+    atomicAdd(&acc[c + 1], b);
+}
+__device__ __forceinline__ void dep_global(double *acc, int c, double off, int sign)
+{
+    atomicAdd(&acc[c], sign * (1.0 - off));
+    atomicAdd(&acc[c + 1], sign * off);
+}
+
+__device__ __forceinline__ double acc_to_weight(unsigned long long a)
+{
+    return (double)(long long)a * (1.0 / (double)(1 << FIX_BITS));
+}
+__device__ __forceinline__ double acc_to_weight(double a) { return a; }
+
+// inclusive scan of x[0..M) in shared memory by one block (deterministic order)
+template <int NT>
+__device__ void block_scan_inclusive(double *x, int M, double *warp_tot)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (M + NT - 1) / NT;
+    const int lo = tid * per, hi = min(M, lo + per);
+    double run = 0.0;
+    for (int i = lo; i < hi; ++i) {
+        run += x[i];
+        x[i] = run;
+    }
+    // exclusive scan of the thread totals
+    double v = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        double t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_tot[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double w = lane < NT / 32 ? warp_tot[lane] : 0.0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            double t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < NT / 32) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    double excl = v - run + (warp > 0 ? warp_tot[warp - 1] : 0.0);
+    for (int i = lo; i < hi; ++i) x[i] += excl;
+    __syncthreads();
+}
+
+// exclusive scan of a[0..M) in shared memory by one block; returns the total
+__device__ int block_scan_exclusive_int(int *a, int M, int *wsum)
+{
+    const int NT = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (M + NT - 1) / NT;
+    const int lo = tid * per, hi = min(M, lo + per);
+    int run = 0;
+    for (int i = lo; i < hi; ++i) {
+        const int v = a[i];
+        a[i] = run;
+        run += v;
+    }
+    int v = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < NT / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        if (lane < NT / 32) wsum[lane] = w;
+    }
+    __syncthreads();
+    const int excl = v - run + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int i = lo; i < hi; ++i) a[i] += excl;
+    const int total = wsum[NT / 32 - 1];
+    __syncthreads();
+    return total;
+}
+
+// ------------------------------------------------------------ field
+
+// Per discharge (one block): densities from the accumulators, Poisson with
+// phi_0 = U_rf sin(2 pi f t + phase), phi_N = 0, and the node field.
+// The tridiagonal system (phi_{i-1} - 2 phi_i + phi_{i+1}) = -rho_i dx^2/eps0
+// is solved exactly by two prefix sums: with s_i = rho_i dx^2/eps0,
+// S1_i = sum_{k<=i} s_k and S2_i = sum_{m<=i} S1_m (i >= 1),
+// phi_i = phi_0 + i D0 - S2_{i-1}, D0 fixed by phi_N = 0.
+template <typename Real>
+__global__ void __launch_bounds__(FIELD_THREADS)
+k_field(WsPtrs W, int par, int diag, int mode)
+{
+    extern __shared__ __align__(16) double fsm[];
+    __shared__ double warp_tot[FIELD_THREADS / 32];
+    __shared__ double s_rho0, s_rhoN, s_D0;
+    using Acc = typename AccK<Real>::T;
+    const int d = blockIdx.x;
+    const Disc &Dd = W.disc[d];
+    const int N = Dd.N, g = Dd.gbase, tid = threadIdx.x;
+    Ctl *ctl = W.ctl;
+    const unsigned long long step = ctl->step[par];
+    const int tn = W.total_nodes;
+    Acc *acc = AccK<Real>::ptr(W);
+    double *x = fsm;  // N+1 entries
+    const double dx = Dd.dx;
+    for (int i = tid; i <= N; i += FIELD_THREADS) {
+        const double vol = (i == 0 || i == N) ? 0.5 * dx : dx;
+        const double scale = Dd.weight / vol;
+        double dn[NSP];
+#pragma unroll
+        for (int s = 0; s < NSP; ++s) {
+            const size_t k = (size_t)s * tn + g + i;
+            dn[s] = acc_to_weight(acc[k]) * scale;
+            if (mode == 0) acc[k] = Acc(0);
+            W.dens[k] = dn[s];
+            if (diag) W.dens_sum[k] += dn[s];
+        }
+        const double rho = QE_ * (dn[2] - dn[0] - dn[1]);
+        W.rho[g + i] = rho;
+        if (i == 0) s_rho0 = rho;
+        if (i == N) s_rhoN = rho;
+        x[i] = rho * dx * dx / EPS0_;
+    }
+    __syncthreads();
+    // scans over interior nodes 1..N-1, stored at x[1..N-1]
+    const int M = N - 1;
+    if (M > 0) {
+        block_scan_inclusive<FIELD_THREADS>(x + 1, M, warp_tot);  // S1
+        block_scan_inclusive<FIELD_THREADS>(x + 1, M, warp_tot);  // S2
+    }
+    const double t = (double)step * Dd.dt;
+    const double phi0 = Dd.U_rf * sin(Dd.omega * t + Dd.phase);
+    if (tid == 0) s_D0 = M > 0 ? (-phi0 + x[M]) / (double)N : -phi0 / (double)N;
+    __syncthreads();
+    const double D0 = s_D0;
+    double *phi = W.phi + g;
+    for (int i = tid; i <= N; i += FIELD_THREADS) {
+        double p;
+        if (i == 0) p = phi0;
+        else if (i == N) p = 0.0;
+        else p = phi0 + (double)i * D0 - (i >= 2 ? x[i - 1] : 0.0);
+        phi[i] = p;
+    }
+    __syncthreads();
+    Real *Er = reinterpret_cast<Real *>(W.Ereal) + g;
+    for (int i = tid; i <= N; i += FIELD_THREADS) {
+        double E;
+        if (i == 0) E = -(phi[1] - phi[0]) / dx - s_rho0 * dx / (2.0 * EPS0_);
+        else if (i == N) E = -(phi[N] - phi[N - 1]) / dx + s_rhoN * dx / (2.0 * EPS0_);
+        else E = -(phi[i + 1] - phi[i - 1]) / (2.0 * dx);
+        W.Efield[g + i] = E;
+        Er[i] = (Real)E;
+        if (diag) W.phi_sum[g + i] += phi[i];
+    }
+    if (diag && tid == 0) W.nsamp[d] += 1ull;
+    if (mode != 0 || blockIdx.x != 0) return;
+    // block 0: chunk table of this step's push and the step counter
+    __syncthreads();
+    if (tid == 0) {
+        int chunk = 0;
+        for (int ds = 0; ds < W.D * NSP; ++ds) {
+            Counts &C = W.cnt[ds];
+            C.n_snap = C.n;
+            C.chunk0 = chunk;
+            C.nchunk = (C.n + CHUNK - 1) / CHUNK;
+            chunk += C.nchunk;
+        }
+        if (chunk > W.max_chunks) {
+            set_status(ctl, ST_CAPACITY);
+            chunk = 0;
+        }
+        ctl->total_chunks = chunk;
+        ctl->ticket = 0u;
+        ctl->step[par ^ 1] = step + 1ull;
+    }
+}
+
+// ------------------------------------------------------------- sort
+
+// block -> (ds, index of the block within ds) from a host-built table
+__device__ __forceinline__ void sort_block(const int *tab, int &ds, int &bi)
+{
+    ds = tab[2 * blockIdx.x];
+    bi = tab[2 * blockIdx.x + 1];
+}
+
+// Histogram of cells (dead slots in bucket N) of one block of SORT_CHUNK
+// slots; written as row bi of the (block x bucket) count matrix of ds.
+template <typename Real>
+__global__ void __launch_bounds__(SORT_WARPS * 32)
+k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
+{
+    extern __shared__ __align__(16) unsigned ssm[];
+    int ds, bi;
+    sort_block(tab, ds, bi);
+    const int d = ds / NSP, s = ds % NSP;
+    const Disc &Dd = W.disc[d];
+    const int N = Dd.N, n = W.cnt[ds].n;
+    const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
+    if (bi >= G) return;
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) ssm[i] = 0;
+    __syncthreads();
+    const int *cell = P.cell[W.ctl->cur] + Dd.pbase[s];
+    const int lo = bi * SORT_CHUNK, hi = min(n, lo + SORT_CHUNK);
+    const int lane = threadIdx.x & 31;
+    for (int i0 = lo + (threadIdx.x & ~31); i0 < hi; i0 += blockDim.x) {
+        const int i = i0 + lane;
+        int b = -1;
+        if (i < hi) {
+            const int c = cell[i];
+            b = c < 0 ? N : c;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&ssm[b], (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    int *row = W.sort_counts + Dd.sort_cbase[s] + (size_t)bi * (N + 1);
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) row[i] = (int)ssm[i];
+}
+
+// Per (d, s): running sums down the blocks per bucket (each (block, bucket)
+// entry becomes the first slot of that block's bucket relative to the bucket
+// start) and the bucket starts (cell_start) by a scan over buckets.
+__global__ void __launch_bounds__(512)
+k_sort_scan(WsPtrs W)
+{
+    extern __shared__ __align__(16) int isx[];
+    __shared__ int wsum[32];
+    const int ds = blockIdx.x;
+    const int d = ds / NSP, s = ds % NSP;
+    const Disc &Dd = W.disc[d];
+    const int N = Dd.N, n = W.cnt[ds].n;
+    const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
+    int *cnt = W.sort_counts + Dd.sort_cbase[s];
+    int *tot = isx;  // N+1
+    for (int c = threadIdx.x; c <= N; c += blockDim.x) {
+        int run = 0;
+        for (int b = 0; b < G; ++b) {
+            const int v = cnt[(size_t)b * (N + 1) + c];
+            cnt[(size_t)b * (N + 1) + c] = run;
+            run += v;
+        }
+        tot[c] = run;
+    }
+    __syncthreads();
+    block_scan_exclusive_int(tot, N + 1, wsum);
+    int *cs = W.cell_start + Dd.cs_base + s * (N + 2);
+    for (int c = threadIdx.x; c <= N; c += blockDim.x) cs[c] = tot[c];
+    if (threadIdx.x == 0) {
+        cs[N + 1] = n;
+        W.sort_live[ds] = tot[N];  // live slots = start of the dead bucket
+    }
+}
+
+// Stable scatter: warp w of block bi owns slots [lo + w*4096, +4096); a
+// per-warp bucket count gives each warp its first slot per bucket, then each
+// warp walks its slots in order, ranking equal buckets inside a 32-slot tile
+// by lane.  Dead slots (bucket N) are dropped.
+template <typename Real>
+__global__ void __launch_bounds__(SORT_WARPS * 32)
+k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
+{
+    extern __shared__ __align__(16) unsigned ssm[];
+    int ds, bi;
+    sort_block(tab, ds, bi);
+    const int d = ds / NSP, s = ds % NSP;
+    const Disc &Dd = W.disc[d];
+    const int N = Dd.N, n = W.cnt[ds].n;
+    const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
+    if (bi >= G) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned *hw = ssm + (size_t)w * (N + 1);
+    for (int i = threadIdx.x; i < SORT_WARPS * (N + 1); i += blockDim.x) ssm[i] = 0;
+    __syncthreads();
+    const int cur = W.ctl->cur, nxt = cur ^ 1;
+    const int pb = Dd.pbase[s];
+    const int *cell = P.cell[cur] + pb;
+    const int lo = bi * SORT_CHUNK + w * SORT_WARP_SLOTS;
+    const int hi = min(n, lo + SORT_WARP_SLOTS);
+    for (int i0 = lo; i0 < hi; i0 += 32) {
+        const int i = i0 + lane;
+        int b = -1;
+        if (i < hi) {
+            const int c = cell[i];
+            b = c < 0 ? N : c;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (b >= 0 && lane == __ffs(peers) - 1) hw[b] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int *base = W.sort_counts + Dd.sort_cbase[s] + (size_t)bi * (N + 1);
+    const int *cstart = W.cell_start + Dd.cs_base + s * (N + 2);
+    for (int c = threadIdx.x; c <= N; c += blockDim.x) {
+        unsigned run = (unsigned)(base[c] + cstart[c]);
+#pragma unroll
+        for (int q = 0; q < SORT_WARPS; ++q) {
+            const unsigned t = ssm[(size_t)q * (N + 1) + c];
+            ssm[(size_t)q * (N + 1) + c] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    const Real *offS = P.off[cur] + pb, *vxS = P.vx[cur] + pb, *vyS = P.vy[cur] + pb,
+               *vzS = P.vz[cur] + pb;
+    int *cellD = P.cell[nxt] + pb;
+    Real *offD = P.off[nxt] + pb, *vxD = P.vx[nxt] + pb, *vyD = P.vy[nxt] + pb,
+         *vzD = P.vz[nxt] + pb;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i0 = lo; i0 < hi; i0 += 32) {
+        const int i = i0 + lane;
+        int b = -1;
+        if (i < hi) {
+            const int c = cell[i];
+            b = c < 0 ? N : c;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        unsigned dst = 0;
+        if (b >= 0) dst = hw[b] + __popc(peers & lt);
+        __syncwarp();
+        if (b >= 0 && lane == __ffs(peers) - 1) hw[b] += __popc(peers);
+        __syncwarp();
+        if (b >= 0 && b < N) {
+            cellD[dst] = b;
+            offD[dst] = offS[i];
+            vxD[dst] = vxS[i];
+            vyD[dst] = vyS[i];
+            vzD[dst] = vzS[i];
+        }
+    }
+}
+
+__global__ void k_sort_finish(WsPtrs W)
+{
+    for (int ds = threadIdx.x; ds < W.D * NSP; ds += blockDim.x) W.cnt[ds].n = W.sort_live[ds];
+    __syncthreads();
+    if (threadIdx.x == 0) W.ctl->cur ^= 1;
+}
+
+// ------------------------------------------------------------ pair pass
+
+template <typename Real>
+struct PairBirth {
+    int c;
+    int pad;
+    Real off, vx, vy, vz;
+};
+
+template <typename Real>
+__device__ __forceinline__ Real pair_sigma(const WsPtrs &W, const TableDesc &T, Real E);
+
+template <>
+__device__ __forceinline__ float pair_sigma<float>(const WsPtrs &W, const TableDesc &T, float E)
+{
+    if (E < (float)T.th) return 0.f;
+    const float *nd = W.lutEf + T.off, *sv = W.lutSf + T.off;
+    const int n = T.n;
+    if (!(E > nd[0])) return sv[0];
+    if (E >= nd[n - 1]) return sv[n - 1];
+    int k = (int)((logf(E) - (float)T.lnE0) * (float)T.inv_dlog);
+    k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
+    while (k > 0 && E < nd[k]) --k;
+    while (k < n - 2 && E >= nd[k + 1]) ++k;
+    const float f = (E - nd[k]) / (nd[k + 1] - nd[k]);
+    return sv[k] + f * (sv[k + 1] - sv[k]);
+}
+template <>
+__device__ __forceinline__ double pair_sigma<double>(const WsPtrs &W, const TableDesc &T, double E)
+{
+    if (E < T.th) return 0.0;
+    const double *nd = W.lutE + T.off, *sv = W.lutS + T.off;
+    const int n = T.n;
+    if (!(E > nd[0])) return sv[0];
+    if (E >= nd[n - 1]) return sv[n - 1];
+    int k = (int)((log(E) - T.lnE0) * T.inv_dlog);
+    k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
+    while (k > 0 && E < nd[k]) --k;
+    while (k < n - 2 && E >= nd[k + 1]) ++k;
+    const double f = (E - nd[k]) / (nd[k + 1] - nd[k]);
+    return sv[k] + f * (sv[k + 1] - sv[k]);
+}
+
+template <typename Real>
+__device__ __forceinline__ void iso_n(Real r1, Real r2, Real n[3])
+{
+    iso_dir<Real>(r1, r2, n);
+}
+
+// One warp per cell: reactions (13), (14), (19) in that order with
+// P = n_target sigma(E) u n1 dt (Eq. 1), n_target from the live target count
+// at the start of each reaction's pass.  Projectiles are taken in slot order;
+// a batch of 32 is evaluated in parallel and the first accepting lane is
+// executed, after which the later lanes are evaluated again, so the result is
+// that of the sequential pass.
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_pair(WsPtrs W, Pools<Real> P, int par)
+{
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= W.total_cells) return;
+    const int d = W.cell_disc[gw];
+    const Disc &Dd = W.disc[d];
+    const int N = Dd.N, c = gw - Dd.ccell_base;
+    const int cur = W.ctl->cur;
+    const unsigned long long step = W.ctl->step[par];
+    const int *cs = W.cell_start + Dd.cs_base;
+    int *cellA = P.cell[cur];
+    Real *offA = P.off[cur], *vxA = P.vx[cur], *vyA = P.vy[cur], *vzA = P.vz[cur];
+    typename AccK<Real>::T *acc = AccK<Real>::ptr(W);
+    PairBirth<Real> *births = reinterpret_cast<PairBirth<Real> *>(W.pair_births) + (size_t)gw * PAIR_BIRTH_CAP;
+    unsigned long long *cnt = W.counters + (size_t)d * C_NCOUNT;
+    int kills[NSP] = {0, 0, 0};
+    int nb = 0;
+    const int rx[3] = {13, 14, 19};
+    for (int k = 0; k < 3; ++k) {
+        const PairC &pc = Dd.pair[k];
+        if (pc.table < 0) continue;
+        const int ps = pc.proj, pt = pc.targ;
+        const int p0 = cs[ps * (N + 2) + c], p1 = cs[ps * (N + 2) + c + 1];
+        const int t0 = cs[pt * (N + 2) + c], t1 = cs[pt * (N + 2) + c + 1];
+        const int range = t1 - t0;
+        if (range <= 0 || p1 <= p0) continue;
+        const int liveT = range - kills[pt];
+        if (liveT <= 0) continue;
+        const TableDesc &T = W.tables[pc.table];
+        const Real coefP = Real((double)liveT * pc.coef);
+        const int pbp = Dd.pbase[ps], pbt = Dd.pbase[pt];
+        bool stop = false;
+        unsigned nviol = 0;
+        for (int b0 = p0; b0 < p1 && !stop; b0 += 32) {
+            const int i = b0 + lane;
+            int from = 0;
+            for (;;) {
+                bool ev = false, ex = false, viol = false;
+                int j = -1;
+                uint4 d0 = make_uint4(0, 0, 0, 0);
+                if (i < p1 && lane >= from && cellA[pbp + i] >= 0) {
+                    d0 = rng_block(Dd.seed, Dd.discharge, ps, 2, rx[k], 0, step, (unsigned)i);
+                    j = t0 + (int)__umulhi(d0.x, (unsigned)range);
+                    int walked = 0;
+                    while (cellA[pbt + j] < 0 && walked < range) {
+                        j = (j + 1 < t1) ? j + 1 : t0;
+                        ++walked;
+                    }
+                    if (cellA[pbt + j] < 0) {
+                        ex = true;
+                    } else {
+                        const Real g0 = vxA[pbp + i] - vxA[pbt + j];
+                        const Real g1 = vyA[pbp + i] - vyA[pbt + j];
+                        const Real g2 = vzA[pbp + i] - vzA[pbt + j];
+                        const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
+                        const Real u = sqrt(u2);
+                        const Real E = Real(pc.Ek) * u2;
+                        Real Pc = coefP * pair_sigma<Real>(W, T, E) * u;
+                        if (Pc > Real(1)) {
+                            viol = true;
+                            Pc = Real(1);
+                        }
+                        ev = unif<Real>(d0.y) < Pc;
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ev || ex);
+                const int l = m ? __ffs(m) - 1 : 32;
+                nviol += __popc(__ballot_sync(0xffffffffu, viol && lane <= l));
+                if (!m) break;
+                const bool exl = __shfl_sync(0xffffffffu, ex, l);
+                if (exl) {
+                    stop = true;  // no live target left for this projectile
+                    break;
+                }
+                if (lane == l) {
+                    const int gi = pbp + i, gj = pbt + j;
+                    atomicAdd(&cnt[C_EVENTS + rx[k]], 1ull);
+                    typename AccK<Real>::T *acc_p = acc + (size_t)ps * W.total_nodes + Dd.gbase;
+                    typename AccK<Real>::T *acc_t = acc + (size_t)pt * W.total_nodes + Dd.gbase;
+                    if (rx[k] != 19) {
+                        cellA[gi] = -1;
+                        dep_global(acc_p, c, offA[gi], -1);
+                    } else {
+                        uint4 d1 = rng_block(Dd.seed, Dd.discharge, ps, 2, 19, 1, step, (unsigned)i);
+                        Real v[3] = {vxA[gi], vyA[gi], vzA[gi]};
+                        Real V[3] = {vxA[gj], vyA[gj], vzA[gj]};
+                        Real nd[3], n2[3], v1[3], Vo[3];
+                        iso_n<Real>(unif<Real>(d0.z), unif<Real>(d0.w), nd);
+                        const Real mf = Real(pc.mfrac), Mf = Real(pc.Mfrac);
+                        Real g0 = v[0] - V[0], g1 = v[1] - V[1], g2 = v[2] - V[2];
+                        Real uu = g0 * g0 + g1 * g1 + g2 * g2 - Real(pc.dloss);
+                        Real up = uu > Real(0) ? sqrt(uu) : Real(0);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            Real vcm = mf * v[q] + Mf * V[q];
+                            v1[q] = vcm + Mf * up * nd[q];
+                            Vo[q] = vcm - mf * up * nd[q];
+                        }
+                        iso_n<Real>(unif<Real>(d1.x), unif<Real>(d1.y), n2);
+                        Real e2[3] = {Vo[0], Vo[1], Vo[2]};
+                        Real a0 = v1[0] - e2[0], a1 = v1[1] - e2[1], a2 = v1[2] - e2[2];
+                        Real ue = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            Real cc = Real(0.5) * (v1[q] + e2[q]);
+                            v1[q] = cc + Real(0.5) * ue * n2[q];
+                            e2[q] = cc - Real(0.5) * ue * n2[q];
+                        }
+                        vxA[gi] = v1[0];
+                        vyA[gi] = v1[1];
+                        vzA[gi] = v1[2];
+                        if (nb < PAIR_BIRTH_CAP) {
+                            PairBirth<Real> &pbr = births[nb];
+                            pbr.c = c;
+                            pbr.off = offA[gi];
+                            pbr.vx = e2[0];
+                            pbr.vy = e2[1];
+                            pbr.vz = e2[2];
+                        } else {
+                            set_status(W.ctl, ST_BIRTHBUF);
+                        }
+                    }
+                    cellA[gj] = -1;
+                    dep_global(acc_t, c, offA[gj], -1);
+                }
+                __syncwarp();
+                __threadfence_block();
+                if (rx[k] == 19) {
+                    ++nb;
+                    ++kills[pt];
+                } else {
+                    ++kills[ps];
+                    ++kills[pt];
+                }
+                from = l + 1;
+                if (from >= 32) break;
+            }
+        }
+        if (lane == 0 && nviol) atomicAdd(&cnt[C_VIOL_PAIR], (unsigned long long)nviol);
+    }
+    if (lane == 0) W.pair_bcount[gw] = nb < PAIR_BIRTH_CAP ? nb : PAIR_BIRTH_CAP;
+}
+
+// Births of (19) appended to the electron array of each discharge in cell
+// order (the order of the sequential pass).
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_pair_append(WsPtrs W, Pools<Real> P)
+{
+    extern __shared__ __align__(16) int pre[];
+    __shared__ int wsum[32];
+    const int d = blockIdx.x;
+    const Disc &Dd = W.disc[d];
+    const int N = Dd.N;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) pre[c] = W.pair_bcount[Dd.ccell_base + c];
+    __syncthreads();
+    const int tot = block_scan_exclusive_int(pre, N, wsum);
+    if (tot == 0) return;
+    const int cur = W.ctl->cur;
+    Counts &C = W.cnt[d * NSP + 0];
+    const int n0 = C.n;
+    typename AccK<Real>::T *acc = AccK<Real>::ptr(W) + Dd.gbase;  // species 0 block
+    const PairBirth<Real> *births = reinterpret_cast<const PairBirth<Real> *>(W.pair_births);
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        const int nbc = W.pair_bcount[Dd.ccell_base + c];
+        for (int r = 0; r < nbc; ++r) {
+            const PairBirth<Real> &b = births[(size_t)(Dd.ccell_base + c) * PAIR_BIRTH_CAP + r];
+            const int dst = n0 + pre[c] + r;
+            if (dst >= Dd.cap[0]) {
+                set_status(W.ctl, ST_CAPACITY);
+                continue;
+            }
+            const int gidx = Dd.pbase[0] + dst;
+            P.cell[cur][gidx] = b.c;
+            P.off[cur][gidx] = b.off;
+            P.vx[cur][gidx] = b.vx;
+            P.vy[cur][gidx] = b.vy;
+            P.vz[cur][gidx] = b.vz;
+            dep_global(acc, b.c, b.off, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) C.n = min(n0 + tot, Dd.cap[0]);
+}
+
+// ------------------------------------------------------------ load / deposit
+
+// Uniform positions in (0, L) and Maxwellian velocities from Philox stream 3
+// (step 0, index = slot): draw 0 gives two Box-Muller pairs, draw 1 the
+// position.  Computed in FP64 and rounded once to the storage precision.
+template <typename Real>
+__global__ void k_load(WsPtrs W, Pools<Real> P, const long long *n_init, const double *vt)
+{
+    const int ds = blockIdx.y;
+    const int d = ds / NSP, s = ds % NSP;
+    const Disc &Dd = W.disc[d];
+    const int n = (int)n_init[ds];
+    const int cur = W.ctl->cur;
+    const double to_n = Dd.dt / Dd.dx;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint4 a = rng_block(Dd.seed, Dd.discharge, s, 3, 0, 0, 0ull, (unsigned)i);
+        const uint4 b = rng_block(Dd.seed, Dd.discharge, s, 3, 0, 1, 0ull, (unsigned)i);
+        double n0, n1, n2, n3;
+        box_muller<double>(a.x, a.y, n0, n1);
+        box_muller<double>(a.z, a.w, n2, n3);
+        const double x = unif<double>(b.x) * Dd.L;
+        const double xx = x / Dd.dx;
+        int c = (int)floor(xx);
+        if (c > Dd.N - 1) c = Dd.N - 1;
+        if (c < 0) c = 0;
+        Real off = (Real)(xx - c);
+        if (off >= Real(1)) {
+            if (c + 1 < Dd.N) {
+                ++c;
+                off = Real(0);
+            } else {
+                off = Real(0.99999994);
+            }
+        }
+        const int g = Dd.pbase[s] + i;
+        P.cell[cur][g] = c;
+        P.off[cur][g] = off;
+        P.vx[cur][g] = (Real)(vt[ds] * n0 * to_n);
+        P.vy[cur][g] = (Real)(vt[ds] * n1 * to_n);
+        P.vz[cur][g] = (Real)(vt[ds] * n2 * to_n);
+    }
+}
+
+// Deposit of every live slot (set-up and after a state change); the caller
+// has cleared the accumulators of the affected discharges.
+template <typename Real>
+__global__ void k_deposit_all(WsPtrs W, Pools<Real> P, int only_disc)
+{
+    const int ds = blockIdx.y;
+    const int d = ds / NSP, s = ds % NSP;
+    if (only_disc >= 0 && d != only_disc) return;
+    const Disc &Dd = W.disc[d];
+    const int n = W.cnt[ds].n;
+    const int cur = W.ctl->cur;
+    typename AccK<Real>::T *acc = AccK<Real>::ptr(W) + (size_t)s * W.total_nodes + Dd.gbase;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int g = Dd.pbase[s] + i;
+        const int c = P.cell[cur][g];
+        if (c >= 0 && c < Dd.N) dep_global(acc, c, P.off[cur][g], 1);
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+cudaError_t configure_kernels(bool fp64, LaunchCfg &L)
+{
+    cudaError_t e;
+    L.field_smem = sizeof(double) * (L.maxN + 2);
+    L.sort_smem = sizeof(unsigned) * SORT_WARPS * (L.maxN + 1);
+    if (fp64) {
+        e = cudaFuncSetAttribute(k_field<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.field_smem);
+        if (e) return e;
+        e = cudaFuncSetAttribute(k_sort_count<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sort_smem);
+        if (e) return e;
+        e = cudaFuncSetAttribute(k_sort_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sort_smem);
+        if (e) return e;
+    } else {
+        e = cudaFuncSetAttribute(k_field<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.field_smem);
+        if (e) return e;
+        e = cudaFuncSetAttribute(k_sort_count<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sort_smem);
+        if (e) return e;
+        e = cudaFuncSetAttribute(k_sort_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sort_smem);
+        if (e) return e;
+    }
+    return cudaFuncSetAttribute(k_sort_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(int) * (L.maxN + 2)));
+}
+
+cudaError_t launch_field(bool fp64, bool diag, int mode, const WsPtrs &W, int par, const LaunchCfg &L,
+                         cudaStream_t st)
+{
+    if (fp64)
+        k_field<double><<<W.D, FIELD_THREADS, L.field_smem, st>>>(W, par, diag ? 1 : 0, mode);
+    else
+        k_field<float><<<W.D, FIELD_THREADS, L.field_smem, st>>>(W, par, diag ? 1 : 0, mode);
+    return cudaGetLastError();
+}
+
+int kernels_per_sort() { return 4; }
+int kernels_per_pair() { return 2; }
+
+cudaError_t launch_sort(bool fp64, const WsPtrs &W, const void *pools, const int *tab, const LaunchCfg &L,
+                        cudaStream_t st)
+{
+    const size_t scan_smem = sizeof(int) * (L.maxN + 2);
+    if (fp64) {
+        const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
+        k_sort_count<double><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
+        k_sort_scan<<<W.D * NSP, 512, scan_smem, st>>>(W);
+        k_sort_scatter<double><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
+    } else {
+        const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
+        k_sort_count<float><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
+        k_sort_scan<<<W.D * NSP, 512, scan_smem, st>>>(W);
+        k_sort_scatter<float><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
+    }
+    k_sort_finish<<<1, 256, 0, st>>>(W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par, const LaunchCfg &L,
+                        cudaStream_t st)
+{
+    const int blocks = (W.total_cells * 32 + 255) / 256;
+    if (fp64) {
+        const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
+        k_pair<double><<<blocks, 256, 0, st>>>(W, P, par);
+        k_pair_append<double><<<W.D, 256, sizeof(int) * (L.maxN + 1), st>>>(W, P);
+    } else {
+        const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
+        k_pair<float><<<blocks, 256, 0, st>>>(W, P, par);
+        k_pair_append<float><<<W.D, 256, sizeof(int) * (L.maxN + 1), st>>>(W, P);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load(bool fp64, const WsPtrs &W, const void *pools, const long long *d_ninit,
+                        const double *d_vt, int max_n, cudaStream_t st)
+{
+    dim3 grid((max_n + 255) / 256 > 0 ? ((max_n + 255) / 256 < 4096 ? (max_n + 255) / 256 : 4096) : 1,
+              W.D * NSP);
+    if (fp64)
+        k_load<double><<<grid, 256, 0, st>>>(W, *static_cast<const Pools<double> *>(pools), d_ninit, d_vt);
+    else
+        k_load<float><<<grid, 256, 0, st>>>(W, *static_cast<const Pools<float> *>(pools), d_ninit, d_vt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_all(bool fp64, const WsPtrs &W, const void *pools, int disc, int max_n,
+                               cudaStream_t st)
+{
+    dim3 grid((max_n + 255) / 256 > 0 ? ((max_n + 255) / 256 < 4096 ? (max_n + 255) / 256 : 4096) : 1,
+              W.D * NSP);
+    if (fp64)
+        k_deposit_all<double><<<grid, 256, 0, st>>>(W, *static_cast<const Pools<double> *>(pools), disc);
+    else
+        k_deposit_all<float><<<grid, 256, 0, st>>>(W, *static_cast<const Pools<float> *>(pools), disc);
+    return cudaGetLastError();
+}
+
+} // namespace o2

@@ -1,0 +1,44 @@
+// o2pic_launch.h -- host-side launch wrappers of the libo2pic kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "o2pic_dev.cuh"
+
+namespace o2 {
+
+struct LaunchCfg {
+    int push_blocks;      // persistent grid of the push
+    size_t push_smem;     // dynamic shared memory of the push (non-diag)
+    size_t push_smem_diag;
+    int sort_blocks;      // sum over (d, s) of sort blocks
+    size_t sort_smem;
+    int pair_blocks;
+    size_t field_smem;
+    int maxN;             // largest cell count over discharges
+    int eedf_max, fm_max; // largest histogram sizes (shared-memory copies in the push)
+};
+
+// push + absorb + null-collision MCC + births + deposit (one time step)
+cudaError_t launch_push(bool fp64, bool diag, const WsPtrs &W, const void *pools,
+                        int par, const LaunchCfg &L, cudaStream_t s);
+cudaError_t push_configure(bool fp64, LaunchCfg &L, int num_sms);
+
+// charge density -> Poisson -> field; per-step bookkeeping (mode 0), or a
+// read-only evaluation of the fields of the current state (mode 1)
+cudaError_t launch_field(bool fp64, bool diag, int mode, const WsPtrs &W, int par,
+                         const LaunchCfg &L, cudaStream_t s);
+
+cudaError_t launch_sort(bool fp64, const WsPtrs &W, const void *pools,
+                        const int *sort_block_ds, const LaunchCfg &L, cudaStream_t s);
+cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par,
+                        const LaunchCfg &L, cudaStream_t s);
+cudaError_t launch_load(bool fp64, const WsPtrs &W, const void *pools, const long long *d_ninit,
+                        const double *d_vt, int max_n, cudaStream_t s);
+cudaError_t launch_deposit_all(bool fp64, const WsPtrs &W, const void *pools, int disc,
+                               int max_n, cudaStream_t s);
+cudaError_t configure_kernels(bool fp64, LaunchCfg &L);
+
+int kernels_per_sort();
+int kernels_per_pair();
+
+} // namespace o2

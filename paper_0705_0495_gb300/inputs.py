@@ -164,10 +164,12 @@ class Discharge:
     iedf_bins: int = 200
     iedf_emax: float = 0.0          # 0 -> 2 U_rf
     fm_bins: int = 64
+    fm_xbins: int = 64
     fm_emax: float = 4.0
     numax_safety: float = 1.05
     cx_isotropic: bool = False
     capacity_factor: float = 1.5
+    capacity_extra: int = 4096
     fp64: bool = True
     weight_override: float = None
     ecap_override: float = 0.0
@@ -203,7 +205,7 @@ class Discharge:
 
     @property
     def capacity(self):
-        return tuple(int(self.capacity_factor * n) + 4096 for n in self.n_init)
+        return tuple(int(self.capacity_factor * n) + self.capacity_extra for n in self.n_init)
 
     @property
     def total_steps(self):

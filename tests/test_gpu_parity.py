@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+FP64 path: step by step, slot by slot (same order, same random streams),
+within 1e-9 of the gap / of the thermal speed.  FP32 path: each step started
+from the oracle's state ("replay"), matched by position, within 1e-5 with
+decision flips counted (at most 1e-4 of particle-steps).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0705_0495_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+QE = 1.602176634e-19
+AMU = 1.66053906660e-27
+ME = 9.1093837015e-31
+MASS = (ME, 16 * AMU + ME, 32 * AMU - ME)
+TOL64 = 1e-9
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _sim(ds, tabs=None, fp64=None):
+    from paper_0705_0495_gb300 import o2pic
+    return o2pic.Simulation(ds if isinstance(ds, list) else [ds],
+                            inputs.xs_tables() if tabs is None else tabs, fp64=fp64)
+
+
+def _vth(d, s):
+    return math.sqrt(max(d.T0_eV[s], 0.0259) * QE / MASS[s])
+
+
+def _cmp_slots(d, g, o, s):
+    """slot-by-slot: same count, same alive flags, max relative errors"""
+    assert len(g["x"]) == len(o["x"]), (s, len(g["x"]), len(o["x"]))
+    assert np.array_equal(g["alive"], o["alive"]), s
+    m = o["alive"]
+    if not m.any():
+        return 0.0, 0.0
+    ex = np.max(np.abs(g["x"][m] - o["x"][m])) / d.L
+    vt = _vth(d, s)
+    ev = max(np.max(np.abs(g[c][m] - o[c][m])) for c in ("vx", "vy", "vz")) / vt
+    return ex, ev
+
+
+def _matched(d, g, o, s, tol):
+    """particles matched by position; returns (n_compared, n_flips, max err of the rest)"""
+    gm, om = g["alive"], o["alive"]
+    gi = np.argsort(g["x"][gm], kind="stable")
+    oi = np.argsort(o["x"][om], kind="stable")
+    gx = {c: g[c][gm][gi] for c in ("x", "vx", "vy", "vz")}
+    ox = {c: o[c][om][oi] for c in ("x", "vx", "vy", "vz")}
+    n = min(len(gx["x"]), len(ox["x"]))
+    extra = abs(len(gx["x"]) - len(ox["x"]))
+    vt = _vth(d, s)
+    err = np.abs(gx["x"][:n] - ox["x"][:n]) / d.L
+    for c in ("vx", "vy", "vz"):
+        err = np.maximum(err, np.abs(gx[c][:n] - ox[c][:n]) / vt)
+    bad = err > tol
+    rest = float(np.max(err[~bad], initial=0.0))
+    return n, int(bad.sum()) + extra, rest
+
+
+# ------------------------------------------------------------------ load
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_initial_load_matches_oracle(fp64):
+    d = inputs.cfg1(fp64=fp64)
+    sim = _sim(d)
+    orc = oracle.Oracle(d, inputs.xs_tables())
+    for s in range(3):
+        ex, ev = _cmp_slots(d, sim.get_state(0, s), orc.get(s), s)
+        lim = 1e-13 if fp64 else 1e-6
+        assert ex < lim and ev < lim, (s, ex, ev)
+    for s in range(3):
+        assert sim.numax(0, s) == pytest.approx(orc.numax(s), rel=1e-13)
+
+
+def test_initial_fields_match_oracle():
+    d = inputs.cfg1()
+    sim = _sim(d)
+    orc = oracle.Oracle(d, inputs.xs_tables())
+    rg, pg, Eg = sim.fields(0)
+    ro, po, Eo = orc.fields()
+    assert np.max(np.abs(rg - ro)) <= 1e-12 * np.max(np.abs(ro))
+    assert np.max(np.abs(pg - po)) <= 1e-11 * np.max(np.abs(po))
+    assert np.max(np.abs(Eg - Eo)) <= 1e-10 * np.max(np.abs(Eo))
+
+
+# --------------------------------------------------------- FP64 parity
+
+def _run_pair(d, steps_list, tabs=None):
+    tabs = inputs.xs_tables() if tabs is None else tabs
+    sim = _sim(d, tabs)
+    orc = oracle.Oracle(d, tabs)
+    done = 0
+    worst = (0.0, 0.0)
+    for k in steps_list:
+        sim.step(k - done)
+        orc.step(k - done)
+        done = k
+        for s in range(3):
+            ex, ev = _cmp_slots(d, sim.get_state(0, s), orc.get(s), s)
+            worst = (max(worst[0], ex), max(worst[1], ev))
+    return sim, orc, worst
+
+
+def test_fp64_step_by_step_cfg1_100_steps():
+    d = inputs.cfg1()
+    sim, orc, (ex, ev) = _run_pair(d, [1, 2, 10, 11, 20, 50, 100])
+    assert ex < TOL64 and ev < TOL64, (ex, ev)
+    gd = sim.diagnostics(0)
+    oc = orc.counters()
+    assert np.array_equal(gd["events"], oc["events"])
+    assert np.array_equal(gd["absorbed"], oc["absorbed"])
+    assert gd["events"][4] > 0 and gd["events"][18] > 0
+
+
+def test_fp64_diagnostics_match_oracle():
+    d = inputs.cfg1(n_op=8000)
+    sim, orc, _ = _run_pair(d, [200])
+    g = sim.diagnostics(0)
+    o = orc.diag()
+    assert g["n_samples"] == o["n_samples"] == 20
+    assert np.max(np.abs(g["dens_sum"] - o["dens_sum"])) <= 1e-9 * np.max(o["dens_sum"])
+    assert np.max(np.abs(g["phi_sum"] - o["phi_sum"])) <= 1e-9 * np.max(np.abs(o["phi_sum"]))
+    for k in ("eedf", "iedf", "fm"):
+        assert np.abs(g[k] - o[k]).sum() <= 2, k
+    assert o["eedf"].sum() > 0 and o["fm"].sum() > 0
+
+
+def test_fp64_ragged_small_and_degenerate_sizes():
+    # 7 cells, counts that fill no chunk or vector evenly, one empty species
+    d = inputs.cfg1(n_cells=7, n_op=2 * 1237 + 2, sort_interval=3, n1=6, diag_every=4,
+                    fm_xbins=5)
+    _, _, (ex, ev) = _run_pair(d, [1, 3, 6, 7, 30])
+    assert ex < TOL64 and ev < TOL64
+    d2 = inputs.cfg1(n_op=2, n_cells=16)
+    _, _, (ex, ev) = _run_pair(d2, [1, 10, 40])
+    assert ex < TOL64 and ev < TOL64
+
+
+def test_fp64_empty_discharge():
+    d = inputs.cfg1(n_op=0)
+    sim, orc, _ = _run_pair(d, [5])
+    assert all(sim.count(0, s) == 0 for s in range(3))
+
+
+def test_fp64_batched_discharges_each_match_their_oracle():
+    ds = [inputs.cfg1(n_op=6000, U_rf=150.0),
+          inputs.cfg1(n_op=3002, n_cells=64, L=0.02, p_Pa=40.0),
+          inputs.cfg1(n_op=9000, n_cells=200, U_rf=60.0, seed=7)]
+    sim = _sim(ds)
+    tabs = inputs.xs_tables()
+    orcs = [oracle.Oracle(d, tabs, discharge=k) for k, d in enumerate(ds)]
+    for steps in (1, 10, 25):
+        done = sim.diagnostics(0)["steps"]
+        sim.step(steps - done)
+        for k, d in enumerate(ds):
+            orcs[k].step(steps - done)
+            for s in range(3):
+                ex, ev = _cmp_slots(d, sim.get_state(k, s), orcs[k].get(s), s)
+                assert ex < TOL64 and ev < TOL64, (k, s, ex, ev)
+
+
+# ----------------------------------------------------- FP32 replay parity
+
+def _replay(d, steps, start=0, orc=None):
+    tabs = inputs.xs_tables()
+    sim = _sim(d, tabs)
+    if orc is None:
+        orc = oracle.Oracle(d, tabs)
+        if start:
+            orc.step(start)
+    compared = flips = 0
+    worst = 0.0
+    for n in range(start, start + steps):
+        for s in range(3):
+            st = orc.get(s)
+            sim.set_state(0, s, st["x"], st["vx"], st["vy"], st["vz"], st["alive"])
+        sim.set_step(n)
+        sim.step(1)
+        orc.step(1)
+        for s in range(3):
+            c, f, w = _matched(d, sim.get_state(0, s), orc.get(s), s, TOL32)
+            compared += c
+            flips += f
+            worst = max(worst, w)
+    return compared, flips, worst
+
+
+def test_fp32_replay_cfg1_100_steps():
+    d = inputs.cfg1(fp64=False)
+    compared, flips, worst = _replay(d, 100)
+    assert compared > 3_000_000
+    assert worst < TOL32, worst
+    assert flips <= 1e-4 * compared, (flips, compared)
+
+
+def test_fp32_replay_ragged_multi_tile_cfg2_geometry():
+    # cfg2's gap, grid, pressure and voltage with 3e5 superparticles: many
+    # chunks and sort blocks, a ragged tail, steps across a sort and a pair pass
+    d = inputs.cfg2(n_op=150_001 * 2 - 1)
+    compared, flips, worst = _replay(d, 4, start=7)
+    assert worst < TOL32
+    assert flips <= 1e-4 * compared, (flips, compared)
+
+
+# ------------------------------------------------- full-size, one step
+
+@pytest.mark.parametrize("name", ["cfg2", "cfg4"])
+def test_full_size_one_step_replay(name):
+    # BASELINE sizes in the bench's launch configuration: the GPU's loaded
+    # state is handed to the oracle and both take one step
+    d = inputs.WORKLOADS[name]()
+    tabs = inputs.xs_tables()
+    sim = _sim(d, tabs)
+    orc = oracle.Oracle(d, tabs, load=False)
+    for s in range(3):
+        st = sim.get_state(0, s)
+        orc.set(s, st["x"], st["vx"], st["vy"], st["vz"], st["alive"])
+        del st
+    sim.step(1)
+    orc.step(1)
+    compared = flips = 0
+    worst = 0.0
+    for s in range(3):
+        c, f, w = _matched(d, sim.get_state(0, s), orc.get(s), s, TOL32)
+        compared, flips, worst = compared + c, flips + f, max(worst, w)
+    assert compared > 0.99 * sum(d.n_init)
+    assert worst < TOL32
+    assert flips <= 1e-4 * compared, (flips, compared)
+    g, o = sim.diagnostics(0), orc.counters()
+    # reaction counts: equal up to flipped decisions
+    assert np.abs(g["events"] - o["events"]).sum() <= max(10, 1e-4 * compared)
+
+
+def test_capacity_overflow_is_reported():
+    from paper_0705_0495_gb300 import o2pic
+    # capacity = initial load: the first ionisation birth cannot be placed
+    d = inputs.cfg1(n_op=2000, capacity_factor=1.0, capacity_extra=0)
+    sim = o2pic.Simulation([d], inputs.xs_tables())
+    with pytest.raises(o2pic.PicError, match="CAPACITY"):
+        for _ in range(50):
+            sim.step(10)
+    # the handle stays usable and the slot count never exceeds the capacity
+    assert sim.count(0, 0) <= d.capacity[0] and sim.count(0, 2) <= d.capacity[2]
