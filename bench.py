@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Throughput of the PIC-MCC time step (push + deposit + MCC, with field
+solve, births, sort and particle-target pass) on GB300, in particle-steps/s.
+
+One bench step is one RF cycle of the workload (all time steps of the cycle).
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
+Multi-GPU (torchrun): every rank advances its own discharge (seed 1 + rank);
+no data-path collective, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_0705_0495_gb300 import inputs  # noqa: E402
+
+METRIC = "particle-steps/s (push+deposit+MCC) and % HBM roofline, FP32/batched vs FP64"
+UNIT = "particle-steps/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5, help="timed RF cycles")
+    p.add_argument("--warmup", type=int, default=3, help="untimed RF cycles")
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="cfg4", choices=sorted(inputs.WORKLOADS))
+    p.add_argument("--fp64", action="store_true", help="run the FP64 path on the workload")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="fraction of the workload's superparticles (same plasma density)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _workload(name, rank=0, fp64=False, scale=1.0):
+    d = inputs.WORKLOADS[name](seed=1 + rank)
+    if fp64:
+        d.fp64 = True
+    if scale != 1.0:
+        # fewer superparticles of larger weight: the plasma density is unchanged
+        d.n_op = max(2, int(d.n_op * scale) & ~1)
+    return d
+
+
+def _describe(d):
+    return (f"{d.L * 100:g} cm gap, {d.n_cells} cells, O2 {d.p_Pa:g} Pa / {d.T_gas:g} K, "
+            f"{d.U_rf:g} V at {d.f_rf / 1e6:g} MHz, dt = T_rf/{d.steps_per_cycle}, "
+            f"{sum(d.n_init):.3g} superparticles (e {d.n_init[0]}, O- {d.n_init[1]}, "
+            f"O2+ {d.n_init[2]}) at {d.n0_m3:g} m^-3, {'FP64' if d.fp64 else 'FP32 mixed'}")
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic(push_slots_per_launch):
+    """DRAM bytes per push launch from a committed ncu capture, scaled by the
+    slots a launch processes; null when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "k_push_traffic.json")
+    src = os.path.join(ROOT, "paper_0705_0495_gb300", "csrc", "o2pic_push.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("source_sha256") != sha:
+            return None
+        return rec["dram_bytes_per_slot"] * push_slots_per_launch
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.out), exist_ok=True)
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.index is not None and parts[0] != str(self.index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        items = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(items) and items[local_rank].isdigit():
+            return int(items[local_rank])
+        return None
+    return local_rank
+
+
+class OracleSample:
+    """The FP64 oracle on a bounded sample of the workload: the same gap,
+    grid, drive, gas and tables with the superparticles scaled down to about
+    `target` (same plasma density), loaded once; each call advances `steps`
+    time steps and returns (particle-steps, seconds)."""
+
+    def __init__(self, name, target=5_000_000, steps=10):
+        import oracle
+        oracle.build()
+        d = _workload(name)
+        total = sum(d.n_init)
+        if total > target:
+            d = _workload(name, scale=target / total)
+        self.d = d
+        self.steps = steps
+        self.o = oracle.Oracle(d, inputs.xs_tables())
+        self.text = (f"{name} discharge with {sum(d.n_init):.3g} superparticles (same plasma "
+                     f"density), {steps} time steps per sample, 1 thread")
+
+    def run(self):
+        p0 = self.o.particle_steps
+        t0 = time.perf_counter()
+        self.o.step(self.steps)
+        dt = time.perf_counter() - t0
+        return self.o.particle_steps - p0, dt
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    d = _workload(a.workload, scale=a.scale)
+    smp = OracleSample(a.workload, target=min(5_000_000, sum(d.n_init)))
+    total_ps, total_t = 0, 0.0
+    for k in range(a.warmup + a.steps):
+        ps, dt = smp.run()
+        if k >= a.warmup:
+            total_ps += ps
+            total_t += dt
+    value = total_ps / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total_t / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{a.workload}: {_describe(d)}",
+                   "step": "bounded sample: " + smp.text},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": smp.text},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_0705_0495_gb300 import build as pbuild
+    from paper_0705_0495_gb300 import o2pic
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        pbuild.build()
+    if dist:
+        tdist.barrier()
+    d = _workload(a.workload, rank, a.fp64, a.scale)
+    tabs = inputs.xs_tables()
+    sim = o2pic.Simulation([d], tabs)
+    spc = d.steps_per_cycle
+    state_bytes = sum(d.n_init) * (12 + (16 if not d.fp64 else 32))
+    flush = state_bytes < 4 * L2_BYTES
+    scratch = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if flush else None
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    sim.step(a.warmup * spc)
+    sim.set_timing(True)
+    sim.timing(reset=True)
+    g0 = sim.diagnostics(0)
+    clocks = Clocks(_gpu_index(local_rank))
+    clocks.start()
+    stream = sim.stream
+    total_ms = 0.0
+    for k in range(a.steps):
+        if flush:
+            scratch.fill_(float(k))
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(spc)
+        e1.record(stream)
+        barrier()
+        total_ms += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    g1 = sim.diagnostics(0)
+    tm = sim.timing()
+    psteps = g1["particle_steps"] - g0["particle_steps"]
+    ms = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    ps_t = torch.tensor([float(psteps)], dtype=torch.float64, device="cuda")
+    if dist:
+        tdist.all_reduce(ms, op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(ps_t, op=tdist.ReduceOp.SUM)
+    total_ms_max = float(ms.item())
+    value = float(ps_t.item()) / (total_ms_max / 1e3)
+
+    # roofline of the dominant kernel (the fused push), CUDA events on its stream
+    peak, peak_kind = _peaks()
+    launches = max(1, tm["push_launches"])
+    dur_s = tm["push_ms"] / 1e3 / launches
+    bytes_per_launch = tm["push_bytes"] / launches
+    achieved = bytes_per_launch / dur_s / 1e9 if dur_s > 0 else 0.0
+    slots_per_launch = (g1["slots_visited"] - g0["slots_visited"]) / launches
+    traffic = _traffic(slots_per_launch)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": f"{peak_kind} HBM copy bandwidth",
+            "push_share_of_step_time": tm["push_ms"] / total_ms if total_ms > 0 else None,
+            "bytes_per_particle_step": bytes_per_launch / max(1.0, psteps / launches)}
+
+    e2e = None
+    if not a.no_e2e:
+        sim.set_timing(False)
+        host = []
+        h2d = 0
+        for s in range(3):
+            st = sim.get_state(0, s)
+            pinned = {}
+            for key in ("x", "vx", "vy", "vz"):
+                t = torch.from_numpy(np.ascontiguousarray(st[key])).pin_memory()
+                pinned[key] = t.numpy()
+                h2d += t.numel() * 8
+            al = torch.from_numpy(st["alive"].astype(np.int32)).pin_memory()
+            pinned["alive"] = al.numpy()
+            h2d += al.numel() * 4
+            host.append(pinned)
+        N = d.n_cells
+        d2h = 8 * (3 * (N + 1) + (N + 1) + d.eedf_bins + 2 * d.iedf_bins
+                   + d.fm_xbins * d.fm_bins + 40 + 1)
+        ps_e2e = 0
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(a.steps):
+            for s in range(3):
+                h = host[s]
+                sim.set_state(0, s, h["x"], h["vx"], h["vy"], h["vz"], h["alive"])
+            gd0 = sim.diagnostics(0)
+            sim.step(spc)
+            gd1 = sim.diagnostics(0)
+            ps_e2e += gd1["particle_steps"] - gd0["particle_steps"]
+        barrier()
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+        pe = torch.tensor([float(ps_e2e)], dtype=torch.float64, device="cuda")
+        if dist:
+            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+            tdist.all_reduce(pe, op=tdist.ReduceOp.SUM)
+        e2e = {"value": float(pe.item()) / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "path": "pic_set_state from pinned host arrays + pic_step(one RF cycle) + "
+                       "pic_diagnostics read back, per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        try:
+            smp = OracleSample(a.workload, target=min(5_000_000, sum(d.n_init)), steps=30)
+            ps, dt = smp.run()
+            cpu = {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": smp.text.replace("per sample", "")}
+        except Exception as ex:  # the baseline is reported, not required
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if d.fp64 else "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": f"{a.workload}: {_describe(d)}",
+                "step": f"one RF cycle = {spc} time steps (sort and pair pass every "
+                        f"{d.sort_interval}/{d.n1} steps, diagnostics every {d.diag_every})",
+                "precision": ("FP64 throughout" if d.fp64 else
+                              "FP32 particles, push and collisions; exact fixed-point charge "
+                              "accumulation; FP64 Poisson, field and diagnostics"),
+                "l2": ("inputs larger than L2: the particle state touched per time step "
+                       f"({state_bytes / 1e6:.0f} MB) exceeds the 129 MB L2"
+                       if not flush else "L2 flushed between timed iterations"),
+                "parallelism": f"{world} GPU(s), one independent discharge per GPU",
+            },
+            "roofline": roof,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": tm["launches"],
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    a = _args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    try:
+        run_ours(a, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -173,10 +173,13 @@ pic_status pic_step(pic_handle *h, long long n_steps);
  *   eedf       [eedf_bins] electrons in the cell [L/2, L/2 + dx), E = m v^2/2
  *   iedf       [2][iedf_bins] O2+ absorbed at x = 0 and x = L, E = M v^2/2
  *   fm         [fm_xbins][fm_bins] O-, E = sign(vx) M vx^2 / 2
- *   counters   [32]: 0-5 absorbed (species*2 + wall), 6-25 events per
+ *   counters   [40]: 0-5 absorbed (species*2 + wall), 6-25 events per
  *              reaction 0..19 (index 6 + reaction), 26 gas nu_max
- *              violations, 27 pair P > 1 clamps, 28-30 live slots per species
- *              (including dead slots not yet compacted), 31 steps taken
+ *              violations, 27 pair P > 1 clamps, 28-30 slots per species
+ *              (including dead slots not yet compacted), 31 steps taken,
+ *              32 particle-steps (live particles pushed, summed over steps),
+ *              33 null-collision candidates, 34 slots visited by the push,
+ *              35-39 reserved (0)
  *   n_samples  number of diagnostic samples accumulated
  * reset != 0 clears the sums and histograms after copying.
  */

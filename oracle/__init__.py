@@ -77,6 +77,8 @@ def lib():
         l.orc_step_index.restype = C.c_longlong
         l.orc_step_index.argtypes = [C.c_void_p]
         l.orc_set_step.argtypes = [C.c_void_p, C.c_longlong]
+        l.orc_particle_steps.restype = C.c_longlong
+        l.orc_particle_steps.argtypes = [C.c_void_p]
         l.orc_count.restype = C.c_longlong
         l.orc_count.argtypes = [C.c_void_p, C.c_int]
         l.orc_get.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, dp, ip]
@@ -177,6 +179,10 @@ class Oracle:
     @property
     def step_index(self):
         return lib().orc_step_index(self.h)
+
+    @property
+    def particle_steps(self):
+        return lib().orc_particle_steps(self.h)
 
     def set_step(self, k):
         lib().orc_set_step(self.h, int(k))

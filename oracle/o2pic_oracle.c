@@ -98,6 +98,7 @@ struct orc_sim {
     double *rho, *phi, *E, *dens[3];
     long long absorbed[3][2], events[20], viol[2], births[3];
     long long nsamp;
+    long long psteps;   /* live particles pushed, summed over steps */
     double *dens_sum[3], *phi_sum;
     long long *eedf, *iedf, *fm;
 };
@@ -851,6 +852,7 @@ static void step_once(orc_sim *s)
         uint32_t w0[4] = {0};
         for (long long i = 0; i < p->n; ++i) {
             if (!p->alive[i]) continue;
+            s->psteps++;
             /* force interpolation (linear) and leapfrog push */
             int c;
             double f;
@@ -864,16 +866,17 @@ static void step_once(orc_sim *s)
                 p->alive[i] = 0;
                 continue;
             }
+            /* distributions sampled after the free flight, before collisions */
+            if (diag) {
+                double v[3] = {p->vx[i], p->vy[i], p->vz[i]};
+                sample_histograms(s, sp, p->x[i], v);
+            }
             /* null-collision test: one Philox block serves four slots */
             if ((i >> 2) != last_blk) {
                 last_blk = i >> 2;
                 rng(s, sp, 0, 0, 0, s->step, (uint32_t)(i >> 2), w0);
             }
             if (unif(w0[i & 3]) < s->pnull[sp]) gas_collision(s, sp, i, bl);
-            if (diag && p->alive[i]) {
-                double v[3] = {p->vx[i], p->vy[i], p->vz[i]};
-                sample_histograms(s, sp, p->x[i], v);
-            }
         }
     }
     append_births(s, bl);
@@ -910,6 +913,7 @@ void orc_step(orc_sim *s, long long nsteps)
 /* ---------------------------------------------------------- accessors */
 
 long long orc_step_index(const orc_sim *s) { return s->step; }
+long long orc_particle_steps(const orc_sim *s) { return s->psteps; }
 void orc_set_step(orc_sim *s, long long step) { s->step = step; }
 long long orc_count(const orc_sim *s, int sp) { return s->p[sp].n; }
 double orc_numax(const orc_sim *s, int sp) { return s->numax[sp]; }

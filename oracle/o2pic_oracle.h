@@ -60,6 +60,7 @@ orc_sim *orc_create(const orc_cfg *cfg, const orc_xs *xs, int n_xs, int load);
 void orc_destroy(orc_sim *s);
 void orc_step(orc_sim *s, long long nsteps);
 long long orc_step_index(const orc_sim *s);
+long long orc_particle_steps(const orc_sim *s);
 long long orc_count(const orc_sim *s, int sp);
 void orc_get(const orc_sim *s, int sp, double *x, double *vx, double *vy,
              double *vz, int *alive);

@@ -10,14 +10,22 @@ namespace o2 {
 constexpr int NSP = 3;                 // 0 e, 1 O-, 2 O2+
 constexpr int CHUNK = 1024;            // slots per push chunk
 constexpr int PUSH_THREADS = 256;      // 4 consecutive slots per thread
-constexpr int BIRTH_CAP = 256;         // births staged per push chunk
+constexpr int SUBTILE = 128;           // slots of one warp in a tile (32 lanes x 4)
+constexpr int SUBTILES = 1024 / SUBTILE;
+constexpr int BIRTH_CAP_W = 32;        // births staged per sub-tile
+constexpr int QCAP = 160;              // candidate queue of one warp (< 32 left + one sub-tile)
+constexpr int BSTAGE = 48;             // births staged by one warp between write-outs
+constexpr int TILES_PER_TICKET = 8;    // tiles taken per atomic ticket by a push block
+constexpr int BIRTHS_THREADS = 512;    // block of the birth-append kernel (sub-tiles)
+constexpr int TILE_ALIGN = BIRTHS_THREADS / (1024 / 128);  // tiles per birth-append block
 constexpr int SORT_WARPS = 4;          // warps per sort block
-constexpr int SORT_WARP_SLOTS = 4096;  // slots per sort warp
+constexpr int SORT_WARP_SLOTS = 8192;  // slots per sort warp (16-bit counters)
+constexpr int SORT_ILP = 8;            // 32-slot rows loaded per warp before ranking
 constexpr int SORT_CHUNK = SORT_WARPS * SORT_WARP_SLOTS;
 constexpr int PAIR_BIRTH_CAP = 16;     // births of (19) per cell per pass
 constexpr int MAX_GAS_CH = 16;
-constexpr int FIELD_THREADS = 512;
-constexpr int FIX_BITS = 26;           // fixed-point deposit: weight * 2^26
+constexpr int FIELD_THREADS = 1024;
+constexpr int FIX_BITS = 24;           // fixed-point deposit: weight * 2^24
 constexpr int MAX_DISCHARGES = 1024;
 constexpr long long SPIN_LIMIT = 1LL << 22;  // polls of a bounded wait
 
@@ -36,6 +44,7 @@ enum {
     C_VIOL_PAIR = 27,
     C_SLOTS = 28,       // slots processed by the push (all species)
     C_CANDS = 29,       // null-collision candidates
+    C_LIVE = 30,        // live particles pushed (particle-steps)
     C_NCOUNT = 32
 };
 
@@ -47,6 +56,7 @@ struct TableDesc {
     double th;          // threshold [eV]
     double lnE0;        // log of the first node
     double inv_dlog;    // (n-1) / log(E_last/E_0)
+    float th_f, lnE0_f, inv_dlog_f, pad_f;  // FP32 copies for the FP32 path
 };
 
 struct GasChan {
@@ -54,6 +64,7 @@ struct GasChan {
     int reaction;
     double coef;        // n_target * dx (normalised frequency per unit u_n * sigma)
     double dloss;       // 2 dE / mu * (dt/dx)^2 (inelastic reduction of u_n^2)
+    float coef_f, dloss_f;
 };
 
 struct SpeciesC {
@@ -70,6 +81,8 @@ struct SpeciesC {
     int nch;
     int table_lo;       // first table of the shared grid (for the index)
     int pad;
+    // FP32 copies (the FP32 path never converts from FP64 on the device)
+    float qm_f, numax_n_f, vgas_n_f, Ek_f, mfrac_f, Mfrac_f, ke_eV_f, pad_f;
     GasChan ch[MAX_GAS_CH];
 };
 
@@ -81,6 +94,7 @@ struct PairC {          // particle-target reaction of one discharge
     double Ek;          // (1/2) mu (dx/dt)^2 / e
     double mfrac, Mfrac;// m/(m+M), M/(m+M) of the pair
     double dloss;       // 2 dE/mu (dt/dx)^2
+    float Ek_f, mfrac_f, Mfrac_f, dloss_f;
 };
 
 struct Disc {
@@ -100,6 +114,7 @@ struct Disc {
     double f16;              // (16): v_e = |v_Om| * f16
     double f17;              // (17): w = sqrt(E_cm * f17)
     double eedf_scale, iedf_scale, fm_scale, fm_emax;
+    float f15_f, f16_f, f17_f, eedf_scale_f, iedf_scale_f, fm_scale_f, fm_emax_f, pad_f;
     int eedf_bins, iedf_bins, fm_bins, fm_xbins;
     int diag_every, n1, sort_interval, pad;
     int eedf_base, iedf_base, fm_base, pad2;
@@ -117,7 +132,7 @@ struct Ctl {
     unsigned int ticket;          // dynamic chunk counter of the push
     int total_chunks;             // chunks in the current push
     int D;                        // discharges
-    int pad;
+    unsigned int births_ticket;   // block order of the birth-append kernel
 };
 
 // Per (discharge, species) dynamic counts.
@@ -140,7 +155,9 @@ struct WsPtrs {
     Disc *disc;
     Counts *cnt;              // [D*3]
     int *chunk_ds;            // [D*3 + 1] first chunk per (d,s) (prefix), device copy
-    unsigned long long *lb;   // look-back status, [max_chunks * 3]
+    int *tile_cnt;            // [max_chunks * SUBTILES * 3] births per sub-tile and product species
+    void *births;             // [max_chunks * SUBTILES * BIRTH_CAP_W] staged birth records
+    unsigned long long *births_lb;  // [max_chunks * SUBTILES / BIRTHS_THREADS * 3] look-back words
     unsigned long long *acc_fix;  // [3 * total_nodes] fixed-point density accumulators
     double *acc_dbl;          // [3 * total_nodes] FP64 accumulators
     double *Efield;           // [total_nodes] E [V/m]
@@ -159,14 +176,22 @@ struct WsPtrs {
     int *sort_counts;         // count matrix
     int *cell_start;          // [sum over d of 3*(N+2)]
     int *sort_live;           // [D*3]
+    int *sort_tot;            // [sum over d of 3*(N+2)] slots per bucket
     int *pair_bcount;         // [total cells] births of (19) per cell
     int *cell_disc;           // [total cells] discharge of each global cell
+    int *pair_first;          // [total cells] first flagged projectile of the current reaction
+    int *pair_kills;          // [total cells * 3] particles killed per species in this pass
     void *pair_births;        // [total cells * PAIR_BIRTH_CAP] records
     int total_nodes;
     int total_cells;
     int max_chunks;
     int D;
 };
+
+// FP64 constant for the FP64 path, its FP32 copy for the FP32 path
+template <typename Real> __device__ __forceinline__ Real pick(double d, float f);
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
 // ---------------------------------------------------------------- Philox
 

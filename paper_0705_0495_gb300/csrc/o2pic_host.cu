@@ -76,7 +76,7 @@ struct Bump {
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t ctl, disc, cnt, lb, acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
+    size_t ctl, disc, cnt, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
         counters, eedf, iedf, fm, tables, lutE, lutS, lutEf, lutSf, sort_counts, cell_start,
         sort_live, pair_bcount, cell_disc, pair_births, sort_tab, ninit, vt;
     size_t cell[2], off[2], vx[2], vy[2], vz[2];
@@ -209,6 +209,7 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.sort_gmax.resize(3 * D);
     for (int d = 0; d < D; ++d) {
         const int N = c[d].n_cells;
+        mc = (mc + TILE_ALIGN - 1) / TILE_ALIGN * TILE_ALIGN;  // tiles of a discharge start aligned
         L.gbase.push_back(tn);
         L.ccell.push_back(tc);
         L.cs_base.push_back((int)csb);
@@ -229,6 +230,7 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
             L.pbase[3 * d + s] = cap;
             L.capr[3 * d + s] = cr;
             cap += cr;
+            mc = (mc + TILES_PER_TICKET - 1) / TILES_PER_TICKET * TILES_PER_TICKET;
             mc += cr / CHUNK;
             const int g = (cr + SORT_CHUNK - 1) / SORT_CHUNK;
             L.sort_gmax[3 * d + s] = g;
@@ -237,6 +239,7 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
             sb += g;
         }
     }
+    mc = (mc + TILE_ALIGN - 1) / TILE_ALIGN * TILE_ALIGN;  // room for the padding after the last species
     int nl = 0;
     for (int i = 0; i < n_xs; ++i) nl += xs[i].n;
     L.total_nodes = tn;
@@ -252,7 +255,9 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.ctl = B.take(sizeof(Ctl));
     L.disc = B.take(sizeof(Disc) * D);
     L.cnt = B.take(sizeof(Counts) * 3 * D);
-    L.lb = B.take(8ull * 3 * mc);
+    L.tile_cnt = B.take(4ull * 3 * SUBTILES * mc);
+    L.births = B.take((size_t)mc * SUBTILES * BIRTH_CAP_W * (fp64 ? 40 : 24));
+    L.births_lb = B.take(8ull * 3 * (mc / TILE_ALIGN + 1));
     L.acc = B.take(8ull * 3 * tn);
     L.Efield = B.take(8ull * tn);
     L.Ereal = B.take(R * tn);
@@ -274,8 +279,17 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.sort_counts = B.take(4ull * std::max(1LL, sortc));
     L.cell_start = B.take(4ull * csb);
     L.sort_live = B.take(4ull * 3 * D);
+    L.sort_tot = B.take(4ull * csb);
+    L.warp_base = B.take(4ull * (3 * D + 1));
     L.pair_bcount = B.take(4ull * tc);
     L.cell_disc = B.take(4ull * tc);
+    L.pair_first = B.take(4ull * tc);
+    L.pair_kills = B.take(4ull * 3 * tc);
+    for (int s = 0; s < 3; ++s) {
+        long long tiles = 0;
+        for (int d = 0; d < D; ++d) tiles += (c[d].capacity[s] + 255) / 256;
+        L.pair_tab[s] = B.take(8ull * std::max(1LL, tiles));
+    }
     L.pair_births = B.take((size_t)tc * PAIR_BIRTH_CAP * (8 + 4 * 8));
     L.sort_tab = B.take(8ull * sb);
     L.ninit = B.take(8ull * 3 * D);
@@ -393,6 +407,13 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
     D.iedf_scale = q.iedf_bins > 0 ? q.iedf_bins / q.iedf_emax_eV : 0.0;
     D.fm_scale = q.fm_bins > 0 ? q.fm_bins / (2.0 * q.fm_emax_eV) : 0.0;
     D.fm_emax = q.fm_emax_eV;
+    D.f15_f = (float)D.f15;
+    D.f16_f = (float)D.f16;
+    D.f17_f = (float)D.f17;
+    D.eedf_scale_f = (float)D.eedf_scale;
+    D.iedf_scale_f = (float)D.iedf_scale;
+    D.fm_scale_f = (float)D.fm_scale;
+    D.fm_emax_f = (float)D.fm_emax;
     D.eedf_base = L.eedf_base[d];
     D.iedf_base = L.iedf_base[d];
     D.fm_base = L.fm_base[d];
@@ -424,6 +445,8 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
             const double nj = (t.reaction == 17) ? q.C_delta * ngas : ngas;
             S.ch[j].coef = nj * D.dx;
             S.ch[j].dloss = 2.0 * t.th * QE / mu * tdx * tdx;
+            S.ch[j].coef_f = (float)S.ch[j].coef;
+            S.ch[j].dloss_f = (float)S.ch[j].dloss;
         }
         // nu_max: largest sum_j n_j sigma_j(E) sqrt(2E/mu) over the nodes up to
         // the cap and the cap itself, times the safety factor
@@ -449,6 +472,13 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
         const double pnull = 1.0 - std::exp(-S.numax * q.dt_s);
         const double thr = std::ceil(pnull * 4294967296.0 - 0.5);
         S.tnull = thr <= 0.0 ? 0u : (thr >= 4294967295.0 ? 0xFFFFFFFFu : (unsigned)thr);
+        S.qm_f = (float)S.qm;
+        S.numax_n_f = (float)S.numax_n;
+        S.vgas_n_f = (float)S.vgas_n;
+        S.Ek_f = (float)S.Ek;
+        S.mfrac_f = (float)S.mfrac;
+        S.Mfrac_f = (float)S.Mfrac;
+        S.ke_eV_f = (float)S.ke_eV;
         h->numax[3 * d + s] = S.numax;
     }
     const int rx[3] = {13, 14, 19};
@@ -464,6 +494,10 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
         P.mfrac = mp / (mp + mt);
         P.Mfrac = mt / (mp + mt);
         P.dloss = P.table >= 0 ? 2.0 * h->tabs[P.table].th * QE / mu * tdx * tdx : 0.0;
+        P.Ek_f = (float)P.Ek;
+        P.mfrac_f = (float)P.mfrac;
+        P.Mfrac_f = (float)P.Mfrac;
+        P.dloss_f = (float)P.dloss;
     }
     h->disc[d] = D;
 }
@@ -505,7 +539,9 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.disc = reinterpret_cast<Disc *>(b + L.disc);
     W.cnt = reinterpret_cast<Counts *>(b + L.cnt);
     W.chunk_ds = nullptr;
-    W.lb = reinterpret_cast<unsigned long long *>(b + L.lb);
+    W.tile_cnt = reinterpret_cast<int *>(b + L.tile_cnt);
+    W.births = b + L.births;
+    W.births_lb = reinterpret_cast<unsigned long long *>(b + L.births_lb);
     W.acc_fix = reinterpret_cast<unsigned long long *>(b + L.acc);
     W.acc_dbl = reinterpret_cast<double *>(b + L.acc);
     W.Efield = reinterpret_cast<double *>(b + L.Efield);
@@ -528,8 +564,11 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.sort_counts = reinterpret_cast<int *>(b + L.sort_counts);
     W.cell_start = reinterpret_cast<int *>(b + L.cell_start);
     W.sort_live = reinterpret_cast<int *>(b + L.sort_live);
+    W.sort_tot = reinterpret_cast<int *>(b + L.sort_tot);
     W.pair_bcount = reinterpret_cast<int *>(b + L.pair_bcount);
     W.cell_disc = reinterpret_cast<int *>(b + L.cell_disc);
+    W.pair_first = reinterpret_cast<int *>(b + L.pair_first);
+    W.pair_kills = reinterpret_cast<int *>(b + L.pair_kills);
     W.pair_births = b + L.pair_births;
     W.total_nodes = L.total_nodes;
     W.total_cells = L.total_cells;
@@ -563,6 +602,9 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
         td[i].th = t.th;
         td[i].lnE0 = std::log(t.E[0]);
         td[i].inv_dlog = (t.n - 1) / std::log(t.E[t.n - 1] / t.E[0]);
+        td[i].th_f = (float)td[i].th;
+        td[i].lnE0_f = (float)td[i].lnE0;
+        td[i].inv_dlog_f = (float)td[i].inv_dlog;
         for (int k = 0; k < t.n; ++k) {
             lE.push_back(t.E[k]);
             lS.push_back(t.S[k]);
@@ -587,6 +629,11 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     h->L.eedf_max = L.eedf_max;
     h->L.fm_max = L.fm_max;
     h->L.sort_blocks = L.sort_blocks;
+    h->L.sort_warp_base = reinterpret_cast<const int *>(b + L.warp_base);
+    std::vector<int> wbase(3 * n_discharges + 1, 0);
+    for (int d = 0; d < n_discharges; ++d)
+        for (int s = 0; s < 3; ++s) wbase[3 * d + s + 1] = wbase[3 * d + s] + cfgs[d].n_cells + 1;
+    h->L.sort_col_warps = wbase[3 * n_discharges];
     CK(configure_kernels(h->fp64, h->L));
     CK(push_configure(h->fp64, h->L, nsm));
 
@@ -628,6 +675,20 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     }
     CK(cudaMemcpyAsync(h->sort_tab, stab.data(), 4 * stab.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(W.cell_disc, cdisc.data(), 4 * cdisc.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b + L.warp_base, wbase.data(), 4 * wbase.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(W.pair_first, 0x7F, 4ull * L.total_cells, st));
+    for (int s = 0; s < 3; ++s) {
+        std::vector<int> pt;
+        for (int d = 0; d < n_discharges; ++d)
+            for (long long t = 0; t < (h->cfg[d].capacity[s] + 255) / 256; ++t) {
+                pt.push_back(d);
+                pt.push_back((int)t);
+            }
+        h->L.pair_blocks_sp[s] = (int)(pt.size() / 2);
+        h->L.pair_tab_sp[s] = reinterpret_cast<const int *>(b + L.pair_tab[s]);
+        if (!pt.empty())
+            CK(cudaMemcpyAsync(b + L.pair_tab[s], pt.data(), 4 * pt.size(), cudaMemcpyHostToDevice, st));
+    }
     long long *d_ninit = reinterpret_cast<long long *>(b + L.ninit);
     double *d_vt = reinterpret_cast<double *>(b + L.vt);
     CK(cudaMemcpyAsync(d_ninit, ninit.data(), 8 * ninit.size(), cudaMemcpyHostToDevice, st));
@@ -665,6 +726,9 @@ static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool time_p
         if (e) return e;
         h->ev_used += 2;
     }
+    e = launch_births(h->fp64, h->W, h->pools(), par, h->W.max_chunks / TILE_ALIGN + 1, st);
+    if (e) return e;
+    ++nk;
     const long long next = n + 1;
     const bool pair = q.n1 > 0 && next % q.n1 == 0;
     const bool sort = pair || (q.sort_interval > 0 && next % q.sort_interval == 0);
@@ -786,7 +850,7 @@ extern "C" pic_status pic_set_step(pic_handle *h, long long step)
     unsigned long long v = (unsigned long long)step;
     CK(cudaMemcpyAsync(&h->W.ctl->step[step & 1], &v, 8, cudaMemcpyHostToDevice, h->stream));
     // look-back words are tagged with the step; a step number can now repeat
-    CK(cudaMemsetAsync(h->W.lb, 0, 8ull * NSP * h->W.max_chunks, h->stream));
+    CK(cudaMemsetAsync(h->W.births_lb, 0, 8ull * 3 * (h->W.max_chunks / TILE_ALIGN + 1), h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->step = step;
     return PIC_OK;
@@ -829,6 +893,10 @@ extern "C" pic_status pic_diagnostics(pic_handle *h, int d, double *dens_sum, do
         for (int k = 0; k < 28; ++k) counters[k] = (long long)c[k];
         for (int s = 0; s < 3; ++s) counters[28 + s] = cn[s].n;
         counters[31] = h->step;
+        counters[32] = (long long)c[C_LIVE];
+        counters[33] = (long long)c[C_CANDS];
+        counters[34] = (long long)c[C_SLOTS];
+        for (int k = 35; k < 40; ++k) counters[k] = 0;
     }
     if (n_samples) *n_samples = (long long)ns;
     if (reset) {

@@ -135,66 +135,195 @@ k_field(WsPtrs W, int par, int diag, int mode)
     Ctl *ctl = W.ctl;
     const unsigned long long step = ctl->step[par];
     const int tn = W.total_nodes;
-    Acc *acc = AccK<Real>::ptr(W);
-    double *x = fsm;  // N+1 entries
     const double dx = Dd.dx;
-    for (int i = tid; i <= N; i += FIELD_THREADS) {
-        const double vol = (i == 0 || i == N) ? 0.5 * dx : dx;
-        const double scale = Dd.weight / vol;
-        double dn[NSP];
-#pragma unroll
-        for (int s = 0; s < NSP; ++s) {
-            const size_t k = (size_t)s * tn + g + i;
-            dn[s] = acc_to_weight(acc[k]) * scale;
-            if (mode == 0) acc[k] = Acc(0);
-            W.dens[k] = dn[s];
-            if (diag) W.dens_sum[k] += dn[s];
-        }
-        const double rho = QE_ * (dn[2] - dn[0] - dn[1]);
-        W.rho[g + i] = rho;
-        if (i == 0) s_rho0 = rho;
-        if (i == N) s_rhoN = rho;
-        x[i] = rho * dx * dx / EPS0_;
-    }
-    __syncthreads();
-    // scans over interior nodes 1..N-1, stored at x[1..N-1]
-    const int M = N - 1;
-    if (M > 0) {
-        block_scan_inclusive<FIELD_THREADS>(x + 1, M, warp_tot);  // S1
-        block_scan_inclusive<FIELD_THREADS>(x + 1, M, warp_tot);  // S2
-    }
     const double t = (double)step * Dd.dt;
     const double phi0 = Dd.U_rf * sin(Dd.omega * t + Dd.phase);
-    if (tid == 0) s_D0 = M > 0 ? (-phi0 + x[M]) / (double)N : -phi0 / (double)N;
-    __syncthreads();
-    const double D0 = s_D0;
-    double *phi = W.phi + g;
-    for (int i = tid; i <= N; i += FIELD_THREADS) {
-        double p;
-        if (i == 0) p = phi0;
-        else if (i == N) p = 0.0;
-        else p = phi0 + (double)i * D0 - (i >= 2 ? x[i - 1] : 0.0);
-        phi[i] = p;
-    }
-    __syncthreads();
     Real *Er = reinterpret_cast<Real *>(W.Ereal) + g;
-    for (int i = tid; i <= N; i += FIELD_THREADS) {
-        double E;
-        if (i == 0) E = -(phi[1] - phi[0]) / dx - s_rho0 * dx / (2.0 * EPS0_);
-        else if (i == N) E = -(phi[N] - phi[N - 1]) / dx + s_rhoN * dx / (2.0 * EPS0_);
-        else E = -(phi[i + 1] - phi[i - 1]) / (2.0 * dx);
-        W.Efield[g + i] = E;
-        Er[i] = (Real)E;
-        if (diag) W.phi_sum[g + i] += phi[i];
+    Acc *acc = AccK<Real>::ptr(W);
+    if constexpr (sizeof(Real) == 4) {
+        // FP32 path: the accumulators are exact fixed-point sums (weight *
+        // 2^FIX_BITS).  With q_i the net charge in these units and
+        // K = e w 2^-FIX_BITS / eps0: interior s_i = K dx q_i, S1 = prefix
+        // sums of q (exact int64), sum_m S1_m (exact int128), and
+        //   E_i = -D0/dx + (K/2)(S1_i + S1_{i-1}),  i = 1..N-1
+        //   E_0 = -D0/dx - K q_0,  E_N = -(D0 - K dx S1_{N-1})/dx + K q_N
+        //   phi_i = phi_0 + i D0 - K dx sum_{m<i} S1_m,  D0 = (K dx S2 - phi_0)/N.
+        long long *S1 = reinterpret_cast<long long *>(fsm);  // N+1 entries
+        __shared__ long long wl[FIELD_THREADS / 32];
+        __shared__ __int128 w128[FIELD_THREADS / 32];
+        __shared__ long long s_q0, s_qN;
+        const double K = QE_ * Dd.weight / (double)(1 << FIX_BITS) / EPS0_;
+        for (int i = tid; i <= N; i += FIELD_THREADS) {
+            long long a[NSP];
+#pragma unroll
+            for (int s = 0; s < NSP; ++s) {
+                const size_t k = (size_t)s * tn + g + i;
+                a[s] = (long long)acc[k];
+                if (mode == 0) acc[k] = Acc(0);
+            }
+            const long long q = a[2] - a[0] - a[1];
+            S1[i] = (i == 0 || i == N) ? 0 : q;
+            if (i == 0) s_q0 = q;
+            if (i == N) s_qN = q;
+            if (diag || mode != 0) {
+                const double vol = (i == 0 || i == N) ? 0.5 * dx : dx;
+                const double sc = Dd.weight / (vol * (double)(1 << FIX_BITS));
+#pragma unroll
+                for (int s = 0; s < NSP; ++s) {
+                    const size_t k = (size_t)s * tn + g + i;
+                    const double dn = (double)a[s] * sc;
+                    W.dens[k] = dn;
+                    if (diag) W.dens_sum[k] += dn;
+                }
+                W.rho[g + i] = QE_ * (double)q * sc;
+            }
+        }
+        __syncthreads();
+        // inclusive int64 scan of S1[1..N-1] and the int128 sum of the result
+        const int M = N - 1, lane = tid & 31, warp = tid >> 5;
+        const int per = (M + FIELD_THREADS - 1) / FIELD_THREADS;
+        const int lo = 1 + tid * per, hi = min(N, lo + per);
+        long long run = 0;
+        for (int i = lo; i < hi; ++i) {
+            run += S1[i];
+            S1[i] = run;
+        }
+        long long v = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long x = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += x;
+        }
+        if (lane == 31) wl[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            long long w = lane < FIELD_THREADS / 32 ? wl[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long x = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += x;
+            }
+            if (lane < FIELD_THREADS / 32) wl[lane] = w;
+        }
+        __syncthreads();
+        const long long excl = v - run + (warp > 0 ? wl[warp - 1] : 0);
+        __int128 part = 0;
+        for (int i = lo; i < hi; ++i) {
+            S1[i] += excl;
+            part += (__int128)S1[i];
+        }
+        // block sum of part
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long plo = (unsigned long long)part, phi_ = (unsigned long long)(part >> 64);
+            plo = __shfl_down_sync(0xffffffffu, plo, o);
+            phi_ = __shfl_down_sync(0xffffffffu, phi_, o);
+            part += ((__int128)(long long)phi_ << 64) | (__int128)plo;
+        }
+        if (lane == 0) w128[warp] = part;
+        __syncthreads();
+        if (tid == 0) {
+            __int128 S2 = 0;
+            for (int w = 0; w < FIELD_THREADS / 32; ++w) S2 += w128[w];
+            s_D0 = (K * dx * (double)S2 - phi0) / (double)N;
+        }
+        __syncthreads();
+        const double D0 = s_D0;
+        for (int i = tid; i <= N; i += FIELD_THREADS) {
+            double E;
+            if (i == 0) E = -D0 / dx - K * (double)s_q0;
+            else if (i == N) E = -(D0 - K * dx * (double)S1[N - 1]) / dx + K * (double)s_qN;
+            else E = -D0 / dx + 0.5 * K * (double)(S1[i] + S1[i - 1]);
+            Er[i] = (Real)E;
+            if (diag || mode != 0) W.Efield[g + i] = E;
+        }
+        if (diag || mode != 0) {
+            // potential: needs the second prefix sum; only for diagnostics
+            __syncthreads();
+            // 16-byte aligned after the N+1 int64 prefix sums
+            __int128 *S2s = reinterpret_cast<__int128 *>(reinterpret_cast<char *>(fsm) +
+                                                         ((8 * (size_t)(N + 1) + 15) & ~(size_t)15));
+            if (tid == 0) {
+                __int128 r = 0;
+                S2s[0] = 0;
+                for (int i = 1; i < N; ++i) {
+                    r += (__int128)S1[i];
+                    S2s[i] = r;
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i <= N; i += FIELD_THREADS) {
+                double p;
+                if (i == 0) p = phi0;
+                else if (i == N) p = 0.0;
+                else p = phi0 + (double)i * D0 - K * dx * (double)S2s[i - 1];
+                W.phi[g + i] = p;
+                if (diag) W.phi_sum[g + i] += p;
+            }
+        }
+    } else {
+        double *x = fsm;  // N+1 entries
+        for (int i = tid; i <= N; i += FIELD_THREADS) {
+            const double vol = (i == 0 || i == N) ? 0.5 * dx : dx;
+            const double scale = Dd.weight / vol;
+            double dn[NSP];
+#pragma unroll
+            for (int s = 0; s < NSP; ++s) {
+                const size_t k = (size_t)s * tn + g + i;
+                dn[s] = acc_to_weight(acc[k]) * scale;
+                if (mode == 0) acc[k] = Acc(0);
+                W.dens[k] = dn[s];
+                if (diag) W.dens_sum[k] += dn[s];
+            }
+            const double rho = QE_ * (dn[2] - dn[0] - dn[1]);
+            W.rho[g + i] = rho;
+            if (i == 0) s_rho0 = rho;
+            if (i == N) s_rhoN = rho;
+            x[i] = rho * dx * dx / EPS0_;
+        }
+        __syncthreads();
+        // scans over interior nodes 1..N-1, stored at x[1..N-1]
+        const int M = N - 1;
+        if (M > 0) {
+            block_scan_inclusive<FIELD_THREADS>(x + 1, M, warp_tot);  // S1
+            block_scan_inclusive<FIELD_THREADS>(x + 1, M, warp_tot);  // S2
+        }
+        if (tid == 0) s_D0 = M > 0 ? (-phi0 + x[M]) / (double)N : -phi0 / (double)N;
+        __syncthreads();
+        const double D0 = s_D0;
+        double *phi = W.phi + g;
+        for (int i = tid; i <= N; i += FIELD_THREADS) {
+            double p;
+            if (i == 0) p = phi0;
+            else if (i == N) p = 0.0;
+            else p = phi0 + (double)i * D0 - (i >= 2 ? x[i - 1] : 0.0);
+            phi[i] = p;
+        }
+        __syncthreads();
+        for (int i = tid; i <= N; i += FIELD_THREADS) {
+            double E;
+            if (i == 0) E = -(phi[1] - phi[0]) / dx - s_rho0 * dx / (2.0 * EPS0_);
+            else if (i == N) E = -(phi[N] - phi[N - 1]) / dx + s_rhoN * dx / (2.0 * EPS0_);
+            else E = -(phi[i + 1] - phi[i - 1]) / (2.0 * dx);
+            W.Efield[g + i] = E;
+            Er[i] = (Real)E;
+            if (diag) W.phi_sum[g + i] += phi[i];
+        }
     }
     if (diag && tid == 0) W.nsamp[d] += 1ull;
     if (mode != 0 || blockIdx.x != 0) return;
-    // block 0: chunk table of this step's push and the step counter
+    // block 0: tile table of this step's push and the step counter
     __syncthreads();
     if (tid == 0) {
+        // tiles of each discharge start at a multiple of TILE_ALIGN, so that the
+        // birth-append blocks (BIRTHS_THREADS sub-tiles) never span two, and
+        // those of each species at a multiple of TILES_PER_TICKET, so that a
+        // push ticket never spans two
         int chunk = 0;
         for (int ds = 0; ds < W.D * NSP; ++ds) {
             Counts &C = W.cnt[ds];
+            if (ds % NSP == 0) chunk = (chunk + TILE_ALIGN - 1) / TILE_ALIGN * TILE_ALIGN;
+            else chunk = (chunk + TILES_PER_TICKET - 1) / TILES_PER_TICKET * TILES_PER_TICKET;
             C.n_snap = C.n;
             C.chunk0 = chunk;
             C.nchunk = (C.n + CHUNK - 1) / CHUNK;
@@ -206,7 +335,17 @@ k_field(WsPtrs W, int par, int diag, int mode)
         }
         ctl->total_chunks = chunk;
         ctl->ticket = 0u;
+        ctl->births_ticket = 0u;
         ctl->step[par ^ 1] = step + 1ull;
+    }
+    __syncthreads();
+    // birth counts of the padding tiles after each species (never pushed)
+    for (int ds = 0; ds < W.D * NSP; ++ds) {
+        const Counts &C = W.cnt[ds];
+        const int t0 = C.chunk0 + C.nchunk;
+        const int t1 = (t0 + TILES_PER_TICKET - 1) / TILES_PER_TICKET * TILES_PER_TICKET;
+        const int n = (t1 - t0) * SUBTILES * NSP;
+        for (int k = tid; k < n; k += FIELD_THREADS) W.tile_cnt[(size_t)t0 * SUBTILES * NSP + k] = 0;
     }
 }
 
@@ -220,7 +359,8 @@ __device__ __forceinline__ void sort_block(const int *tab, int &ds, int &bi)
 }
 
 // Histogram of cells (dead slots in bucket N) of one block of SORT_CHUNK
-// slots; written as row bi of the (block x bucket) count matrix of ds.
+// slots; written as row bi of the (block x bucket) count matrix of ds.  Each
+// warp reads SORT_ILP slots per lane before counting, to keep loads in flight.
 template <typename Real>
 __global__ void __launch_bounds__(SORT_WARPS * 32)
 k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
@@ -236,28 +376,74 @@ k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
     for (int i = threadIdx.x; i <= N; i += blockDim.x) ssm[i] = 0;
     __syncthreads();
     const int *cell = P.cell[W.ctl->cur] + Dd.pbase[s];
-    const int lo = bi * SORT_CHUNK, hi = min(n, lo + SORT_CHUNK);
-    const int lane = threadIdx.x & 31;
-    for (int i0 = lo + (threadIdx.x & ~31); i0 < hi; i0 += blockDim.x) {
-        const int i = i0 + lane;
-        int b = -1;
-        if (i < hi) {
-            const int c = cell[i];
-            b = c < 0 ? N : c;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lo = bi * SORT_CHUNK + w * SORT_WARP_SLOTS;
+    const int hi = min(n, lo + SORT_WARP_SLOTS);
+    for (int i0 = lo; i0 < hi; i0 += 32 * SORT_ILP) {
+        int b[SORT_ILP];
+#pragma unroll
+        for (int r = 0; r < SORT_ILP; ++r) {
+            const int i = i0 + r * 32 + lane;
+            b[r] = -1;
+            if (i < hi) {
+                const int c = cell[i];
+                b[r] = c < 0 ? N : c;
+            }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&ssm[b], (unsigned)__popc(peers));
+#pragma unroll
+        for (int r = 0; r < SORT_ILP; ++r) {
+            const unsigned peers = __match_any_sync(0xffffffffu, b[r]);
+            if (b[r] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&ssm[b[r]], (unsigned)__popc(peers));
+        }
     }
     __syncthreads();
     int *row = W.sort_counts + Dd.sort_cbase[s] + (size_t)bi * (N + 1);
     for (int i = threadIdx.x; i <= N; i += blockDim.x) row[i] = (int)ssm[i];
 }
 
-// Per (d, s): running sums down the blocks per bucket (each (block, bucket)
-// entry becomes the first slot of that block's bucket relative to the bucket
-// start) and the bucket starts (cell_start) by a scan over buckets.
+// One warp per (d, s, bucket): running sums down the sort blocks, so each
+// (block, bucket) entry becomes that block's first slot inside the bucket;
+// the bucket total goes to sort_tot.
+__global__ void __launch_bounds__(256)
+k_sort_colscan(WsPtrs W, const int *warp_base)
+{
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    // warp -> (ds, bucket): the buckets of all (d, s) laid end to end
+    const int nds = W.D * NSP;
+    if (gw >= warp_base[nds]) return;
+    int lo = 0, hi = nds;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (warp_base[mid] <= gw) lo = mid; else hi = mid;
+    }
+    const int ds = lo;
+    const int c = gw - warp_base[ds];
+    const int d = ds / NSP, s = ds % NSP;
+    const Disc &Dd = W.disc[d];
+    const int N = Dd.N;
+    const int n = W.cnt[ds].n;
+    const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
+    int *cnt = W.sort_counts + Dd.sort_cbase[s];
+    int carry = 0;
+    for (int b0 = 0; b0 < G; b0 += 32) {
+        const int b = b0 + lane;
+        const int v = b < G ? cnt[(size_t)b * (N + 1) + c] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (b < G) cnt[(size_t)b * (N + 1) + c] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) W.sort_tot[Dd.cs_base + s * (N + 2) + c] = carry;
+}
+
+// Per (d, s): bucket starts (cell_start) by a scan over the bucket totals.
 __global__ void __launch_bounds__(512)
-k_sort_scan(WsPtrs W)
+k_sort_cellscan(WsPtrs W)
 {
     extern __shared__ __align__(16) int isx[];
     __shared__ int wsum[32];
@@ -265,18 +451,9 @@ k_sort_scan(WsPtrs W)
     const int d = ds / NSP, s = ds % NSP;
     const Disc &Dd = W.disc[d];
     const int N = Dd.N, n = W.cnt[ds].n;
-    const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
-    int *cnt = W.sort_counts + Dd.sort_cbase[s];
+    const int *tot_g = W.sort_tot + Dd.cs_base + s * (N + 2);
     int *tot = isx;  // N+1
-    for (int c = threadIdx.x; c <= N; c += blockDim.x) {
-        int run = 0;
-        for (int b = 0; b < G; ++b) {
-            const int v = cnt[(size_t)b * (N + 1) + c];
-            cnt[(size_t)b * (N + 1) + c] = run;
-            run += v;
-        }
-        tot[c] = run;
-    }
+    for (int c = threadIdx.x; c <= N; c += blockDim.x) tot[c] = n > 0 ? tot_g[c] : 0;
     __syncthreads();
     block_scan_exclusive_int(tot, N + 1, wsum);
     int *cs = W.cell_start + Dd.cs_base + s * (N + 2);
@@ -287,15 +464,16 @@ k_sort_scan(WsPtrs W)
     }
 }
 
-// Stable scatter: warp w of block bi owns slots [lo + w*4096, +4096); a
-// per-warp bucket count gives each warp its first slot per bucket, then each
-// warp walks its slots in order, ranking equal buckets inside a 32-slot tile
-// by lane.  Dead slots (bucket N) are dropped.
+// Stable scatter: warp w of block bi owns slots [lo + w*SORT_WARP_SLOTS, ...);
+// a per-warp bucket count (16-bit) gives each warp its first slot per bucket
+// relative to the block's, then each warp walks its slots in order, ranking
+// equal buckets inside a 32-slot row by lane.  Dead slots (bucket N) are
+// dropped.  SORT_ILP rows are loaded before they are ranked.
 template <typename Real>
 __global__ void __launch_bounds__(SORT_WARPS * 32)
 k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
 {
-    extern __shared__ __align__(16) unsigned ssm[];
+    extern __shared__ __align__(16) unsigned short hsm[];
     int ds, bi;
     sort_block(tab, ds, bi);
     const int d = ds / NSP, s = ds % NSP;
@@ -304,63 +482,85 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
     const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
     if (bi >= G) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned *hw = ssm + (size_t)w * (N + 1);
-    for (int i = threadIdx.x; i < SORT_WARPS * (N + 1); i += blockDim.x) ssm[i] = 0;
+    const int stride = (N + 2) & ~1;
+    unsigned short *hw = hsm + (size_t)w * stride;
+    for (int i = threadIdx.x; i < SORT_WARPS * stride; i += blockDim.x) hsm[i] = 0;
     __syncthreads();
     const int cur = W.ctl->cur, nxt = cur ^ 1;
     const int pb = Dd.pbase[s];
     const int *cell = P.cell[cur] + pb;
     const int lo = bi * SORT_CHUNK + w * SORT_WARP_SLOTS;
     const int hi = min(n, lo + SORT_WARP_SLOTS);
-    for (int i0 = lo; i0 < hi; i0 += 32) {
-        const int i = i0 + lane;
-        int b = -1;
-        if (i < hi) {
-            const int c = cell[i];
-            b = c < 0 ? N : c;
+    for (int i0 = lo; i0 < hi; i0 += 32 * SORT_ILP) {
+        int b[SORT_ILP];
+#pragma unroll
+        for (int r = 0; r < SORT_ILP; ++r) {
+            const int i = i0 + r * 32 + lane;
+            b[r] = -1;
+            if (i < hi) {
+                const int c = cell[i];
+                b[r] = c < 0 ? N : c;
+            }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        if (b >= 0 && lane == __ffs(peers) - 1) hw[b] += __popc(peers);
-        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < SORT_ILP; ++r) {
+            const unsigned peers = __match_any_sync(0xffffffffu, b[r]);
+            if (b[r] >= 0 && lane == __ffs(peers) - 1) hw[b[r]] += (unsigned short)__popc(peers);
+            __syncwarp();
+        }
     }
     __syncthreads();
-    const int *base = W.sort_counts + Dd.sort_cbase[s] + (size_t)bi * (N + 1);
-    const int *cstart = W.cell_start + Dd.cs_base + s * (N + 2);
+    // per bucket: warp offsets relative to the block's first slot in it
     for (int c = threadIdx.x; c <= N; c += blockDim.x) {
-        unsigned run = (unsigned)(base[c] + cstart[c]);
+        unsigned run = 0;
 #pragma unroll
         for (int q = 0; q < SORT_WARPS; ++q) {
-            const unsigned t = ssm[(size_t)q * (N + 1) + c];
-            ssm[(size_t)q * (N + 1) + c] = run;
+            const unsigned t = hsm[(size_t)q * stride + c];
+            hsm[(size_t)q * stride + c] = (unsigned short)run;
             run += t;
         }
     }
     __syncthreads();
+    const int *base = W.sort_counts + Dd.sort_cbase[s] + (size_t)bi * (N + 1);
+    const int *cstart = W.cell_start + Dd.cs_base + s * (N + 2);
     const Real *offS = P.off[cur] + pb, *vxS = P.vx[cur] + pb, *vyS = P.vy[cur] + pb,
                *vzS = P.vz[cur] + pb;
     int *cellD = P.cell[nxt] + pb;
     Real *offD = P.off[nxt] + pb, *vxD = P.vx[nxt] + pb, *vyD = P.vy[nxt] + pb,
          *vzD = P.vz[nxt] + pb;
     const unsigned lt = (1u << lane) - 1u;
-    for (int i0 = lo; i0 < hi; i0 += 32) {
-        const int i = i0 + lane;
-        int b = -1;
-        if (i < hi) {
-            const int c = cell[i];
-            b = c < 0 ? N : c;
+    for (int i0 = lo; i0 < hi; i0 += 32 * SORT_ILP) {
+        int b[SORT_ILP];
+        int dst[SORT_ILP];
+#pragma unroll
+        for (int r = 0; r < SORT_ILP; ++r) {
+            const int i = i0 + r * 32 + lane;
+            b[r] = -1;
+            if (i < hi) {
+                const int c = cell[i];
+                b[r] = c < 0 ? N : c;
+            }
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        unsigned dst = 0;
-        if (b >= 0) dst = hw[b] + __popc(peers & lt);
-        __syncwarp();
-        if (b >= 0 && lane == __ffs(peers) - 1) hw[b] += __popc(peers);
-        __syncwarp();
-        if (b >= 0 && b < N) {
-            cellD[dst] = b;
-            offD[dst] = offS[i];
-            vxD[dst] = vxS[i];
-            vyD[dst] = vyS[i];
-            vzD[dst] = vzS[i];
+#pragma unroll
+        for (int r = 0; r < SORT_ILP; ++r) {
+            const unsigned peers = __match_any_sync(0xffffffffu, b[r]);
+            dst[r] = -1;
+            if (b[r] >= 0 && b[r] < N) dst[r] = (int)hw[b[r]] + __popc(peers & lt);
+            __syncwarp();
+            if (b[r] >= 0 && lane == __ffs(peers) - 1) hw[b[r]] += (unsigned short)__popc(peers);
+            __syncwarp();
+        }
+#pragma unroll
+        for (int r = 0; r < SORT_ILP; ++r) {
+            if (dst[r] >= 0) {
+                const int i = i0 + r * 32 + lane;
+                const int g = cstart[b[r]] + base[b[r]] + dst[r];
+                cellD[g] = b[r];
+                offD[g] = offS[i];
+                vxD[g] = vxS[i];
+                vyD[g] = vyS[i];
+                vzD[g] = vzS[i];
+            }
         }
     }
 }
@@ -421,19 +621,76 @@ __device__ __forceinline__ void iso_n(Real r1, Real r2, Real n[3])
     iso_dir<Real>(r1, r2, n);
 }
 
-// One warp per cell: reactions (13), (14), (19) in that order with
-// P = n_target sigma(E) u n1 dt (Eq. 1), n_target from the live target count
-// at the start of each reaction's pass.  Projectiles are taken in slot order;
-// a batch of 32 is evaluated in parallel and the first accepting lane is
-// executed, after which the later lanes are evaluated again, so the result is
-// that of the sequential pass.
+constexpr int NO_FLAG = 0x7F7F7F7F;  // larger than any slot index
+
+// Particle-target reaction k (0: (13), 1: (14), 2: (19)) evaluated for every
+// projectile at once, as if it were the first of its cell: a random target
+// of the cell (walking past dead ones), P = n_target sigma(E) u n1 dt (Eq. 1)
+// with n_target from the live target count at the start of the reaction's
+// pass, and the acceptance draw.  Nothing is changed here; the smallest
+// projectile index of a cell that collides, finds no live target, or has
+// P > 1 is recorded, and the sequential pass of that cell restarts there.
+// Before it, every projectile's outcome is exactly that of the sequential
+// pass, because no earlier projectile of the cell changed anything.
 template <typename Real>
 __global__ void __launch_bounds__(256)
-k_pair(WsPtrs W, Pools<Real> P, int par)
+k_pair_eval(WsPtrs W, Pools<Real> P, int par, int k, const int *tab)
+{
+    const int d = tab[2 * blockIdx.x], tile = tab[2 * blockIdx.x + 1];
+    const Disc &Dd = W.disc[d];
+    const PairC &pc = Dd.pair[k];
+    if (pc.table < 0) return;
+    const int ps = pc.proj, pt = pc.targ;
+    const int i = tile * 256 + threadIdx.x;
+    if (i >= W.cnt[d * NSP + ps].n) return;
+    const int cur = W.ctl->cur;
+    const int pbp = Dd.pbase[ps], pbt = Dd.pbase[pt];
+    const int c = P.cell[cur][pbp + i];
+    if (c < 0) return;
+    const int N = Dd.N;
+    const int *cs = W.cell_start + Dd.cs_base;
+    const int t0 = cs[pt * (N + 2) + c], t1 = cs[pt * (N + 2) + c + 1];
+    const int range = t1 - t0;
+    if (range <= 0) return;
+    const int liveT = range - W.pair_kills[(size_t)(Dd.ccell_base + c) * NSP + pt];
+    if (liveT <= 0) return;
+    const int rx = k == 0 ? 13 : (k == 1 ? 14 : 19);
+    const unsigned long long step = W.ctl->step[par];
+    const uint4 d0 = rng_block(Dd.seed, Dd.discharge, ps, 2, rx, 0, step, (unsigned)i);
+    int j = t0 + (int)__umulhi(d0.x, (unsigned)range);
+    int walked = 0;
+    const int *cellA = P.cell[cur];
+    while (cellA[pbt + j] < 0 && walked < range) {
+        j = (j + 1 < t1) ? j + 1 : t0;
+        ++walked;
+    }
+    bool flag = cellA[pbt + j] < 0;
+    if (!flag) {
+        const Real g0 = P.vx[cur][pbp + i] - P.vx[cur][pbt + j];
+        const Real g1 = P.vy[cur][pbp + i] - P.vy[cur][pbt + j];
+        const Real g2 = P.vz[cur][pbp + i] - P.vz[cur][pbt + j];
+        const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
+        const Real u = sqrt(u2);
+        const Real E = pick<Real>(pc.Ek, pc.Ek_f) * u2;
+        const Real Pc = Real((double)liveT * pc.coef) * pair_sigma<Real>(W, W.tables[pc.table], E) * u;
+        flag = Pc > Real(1) || unif<Real>(d0.y) < Pc;
+    }
+    if (flag) atomicMin(&W.pair_first[Dd.ccell_base + c], i);
+}
+
+// Sequential pass of reaction k over one flagged cell (one warp), from its
+// first flagged projectile on: projectiles in slot order, a batch of 32
+// evaluated in parallel, the first accepting lane executed, the later lanes
+// evaluated again.  Kills, (19)'s scattering and its births happen here.
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
 {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (gw >= W.total_cells) return;
+    const int first = W.pair_first[gw];
+    if (first == NO_FLAG) return;
     const int d = W.cell_disc[gw];
     const Disc &Dd = W.disc[d];
     const int N = Dd.N, c = gw - Dd.ccell_base;
@@ -445,132 +702,133 @@ k_pair(WsPtrs W, Pools<Real> P, int par)
     typename AccK<Real>::T *acc = AccK<Real>::ptr(W);
     PairBirth<Real> *births = reinterpret_cast<PairBirth<Real> *>(W.pair_births) + (size_t)gw * PAIR_BIRTH_CAP;
     unsigned long long *cnt = W.counters + (size_t)d * C_NCOUNT;
-    int kills[NSP] = {0, 0, 0};
-    int nb = 0;
-    const int rx[3] = {13, 14, 19};
-    for (int k = 0; k < 3; ++k) {
-        const PairC &pc = Dd.pair[k];
-        if (pc.table < 0) continue;
-        const int ps = pc.proj, pt = pc.targ;
-        const int p0 = cs[ps * (N + 2) + c], p1 = cs[ps * (N + 2) + c + 1];
-        const int t0 = cs[pt * (N + 2) + c], t1 = cs[pt * (N + 2) + c + 1];
-        const int range = t1 - t0;
-        if (range <= 0 || p1 <= p0) continue;
-        const int liveT = range - kills[pt];
-        if (liveT <= 0) continue;
-        const TableDesc &T = W.tables[pc.table];
-        const Real coefP = Real((double)liveT * pc.coef);
-        const int pbp = Dd.pbase[ps], pbt = Dd.pbase[pt];
-        bool stop = false;
-        unsigned nviol = 0;
-        for (int b0 = p0; b0 < p1 && !stop; b0 += 32) {
-            const int i = b0 + lane;
-            int from = 0;
-            for (;;) {
-                bool ev = false, ex = false, viol = false;
-                int j = -1;
-                uint4 d0 = make_uint4(0, 0, 0, 0);
-                if (i < p1 && lane >= from && cellA[pbp + i] >= 0) {
-                    d0 = rng_block(Dd.seed, Dd.discharge, ps, 2, rx[k], 0, step, (unsigned)i);
-                    j = t0 + (int)__umulhi(d0.x, (unsigned)range);
-                    int walked = 0;
-                    while (cellA[pbt + j] < 0 && walked < range) {
-                        j = (j + 1 < t1) ? j + 1 : t0;
-                        ++walked;
-                    }
-                    if (cellA[pbt + j] < 0) {
-                        ex = true;
-                    } else {
-                        const Real g0 = vxA[pbp + i] - vxA[pbt + j];
-                        const Real g1 = vyA[pbp + i] - vyA[pbt + j];
-                        const Real g2 = vzA[pbp + i] - vzA[pbt + j];
-                        const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
-                        const Real u = sqrt(u2);
-                        const Real E = Real(pc.Ek) * u2;
-                        Real Pc = coefP * pair_sigma<Real>(W, T, E) * u;
-                        if (Pc > Real(1)) {
-                            viol = true;
-                            Pc = Real(1);
-                        }
-                        ev = unif<Real>(d0.y) < Pc;
-                    }
+    int *kills = W.pair_kills + (size_t)gw * NSP;
+    int nb = W.pair_bcount[gw];
+    const int rx = k == 0 ? 13 : (k == 1 ? 14 : 19);
+    const PairC &pc = Dd.pair[k];
+    const int ps = pc.proj, pt = pc.targ;
+    const int p1 = cs[ps * (N + 2) + c + 1];
+    const int t0 = cs[pt * (N + 2) + c], t1 = cs[pt * (N + 2) + c + 1];
+    const int range = t1 - t0;
+    const int liveT = range - kills[pt];
+    const TableDesc &T = W.tables[pc.table];
+    const Real coefP = Real((double)liveT * pc.coef);
+    const int pbp = Dd.pbase[ps], pbt = Dd.pbase[pt];
+    bool stop = false;
+    unsigned nviol = 0;
+    int nkp = 0, nkt = 0;
+    for (int b0 = first; b0 < p1 && !stop; b0 += 32) {
+        const int i = b0 + lane;
+        int from = 0;
+        for (;;) {
+            bool ev = false, ex = false, viol = false;
+            int j = -1;
+            uint4 d0 = make_uint4(0, 0, 0, 0);
+            if (i < p1 && lane >= from && cellA[pbp + i] >= 0) {
+                d0 = rng_block(Dd.seed, Dd.discharge, ps, 2, rx, 0, step, (unsigned)i);
+                j = t0 + (int)__umulhi(d0.x, (unsigned)range);
+                int walked = 0;
+                while (cellA[pbt + j] < 0 && walked < range) {
+                    j = (j + 1 < t1) ? j + 1 : t0;
+                    ++walked;
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, ev || ex);
-                const int l = m ? __ffs(m) - 1 : 32;
-                nviol += __popc(__ballot_sync(0xffffffffu, viol && lane <= l));
-                if (!m) break;
-                const bool exl = __shfl_sync(0xffffffffu, ex, l);
-                if (exl) {
-                    stop = true;  // no live target left for this projectile
-                    break;
-                }
-                if (lane == l) {
-                    const int gi = pbp + i, gj = pbt + j;
-                    atomicAdd(&cnt[C_EVENTS + rx[k]], 1ull);
-                    typename AccK<Real>::T *acc_p = acc + (size_t)ps * W.total_nodes + Dd.gbase;
-                    typename AccK<Real>::T *acc_t = acc + (size_t)pt * W.total_nodes + Dd.gbase;
-                    if (rx[k] != 19) {
-                        cellA[gi] = -1;
-                        dep_global(acc_p, c, offA[gi], -1);
-                    } else {
-                        uint4 d1 = rng_block(Dd.seed, Dd.discharge, ps, 2, 19, 1, step, (unsigned)i);
-                        Real v[3] = {vxA[gi], vyA[gi], vzA[gi]};
-                        Real V[3] = {vxA[gj], vyA[gj], vzA[gj]};
-                        Real nd[3], n2[3], v1[3], Vo[3];
-                        iso_n<Real>(unif<Real>(d0.z), unif<Real>(d0.w), nd);
-                        const Real mf = Real(pc.mfrac), Mf = Real(pc.Mfrac);
-                        Real g0 = v[0] - V[0], g1 = v[1] - V[1], g2 = v[2] - V[2];
-                        Real uu = g0 * g0 + g1 * g1 + g2 * g2 - Real(pc.dloss);
-                        Real up = uu > Real(0) ? sqrt(uu) : Real(0);
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            Real vcm = mf * v[q] + Mf * V[q];
-                            v1[q] = vcm + Mf * up * nd[q];
-                            Vo[q] = vcm - mf * up * nd[q];
-                        }
-                        iso_n<Real>(unif<Real>(d1.x), unif<Real>(d1.y), n2);
-                        Real e2[3] = {Vo[0], Vo[1], Vo[2]};
-                        Real a0 = v1[0] - e2[0], a1 = v1[1] - e2[1], a2 = v1[2] - e2[2];
-                        Real ue = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            Real cc = Real(0.5) * (v1[q] + e2[q]);
-                            v1[q] = cc + Real(0.5) * ue * n2[q];
-                            e2[q] = cc - Real(0.5) * ue * n2[q];
-                        }
-                        vxA[gi] = v1[0];
-                        vyA[gi] = v1[1];
-                        vzA[gi] = v1[2];
-                        if (nb < PAIR_BIRTH_CAP) {
-                            PairBirth<Real> &pbr = births[nb];
-                            pbr.c = c;
-                            pbr.off = offA[gi];
-                            pbr.vx = e2[0];
-                            pbr.vy = e2[1];
-                            pbr.vz = e2[2];
-                        } else {
-                            set_status(W.ctl, ST_BIRTHBUF);
-                        }
-                    }
-                    cellA[gj] = -1;
-                    dep_global(acc_t, c, offA[gj], -1);
-                }
-                __syncwarp();
-                __threadfence_block();
-                if (rx[k] == 19) {
-                    ++nb;
-                    ++kills[pt];
+                if (cellA[pbt + j] < 0) {
+                    ex = true;
                 } else {
-                    ++kills[ps];
-                    ++kills[pt];
+                    const Real g0 = vxA[pbp + i] - vxA[pbt + j];
+                    const Real g1 = vyA[pbp + i] - vyA[pbt + j];
+                    const Real g2 = vzA[pbp + i] - vzA[pbt + j];
+                    const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
+                    const Real u = sqrt(u2);
+                    const Real E = pick<Real>(pc.Ek, pc.Ek_f) * u2;
+                    Real Pc = coefP * pair_sigma<Real>(W, T, E) * u;
+                    if (Pc > Real(1)) {
+                        viol = true;
+                        Pc = Real(1);
+                    }
+                    ev = unif<Real>(d0.y) < Pc;
                 }
-                from = l + 1;
-                if (from >= 32) break;
             }
+            const unsigned m = __ballot_sync(0xffffffffu, ev || ex);
+            const int l = m ? __ffs(m) - 1 : 32;
+            nviol += __popc(__ballot_sync(0xffffffffu, viol && lane <= l));
+            if (!m) break;
+            const bool exl = __shfl_sync(0xffffffffu, ex, l);
+            if (exl) {
+                stop = true;  // no live target left for this projectile
+                break;
+            }
+            if (lane == l) {
+                const int gi = pbp + i, gj = pbt + j;
+                atomicAdd(&cnt[C_EVENTS + rx], 1ull);
+                typename AccK<Real>::T *acc_p = acc + (size_t)ps * W.total_nodes + Dd.gbase;
+                typename AccK<Real>::T *acc_t = acc + (size_t)pt * W.total_nodes + Dd.gbase;
+                if (rx != 19) {
+                    cellA[gi] = -1;
+                    dep_global(acc_p, c, offA[gi], -1);
+                } else {
+                    uint4 d1 = rng_block(Dd.seed, Dd.discharge, ps, 2, 19, 1, step, (unsigned)i);
+                    Real v[3] = {vxA[gi], vyA[gi], vzA[gi]};
+                    Real V[3] = {vxA[gj], vyA[gj], vzA[gj]};
+                    Real nd[3], n2[3], v1[3], Vo[3];
+                    iso_n<Real>(unif<Real>(d0.z), unif<Real>(d0.w), nd);
+                    const Real mf = pick<Real>(pc.mfrac, pc.mfrac_f), Mf = pick<Real>(pc.Mfrac, pc.Mfrac_f);
+                    Real g0 = v[0] - V[0], g1 = v[1] - V[1], g2 = v[2] - V[2];
+                    Real uu = g0 * g0 + g1 * g1 + g2 * g2 - pick<Real>(pc.dloss, pc.dloss_f);
+                    Real up = uu > Real(0) ? sqrt(uu) : Real(0);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        Real vcm = mf * v[q] + Mf * V[q];
+                        v1[q] = vcm + Mf * up * nd[q];
+                        Vo[q] = vcm - mf * up * nd[q];
+                    }
+                    iso_n<Real>(unif<Real>(d1.x), unif<Real>(d1.y), n2);
+                    Real e2[3] = {Vo[0], Vo[1], Vo[2]};
+                    Real a0 = v1[0] - e2[0], a1 = v1[1] - e2[1], a2 = v1[2] - e2[2];
+                    Real ue = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        Real cc = Real(0.5) * (v1[q] + e2[q]);
+                        v1[q] = cc + Real(0.5) * ue * n2[q];
+                        e2[q] = cc - Real(0.5) * ue * n2[q];
+                    }
+                    vxA[gi] = v1[0];
+                    vyA[gi] = v1[1];
+                    vzA[gi] = v1[2];
+                    if (nb < PAIR_BIRTH_CAP) {
+                        PairBirth<Real> &pbr = births[nb];
+                        pbr.c = c;
+                        pbr.off = offA[gi];
+                        pbr.vx = e2[0];
+                        pbr.vy = e2[1];
+                        pbr.vz = e2[2];
+                    } else {
+                        set_status(W.ctl, ST_BIRTHBUF);
+                    }
+                }
+                cellA[gj] = -1;
+                dep_global(acc_t, c, offA[gj], -1);
+            }
+            __syncwarp();
+            __threadfence_block();
+            if (rx == 19) {
+                ++nb;
+                ++nkt;
+            } else {
+                ++nkp;
+                ++nkt;
+            }
+            from = l + 1;
+            if (from >= 32) break;
         }
-        if (lane == 0 && nviol) atomicAdd(&cnt[C_VIOL_PAIR], (unsigned long long)nviol);
     }
-    if (lane == 0) W.pair_bcount[gw] = nb < PAIR_BIRTH_CAP ? nb : PAIR_BIRTH_CAP;
+    if (lane == 0) {
+        if (nviol) atomicAdd(&cnt[C_VIOL_PAIR], (unsigned long long)nviol);
+        kills[ps] += nkp;
+        kills[pt] += nkt;
+        W.pair_bcount[gw] = nb < PAIR_BIRTH_CAP ? nb : PAIR_BIRTH_CAP;
+        W.pair_first[gw] = NO_FLAG;
+    }
 }
 
 // Births of (19) appended to the electron array of each discharge in cell
@@ -584,7 +842,11 @@ k_pair_append(WsPtrs W, Pools<Real> P)
     const int d = blockIdx.x;
     const Disc &Dd = W.disc[d];
     const int N = Dd.N;
-    for (int c = threadIdx.x; c < N; c += blockDim.x) pre[c] = W.pair_bcount[Dd.ccell_base + c];
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        pre[c] = W.pair_bcount[Dd.ccell_base + c];
+#pragma unroll
+        for (int q = 0; q < NSP; ++q) W.pair_kills[(size_t)(Dd.ccell_base + c) * NSP + q] = 0;
+    }
     __syncthreads();
     const int tot = block_scan_exclusive_int(pre, N, wsum);
     if (tot == 0) return;
@@ -612,6 +874,7 @@ k_pair_append(WsPtrs W, Pools<Real> P)
         }
     }
     __syncthreads();
+    for (int c = threadIdx.x; c < N; c += blockDim.x) W.pair_bcount[Dd.ccell_base + c] = 0;
     if (threadIdx.x == 0) C.n = min(n0 + tot, Dd.cap[0]);
 }
 
@@ -682,24 +945,25 @@ __global__ void k_deposit_all(WsPtrs W, Pools<Real> P, int only_disc)
 cudaError_t configure_kernels(bool fp64, LaunchCfg &L)
 {
     cudaError_t e;
-    L.field_smem = sizeof(double) * (L.maxN + 2);
-    L.sort_smem = sizeof(unsigned) * SORT_WARPS * (L.maxN + 1);
+    L.field_smem = sizeof(double) * (L.maxN + 2) + 16 * (L.maxN + 2) + 16;
+    L.sort_smem = sizeof(unsigned) * (L.maxN + 1);
+    L.scatter_smem = sizeof(unsigned short) * SORT_WARPS * ((L.maxN + 2) & ~1);
     if (fp64) {
         e = cudaFuncSetAttribute(k_field<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.field_smem);
         if (e) return e;
         e = cudaFuncSetAttribute(k_sort_count<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sort_smem);
         if (e) return e;
-        e = cudaFuncSetAttribute(k_sort_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sort_smem);
+        e = cudaFuncSetAttribute(k_sort_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.scatter_smem);
         if (e) return e;
     } else {
         e = cudaFuncSetAttribute(k_field<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.field_smem);
         if (e) return e;
         e = cudaFuncSetAttribute(k_sort_count<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sort_smem);
         if (e) return e;
-        e = cudaFuncSetAttribute(k_sort_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sort_smem);
+        e = cudaFuncSetAttribute(k_sort_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.scatter_smem);
         if (e) return e;
     }
-    return cudaFuncSetAttribute(k_sort_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_sort_cellscan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(int) * (L.maxN + 2)));
 }
 
@@ -713,23 +977,26 @@ cudaError_t launch_field(bool fp64, bool diag, int mode, const WsPtrs &W, int pa
     return cudaGetLastError();
 }
 
-int kernels_per_sort() { return 4; }
-int kernels_per_pair() { return 2; }
+int kernels_per_sort() { return 5; }
+int kernels_per_pair() { return 7; }
 
 cudaError_t launch_sort(bool fp64, const WsPtrs &W, const void *pools, const int *tab, const LaunchCfg &L,
                         cudaStream_t st)
 {
     const size_t scan_smem = sizeof(int) * (L.maxN + 2);
+    const int cs_blocks = (L.sort_col_warps * 32 + 255) / 256;
     if (fp64) {
         const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
         k_sort_count<double><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
-        k_sort_scan<<<W.D * NSP, 512, scan_smem, st>>>(W);
-        k_sort_scatter<double><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
+        k_sort_colscan<<<cs_blocks, 256, 0, st>>>(W, L.sort_warp_base);
+        k_sort_cellscan<<<W.D * NSP, 512, scan_smem, st>>>(W);
+        k_sort_scatter<double><<<L.sort_blocks, SORT_WARPS * 32, L.scatter_smem, st>>>(W, P, tab);
     } else {
         const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
         k_sort_count<float><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
-        k_sort_scan<<<W.D * NSP, 512, scan_smem, st>>>(W);
-        k_sort_scatter<float><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
+        k_sort_colscan<<<cs_blocks, 256, 0, st>>>(W, L.sort_warp_base);
+        k_sort_cellscan<<<W.D * NSP, 512, scan_smem, st>>>(W);
+        k_sort_scatter<float><<<L.sort_blocks, SORT_WARPS * 32, L.scatter_smem, st>>>(W, P, tab);
     }
     k_sort_finish<<<1, 256, 0, st>>>(W);
     return cudaGetLastError();
@@ -738,16 +1005,28 @@ cudaError_t launch_sort(bool fp64, const WsPtrs &W, const void *pools, const int
 cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par, const LaunchCfg &L,
                         cudaStream_t st)
 {
-    const int blocks = (W.total_cells * 32 + 255) / 256;
-    if (fp64) {
-        const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
-        k_pair<double><<<blocks, 256, 0, st>>>(W, P, par);
-        k_pair_append<double><<<W.D, 256, sizeof(int) * (L.maxN + 1), st>>>(W, P);
-    } else {
-        const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
-        k_pair<float><<<blocks, 256, 0, st>>>(W, P, par);
-        k_pair_append<float><<<W.D, 256, sizeof(int) * (L.maxN + 1), st>>>(W, P);
+    const int fix_blocks = (W.total_cells * 32 + 255) / 256;
+    const int ps_of[3] = {0, 1, 0};  // projectile species of (13), (14), (19)
+    for (int k = 0; k < 3; ++k) {
+        const int ps = ps_of[k];
+        if (fp64) {
+            const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
+            if (L.pair_blocks_sp[ps] > 0)
+                k_pair_eval<double><<<L.pair_blocks_sp[ps], 256, 0, st>>>(W, P, par, k, L.pair_tab_sp[ps]);
+            k_pair_fix<double><<<fix_blocks, 256, 0, st>>>(W, P, par, k);
+        } else {
+            const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
+            if (L.pair_blocks_sp[ps] > 0)
+                k_pair_eval<float><<<L.pair_blocks_sp[ps], 256, 0, st>>>(W, P, par, k, L.pair_tab_sp[ps]);
+            k_pair_fix<float><<<fix_blocks, 256, 0, st>>>(W, P, par, k);
+        }
     }
+    if (fp64)
+        k_pair_append<double><<<W.D, 256, sizeof(int) * (L.maxN + 1), st>>>(
+            W, *static_cast<const Pools<double> *>(pools));
+    else
+        k_pair_append<float><<<W.D, 256, sizeof(int) * (L.maxN + 1), st>>>(
+            W, *static_cast<const Pools<float> *>(pools));
     return cudaGetLastError();
 }
 

@@ -11,8 +11,12 @@ struct LaunchCfg {
     size_t push_smem;     // dynamic shared memory of the push (non-diag)
     size_t push_smem_diag;
     int sort_blocks;      // sum over (d, s) of sort blocks
-    size_t sort_smem;
-    int pair_blocks;
+    size_t sort_smem;     // count kernel
+    size_t scatter_smem;  // scatter kernel
+    int sort_col_warps;   // warps of the column scan (sum over (d, s) of N+1)
+    const int *sort_warp_base;  // device [D*3+1]: first column-scan warp per (d, s)
+    int pair_blocks_sp[NSP];          // evaluation blocks per projectile species
+    const int *pair_tab_sp[NSP];      // device [(d, tile)] tables per species
     size_t field_smem;
     int maxN;             // largest cell count over discharges
     int eedf_max, fm_max; // largest histogram sizes (shared-memory copies in the push)
@@ -22,6 +26,9 @@ struct LaunchCfg {
 cudaError_t launch_push(bool fp64, bool diag, const WsPtrs &W, const void *pools,
                         int par, const LaunchCfg &L, cudaStream_t s);
 cudaError_t push_configure(bool fp64, LaunchCfg &L, int num_sms);
+// births of the push appended in parent order
+cudaError_t launch_births(bool fp64, const WsPtrs &W, const void *pools, int par, int max_blocks,
+                          cudaStream_t s);
 
 // charge density -> Poisson -> field; per-step bookkeeping (mode 0), or a
 // read-only evaluation of the fields of the current state (mode 1)

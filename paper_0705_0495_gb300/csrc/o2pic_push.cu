@@ -2,26 +2,35 @@
 //
 // One launch advances every live superparticle of every discharge by one time
 // step (paper Sec. II (i) and Sec. III):
-//   gather E at x^n (linear interpolation from a shared-memory copy of the
-//   node field) -> leapfrog v^{n+1/2}, x^{n+1} -> absorption at x < 0 or
-//   x >= L -> null-collision test against nu_max (one Philox4x32-10 block
-//   serves four consecutive slots) -> for candidates, a gas molecule from the
-//   Maxwellian at T, channel walk over sum_j n_j sigma_j(E) u and the
-//   kinematics of the chosen reaction -> births staged per chunk and appended
-//   in parent order through a decoupled look-back over chunks -> linear
-//   charge assignment of x^{n+1} into a per-block shared-memory grid (warp
-//   aggregated, exact fixed point in the FP32 path), flushed to the global
-//   accumulators with one atomic per touched node.
+//   phase A, four consecutive slots per thread: gather E at x^n (linear
+//   interpolation from a shared-memory copy of the node field) -> leapfrog
+//   v^{n+1/2}, x^{n+1} -> absorption at x < 0 or x >= L -> null-collision
+//   test against nu_max (one Philox4x32-10 block serves the four slots) ->
+//   linear charge assignment of x^{n+1} into a per-block shared-memory grid
+//   (warp aggregated, exact fixed point in the FP32 path) -> candidates
+//   queued in shared memory;
+//   phase B, one queued candidate per thread (no divergence across the
+//   collision code): a gas molecule from the Maxwellian at T, the channel
+//   walk over sum_j n_j sigma_j(E) u and the kinematics of the chosen
+//   reaction; a particle that dies leaves the shared grid again; births are
+//   staged per 1024-slot tile and appended in parent order by k_births.
+//   The shared grid is flushed to the global accumulators with one atomic
+//   per touched node.
 //
 // Particles are SoA with the position as (int32 cell, offset in [0,1)) and
-// velocities in cells per step.  Slots are processed in chunks of 1024
-// (256 threads x 4 consecutive slots, 16-byte vector loads), handed out in
-// increasing order by an atomic ticket to a persistent grid.
+// velocities in cells per step.  Slots are processed in tiles of 1024
+// (256 threads x 4 consecutive slots, 16-byte vector loads); a persistent grid
+// takes TILES_PER_TICKET tiles at a time from an atomic ticket.  No block ever
+// waits for another.
 #include <cstdio>
 
 #include "o2pic_launch.h"
 
 namespace o2 {
+
+// three 256-thread blocks per SM in the FP32 path (the rare collision path
+// may spill a little), two in the FP64 path
+template <typename Real> struct PushOcc { static constexpr int blocks = sizeof(Real) == 4 ? 3 : 2; };
 
 template <typename Real> struct AccT;
 template <> struct AccT<float> { using T = unsigned long long; };
@@ -67,17 +76,6 @@ __device__ __forceinline__ void st4(double *p, const double v[4])
     reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 // Interpolation of the gas-channel cross sections of one projectile at the
 // centre-of-mass energy E [eV]: piecewise linear in E on the shared geometric
 // grid, end values held outside it, zero below each channel's threshold.
@@ -102,7 +100,7 @@ __device__ __forceinline__ XsPoint<Real> xs_locate(const TableDesc &T, const Rea
         p.region = 2; p.k = n - 2; p.f = Real(1);
         return p;
     }
-    Real t = (log(E) - Real(T.lnE0)) * Real(T.inv_dlog);
+    Real t = (log(E) - pick<Real>(T.lnE0, T.lnE0_f)) * pick<Real>(T.inv_dlog, T.inv_dlog_f);
     int k = (int)t;
     k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
     // the logarithm only guesses the segment; the node comparison decides
@@ -118,7 +116,7 @@ template <typename Real>
 __device__ __forceinline__ Real xs_value(const TableDesc &T, const Real *lutS,
                                          const XsPoint<Real> &p, Real E)
 {
-    if (E < Real(T.th)) return Real(0);
+    if (E < pick<Real>(T.th, T.th_f)) return Real(0);
     const Real *s = lutS + T.off;
     if (p.region == 0) return s[0];
     if (p.region == 2) return s[T.n - 1];
@@ -165,11 +163,19 @@ struct BirthStage {
 };
 
 template <typename Real>
+struct BirthRec {
+    int c;
+    int pad;
+    Real off, vx, vy, vz;
+};
+
+template <typename Real>
 __device__ __forceinline__ void stage_birth(const BirthStage<Real> &B, Ctl *ctl, int tag,
-                                            int sp, int c, Real off, const Real v[3])
+                                            int sp, int c, Real off, const Real v[3], int &staged)
 {
+    ++staged;
     int pos = atomicAdd(B.nb, 1);
-    if (pos >= BIRTH_CAP) {
+    if (pos >= BSTAGE) {
         set_status(ctl, ST_BIRTHBUF);
         return;
     }
@@ -184,10 +190,10 @@ __device__ __forceinline__ void stage_birth(const BirthStage<Real> &B, Ctl *ctl,
 // One gas-target candidate (null-collision method).  Returns false if the
 // particle died.  v is updated in place; products are staged.
 template <typename Real>
-__device__ __noinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int s, unsigned idx,
+__device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int s, unsigned idx,
                                          unsigned long long step, Real &vx, Real &vy, Real &vz,
                                          int c, Real off, int tag, const BirthStage<Real> &B,
-                                         unsigned *s_cnt)
+                                         unsigned *s_cnt, int &staged)
 {
     const SpeciesC &S = Dd.sp[s];
     const Real *lutE = Lut<Real>::E(W);
@@ -197,14 +203,15 @@ __device__ __noinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int s,
     Real n0, n1, n2, n3;
     box_muller<Real>(a.x, a.y, n0, n1);
     box_muller<Real>(a.z, a.w, n2, n3);
-    const Real vg = Real(S.vgas_n);
+    const Real vg = pick<Real>(S.vgas_n, S.vgas_n_f);
     Real V[3] = {vg * n0, vg * n1, vg * n2};
     Real v[3] = {vx, vy, vz};
     Real g0 = v[0] - V[0], g1 = v[1] - V[1], g2 = v[2] - V[2];
     Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
     Real u = sqrt(u2);
-    Real E = Real(S.Ek) * u2;
-    Real target = unif<Real>(b.x) * Real(S.numax_n);
+    Real E = pick<Real>(S.Ek, S.Ek_f) * u2;
+    const Real numax_n = pick<Real>(S.numax_n, S.numax_n_f);
+    Real target = unif<Real>(b.x) * numax_n;
     const TableDesc &T0 = W.tables[S.table_lo];
     XsPoint<Real> pt = xs_locate<Real>(T0, lutE, E);
     Real cum = Real(0);
@@ -212,17 +219,17 @@ __device__ __noinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int s,
     for (int j = 0; j < S.nch; ++j) {
         const GasChan &ch = S.ch[j];
         Real sg = xs_value<Real>(W.tables[ch.table], lutS, pt, E);
-        cum += Real(ch.coef) * sg * u;
+        cum += pick<Real>(ch.coef, ch.coef_f) * sg * u;
         if (chosen < 0 && target < cum) chosen = j;
     }
-    if (cum > Real(S.numax_n)) atomicAdd(&s_cnt[C_VIOL_GAS], 1u);
+    if (cum > numax_n) atomicAdd(&s_cnt[C_VIOL_GAS], 1u);
     if (chosen < 0) return true;  // null event
     const GasChan &ch = S.ch[chosen];
     const int r = ch.reaction;
     atomicAdd(&s_cnt[C_EVENTS + r], 1u);
     Real nd[3];
     iso_dir<Real>(unif<Real>(b.y), unif<Real>(b.z), nd);
-    const Real mf = Real(S.mfrac), Mf = Real(S.Mfrac);
+    const Real mf = pick<Real>(S.mfrac, S.mfrac_f), Mf = pick<Real>(S.Mfrac, S.Mfrac_f);
     Real vo[3], Vo[3];
     switch (r) {
     case 4: case 5:
@@ -239,43 +246,43 @@ __device__ __noinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int s,
         return true;
     case 15: {
         const TableDesc &Tc = W.tables[ch.table];
-        Real Ea = E - Real(Tc.th);
+        Real Ea = E - pick<Real>(Tc.th, Tc.th_f);
         Ea = Ea > Real(0) ? Ea : Real(0);
-        Real w = sqrt(Ea * Real(Dd.f15));
+        Real w = sqrt(Ea * pick<Real>(Dd.f15, Dd.f15_f));
         Real pv[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) pv[q] = mf * v[q] + Mf * V[q] + w * nd[q];
-        stage_birth<Real>(B, W.ctl, tag, 1, c, off, pv);
+        stage_birth<Real>(B, W.ctl, tag, 1, c, off, pv, staged);
         return false;
     }
     case 16: {
-        Real sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * Real(Dd.f16);
+        Real sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * pick<Real>(Dd.f16, Dd.f16_f);
         Real pv[3] = {sp * nd[0], sp * nd[1], sp * nd[2]};
-        stage_birth<Real>(B, W.ctl, tag, 0, c, off, pv);
+        stage_birth<Real>(B, W.ctl, tag, 0, c, off, pv, staged);
         return false;
     }
     case 17: {
-        Real w = sqrt(E * Real(Dd.f17));
+        Real w = sqrt(E * pick<Real>(Dd.f17, Dd.f17_f));
         Real pv[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) pv[q] = mf * v[q] + Mf * V[q] + w * nd[q];
-        stage_birth<Real>(B, W.ctl, tag, 0, c, off, pv);
+        stage_birth<Real>(B, W.ctl, tag, 0, c, off, pv, staged);
         return false;
     }
     case 18: {
-        cm_scatter<Real>(mf, Mf, v, V, Real(ch.dloss), nd, vo, Vo);
+        cm_scatter<Real>(mf, Mf, v, V, pick<Real>(ch.dloss, ch.dloss_f), nd, vo, Vo);
         uint4 e = rng_block(Dd.seed, Dd.discharge, s, 1, 0, 2, step, idx);
         Real n2v[3];
         iso_dir<Real>(unif<Real>(e.x), unif<Real>(e.y), n2v);
         Real e2[3] = {Vo[0], Vo[1], Vo[2]};
         ee_elastic<Real>(vo, e2, n2v);
         vx = vo[0]; vy = vo[1]; vz = vo[2];
-        stage_birth<Real>(B, W.ctl, tag, 0, c, off, e2);
-        stage_birth<Real>(B, W.ctl, tag | 1, 2, c, off, Vo);
+        stage_birth<Real>(B, W.ctl, tag, 0, c, off, e2, staged);
+        stage_birth<Real>(B, W.ctl, tag | 1, 2, c, off, Vo, staged);
         return true;
     }
     default:  // 7-12: inelastic, Eq. 5
-        cm_scatter<Real>(mf, Mf, v, V, Real(ch.dloss), nd, vo, Vo);
+        cm_scatter<Real>(mf, Mf, v, V, pick<Real>(ch.dloss, ch.dloss_f), nd, vo, Vo);
         vx = vo[0]; vy = vo[1]; vz = vo[2];
         return true;
     }
@@ -312,6 +319,21 @@ __device__ __forceinline__ void deposit_warp(double *sAcc, int c, double off)
     }
 }
 
+// removal of one particle deposited in phase A (it died in a collision):
+// the same fixed-point weights, so the accumulator returns exactly
+__device__ __forceinline__ void deposit_shared_remove(unsigned long long *sAcc, int c, float off)
+{
+    const unsigned w1 = __float2uint_rn(off * (float)(1 << FIX_BITS));
+    const unsigned w0 = (1u << FIX_BITS) - w1;
+    atomicAdd(&sAcc[c], 0ull - (unsigned long long)w0);
+    atomicAdd(&sAcc[c + 1], 0ull - (unsigned long long)w1);
+}
+__device__ __forceinline__ void deposit_shared_remove(double *sAcc, int c, double off)
+{
+    atomicAdd(&sAcc[c], -(1.0 - off));
+    atomicAdd(&sAcc[c + 1], -off);
+}
+
 // charge of one particle added to (sign > 0) or removed from the global
 // accumulator of its species (births, pair-pass kills)
 __device__ __forceinline__ void deposit_global(unsigned long long *acc, int c, float off, int sign)
@@ -333,26 +355,89 @@ template <typename Real> __device__ __forceinline__ typename AccT<Real>::T *acc_
 template <> __device__ __forceinline__ unsigned long long *acc_global<float>(const WsPtrs &W) { return W.acc_fix; }
 template <> __device__ __forceinline__ double *acc_global<double>(const WsPtrs &W) { return W.acc_dbl; }
 
+// Charge of the four slots of a thread into the shared grid.  When every
+// lane's four slots sit in one cell, a lane's four weights are summed first
+// (4 * 32 * 2^FIX_BITS < 2^32); when the whole warp shares that cell, no
+// match is needed at all.
+__device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep[4], const float off[4])
+{
+    unsigned w0[4], w1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        w1[k] = dep[k] >= 0 ? __float2uint_rn(off[k] * (float)(1 << FIX_BITS)) : 0u;
+        w0[k] = dep[k] >= 0 ? (1u << FIX_BITS) - w1[k] : 0u;
+    }
+    const int lane = threadIdx.x & 31;
+    const bool same = dep[0] >= 0 && dep[1] == dep[0] && dep[2] == dep[0] && dep[3] == dep[0];
+    if (__all_sync(0xffffffffu, same)) {
+        const unsigned a = w0[0] + w0[1] + w0[2] + w0[3];
+        const unsigned b = w1[0] + w1[1] + w1[2] + w1[3];
+        const int c0 = __shfl_sync(0xffffffffu, dep[0], 0);
+        if (__all_sync(0xffffffffu, dep[0] == c0)) {
+            const unsigned sa = __reduce_add_sync(0xffffffffu, a);
+            const unsigned sb = __reduce_add_sync(0xffffffffu, b);
+            if (lane == 0) {
+                atomicAdd(&sAcc[c0], (unsigned long long)sa);
+                atomicAdd(&sAcc[c0 + 1], (unsigned long long)sb);
+            }
+        } else {
+            const unsigned peers = __match_any_sync(0xffffffffu, dep[0]);
+            const unsigned sa = __reduce_add_sync(peers, a);
+            const unsigned sb = __reduce_add_sync(peers, b);
+            if (lane == __ffs(peers) - 1) {
+                atomicAdd(&sAcc[dep[0]], (unsigned long long)sa);
+                atomicAdd(&sAcc[dep[0] + 1], (unsigned long long)sb);
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned peers = __match_any_sync(0xffffffffu, dep[k]);
+        const unsigned sa = __reduce_add_sync(peers, w0[k]);
+        const unsigned sb = __reduce_add_sync(peers, w1[k]);
+        if (dep[k] >= 0 && lane == __ffs(peers) - 1) {
+            atomicAdd(&sAcc[dep[k]], (unsigned long long)sa);
+            atomicAdd(&sAcc[dep[k] + 1], (unsigned long long)sb);
+        }
+    }
+}
+__device__ __forceinline__ void deposit4(double *sAcc, const int dep[4], const double off[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (dep[k] >= 0) {
+            atomicAdd(&sAcc[dep[k]], 1.0 - off[k]);
+            atomicAdd(&sAcc[dep[k] + 1], off[k]);
+        }
+    }
+}
+
 template <typename Real, bool DIAG>
-__global__ void __launch_bounds__(PUSH_THREADS)
+__global__ void __launch_bounds__(PUSH_THREADS, PushOcc<Real>::blocks)
 k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
 {
     using Acc = typename AccT<Real>::T;
+    constexpr int NW = PUSH_THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     Acc *sAcc = reinterpret_cast<Acc *>(smem);
     Real *sE = reinterpret_cast<Real *>(sAcc + (Nmax + 2));
-    Real *bOff = sE + (Nmax + 2);
-    Real *bVx = bOff + BIRTH_CAP;
-    Real *bVy = bVx + BIRTH_CAP;
-    Real *bVz = bVy + BIRTH_CAP;
-    int *bCell = reinterpret_cast<int *>(bVz + BIRTH_CAP);
-    int *bTag = bCell + BIRTH_CAP;
-    int *bRank = bTag + BIRTH_CAP;
-    unsigned *sEedf = reinterpret_cast<unsigned *>(bRank + BIRTH_CAP);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    // per-warp candidate queue (index, vx after the push) and staged births
+    Real *qVx = sE + (Nmax + 2) + w * QCAP;
+    Real *bOff = sE + (Nmax + 2) + NW * QCAP + w * BSTAGE;
+    Real *bVx = bOff + NW * BSTAGE;
+    Real *bVy = bVx + NW * BSTAGE;
+    Real *bVz = bVy + NW * BSTAGE;
+    int *ibase = reinterpret_cast<int *>(sE + (Nmax + 2) + NW * QCAP + 4 * NW * BSTAGE);
+    int *qIdx = ibase + w * QCAP;
+    int *bCell = ibase + NW * QCAP + w * BSTAGE;
+    int *bTag = ibase + NW * QCAP + NW * BSTAGE + w * BSTAGE;
+    unsigned *sEedf = reinterpret_cast<unsigned *>(ibase + NW * QCAP + 2 * NW * BSTAGE);
     unsigned *sFm = sEedf + eedf_max;
 
-    __shared__ int s_ticket, s_nb;
-    __shared__ int s_bc[NSP], s_bx[NSP];
+    __shared__ int s_ticket[2];
+    __shared__ int s_wnb[NW];
     __shared__ unsigned s_cnt[C_NCOUNT];
 
     Ctl *ctl = W.ctl;
@@ -363,11 +448,13 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     int *cellA = P.cell[cur];
     Real *offA = P.off[cur], *vxA = P.vx[cur], *vyA = P.vy[cur], *vzA = P.vz[cur];
     Acc *accG = acc_global<Real>(W);
-    const int tid = threadIdx.x;
-    BirthStage<Real> B{bCell, bTag, bOff, bVx, bVy, bVz, &s_nb};
+    BirthRec<Real> *stage = reinterpret_cast<BirthRec<Real> *>(W.births);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    BirthStage<Real> B{bCell, bTag, bOff, bVx, bVy, bVz, &s_wnb[w]};
 
     int ds = -1, d = -1;
     for (int q = tid; q < C_NCOUNT; q += PUSH_THREADS) s_cnt[q] = 0;
+    if (lane == 0) s_wnb[w] = 0;
 
     auto flush = [&](int fds) {
         const int fd = fds / NSP, fs = fds % NSP;
@@ -392,21 +479,18 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         __syncthreads();
     };
 
-    for (;;) {
-        if (tid == 0) {
-            s_ticket = (int)atomicAdd(&ctl->ticket, 1u);
-            s_nb = 0;
-        }
-        if (tid < NSP) s_bc[tid] = 0;
+    for (int it = 0;; ++it) {
+        // two ticket buffers: a buffer is rewritten only after the barrier
+        // that every reader of its previous value has passed
+        if (tid == 0) s_ticket[it & 1] = (int)atomicAdd(&ctl->ticket, (unsigned)TILES_PER_TICKET);
         __syncthreads();
-        const int t = s_ticket;
-        if (t >= total) break;
+        const int tbeg = s_ticket[it & 1];
+        if (tbeg >= total) break;
+        // tiles of one (discharge, species) start at a multiple of
+        // TILES_PER_TICKET, so a ticket belongs to one (d, s) or to padding
         int nx = ds < 0 ? 0 : ds;
-        while (nx < nds && !(t >= W.cnt[nx].chunk0 && t < W.cnt[nx].chunk0 + W.cnt[nx].nchunk)) ++nx;
-        if (nx >= nds) {  // cannot happen with a consistent chunk table
-            if (tid == 0) set_status(ctl, ST_BADSTATE);
-            break;
-        }
+        while (nx < nds && !(tbeg >= W.cnt[nx].chunk0 && tbeg < W.cnt[nx].chunk0 + W.cnt[nx].nchunk)) ++nx;
+        if (nx >= nds) continue;
         if (nx != ds) {
             if (ds >= 0) flush(ds);
             const int nd = nx / NSP;
@@ -431,202 +515,353 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         const Counts &C = W.cnt[ds];
         const int N = Dd.N;
         const int pb = Dd.pbase[s];
-        const int base = pb + (t - C.chunk0) * CHUNK;
         const int end = pb + C.n_snap;
-        const int i0 = base + 4 * tid;
-        const Real qm = Real(S.qm);
+        const int tend = min(tbeg + TILES_PER_TICKET, C.chunk0 + C.nchunk);
+        const Real qm = pick<Real>(S.qm, S.qm_f);
+        const unsigned tnull = S.tnull;
+        const int wbase0 = pb + (tbeg - C.chunk0) * CHUNK + w * SUBTILE;  // warp's first sub-tile
+        int qn = 0;  // warp-uniform queue length
 
-        int c[4];
-        Real off[4], vx[4];
-        const bool full = i0 + 3 < end;
-        if (full) {
-            ld4(cellA + i0, c);
-            ld4(offA + i0, off);
-            ld4(vxA + i0, vx);
-        } else {
+        // ---- phase B: the queued candidates of this warp, one per lane;
+        // births grouped by sub-tile and written in parent order
+        auto drain = [&]() {
+            if (lane == 0) atomicAdd(&s_cnt[C_CANDS], (unsigned)qn);
+            int staged = 0;
+            for (int q = lane; q < qn; q += 32) {
+                const int i = qIdx[q];
+                const int cq = cellA[i];
+                const Real oq = offA[i];
+                Real ux = qVx[q], vy = vyA[i], vz = vzA[i];
+                const int rel = i - wbase0;  // (tile offset) * CHUNK + slot in sub-tile
+                const int tag = (((rel / CHUNK) << 7) | (rel % CHUNK)) << 1;
+                const bool alive = gas_collide<Real>(W, Dd, s, (unsigned)(i - pb), step, ux, vy, vz, cq, oq,
+                                                     tag, B, s_cnt, staged);
+                if (alive) {
+                    vxA[i] = ux;
+                    vyA[i] = vy;
+                    vzA[i] = vz;
+                } else {
+                    cellA[i] = -1;
+                    deposit_shared_remove(sAcc, cq, oq);
+                }
+            }
+            qn = 0;
+            if (!__any_sync(0xffffffffu, staged != 0)) return;
+            __syncwarp();
+            const int nb = min(s_wnb[w], BSTAGE);
+            for (int r = lane; r < nb; r += 32) {
+                const int tg = bTag[r];  // ((tile offset << 7 | slot) << 1 | product) << 2 | species
+                const int tile_off = tg >> 10, sp = tg & 3;
+                int rank = 0, count = 0, below = 0;
+                for (int q = 0; q < nb; ++q) {
+                    const int tq = bTag[q];
+                    if ((tq >> 10) != tile_off) continue;
+                    const int sq = tq & 3;
+                    if (sq == sp) {
+                        ++count;
+                        rank += tq < tg;
+                    } else if (sq < sp) {
+                        ++below;
+                    }
+                }
+                const int sub = (tbeg + tile_off) * SUBTILES + w;
+                if (below + rank < BIRTH_CAP_W) {
+                    BirthRec<Real> &rec = stage[(size_t)sub * BIRTH_CAP_W + below + rank];
+                    rec.c = bCell[r];
+                    rec.off = bOff[r];
+                    rec.vx = bVx[r];
+                    rec.vy = bVy[r];
+                    rec.vz = bVz[r];
+                } else {
+                    set_status(ctl, ST_BIRTHBUF);
+                }
+                if (rank == 0) W.tile_cnt[(size_t)sub * NSP + sp] = count;
+            }
+            __syncwarp();
+            if (lane == 0) s_wnb[w] = 0;
+            __syncwarp();
+        };
+
+        for (int t = tbeg; t < tend; ++t) {
+            const int sbase = wbase0 + (t - tbeg) * CHUNK;
+            const int i0 = sbase + 4 * lane;
+            const int sub = t * SUBTILES + w;
+            if (lane < NSP) W.tile_cnt[(size_t)sub * NSP + lane] = 0;
+
+            // ---- phase A: push, absorb, null test, deposit, candidate queue
+            int c[4];
+            Real off[4], vx[4];
+            const bool full = i0 + 3 < end;
+            if (full) {
+                ld4(cellA + i0, c);
+                ld4(offA + i0, off);
+                ld4(vxA + i0, vx);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const bool in = i0 + k < end;
+                    c[k] = in ? cellA[i0 + k] : -2;
+                    off[k] = in ? offA[i0 + k] : Real(0);
+                    vx[k] = in ? vxA[i0 + k] : Real(0);
+                }
+            }
+            uint4 w4 = make_uint4(0, 0, 0, 0);
+            if (c[0] >= 0 || c[1] >= 0 || c[2] >= 0 || c[3] >= 0)
+                w4 = rng_block(Dd.seed, Dd.discharge, s, 0, 0, 0, step, (unsigned)((i0 - pb) >> 2));
+            const unsigned wk[4] = {w4.x, w4.y, w4.z, w4.w};
+            unsigned nslots = 0, nlive = 0;
+            int dep[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const bool in = i0 + k < end;
-                c[k] = in ? cellA[i0 + k] : -2;
-                off[k] = in ? offA[i0 + k] : Real(0);
-                vx[k] = in ? vxA[i0 + k] : Real(0);
-            }
-        }
-        uint4 w4 = make_uint4(0, 0, 0, 0);
-        if (c[0] >= 0 || c[1] >= 0 || c[2] >= 0 || c[3] >= 0)
-            w4 = rng_block(Dd.seed, Dd.discharge, s, 0, 0, 0, step, (unsigned)((i0 - pb) >> 2));
-        const unsigned wk[4] = {w4.x, w4.y, w4.z, w4.w};
-        unsigned nslots = 0, ncand = 0;
-
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int ck = c[k];
-            int dep = -1;
-            if (ck >= -1) ++nslots;
-            if (ck >= 0) {
-                const Real e0 = sE[ck], e1 = sE[ck + 1];
-                const Real ep = e0 + off[k] * (e1 - e0);
-                Real v = vx[k] + qm * ep;
-                Real o = off[k] + v;
-                Real fl = floor(o);
-                bool bad = !(fl > Real(-2 * N - 4) && fl < Real(2 * N + 4));
-                int cn = bad ? (v < Real(0) ? -1 : N) : ck + (int)fl;
-                o -= fl;
-                if (o >= Real(1)) { o -= Real(1); cn += 1; }
-                vx[k] = v;
-                if (cn < 0 || cn >= N) {
-                    const int wall = cn < 0 ? 0 : 1;
-                    atomicAdd(&s_cnt[C_ABS + 2 * s + wall], 1u);
-                    if (s == 2 && Dd.iedf_bins > 0) {
-                        Real vy = vyA[i0 + k], vz = vzA[i0 + k];
-                        Real Ei = Real(S.ke_eV) * (v * v + vy * vy + vz * vz);
-                        Real bb = floor(Ei * Real(Dd.iedf_scale));
-                        if (bb >= Real(0) && bb < Real(Dd.iedf_bins))
-                            atomicAdd(&W.iedf[Dd.iedf_base + wall * Dd.iedf_bins + (int)bb], 1u);
-                    }
-                    c[k] = -1;
-                } else {
-                    off[k] = o;
-                    c[k] = cn;
-                    bool alive = true;
-                    Real vy = Real(0), vz = Real(0);
-                    bool have_v = false;
-                    if (wk[k] < S.tnull) {
-                        ++ncand;
-                        vy = vyA[i0 + k];
-                        vz = vzA[i0 + k];
-                        have_v = true;
-                        Real ux = vx[k];
-                        alive = gas_collide<Real>(W, Dd, s, (unsigned)(i0 + k - pb), step, ux, vy, vz,
-                                                  cn, o, ((tid << 2) | k) << 1, B, s_cnt);
-                        if (alive) {
-                            vx[k] = ux;
-                            vyA[i0 + k] = vy;
-                            vzA[i0 + k] = vz;
-                        } else {
-                            c[k] = -1;
+                const int ck = c[k];
+                dep[k] = -1;
+                bool cand = false;
+                if (ck >= -1) ++nslots;
+                if (ck >= 0) {
+                    ++nlive;
+                    const Real e0 = sE[ck], e1 = sE[ck + 1];
+                    const Real ep = e0 + off[k] * (e1 - e0);
+                    const Real v = vx[k] + qm * ep;
+                    Real o = off[k] + v;
+                    const Real fl = floor(o);
+                    const bool bad = !(fl > Real(-2 * N - 4) && fl < Real(2 * N + 4));
+                    int cn = bad ? (v < Real(0) ? -1 : N) : ck + (int)fl;
+                    o -= fl;
+                    if (o >= Real(1)) { o -= Real(1); cn += 1; }
+                    vx[k] = v;
+                    if (cn < 0 || cn >= N) {
+                        const int wall = cn < 0 ? 0 : 1;
+                        atomicAdd(&s_cnt[C_ABS + 2 * s + wall], 1u);
+                        if (s == 2 && Dd.iedf_bins > 0) {
+                            const Real vy = vyA[i0 + k], vz = vzA[i0 + k];
+                            const Real Ei = pick<Real>(S.ke_eV, S.ke_eV_f) * (v * v + vy * vy + vz * vz);
+                            const Real bb = floor(Ei * pick<Real>(Dd.iedf_scale, Dd.iedf_scale_f));
+                            if (bb >= Real(0) && bb < Real(Dd.iedf_bins))
+                                atomicAdd(&W.iedf[Dd.iedf_base + wall * Dd.iedf_bins + (int)bb], 1u);
                         }
-                    }
-                    if (alive) {
-                        dep = cn;
+                        c[k] = -1;
+                    } else {
+                        off[k] = o;
+                        c[k] = cn;
+                        dep[k] = cn;
+                        cand = wk[k] < tnull;
                         if (DIAG) {
+                            // distributions after the free flight, before collisions
                             if (s == 0 && cn == N / 2 && Dd.eedf_bins > 0) {
-                                if (!have_v) { vy = vyA[i0 + k]; vz = vzA[i0 + k]; }
-                                Real Ee = Real(S.ke_eV) * (vx[k] * vx[k] + vy * vy + vz * vz);
-                                Real bb = floor(Ee * Real(Dd.eedf_scale));
+                                const Real vy = vyA[i0 + k], vz = vzA[i0 + k];
+                                const Real Ee = pick<Real>(S.ke_eV, S.ke_eV_f) * (v * v + vy * vy + vz * vz);
+                                const Real bb = floor(Ee * pick<Real>(Dd.eedf_scale, Dd.eedf_scale_f));
                                 if (bb >= Real(0) && bb < Real(Dd.eedf_bins)) atomicAdd(&sEedf[(int)bb], 1u);
                             }
                             if (s == 1 && Dd.fm_bins > 0) {
-                                Real Es = Real(S.ke_eV) * vx[k] * vx[k];
-                                if (vx[k] < Real(0)) Es = -Es;
-                                Real bb = floor((Es + Real(Dd.fm_emax)) * Real(Dd.fm_scale));
+                                Real Es = pick<Real>(S.ke_eV, S.ke_eV_f) * v * v;
+                                if (v < Real(0)) Es = -Es;
+                                const Real bb = floor((Es + pick<Real>(Dd.fm_emax, Dd.fm_emax_f)) *
+                                                      pick<Real>(Dd.fm_scale, Dd.fm_scale_f));
                                 if (bb >= Real(0) && bb < Real(Dd.fm_bins)) {
-                                    int xb = (int)(((long long)cn * Dd.fm_xbins) / N);
+                                    const int xb = (int)(((long long)cn * Dd.fm_xbins) / N);
                                     atomicAdd(&sFm[xb * Dd.fm_bins + (int)bb], 1u);
                                 }
                             }
                         }
                     }
                 }
+                const unsigned m = __ballot_sync(0xffffffffu, cand);
+                if (cand) {
+                    const int pos = qn + __popc(m & lt_mask);
+                    qIdx[pos] = i0 + k;
+                    qVx[pos] = vx[k];
+                }
+                qn += __popc(m);
             }
-            deposit_warp(sAcc, dep, off[k]);
-        }
-        if (nslots) atomicAdd(&s_cnt[C_SLOTS], nslots);
-        if (ncand) atomicAdd(&s_cnt[C_CANDS], ncand);
-        if (full) {
-            st4(cellA + i0, c);
-            st4(offA + i0, off);
-            st4(vxA + i0, vx);
-        } else {
+            deposit4(sAcc, dep, off);
+            {
+                const unsigned ws = __reduce_add_sync(0xffffffffu, nslots);
+                const unsigned wl = __reduce_add_sync(0xffffffffu, nlive);
+                if (lane == 0) {
+                    if (ws) atomicAdd(&s_cnt[C_SLOTS], ws);
+                    if (wl) atomicAdd(&s_cnt[C_LIVE], wl);
+                }
+            }
+            if (full) {
+                st4(cellA + i0, c);
+                st4(offA + i0, off);
+                st4(vxA + i0, vx);
+            } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (i0 + k < end) {
-                    cellA[i0 + k] = c[k];
-                    offA[i0 + k] = off[k];
-                    vxA[i0 + k] = vx[k];
-                }
-            }
-        }
-        __syncthreads();
-
-        // ---- births: order within the chunk by (slot, product), then the
-        // decoupled look-back gives this chunk's place among all chunks of
-        // its discharge (chunks are numbered in (species, slot) order).
-        const int nb = s_nb < BIRTH_CAP ? s_nb : BIRTH_CAP;
-        for (int r = tid; r < nb; r += PUSH_THREADS) {
-            const int tg = bTag[r];
-            const int sp = tg & 3;
-            int rank = 0;
-            for (int q = 0; q < nb; ++q) {
-                const int tq = bTag[q];
-                rank += ((tq & 3) == sp) && (tq < tg);
-            }
-            bRank[r] = rank;
-            atomicAdd(&s_bc[sp], 1);
-        }
-        __syncthreads();
-        if (tid < NSP) {
-            const int sp = tid;
-            const unsigned long long epoch = (step + 1ull) & 0xFFFFFFFFull;
-            const int first = W.cnt[d * NSP].chunk0;
-            const unsigned own = (unsigned)s_bc[sp];
-            unsigned long long *lb = W.lb + (size_t)t * NSP + sp;
-            unsigned excl = 0;
-            if (t > first) {
-                st_release(lb, (epoch << 32) | own);
-                int j = t - 1;
-                long long spins = 0;
-                while (j >= first) {
-                    unsigned long long v = ld_acquire(W.lb + (size_t)j * NSP + sp);
-                    if ((v >> 32) != epoch) {
-                        if (++spins > SPIN_LIMIT) {
-                            set_status(ctl, ST_TIMEOUT);
-                            break;
-                        }
-                        __nanosleep(32);
-                        continue;
+                for (int k = 0; k < 4; ++k) {
+                    if (i0 + k < end) {
+                        cellA[i0 + k] = c[k];
+                        offA[i0 + k] = off[k];
+                        vxA[i0 + k] = vx[k];
                     }
-                    excl += (unsigned)(v & 0x7FFFFFFFull);
-                    if (v & 0x80000000ull) break;
-                    --j;
                 }
             }
-            st_release(lb, (epoch << 32) | 0x80000000ull | (unsigned long long)(excl + own));
-            s_bx[sp] = (int)excl;
-            const int last = W.cnt[d * NSP + 2].chunk0 + W.cnt[d * NSP + 2].nchunk - 1;
-            if (t == last) {
-                Counts *cs = W.cnt + d * NSP + sp;
-                const long long nn = (long long)cs->n_snap + excl + own;
-                cs->n = (int)(nn < Dd.cap[sp] ? nn : Dd.cap[sp]);
+            __syncwarp();
+            if (qn >= 32) drain();
+        }
+        if (qn > 0) drain();
+    }
+    if (ds >= 0) flush(ds);
+}
+
+// Births of one step appended after the survivors, per discharge and
+// product species in tile order (tiles are numbered in (parent species,
+// slot) order), i.e. in parent order; their charge is deposited.  Each block
+// takes BIRTHS_THREADS consecutive tiles (one per thread, coalesced counts)
+// in ticket order; its place among the blocks of its discharge comes from a
+// look-back over the blocks before it, which only publish sums, so the chain
+// resolves within a few block latencies (waits are bounded).
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(BIRTHS_THREADS)
+k_births(WsPtrs W, Pools<Real> P, int par)
+{
+    using Acc = typename AccT<Real>::T;
+    __shared__ int wsum[NSP][BIRTHS_THREADS / 32];
+    __shared__ int s_blk, s_excl[NSP], s_tot[NSP];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Ctl *ctl = W.ctl;
+    if (tid == 0) s_blk = (int)atomicAdd(&ctl->births_ticket, 1u);
+    __syncthreads();
+    const int blk = s_blk;  // blocks in ticket order: all earlier ones are running or done
+    const int total = ctl->total_chunks * SUBTILES;  // sub-tiles
+    const int t = blk * BIRTHS_THREADS + tid;       // this thread's sub-tile
+    const int tfirst_blk = blk * BIRTHS_THREADS;
+    if (tfirst_blk >= total) return;
+    // discharge of the block: every discharge's tiles start at a multiple of
+    // BIRTHS_THREADS, so a block never spans two discharges
+    int d = 0;
+    {
+        int lo = 0, hi = W.D;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (W.cnt[mid * NSP].chunk0 * SUBTILES <= tfirst_blk) lo = mid; else hi = mid;
+        }
+        d = lo;
+    }
+    const int T1 = (W.cnt[d * NSP + 2].chunk0 + W.cnt[d * NSP + 2].nchunk) * SUBTILES;
+    int mine[NSP] = {0, 0, 0};
+    const bool in = t < total && t < T1;
+    if (in) {
+        const int *tc = W.tile_cnt + (size_t)t * NSP;
+#pragma unroll
+        for (int q = 0; q < NSP; ++q) mine[q] = tc[q];
+    }
+    int excl[NSP];
+#pragma unroll
+    for (int q = 0; q < NSP; ++q) {
+        int v = mine[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += x;
+        }
+        if (lane == 31) wsum[q][warp] = v;
+        excl[q] = v - mine[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NSP; ++q) {
+            int v = lane < BIRTHS_THREADS / 32 ? wsum[q][lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += x;
+            }
+            if (lane < BIRTHS_THREADS / 32) wsum[q][lane] = v;
+            if (lane == 31) s_tot[q] = v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NSP; ++q) excl[q] += warp > 0 ? wsum[q][warp - 1] : 0;
+    // look-back over the earlier blocks of this discharge
+    if (tid < NSP) {
+        const int q = tid;
+        const unsigned long long epoch = (ctl->step[par] + 1ull) & 0xFFFFFFFFull;
+        const int first_blk = W.cnt[d * NSP].chunk0 * SUBTILES / BIRTHS_THREADS;
+        unsigned long long *lb = W.births_lb + (size_t)blk * NSP + q;
+        const unsigned own = (unsigned)s_tot[q];
+        unsigned ex = 0;
+        if (blk > first_blk) {
+            st_release_u64(lb, (epoch << 32) | own);
+            int j = blk - 1;
+            long long spins = 0;
+            while (j >= first_blk) {
+                const unsigned long long v = ld_acquire_u64(W.births_lb + (size_t)j * NSP + q);
+                if ((v >> 32) != epoch) {
+                    if (++spins > SPIN_LIMIT) {
+                        set_status(ctl, ST_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                    continue;
+                }
+                ex += (unsigned)(v & 0x7FFFFFFFull);
+                if (v & 0x80000000ull) break;
+                --j;
             }
         }
-        __syncthreads();
-        for (int r = tid; r < nb; r += PUSH_THREADS) {
-            const int sp = bTag[r] & 3;
-            const long long dst = (long long)W.cnt[d * NSP + sp].n_snap + s_bx[sp] + bRank[r];
-            if (dst >= Dd.cap[sp]) {
+        st_release_u64(lb, (epoch << 32) | 0x80000000ull | (unsigned long long)(ex + own));
+        s_excl[q] = (int)ex;
+        // the block holding the last tile of the discharge sets the counts
+        if (tfirst_blk <= T1 - 1 && T1 - 1 < tfirst_blk + BIRTHS_THREADS) {
+            Counts &cs = W.cnt[d * NSP + q];
+            const long long nn = (long long)cs.n_snap + ex + own;
+            cs.n = (int)(nn < W.disc[d].cap[q] ? nn : W.disc[d].cap[q]);
+        }
+    }
+    __syncthreads();
+    if (!in) return;
+    int nsum = mine[0] + mine[1] + mine[2];
+    if (nsum == 0) return;
+    const Disc &Dd = W.disc[d];
+    const int cur = ctl->cur;
+    const BirthRec<Real> *stage = reinterpret_cast<const BirthRec<Real> *>(W.births);
+    Acc *accG = acc_global<Real>(W);
+    int off0 = 0;
+    for (int q = 0; q < NSP; ++q) {
+        const int n0 = W.cnt[d * NSP + q].n_snap;
+        const int start = s_excl[q] + excl[q];
+        for (int r = 0; r < mine[q]; ++r) {
+            const BirthRec<Real> &b = stage[(size_t)t * BIRTH_CAP_W + off0 + r];
+            const long long dst = (long long)n0 + start + r;
+            if (dst >= Dd.cap[q]) {
                 set_status(ctl, ST_CAPACITY);
                 continue;
             }
-            const int g = Dd.pbase[sp] + (int)dst;
-            cellA[g] = bCell[r];
-            offA[g] = bOff[r];
-            vxA[g] = bVx[r];
-            vyA[g] = bVy[r];
-            vzA[g] = bVz[r];
-            deposit_global(accG + (size_t)sp * W.total_nodes + Dd.gbase, bCell[r], bOff[r], 1);
+            const int g = Dd.pbase[q] + (int)dst;
+            P.cell[cur][g] = b.c;
+            P.off[cur][g] = b.off;
+            P.vx[cur][g] = b.vx;
+            P.vy[cur][g] = b.vy;
+            P.vz[cur][g] = b.vz;
+            deposit_global(accG + (size_t)q * W.total_nodes + Dd.gbase, b.c, b.off, 1);
         }
-        __syncthreads();
+        off0 += mine[q];
     }
-    if (ds >= 0) flush(ds);
 }
 
 template <typename Real>
 static size_t push_smem_bytes(int Nmax, int eedf_max, int fm_max)
 {
     using Acc = typename AccT<Real>::T;
+    constexpr int NW = PUSH_THREADS / 32;
     size_t b = sizeof(Acc) * (Nmax + 2) + sizeof(Real) * (Nmax + 2);
-    b += 4 * sizeof(Real) * BIRTH_CAP + 3 * sizeof(int) * BIRTH_CAP;
+    b += sizeof(Real) * NW * QCAP + sizeof(int) * NW * QCAP;
+    b += 4 * sizeof(Real) * NW * BSTAGE + 2 * sizeof(int) * NW * BSTAGE;
     b += sizeof(unsigned) * (eedf_max + fm_max);
     return (b + 15) & ~size_t(15);
 }
@@ -682,6 +917,16 @@ cudaError_t launch_push(bool fp64, bool diag, const WsPtrs &W, const void *pools
         else
             k_push<float, false><<<L.push_blocks, PUSH_THREADS, sm, st>>>(W, P, par, L.maxN, em, fm);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_births(bool fp64, const WsPtrs &W, const void *pools, int par, int max_blocks,
+                          cudaStream_t st)
+{
+    if (fp64)
+        k_births<double><<<max_blocks, BIRTHS_THREADS, 0, st>>>(W, *static_cast<const Pools<double> *>(pools), par);
+    else
+        k_births<float><<<max_blocks, BIRTHS_THREADS, 0, st>>>(W, *static_cast<const Pools<float> *>(pools), par);
     return cudaGetLastError();
 }
 

@@ -196,7 +196,7 @@ class Discharge:
         lateral area A enters only through this number, Sec. II)."""
         if self.weight_override is not None:
             return self.weight_override
-        return self.n0_m3 * self.L / self.n_op
+        return self.n0_m3 * self.L / self.n_op if self.n_op > 0 else 0.0
 
     @property
     def ecap_eV(self):

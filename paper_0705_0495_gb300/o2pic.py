@@ -238,14 +238,16 @@ class Simulation:
         eedf = np.zeros(max(dd.eedf_bins, 1), dtype=np.int64)
         iedf = np.zeros((2, max(dd.iedf_bins, 1)), dtype=np.int64)
         fm = np.zeros((max(dd.fm_xbins, 1), max(dd.fm_bins, 1)), dtype=np.int64)
-        cnt = np.zeros(32, dtype=np.int64)
+        cnt = np.zeros(40, dtype=np.int64)
         ns = C.c_longlong()
         self._check(self.lib.pic_diagnostics(self.h, d, _dp(dens), _dp(phi), _lp(eedf), _lp(iedf),
                                              _lp(fm), _lp(cnt), C.byref(ns), 1 if reset else 0))
         return {"n_samples": ns.value, "dens_sum": dens, "phi_sum": phi, "eedf": eedf,
                 "iedf": iedf, "fm": fm, "absorbed": cnt[0:6].reshape(3, 2),
                 "events": cnt[6:26].copy(), "violations": cnt[26:28].copy(),
-                "slots": cnt[28:31].copy(), "steps": int(cnt[31])}
+                "slots": cnt[28:31].copy(), "steps": int(cnt[31]),
+                "particle_steps": int(cnt[32]), "candidates": int(cnt[33]),
+                "slots_visited": int(cnt[34])}
 
     def set_timing(self, on=True):
         self._check(self.lib.pic_set_timing(self.h, 1 if on else 0))

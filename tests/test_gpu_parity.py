@@ -56,8 +56,27 @@ def _cmp_slots(d, g, o, s):
     return ex, ev
 
 
+def _slotwise(d, g, o, s, tol):
+    """slot by slot (valid while both sides keep the same order)"""
+    if len(g["x"]) != len(o["x"]):
+        return None
+    vt = _vth(d, s)
+    err = np.abs(g["x"] - o["x"]) / d.L
+    for c in ("vx", "vy", "vz"):
+        err = np.maximum(err, np.abs(g[c] - o[c]) / vt)
+    both = g["alive"] & o["alive"]
+    bad = (g["alive"] != o["alive"]) | (both & (err > tol))
+    rest = float(np.max(err[both & ~bad], initial=0.0))
+    return int(both.sum()), int(bad.sum()), rest
+
+
 def _matched(d, g, o, s, tol):
-    """particles matched by position; returns (n_compared, n_flips, max err of the rest)"""
+    """Decision flips under the better of two pairings: slot by slot, and by
+    sorted position (a sort can reorder a cell after one flipped particle).
+    Returns (n_compared, n_flips, max error of the non-flipped)."""
+    best = _slotwise(d, g, o, s, tol)
+    if best is not None and best[1] == 0:
+        return best
     gm, om = g["alive"], o["alive"]
     gi = np.argsort(g["x"][gm], kind="stable")
     oi = np.argsort(o["x"][om], kind="stable")
@@ -71,7 +90,10 @@ def _matched(d, g, o, s, tol):
         err = np.maximum(err, np.abs(gx[c][:n] - ox[c][:n]) / vt)
     bad = err > tol
     rest = float(np.max(err[~bad], initial=0.0))
-    return n, int(bad.sum()) + extra, rest
+    byx = (n, int(bad.sum()) + extra, rest)
+    if best is None or byx[1] < best[1]:
+        best = byx
+    return best
 
 
 # ------------------------------------------------------------------ load
