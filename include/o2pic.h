@@ -229,6 +229,40 @@ pic_status pic_set_timing(pic_handle *h, int on);
 pic_status pic_timing(pic_handle *h, double *push_ms, long long *push_launches,
                       long long *launches, double *push_bytes, int reset);
 
+/*
+ * pic_field_solve_static -- charge deposit, Poisson solve and field of ONE
+ * discharge from particle arrays that the caller owns, without allocating
+ * any memory.  The paper has no counterpart: this entry point serves callers
+ * that cannot allocate device memory (code inside a host framework that
+ * owns every allocation, code that must not call cudaMalloc in the middle of
+ * its own GPU work because that call can synchronise the device, code with
+ * a memory budget fixed up front) and so cannot use pic_init's workspace.
+ * It computes what pic_fields() computes for a handle, from the same
+ * particle representation.
+ *   cfg        the discharge (L_m, n_cells, U_rf_V, f_rf_Hz, rf_phase, dt_s,
+ *              weight_m2 and precision are used)
+ *   step       time-step number n; phi(x = 0) = U_rf sin(2 pi f n dt + phase)
+ *   d_cell[s]  device array of n[s] cell indices per species (< 0 = dead)
+ *   d_off[s]   device array of n[s] offsets in [0, 1): float for
+ *              PIC_FP32_MIXED, double for PIC_FP64
+ *   n[s]       host array of the three slot counts
+ *   d_rho, d_phi, d_E  device outputs, n_cells + 1 doubles each (SI)
+ *   cuda_stream  the work is queued on this stream (NULL = legacy default);
+ *              the outputs are valid once the stream has reached this point
+ * Limit: n_cells <= 4096 (larger grids fail with PIC_EINVAL).  Scratch: one
+ * fixed array of 3 x 4097 x 8 bytes in device memory, which every GPU that
+ * loads this library reserves until the process exits.  The first call on a
+ * device looks up that array's device address with the device current; make
+ * that first call before any stream capture on the device.  All calls on a
+ * device share the array and clear it first: calls that can run at the same
+ * time on the GPU (unordered streams) race and corrupt each other's output.
+ */
+pic_status pic_field_solve_static(const pic_config *cfg, long long step,
+                                  const int *const *d_cell,
+                                  const void *const *d_off, const long long *n,
+                                  double *d_rho, double *d_phi, double *d_E,
+                                  void *cuda_stream);
+
 void pic_destroy(pic_handle *h);
 
 /* Text of the last error on this handle (or of the calling thread's last

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libo2pic.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["o2pic_push.cu", "o2pic_kernels.cu", "o2pic_host.cu"]
+SOURCES = ["o2pic_push.cu", "o2pic_kernels.cu", "o2pic_host.cu", "o2pic_static.cu"]
 HEADERS = ["o2pic_dev.cuh", "o2pic_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

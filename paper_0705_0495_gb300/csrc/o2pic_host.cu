@@ -1091,6 +1091,8 @@ extern "C" void pic_destroy(pic_handle *h)
     delete h;
 }
 
+void o2::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 extern "C" const char *pic_last_error(const pic_handle *h)
 {
     if (h) return h->err.c_str();

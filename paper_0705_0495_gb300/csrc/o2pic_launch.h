@@ -45,6 +45,9 @@ cudaError_t launch_deposit_all(bool fp64, const WsPtrs &W, const void *pools, in
                                int max_n, cudaStream_t s);
 cudaError_t configure_kernels(bool fp64, LaunchCfg &L);
 
+// text returned by pic_last_error(NULL) for calls without a handle
+void set_last_error(const char *msg);
+
 int kernels_per_sort();
 int kernels_per_pair();
 

@@ -49,7 +49,7 @@ class pic_config(C.Structure):
 
 EXPORTS = ["pic_workspace_size", "pic_init", "pic_step", "pic_diagnostics", "pic_get_state",
            "pic_set_state", "pic_set_step", "pic_fields", "pic_numax", "pic_set_timing",
-           "pic_timing", "pic_destroy", "pic_last_error"]
+           "pic_timing", "pic_destroy", "pic_last_error", "pic_field_solve_static"]
 
 _lib = None
 
@@ -91,6 +91,9 @@ def load(path: str = LIB_PATH):
     l.pic_destroy.argtypes = [vp]
     l.pic_last_error.restype = C.c_char_p
     l.pic_last_error.argtypes = [vp]
+    l.pic_field_solve_static.restype = C.c_int
+    l.pic_field_solve_static.argtypes = [C.POINTER(pic_config), C.c_longlong, C.POINTER(C.c_void_p),
+                                         C.POINTER(C.c_void_p), lp, vp, vp, vp, vp]
     _lib = l
     return l
 
@@ -259,3 +262,17 @@ class Simulation:
                                         1 if reset else 0))
         return {"push_ms": ms.value, "push_launches": pl.value, "launches": la.value,
                 "push_bytes": bts.value}
+
+
+def field_solve_static(cfg: pic_config, step: int, cell_ptrs, off_ptrs, counts, rho_ptr, phi_ptr, E_ptr,
+                       stream_ptr=0) -> None:
+    """pic_field_solve_static: deposit and field solve from caller-owned device
+    arrays (pointers as ints), with no allocation (see include/o2pic.h)."""
+    lib = load()
+    cells = (C.c_void_p * 3)(*[C.c_void_p(p) for p in cell_ptrs])
+    offs = (C.c_void_p * 3)(*[C.c_void_p(p) for p in off_ptrs])
+    n = (C.c_longlong * 3)(*[int(v) for v in counts])
+    rc = lib.pic_field_solve_static(C.byref(cfg), int(step), cells, offs, n, C.c_void_p(rho_ptr),
+                                    C.c_void_p(phi_ptr), C.c_void_p(E_ptr), C.c_void_p(stream_ptr))
+    if rc != 0:
+        raise PicError(rc, lib.pic_last_error(None).decode())
