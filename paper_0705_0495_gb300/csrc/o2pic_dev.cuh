@@ -62,6 +62,8 @@ struct TableDesc {
 struct GasChan {
     int table;          // index into the table descriptors
     int reaction;
+    double th;          // threshold [eV]
+    float th_f, pad_f;
     double coef;        // n_target * dx (normalised frequency per unit u_n * sigma)
     double dloss;       // 2 dE / mu * (dt/dx)^2 (inelastic reduction of u_n^2)
     float coef_f, dloss_f;
@@ -80,7 +82,8 @@ struct SpeciesC {
     unsigned int tnull; // null-collision threshold on a 32-bit word
     int nch;
     int table_lo;       // first table of the shared grid (for the index)
-    int pad;
+    int gtab_ld;        // row length of the node-major gas table (multiple of 4)
+    int gtab_off;       // first element of this (discharge, species) gas table
     // FP32 copies (the FP32 path never converts from FP64 on the device)
     float qm_f, numax_n_f, vgas_n_f, Ek_f, mfrac_f, Mfrac_f, ke_eV_f, pad_f;
     GasChan ch[MAX_GAS_CH];
@@ -94,7 +97,7 @@ struct PairC {          // particle-target reaction of one discharge
     double Ek;          // (1/2) mu (dx/dt)^2 / e
     double mfrac, Mfrac;// m/(m+M), M/(m+M) of the pair
     double dloss;       // 2 dE/mu (dt/dx)^2
-    float Ek_f, mfrac_f, Mfrac_f, dloss_f;
+    float Ek_f, mfrac_f, Mfrac_f, dloss_f, coef_f, pad_f;
 };
 
 struct Disc {
@@ -109,6 +112,8 @@ struct Disc {
     double dx, dt, L, weight;
     double U_rf, omega, phase;
     double vol_fix;          // density per accumulated unit (interior node)
+    double dens_fix, dens_fix_wall;  // weight / (node volume * 2^FIX_BITS), inside / at walls
+    double Kfix;             // e weight 2^-FIX_BITS / eps0
     double kE;               // dt^2/dx
     double f15, mu2_15;      // reaction (15) product speed factor
     double f16;              // (16): v_e = |v_Om| * f16
@@ -165,14 +170,19 @@ struct WsPtrs {
     double *phi;              // [total_nodes]
     double *rho;              // [total_nodes]
     double *dens;             // [3 * total_nodes]
-    double *dens_sum;         // [3 * total_nodes]
-    double *phi_sum;          // [total_nodes]
+    double *dens_sum;         // [3 * total_nodes] (FP64 path)
+    double *phi_sum;          // [total_nodes] (FP64 path)
+    long long *dens_sum_fix;  // same memory as dens_sum: exact fixed-point sums (FP32 path)
+    __int128 *phi_s2_sum;     // [total_nodes] sums of S2_{i-1} (FP32 path)
+    double *phi0_sum, *D0_sum;// [D] sums of phi_0 and D0 (FP32 path)
     unsigned long long *nsamp;// [D]
     unsigned long long *counters; // [D * C_NCOUNT]
     unsigned int *eedf, *iedf, *fm;
     TableDesc *tables;
     double *lutE, *lutS;      // FP64 nodes and values
     float *lutEf, *lutSf;     // FP32 copies
+    double *gtab;             // node-major gas tables: n_j dx sigma_j(E_k), [k][j] per (d, s)
+    float *gtabf;
     int *sort_counts;         // count matrix
     int *cell_start;          // [sum over d of 3*(N+2)]
     int *sort_live;           // [D*3]

@@ -76,12 +76,13 @@ struct Bump {
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t ctl, disc, cnt, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
+    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
         counters, eedf, iedf, fm, tables, lutE, lutS, lutEf, lutSf, sort_counts, cell_start,
         sort_live, pair_bcount, cell_disc, pair_births, sort_tab, ninit, vt;
     size_t cell[2], off[2], vx[2], vy[2], vz[2];
     size_t total;
     int total_nodes, total_cells, max_chunks, total_cap, sort_blocks, n_lut, maxN, eedf_max, fm_max;
+    long long gtab_n;  // elements of the node-major gas tables
     std::vector<int> pbase, capr, gbase, ccell, sort_cbase, sort_gmax, cs_base, eedf_base, iedf_base,
         fm_base;
 };
@@ -242,6 +243,20 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     mc = (mc + TILE_ALIGN - 1) / TILE_ALIGN * TILE_ALIGN;  // room for the padding after the last species
     int nl = 0;
     for (int i = 0; i < n_xs; ++i) nl += xs[i].n;
+    // node-major gas tables: per (d, s), rows of the shared grid, 4-padded
+    long long gn = 0;
+    {
+        int nodes[3] = {0, 0, 0}, nch[3] = {0, 0, 0};
+        for (int i = 0; i < n_xs; ++i) {
+            if (targ_of(xs[i].reaction) >= 0) continue;
+            const int s = proj_of(xs[i].reaction);
+            nodes[s] = xs[i].n;
+            ++nch[s];
+        }
+        for (int s = 0; s < 3; ++s) gn += (long long)nodes[s] * ((nch[s] + 3) / 4 * 4) + 4;
+        gn *= D;
+    }
+    L.gtab_n = gn;
     L.total_nodes = tn;
     L.total_cells = tc;
     L.max_chunks = mc;
@@ -267,6 +282,9 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.dens_sum = B.take(8ull * 3 * tn);
     L.phi_sum = B.take(8ull * tn);
     L.nsamp = B.take(8ull * D);
+    L.phi_s2_sum = B.take(16ull * tn);
+    L.phi0_sum = B.take(8ull * D);
+    L.D0_sum = B.take(8ull * D);
     L.counters = B.take(8ull * C_NCOUNT * D);
     L.eedf = B.take(4ull * std::max(1LL, eb));
     L.iedf = B.take(4ull * std::max(1LL, ib));
@@ -276,6 +294,8 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.lutS = B.take(8ull * std::max(1, nl));
     L.lutEf = B.take(4ull * std::max(1, nl));
     L.lutSf = B.take(4ull * std::max(1, nl));
+    L.gtab = B.take(8ull * std::max(1LL, gn));
+    L.gtabf = B.take(4ull * std::max(1LL, gn));
     L.sort_counts = B.take(4ull * std::max(1LL, sortc));
     L.cell_start = B.take(4ull * csb);
     L.sort_live = B.take(4ull * 3 * D);
@@ -394,6 +414,9 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
     D.phase = q.rf_phase;
     const double tdx = q.dt_s / D.dx, xdt = D.dx / q.dt_s;
     D.kE = q.dt_s * q.dt_s / D.dx;
+    D.dens_fix = q.weight_m2 / (D.dx * (double)(1 << FIX_BITS));
+    D.dens_fix_wall = q.weight_m2 / (0.5 * D.dx * (double)(1 << FIX_BITS));
+    D.Kfix = QE * q.weight_m2 / (double)(1 << FIX_BITS) / 8.8541878128e-12;
     const double mu2 = M_O * MASS[1] / (M_O + MASS[1]);
     D.mu2_15 = mu2;
     D.f15 = 2.0 * QE * mu2 / (MASS[1] * MASS[1]) * tdx * tdx;
@@ -447,6 +470,8 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
             S.ch[j].dloss = 2.0 * t.th * QE / mu * tdx * tdx;
             S.ch[j].coef_f = (float)S.ch[j].coef;
             S.ch[j].dloss_f = (float)S.ch[j].dloss;
+            S.ch[j].th = t.th;
+            S.ch[j].th_f = (float)t.th;
         }
         // nu_max: largest sum_j n_j sigma_j(E) sqrt(2E/mu) over the nodes up to
         // the cap and the cap itself, times the safety factor
@@ -498,6 +523,7 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
         P.mfrac_f = (float)P.mfrac;
         P.Mfrac_f = (float)P.Mfrac;
         P.dloss_f = (float)P.dloss;
+        P.coef_f = (float)P.coef;
     }
     h->disc[d] = D;
 }
@@ -552,6 +578,10 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.dens_sum = reinterpret_cast<double *>(b + L.dens_sum);
     W.phi_sum = reinterpret_cast<double *>(b + L.phi_sum);
     W.nsamp = reinterpret_cast<unsigned long long *>(b + L.nsamp);
+    W.dens_sum_fix = reinterpret_cast<long long *>(b + L.dens_sum);
+    W.phi_s2_sum = reinterpret_cast<__int128 *>(b + L.phi_s2_sum);
+    W.phi0_sum = reinterpret_cast<double *>(b + L.phi0_sum);
+    W.D0_sum = reinterpret_cast<double *>(b + L.D0_sum);
     W.counters = reinterpret_cast<unsigned long long *>(b + L.counters);
     W.eedf = reinterpret_cast<unsigned *>(b + L.eedf);
     W.iedf = reinterpret_cast<unsigned *>(b + L.iedf);
@@ -561,6 +591,8 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.lutS = reinterpret_cast<double *>(b + L.lutS);
     W.lutEf = reinterpret_cast<float *>(b + L.lutEf);
     W.lutSf = reinterpret_cast<float *>(b + L.lutSf);
+    W.gtab = reinterpret_cast<double *>(b + L.gtab);
+    W.gtabf = reinterpret_cast<float *>(b + L.gtabf);
     W.sort_counts = reinterpret_cast<int *>(b + L.sort_counts);
     W.cell_start = reinterpret_cast<int *>(b + L.cell_start);
     W.sort_live = reinterpret_cast<int *>(b + L.sort_live);
@@ -621,6 +653,27 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     h->disc.resize(n_discharges);
     h->numax.assign(3 * n_discharges, 0.0);
     for (int d = 0; d < n_discharges; ++d) build_disc(h, d, gas, gcount, pair_tab);
+    // node-major gas tables: row k of (d, s) holds n_j dx sigma_j(E_k), j < nch
+    std::vector<double> gt(std::max(1LL, L.gtab_n), 0.0);
+    std::vector<float> gtf(std::max(1LL, L.gtab_n), 0.0f);
+    {
+        long long off = 0;
+        for (int d = 0; d < n_discharges; ++d)
+            for (int s = 0; s < 3; ++s) {
+                SpeciesC &S = h->disc[d].sp[s];
+                const int ld = (S.nch + 3) / 4 * 4;
+                const int nodes = S.nch > 0 ? h->tabs[S.ch[0].table].n : 0;
+                S.gtab_ld = ld;
+                S.gtab_off = (int)off;
+                for (int k = 0; k < nodes; ++k)
+                    for (int j = 0; j < S.nch; ++j) {
+                        const double v = S.ch[j].coef * h->tabs[S.ch[j].table].S[k];
+                        gt[off + (long long)k * ld + j] = v;
+                        gtf[off + (long long)k * ld + j] = (float)v;
+                    }
+                off += (long long)nodes * ld + 4;
+            }
+    }
 
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
@@ -666,6 +719,8 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     CK(cudaMemcpyAsync(W.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(W.disc, h->disc.data(), sizeof(Disc) * n_discharges, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(W.cnt, cnt.data(), sizeof(Counts) * cnt.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(W.gtab, gt.data(), 8 * gt.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(W.gtabf, gtf.data(), 4 * gtf.size(), cudaMemcpyHostToDevice, st));
     if (n_xs > 0) {
         CK(cudaMemcpyAsync(W.tables, td.data(), sizeof(TableDesc) * n_xs, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(W.lutE, lE.data(), 8 * lE.size(), cudaMemcpyHostToDevice, st));
@@ -865,11 +920,29 @@ extern "C" pic_status pic_diagnostics(pic_handle *h, int d, double *dens_sum, do
     const Disc &D = h->disc[d];
     const int N = q.n_cells, tn = h->W.total_nodes;
     cudaStream_t st = h->stream;
-    if (dens_sum)
-        for (int s = 0; s < 3; ++s)
-            CK(cudaMemcpyAsync(dens_sum + (size_t)s * (N + 1), h->W.dens_sum + (size_t)s * tn + D.gbase,
-                               8 * (N + 1), cudaMemcpyDeviceToHost, st));
-    if (phi_sum) CK(cudaMemcpyAsync(phi_sum, h->W.phi_sum + D.gbase, 8 * (N + 1), cudaMemcpyDeviceToHost, st));
+    // FP32 path: exact integer sums, scaled here; FP64 path: FP64 sums
+    std::vector<long long> dfix(h->fp64 ? 0 : 3 * (size_t)(N + 1));
+    std::vector<__int128> s2(h->fp64 ? 0 : (size_t)(N + 1));
+    double p0s = 0.0, d0s = 0.0;
+    if (dens_sum) {
+        for (int s = 0; s < 3; ++s) {
+            if (h->fp64)
+                CK(cudaMemcpyAsync(dens_sum + (size_t)s * (N + 1), h->W.dens_sum + (size_t)s * tn + D.gbase,
+                                   8 * (N + 1), cudaMemcpyDeviceToHost, st));
+            else
+                CK(cudaMemcpyAsync(dfix.data() + (size_t)s * (N + 1), h->W.dens_sum_fix + (size_t)s * tn + D.gbase,
+                                   8 * (N + 1), cudaMemcpyDeviceToHost, st));
+        }
+    }
+    if (phi_sum) {
+        if (h->fp64) {
+            CK(cudaMemcpyAsync(phi_sum, h->W.phi_sum + D.gbase, 8 * (N + 1), cudaMemcpyDeviceToHost, st));
+        } else {
+            CK(cudaMemcpyAsync(s2.data(), h->W.phi_s2_sum + D.gbase, 16 * (N + 1), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&p0s, h->W.phi0_sum + d, 8, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&d0s, h->W.D0_sum + d, 8, cudaMemcpyDeviceToHost, st));
+        }
+    }
     std::vector<unsigned> e(std::max(1, q.eedf_bins)), i2(std::max(1, 2 * q.iedf_bins)),
         f(std::max(1, D.fm_xbins * q.fm_bins));
     if (q.eedf_bins)
@@ -886,6 +959,17 @@ extern "C" pic_status pic_diagnostics(pic_handle *h, int d, double *dens_sum, do
     Counts cn[3];
     CK(cudaMemcpyAsync(cn, h->W.cnt + 3 * d, sizeof cn, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (!h->fp64 && dens_sum)
+        for (int s = 0; s < 3; ++s)
+            for (int i = 0; i <= N; ++i)
+                dens_sum[(size_t)s * (N + 1) + i] =
+                    (double)dfix[(size_t)s * (N + 1) + i] * ((i == 0 || i == N) ? D.dens_fix_wall : D.dens_fix);
+    if (!h->fp64 && phi_sum) {
+        const double Kdx = 1.602176634e-19 * q.weight_m2 / (double)(1 << FIX_BITS) / 8.8541878128e-12 * D.dx;
+        phi_sum[0] = p0s;
+        phi_sum[N] = 0.0;
+        for (int i = 1; i < N; ++i) phi_sum[i] = p0s + (double)i * d0s - Kdx * (double)s2[i];
+    }
     if (eedf) for (int k = 0; k < q.eedf_bins; ++k) eedf[k] = e[k];
     if (iedf) for (int k = 0; k < 2 * q.iedf_bins; ++k) iedf[k] = i2[k];
     if (fm) for (int k = 0; k < D.fm_xbins * q.fm_bins; ++k) fm[k] = f[k];
@@ -903,6 +987,9 @@ extern "C" pic_status pic_diagnostics(pic_handle *h, int d, double *dens_sum, do
         for (int s = 0; s < 3; ++s)
             CK(cudaMemsetAsync(h->W.dens_sum + (size_t)s * tn + D.gbase, 0, 8 * (N + 1), st));
         CK(cudaMemsetAsync(h->W.phi_sum + D.gbase, 0, 8 * (N + 1), st));
+        CK(cudaMemsetAsync(h->W.phi_s2_sum + D.gbase, 0, 16 * (N + 1), st));
+        CK(cudaMemsetAsync(h->W.phi0_sum + d, 0, 8, st));
+        CK(cudaMemsetAsync(h->W.D0_sum + d, 0, 8, st));
         if (q.eedf_bins) CK(cudaMemsetAsync(h->W.eedf + D.eedf_base, 0, 4 * q.eedf_bins, st));
         if (q.iedf_bins) CK(cudaMemsetAsync(h->W.iedf + D.iedf_base, 0, 8 * q.iedf_bins, st));
         if (q.fm_bins) CK(cudaMemsetAsync(h->W.fm + D.fm_base, 0, 4 * (size_t)D.fm_xbins * q.fm_bins, st));

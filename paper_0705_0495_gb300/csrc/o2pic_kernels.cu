@@ -136,23 +136,32 @@ k_field(WsPtrs W, int par, int diag, int mode)
     const unsigned long long step = ctl->step[par];
     const int tn = W.total_nodes;
     const double dx = Dd.dx;
-    const double t = (double)step * Dd.dt;
-    const double phi0 = Dd.U_rf * sin(Dd.omega * t + Dd.phase);
+    // FP64 scalars once per block: GB300 runs FP64 on few units, and 1024
+    // threads each evaluating sin() would cost more than the whole solve
+    __shared__ double s_phi0;
+    if (tid == 0) s_phi0 = Dd.U_rf * sin(Dd.omega * ((double)step * Dd.dt) + Dd.phase);
+    __syncthreads();
+    const double phi0 = s_phi0;
     Real *Er = reinterpret_cast<Real *>(W.Ereal) + g;
     Acc *acc = AccK<Real>::ptr(W);
     if constexpr (sizeof(Real) == 4) {
         // FP32 path: the accumulators are exact fixed-point sums (weight *
         // 2^FIX_BITS).  With q_i the net charge in these units and
         // K = e w 2^-FIX_BITS / eps0: interior s_i = K dx q_i, S1 = prefix
-        // sums of q (exact int64), sum_m S1_m (exact int128), and
-        //   E_i = -D0/dx + (K/2)(S1_i + S1_{i-1}),  i = 1..N-1
-        //   E_0 = -D0/dx - K q_0,  E_N = -(D0 - K dx S1_{N-1})/dx + K q_N
-        //   phi_i = phi_0 + i D0 - K dx sum_{m<i} S1_m,  D0 = (K dx S2 - phi_0)/N.
+        // sums of q (exact int64), S2 = prefix sums of S1 (exact int128), and
+        //   phi_i = phi_0 + i D0 - K dx S2_{i-1},  D0 = (K dx S2_{N-1} - phi_0)/N
+        //   E_i = (K/2) (T_i - T0),  T0 = 2 D0 / (K dx), with the integers
+        //   T_i = S1_i + S1_{i-1} inside, T_0 = -2 q_0, T_N = 2 (S1_{N-1} + q_N)
+        // (the wall values are Gauss's law on the half cells).  T_i - round(T0)
+        // is exact, so E leaves FP64 only through O(1) constants.
         long long *S1 = reinterpret_cast<long long *>(fsm);  // N+1 entries
         __shared__ long long wl[FIELD_THREADS / 32];
         __shared__ __int128 w128[FIELD_THREADS / 32];
-        __shared__ long long s_q0, s_qN;
-        const double K = QE_ * Dd.weight / (double)(1 << FIX_BITS) / EPS0_;
+        __shared__ long long s_q0, s_qN, s_T0i;
+        __shared__ float s_hKf, s_frf;
+        __shared__ int s_intE;
+        const double K = Dd.Kfix;  // e w 2^-FIX_BITS / eps0
+        const bool full = diag || mode != 0;
         for (int i = tid; i <= N; i += FIELD_THREADS) {
             long long a[NSP];
 #pragma unroll
@@ -160,21 +169,16 @@ k_field(WsPtrs W, int par, int diag, int mode)
                 const size_t k = (size_t)s * tn + g + i;
                 a[s] = (long long)acc[k];
                 if (mode == 0) acc[k] = Acc(0);
+                if (diag) W.dens_sum_fix[k] += a[s];  // exact sums; scaled at read-out
             }
             const long long q = a[2] - a[0] - a[1];
             S1[i] = (i == 0 || i == N) ? 0 : q;
             if (i == 0) s_q0 = q;
             if (i == N) s_qN = q;
-            if (diag || mode != 0) {
-                const double vol = (i == 0 || i == N) ? 0.5 * dx : dx;
-                const double sc = Dd.weight / (vol * (double)(1 << FIX_BITS));
+            if (full) {
+                const double sc = (i == 0 || i == N) ? Dd.dens_fix_wall : Dd.dens_fix;
 #pragma unroll
-                for (int s = 0; s < NSP; ++s) {
-                    const size_t k = (size_t)s * tn + g + i;
-                    const double dn = (double)a[s] * sc;
-                    W.dens[k] = dn;
-                    if (diag) W.dens_sum[k] += dn;
-                }
+                for (int s = 0; s < NSP; ++s) W.dens[(size_t)s * tn + g + i] = (double)a[s] * sc;
                 W.rho[g + i] = QE_ * (double)q * sc;
             }
         }
@@ -212,54 +216,64 @@ k_field(WsPtrs W, int par, int diag, int mode)
             S1[i] += excl;
             part += (__int128)S1[i];
         }
-        // block sum of part
+        // inclusive int128 scan of the thread parts (the total is S2_{N-1})
+        __int128 pv = part;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long plo = (unsigned long long)part, phi_ = (unsigned long long)(part >> 64);
-            plo = __shfl_down_sync(0xffffffffu, plo, o);
-            phi_ = __shfl_down_sync(0xffffffffu, phi_, o);
-            part += ((__int128)(long long)phi_ << 64) | (__int128)plo;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long lo_ = __shfl_up_sync(0xffffffffu, (unsigned long long)pv, o);
+            const long long hi_ = __shfl_up_sync(0xffffffffu, (long long)(pv >> 64), o);
+            if (lane >= o) pv += ((__int128)hi_ << 64) | (__int128)lo_;
         }
-        if (lane == 0) w128[warp] = part;
+        if (lane == 31) w128[warp] = pv;
         __syncthreads();
         if (tid == 0) {
-            __int128 S2 = 0;
-            for (int w = 0; w < FIELD_THREADS / 32; ++w) S2 += w128[w];
-            s_D0 = (K * dx * (double)S2 - phi0) / (double)N;
+            __int128 r = 0;
+            for (int w = 0; w < FIELD_THREADS / 32; ++w) {
+                r += w128[w];
+                w128[w] = r;
+            }
+            const double D0 = (K * dx * (double)r - phi0) / (double)N;
+            s_D0 = D0;
+            const double T0 = 2.0 * D0 / (K * dx);
+            s_intE = (K > 0.0 && fabs(T0) < 4.0e18) ? 1 : 0;
+            const long long T0i = s_intE ? llround(T0) : 0;
+            s_T0i = T0i;
+            s_hKf = (float)(0.5 * K);
+            s_frf = (float)(T0 - (double)T0i);
+            if (diag) {
+                W.phi0_sum[d] += phi0;
+                W.D0_sum[d] += D0;
+            }
         }
         __syncthreads();
-        const double D0 = s_D0;
+        const long long T0i = s_T0i;
+        const float hKf = s_hKf, frf = s_frf;
+        const bool intE = s_intE != 0;
         for (int i = tid; i <= N; i += FIELD_THREADS) {
-            double E;
-            if (i == 0) E = -D0 / dx - K * (double)s_q0;
-            else if (i == N) E = -(D0 - K * dx * (double)S1[N - 1]) / dx + K * (double)s_qN;
-            else E = -D0 / dx + 0.5 * K * (double)(S1[i] + S1[i - 1]);
-            Er[i] = (Real)E;
-            if (diag || mode != 0) W.Efield[g + i] = E;
+            const long long Ti = (i == 0) ? -2 * s_q0 : (i == N ? 2 * (S1[N - 1] + s_qN) : S1[i] + S1[i - 1]);
+            if (intE) {
+                Er[i] = hKf * (__ll2float_rn(Ti - T0i) - frf);
+                if (full) W.Efield[g + i] = 0.5 * K * ((double)(Ti - T0i) - (double)frf);
+            } else {  // no charge or an extreme field: evaluate in FP64
+                const double E = -s_D0 / dx + 0.5 * K * (double)Ti;
+                Er[i] = (Real)E;
+                if (full) W.Efield[g + i] = E;
+            }
         }
-        if (diag || mode != 0) {
-            // potential: needs the second prefix sum; only for diagnostics
-            __syncthreads();
-            // 16-byte aligned after the N+1 int64 prefix sums
-            __int128 *S2s = reinterpret_cast<__int128 *>(reinterpret_cast<char *>(fsm) +
-                                                         ((8 * (size_t)(N + 1) + 15) & ~(size_t)15));
-            if (tid == 0) {
-                __int128 r = 0;
-                S2s[0] = 0;
-                for (int i = 1; i < N; ++i) {
-                    r += (__int128)S1[i];
-                    S2s[i] = r;
-                }
-            }
-            __syncthreads();
-            for (int i = tid; i <= N; i += FIELD_THREADS) {
-                double p;
-                if (i == 0) p = phi0;
-                else if (i == N) p = 0.0;
-                else p = phi0 + (double)i * D0 - K * dx * (double)S2s[i - 1];
+        const double D0 = s_D0;
+        if (full) {
+            // potential and the exact running sums of S2 for its average
+            const __int128 before = (warp > 0 ? w128[warp - 1] : (__int128)0) + pv - part;
+            __int128 r = before;
+            for (int i = lo; i < hi; ++i) {
+                // r = S2_{i-1} when node i is reached
+                double p = phi0 + (double)i * D0 - K * dx * (double)r;
+                if (diag) W.phi_s2_sum[g + i] += r;
                 W.phi[g + i] = p;
-                if (diag) W.phi_sum[g + i] += p;
+                r += (__int128)S1[i];
             }
+            if (tid == 0) W.phi[g] = phi0;
+            if (tid == 0) W.phi[g + N] = 0.0;
         }
     } else {
         double *x = fsm;  // N+1 entries
@@ -392,6 +406,12 @@ k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
         }
 #pragma unroll
         for (int r = 0; r < SORT_ILP; ++r) {
+            // sorted runs: a whole row in one bucket needs no match
+            const int b0 = __shfl_sync(0xffffffffu, b[r], 0);
+            if (__all_sync(0xffffffffu, b[r] == b0)) {
+                if (lane == 0 && b0 >= 0) atomicAdd(&ssm[b0], 32u);
+                continue;
+            }
             const unsigned peers = __match_any_sync(0xffffffffu, b[r]);
             if (b[r] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&ssm[b[r]], (unsigned)__popc(peers));
         }
@@ -504,6 +524,12 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
         }
 #pragma unroll
         for (int r = 0; r < SORT_ILP; ++r) {
+            const int b0 = __shfl_sync(0xffffffffu, b[r], 0);
+            if (__all_sync(0xffffffffu, b[r] == b0)) {
+                if (lane == 0 && b0 >= 0) hw[b0] += (unsigned short)32;
+                __syncwarp();
+                continue;
+            }
             const unsigned peers = __match_any_sync(0xffffffffu, b[r]);
             if (b[r] >= 0 && lane == __ffs(peers) - 1) hw[b[r]] += (unsigned short)__popc(peers);
             __syncwarp();
@@ -543,23 +569,47 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
         }
 #pragma unroll
         for (int r = 0; r < SORT_ILP; ++r) {
-            const unsigned peers = __match_any_sync(0xffffffffu, b[r]);
             dst[r] = -1;
+            const int b0 = __shfl_sync(0xffffffffu, b[r], 0);
+            if (__all_sync(0xffffffffu, b[r] == b0)) {
+                // a whole row in one bucket: ranks are the lanes
+                if (b0 >= 0 && b0 < N) dst[r] = (int)hw[b0] + lane;
+                __syncwarp();
+                if (lane == 0 && b0 >= 0) hw[b0] += (unsigned short)32;
+                __syncwarp();
+                continue;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, b[r]);
             if (b[r] >= 0 && b[r] < N) dst[r] = (int)hw[b[r]] + __popc(peers & lt);
             __syncwarp();
             if (b[r] >= 0 && lane == __ffs(peers) - 1) hw[b[r]] += (unsigned short)__popc(peers);
             __syncwarp();
         }
+        // every load of the rows first (read-only path), then the stores: the
+        // source and destination arrays never overlap
+        Real ro[SORT_ILP], rx[SORT_ILP], ry[SORT_ILP], rz[SORT_ILP];
+        int gd[SORT_ILP];
 #pragma unroll
         for (int r = 0; r < SORT_ILP; ++r) {
+            gd[r] = -1;
             if (dst[r] >= 0) {
                 const int i = i0 + r * 32 + lane;
-                const int g = cstart[b[r]] + base[b[r]] + dst[r];
+                gd[r] = __ldg(&cstart[b[r]]) + __ldg(&base[b[r]]) + dst[r];
+                ro[r] = __ldg(&offS[i]);
+                rx[r] = __ldg(&vxS[i]);
+                ry[r] = __ldg(&vyS[i]);
+                rz[r] = __ldg(&vzS[i]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < SORT_ILP; ++r) {
+            if (gd[r] >= 0) {
+                const int g = gd[r];
                 cellD[g] = b[r];
-                offD[g] = offS[i];
-                vxD[g] = vxS[i];
-                vyD[g] = vyS[i];
-                vzD[g] = vzS[i];
+                offD[g] = ro[r];
+                vxD[g] = rx[r];
+                vyD[g] = ry[r];
+                vzD[g] = rz[r];
             }
         }
     }
@@ -587,12 +637,12 @@ __device__ __forceinline__ Real pair_sigma(const WsPtrs &W, const TableDesc &T, 
 template <>
 __device__ __forceinline__ float pair_sigma<float>(const WsPtrs &W, const TableDesc &T, float E)
 {
-    if (E < (float)T.th) return 0.f;
+    if (E < T.th_f) return 0.f;
     const float *nd = W.lutEf + T.off, *sv = W.lutSf + T.off;
     const int n = T.n;
     if (!(E > nd[0])) return sv[0];
     if (E >= nd[n - 1]) return sv[n - 1];
-    int k = (int)((logf(E) - (float)T.lnE0) * (float)T.inv_dlog);
+    int k = (int)((logf(E) - T.lnE0_f) * T.inv_dlog_f);
     k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
     while (k > 0 && E < nd[k]) --k;
     while (k < n - 2 && E >= nd[k + 1]) ++k;
@@ -672,7 +722,7 @@ k_pair_eval(WsPtrs W, Pools<Real> P, int par, int k, const int *tab)
         const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
         const Real u = sqrt(u2);
         const Real E = pick<Real>(pc.Ek, pc.Ek_f) * u2;
-        const Real Pc = Real((double)liveT * pc.coef) * pair_sigma<Real>(W, W.tables[pc.table], E) * u;
+        const Real Pc = Real(liveT) * pick<Real>(pc.coef, pc.coef_f) * pair_sigma<Real>(W, W.tables[pc.table], E) * u;
         flag = Pc > Real(1) || unif<Real>(d0.y) < Pc;
     }
     if (flag) atomicMin(&W.pair_first[Dd.ccell_base + c], i);
@@ -712,7 +762,7 @@ k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
     const int range = t1 - t0;
     const int liveT = range - kills[pt];
     const TableDesc &T = W.tables[pc.table];
-    const Real coefP = Real((double)liveT * pc.coef);
+    const Real coefP = Real(liveT) * pick<Real>(pc.coef, pc.coef_f);
     const int pbp = Dd.pbase[ps], pbt = Dd.pbase[pt];
     bool stop = false;
     unsigned nviol = 0;

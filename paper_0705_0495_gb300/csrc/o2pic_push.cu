@@ -36,6 +36,26 @@ template <typename Real> struct AccT;
 template <> struct AccT<float> { using T = unsigned long long; };
 template <> struct AccT<double> { using T = double; };
 
+template <typename Real> struct GasTab;
+template <> struct GasTab<float> {
+    static constexpr int VEC = 4;
+    static __device__ __forceinline__ const float *ptr(const WsPtrs &W) { return W.gtabf; }
+    static __device__ __forceinline__ void load(const float *p, float v[4])
+    {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <> struct GasTab<double> {
+    static constexpr int VEC = 2;
+    static __device__ __forceinline__ const double *ptr(const WsPtrs &W) { return W.gtab; }
+    static __device__ __forceinline__ void load(const double *p, double v[2])
+    {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    }
+};
+
 template <typename Real> struct Lut;
 template <> struct Lut<float> {
     static __device__ __forceinline__ const float *E(const WsPtrs &W) { return W.lutEf; }
@@ -214,13 +234,30 @@ __device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int
     Real target = unif<Real>(b.x) * numax_n;
     const TableDesc &T0 = W.tables[S.table_lo];
     XsPoint<Real> pt = xs_locate<Real>(T0, lutE, E);
+    // node-major table of n_j dx sigma_j(E_k): the rows k and k+1 of every
+    // channel come in a few 16-byte loads
+    const Real *row = GasTab<Real>::ptr(W) + S.gtab_off;
+    const int ld = S.gtab_ld;
+    const Real *ra = row + (size_t)pt.k * ld;
+    const Real *rb = ra + ld;
     Real cum = Real(0);
     int chosen = -1;
-    for (int j = 0; j < S.nch; ++j) {
-        const GasChan &ch = S.ch[j];
-        Real sg = xs_value<Real>(W.tables[ch.table], lutS, pt, E);
-        cum += pick<Real>(ch.coef, ch.coef_f) * sg * u;
-        if (chosen < 0 && target < cum) chosen = j;
+    for (int j0 = 0; j0 < S.nch; j0 += GasTab<Real>::VEC) {
+        Real a[GasTab<Real>::VEC], b[GasTab<Real>::VEC];
+        GasTab<Real>::load(ra + j0, a);
+        GasTab<Real>::load(rb + j0, b);
+#pragma unroll
+        for (int q = 0; q < GasTab<Real>::VEC; ++q) {
+            const int j = j0 + q;
+            if (j >= S.nch) break;
+            Real v;
+            if (E < pick<Real>(S.ch[j].th, S.ch[j].th_f)) v = Real(0);
+            else if (pt.region == 0) v = a[q];
+            else if (pt.region == 2) v = b[q];
+            else v = a[q] + pt.f * (b[q] - a[q]);
+            cum += v * u;
+            if (chosen < 0 && target < cum) chosen = j;
+        }
     }
     if (cum > numax_n) atomicAdd(&s_cnt[C_VIOL_GAS], 1u);
     if (chosen < 0) return true;  // null event
@@ -319,14 +356,30 @@ __device__ __forceinline__ void deposit_warp(double *sAcc, int c, double off)
     }
 }
 
+// Exact 64-bit accumulation in shared memory with native 32-bit atomics: the
+// node's low word takes the add, and the value it returns tells whether the
+// add carried into the high word.
+__device__ __forceinline__ void acc64_add(unsigned long long *node, unsigned v)
+{
+    unsigned *w = reinterpret_cast<unsigned *>(node);  // little endian: w[0] low, w[1] high
+    const unsigned old = atomicAdd(&w[0], v);
+    if (old + v < old) atomicAdd(&w[1], 1u);
+}
+__device__ __forceinline__ void acc64_sub(unsigned long long *node, unsigned v)
+{
+    unsigned *w = reinterpret_cast<unsigned *>(node);
+    const unsigned old = atomicSub(&w[0], v);
+    if (old < v) atomicSub(&w[1], 1u);
+}
+
 // removal of one particle deposited in phase A (it died in a collision):
 // the same fixed-point weights, so the accumulator returns exactly
 __device__ __forceinline__ void deposit_shared_remove(unsigned long long *sAcc, int c, float off)
 {
     const unsigned w1 = __float2uint_rn(off * (float)(1 << FIX_BITS));
     const unsigned w0 = (1u << FIX_BITS) - w1;
-    atomicAdd(&sAcc[c], 0ull - (unsigned long long)w0);
-    atomicAdd(&sAcc[c + 1], 0ull - (unsigned long long)w1);
+    acc64_sub(&sAcc[c], w0);
+    acc64_sub(&sAcc[c + 1], w1);
 }
 __device__ __forceinline__ void deposit_shared_remove(double *sAcc, int c, double off)
 {
@@ -377,16 +430,16 @@ __device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep
             const unsigned sa = __reduce_add_sync(0xffffffffu, a);
             const unsigned sb = __reduce_add_sync(0xffffffffu, b);
             if (lane == 0) {
-                atomicAdd(&sAcc[c0], (unsigned long long)sa);
-                atomicAdd(&sAcc[c0 + 1], (unsigned long long)sb);
+                acc64_add(&sAcc[c0], sa);
+                acc64_add(&sAcc[c0 + 1], sb);
             }
         } else {
             const unsigned peers = __match_any_sync(0xffffffffu, dep[0]);
             const unsigned sa = __reduce_add_sync(peers, a);
             const unsigned sb = __reduce_add_sync(peers, b);
             if (lane == __ffs(peers) - 1) {
-                atomicAdd(&sAcc[dep[0]], (unsigned long long)sa);
-                atomicAdd(&sAcc[dep[0] + 1], (unsigned long long)sb);
+                acc64_add(&sAcc[dep[0]], sa);
+                acc64_add(&sAcc[dep[0] + 1], sb);
             }
         }
         return;
@@ -397,8 +450,8 @@ __device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep
         const unsigned sa = __reduce_add_sync(peers, w0[k]);
         const unsigned sb = __reduce_add_sync(peers, w1[k]);
         if (dep[k] >= 0 && lane == __ffs(peers) - 1) {
-            atomicAdd(&sAcc[dep[k]], (unsigned long long)sa);
-            atomicAdd(&sAcc[dep[k] + 1], (unsigned long long)sb);
+            acc64_add(&sAcc[dep[k]], sa);
+            acc64_add(&sAcc[dep[k] + 1], sb);
         }
     }
 }

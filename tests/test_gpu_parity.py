@@ -164,6 +164,28 @@ def test_fp64_diagnostics_match_oracle():
     assert o["eedf"].sum() > 0 and o["fm"].sum() > 0
 
 
+def test_fp32_diagnostic_sums_match_per_step_fields():
+    # the FP32 path accumulates exact integer sums of the charge and of the
+    # potential's second prefix sum; scaled at read-out they must equal the
+    # sums of the per-step FP64 fields
+    d = inputs.cfg1(fp64=False, n_op=8000, diag_every=1)
+    sim = _sim(d)
+    QEl = 1.602176634e-19
+    rho_acc = np.zeros(d.n_cells + 1)
+    phi_acc = np.zeros(d.n_cells + 1)
+    for _ in range(25):
+        rho, phi, _ = sim.fields(0)
+        rho_acc += rho
+        phi_acc += phi
+        sim.step(1)
+    g = sim.diagnostics(0)
+    assert g["n_samples"] == 25
+    dens = g["dens_sum"]
+    rho_diag = QEl * (dens[2] - dens[0] - dens[1])
+    assert np.max(np.abs(rho_diag - rho_acc)) <= 1e-9 * np.max(np.abs(rho_acc))
+    assert np.max(np.abs(g["phi_sum"] - phi_acc)) <= 1e-9 * np.max(np.abs(phi_acc))
+
+
 def test_fp64_ragged_small_and_degenerate_sizes():
     # 7 cells, counts that fill no chunk or vector evenly, one empty species
     d = inputs.cfg1(n_cells=7, n_op=2 * 1237 + 2, sort_interval=3, n1=6, diag_every=4,
