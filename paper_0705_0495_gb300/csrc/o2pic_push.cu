@@ -242,6 +242,7 @@ __device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int
     const Real *rb = ra + ld;
     Real cum = Real(0);
     int chosen = -1;
+    // channel walk with selects only: the lanes of a warp stay together
     for (int j0 = 0; j0 < S.nch; j0 += GasTab<Real>::VEC) {
         Real a[GasTab<Real>::VEC], b[GasTab<Real>::VEC];
         GasTab<Real>::load(ra + j0, a);
@@ -249,14 +250,12 @@ __device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int
 #pragma unroll
         for (int q = 0; q < GasTab<Real>::VEC; ++q) {
             const int j = j0 + q;
-            if (j >= S.nch) break;
-            Real v;
-            if (E < pick<Real>(S.ch[j].th, S.ch[j].th_f)) v = Real(0);
-            else if (pt.region == 0) v = a[q];
-            else if (pt.region == 2) v = b[q];
-            else v = a[q] + pt.f * (b[q] - a[q]);
+            if (j >= S.nch) break;  // uniform: one species per warp
+            // below the grid f = 0 gives a exactly; above it, the last node
+            Real v = pt.region == 2 ? b[q] : a[q] + pt.f * (b[q] - a[q]);
+            v = E < pick<Real>(S.ch[j].th, S.ch[j].th_f) ? Real(0) : v;
             cum += v * u;
-            if (chosen < 0 && target < cum) chosen = j;
+            chosen = (chosen < 0 && target < cum) ? j : chosen;
         }
     }
     if (cum > numax_n) atomicAdd(&s_cnt[C_VIOL_GAS], 1u);
@@ -267,62 +266,56 @@ __device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int
     Real nd[3];
     iso_dir<Real>(unif<Real>(b.y), unif<Real>(b.z), nd);
     const Real mf = pick<Real>(S.mfrac, S.mfrac_f), Mf = pick<Real>(S.Mfrac, S.Mfrac_f);
+    // one centre-of-mass scattering serves every channel that scatters:
+    // elastic (4), (5), isotropic (6) with no loss, (7)-(12) and (18) with
+    // the loss of Eq. 5; its result is unused by (15)-(17) and resonant (6)
+    const bool elastic = r <= 6;
+    const bool dies = r >= 15 && r <= 17;
     Real vo[3], Vo[3];
-    switch (r) {
-    case 4: case 5:
-        cm_scatter<Real>(mf, Mf, v, V, Real(0), nd, vo, Vo);
-        vx = vo[0]; vy = vo[1]; vz = vo[2];
-        return true;
-    case 6:
-        if (Dd.cx_iso) {
-            cm_scatter<Real>(mf, Mf, v, V, Real(0), nd, vo, Vo);
-            vx = vo[0]; vy = vo[1]; vz = vo[2];
-        } else {
-            vx = V[0]; vy = V[1]; vz = V[2];  // resonant exchange
-        }
-        return true;
-    case 15: {
-        const TableDesc &Tc = W.tables[ch.table];
-        Real Ea = E - pick<Real>(Tc.th, Tc.th_f);
-        Ea = Ea > Real(0) ? Ea : Real(0);
-        Real w = sqrt(Ea * pick<Real>(Dd.f15, Dd.f15_f));
-        Real pv[3];
+    cm_scatter<Real>(mf, Mf, v, V, elastic ? Real(0) : pick<Real>(ch.dloss, ch.dloss_f), nd, vo, Vo);
+    const bool swap = r == 6 && !Dd.cx_iso;  // resonant exchange: the ion takes the gas velocity
 #pragma unroll
-        for (int q = 0; q < 3; ++q) pv[q] = mf * v[q] + Mf * V[q] + w * nd[q];
-        stage_birth<Real>(B, W.ctl, tag, 1, c, off, pv, staged);
-        return false;
-    }
-    case 16: {
-        Real sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * pick<Real>(Dd.f16, Dd.f16_f);
-        Real pv[3] = {sp * nd[0], sp * nd[1], sp * nd[2]};
-        stage_birth<Real>(B, W.ctl, tag, 0, c, off, pv, staged);
-        return false;
-    }
-    case 17: {
-        Real w = sqrt(E * pick<Real>(Dd.f17, Dd.f17_f));
-        Real pv[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) pv[q] = mf * v[q] + Mf * V[q] + w * nd[q];
-        stage_birth<Real>(B, W.ctl, tag, 0, c, off, pv, staged);
-        return false;
-    }
-    case 18: {
-        cm_scatter<Real>(mf, Mf, v, V, pick<Real>(ch.dloss, ch.dloss_f), nd, vo, Vo);
+    for (int q = 0; q < 3; ++q) vo[q] = swap ? V[q] : vo[q];
+    if (r == 18) {
+        // ionisation: the O2 splits into O2+ and a second electron with the
+        // post-collision O2 velocity, then the two electrons collide
+        // elastically (isotropic in their centre of mass)
         uint4 e = rng_block(Dd.seed, Dd.discharge, s, 1, 0, 2, step, idx);
         Real n2v[3];
         iso_dir<Real>(unif<Real>(e.x), unif<Real>(e.y), n2v);
         Real e2[3] = {Vo[0], Vo[1], Vo[2]};
         ee_elastic<Real>(vo, e2, n2v);
-        vx = vo[0]; vy = vo[1]; vz = vo[2];
         stage_birth<Real>(B, W.ctl, tag, 0, c, off, e2, staged);
         stage_birth<Real>(B, W.ctl, tag | 1, 2, c, off, Vo, staged);
-        return true;
     }
-    default:  // 7-12: inelastic, Eq. 5
-        cm_scatter<Real>(mf, Mf, v, V, pick<Real>(ch.dloss, ch.dloss_f), nd, vo, Vo);
+    if (!dies) {
         vx = vo[0]; vy = vo[1]; vz = vo[2];
         return true;
     }
+    // (15) attachment: O- with the CM velocity plus half the relative
+    // energy above threshold shared back to back with O; (16) detachment:
+    // electron with a tenth of the O- energy, isotropic; (17) associative
+    // detachment: electron with the CM energy about the CM velocity
+    Real w;
+    if (r == 16) {
+        w = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * pick<Real>(Dd.f16, Dd.f16_f);
+    } else {
+        Real arg;
+        if (r == 15) {
+            const TableDesc &Tc = W.tables[ch.table];
+            const Real Ea = E - pick<Real>(Tc.th, Tc.th_f);
+            arg = (Ea > Real(0) ? Ea : Real(0)) * pick<Real>(Dd.f15, Dd.f15_f);
+        } else {
+            arg = E * pick<Real>(Dd.f17, Dd.f17_f);
+        }
+        w = sqrt(arg);
+    }
+    const Real A = r == 16 ? Real(0) : Real(1);
+    Real pv[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) pv[q] = A * (mf * v[q] + Mf * V[q]) + w * nd[q];
+    stage_birth<Real>(B, W.ctl, tag, r == 15 ? 1 : 0, c, off, pv, staged);
+    return false;
 }
 
 template <typename Acc> __device__ __forceinline__ void acc_add(Acc *a, Acc v);
@@ -331,30 +324,6 @@ template <> __device__ __forceinline__ void acc_add(unsigned long long *a, unsig
     atomicAdd(a, v);
 }
 template <> __device__ __forceinline__ void acc_add(double *a, double v) { atomicAdd(a, v); }
-
-// deposit of one slot per lane, aggregated over lanes that share a cell
-__device__ __forceinline__ void deposit_warp(unsigned long long *sAcc, int c, float off)
-{
-    unsigned w1 = 0, w0 = 0;
-    if (c >= 0) {
-        w1 = __float2uint_rn(off * (float)(1 << FIX_BITS));
-        w0 = (1u << FIX_BITS) - w1;
-    }
-    unsigned peers = __match_any_sync(0xffffffffu, c);
-    unsigned s0 = __reduce_add_sync(peers, w0);
-    unsigned s1 = __reduce_add_sync(peers, w1);
-    if (c >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
-        atomicAdd(&sAcc[c], (unsigned long long)s0);
-        atomicAdd(&sAcc[c + 1], (unsigned long long)s1);
-    }
-}
-__device__ __forceinline__ void deposit_warp(double *sAcc, int c, double off)
-{
-    if (c >= 0) {
-        atomicAdd(&sAcc[c], 1.0 - off);
-        atomicAdd(&sAcc[c + 1], off);
-    }
-}
 
 // Exact 64-bit accumulation in shared memory with native 32-bit atomics: the
 // node's low word takes the add, and the value it returns tells whether the
@@ -408,10 +377,11 @@ template <typename Real> __device__ __forceinline__ typename AccT<Real>::T *acc_
 template <> __device__ __forceinline__ unsigned long long *acc_global<float>(const WsPtrs &W) { return W.acc_fix; }
 template <> __device__ __forceinline__ double *acc_global<double>(const WsPtrs &W) { return W.acc_dbl; }
 
-// Charge of the four slots of a thread into the shared grid.  When every
-// lane's four slots sit in one cell, a lane's four weights are summed first
-// (4 * 32 * 2^FIX_BITS < 2^32); when the whole warp shares that cell, no
-// match is needed at all.
+// Charge of the four slots of a thread into the shared grid.  When the
+// whole warp's slots sit in one cell (sorted, slow particles), the weights
+// are summed over the warp and one lane adds them; otherwise every lane adds
+// its own (its four weights summed first when they share a cell, and
+// 4 * 32 * 2^FIX_BITS < 2^32).  No lane-matching: it runs on a narrow pipe.
 __device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep[4], const float off[4])
 {
     unsigned w0[4], w1[4];
@@ -422,36 +392,28 @@ __device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep
     }
     const int lane = threadIdx.x & 31;
     const bool same = dep[0] >= 0 && dep[1] == dep[0] && dep[2] == dep[0] && dep[3] == dep[0];
-    if (__all_sync(0xffffffffu, same)) {
-        const unsigned a = w0[0] + w0[1] + w0[2] + w0[3];
-        const unsigned b = w1[0] + w1[1] + w1[2] + w1[3];
-        const int c0 = __shfl_sync(0xffffffffu, dep[0], 0);
-        if (__all_sync(0xffffffffu, dep[0] == c0)) {
-            const unsigned sa = __reduce_add_sync(0xffffffffu, a);
-            const unsigned sb = __reduce_add_sync(0xffffffffu, b);
-            if (lane == 0) {
-                acc64_add(&sAcc[c0], sa);
-                acc64_add(&sAcc[c0 + 1], sb);
-            }
-        } else {
-            const unsigned peers = __match_any_sync(0xffffffffu, dep[0]);
-            const unsigned sa = __reduce_add_sync(peers, a);
-            const unsigned sb = __reduce_add_sync(peers, b);
-            if (lane == __ffs(peers) - 1) {
-                acc64_add(&sAcc[dep[0]], sa);
-                acc64_add(&sAcc[dep[0] + 1], sb);
-            }
+    const unsigned a = w0[0] + w0[1] + w0[2] + w0[3];
+    const unsigned b = w1[0] + w1[1] + w1[2] + w1[3];
+    const int c0 = __shfl_sync(0xffffffffu, dep[0], 0);
+    if (__all_sync(0xffffffffu, same && dep[0] == c0)) {
+        const unsigned sa = __reduce_add_sync(0xffffffffu, a);
+        const unsigned sb = __reduce_add_sync(0xffffffffu, b);
+        if (lane == 0) {
+            acc64_add(&sAcc[c0], sa);
+            acc64_add(&sAcc[c0 + 1], sb);
         }
+        return;
+    }
+    if (same) {
+        acc64_add(&sAcc[dep[0]], a);
+        acc64_add(&sAcc[dep[0] + 1], b);
         return;
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const unsigned peers = __match_any_sync(0xffffffffu, dep[k]);
-        const unsigned sa = __reduce_add_sync(peers, w0[k]);
-        const unsigned sb = __reduce_add_sync(peers, w1[k]);
-        if (dep[k] >= 0 && lane == __ffs(peers) - 1) {
-            acc64_add(&sAcc[dep[k]], sa);
-            acc64_add(&sAcc[dep[k] + 1], sb);
+        if (dep[k] >= 0) {
+            acc64_add(&sAcc[dep[k]], w0[k]);
+            acc64_add(&sAcc[dep[k] + 1], w1[k]);
         }
     }
 }
