@@ -30,7 +30,12 @@ namespace o2 {
 
 // three 256-thread blocks per SM in the FP32 path (the rare collision path
 // may spill a little), two in the FP64 path
-template <typename Real> struct PushOcc { static constexpr int blocks = sizeof(Real) == 4 ? 3 : 2; };
+#ifndef O2_PUSH_BLOCKS_F32
+#define O2_PUSH_BLOCKS_F32 3
+#endif
+template <typename Real> struct PushOcc {
+    static constexpr int blocks = sizeof(Real) == 4 ? O2_PUSH_BLOCKS_F32 : 2;
+};
 
 template <typename Real> struct AccT;
 template <> struct AccT<float> { using T = unsigned long long; };
@@ -325,30 +330,48 @@ template <> __device__ __forceinline__ void acc_add(unsigned long long *a, unsig
 }
 template <> __device__ __forceinline__ void acc_add(double *a, double v) { atomicAdd(a, v); }
 
-// Exact 64-bit accumulation in shared memory with native 32-bit atomics: the
-// node's low word takes the add, and the value it returns tells whether the
-// add carried into the high word.
-__device__ __forceinline__ void acc64_add(unsigned long long *node, unsigned v)
+// Shared charge grid of the FP32 path: the 8 bytes of a node hold two
+// signed 32-bit sums, of the low SPLIT_BITS bits of the fixed-point weights
+// (word 0) and of the rest (word 1); the node's value is
+// word1 * 2^SPLIT_BITS + word0.  Adds are plain 32-bit atomics whose result
+// is not needed (no carry), and both sums stay exact while a block adds at
+// most FLUSH_TICKETS tickets of weights before it flushes (each weight is
+// below 2^FIX_BITS, so word 1 stays below 2^(FIX_BITS - SPLIT_BITS) per
+// particle and word 0 below 2^SPLIT_BITS per add).
+constexpr int SPLIT_BITS = 12;
+constexpr int FLUSH_TICKETS = 32;
+static_assert((long long)FLUSH_TICKETS * TILES_PER_TICKET * CHUNK * (1LL << (FIX_BITS - SPLIT_BITS)) < (1LL << 31),
+              "split sums must stay within int32");
+__device__ __forceinline__ void split_add(unsigned long long *node, unsigned v)
 {
-    unsigned *w = reinterpret_cast<unsigned *>(node);  // little endian: w[0] low, w[1] high
-    const unsigned old = atomicAdd(&w[0], v);
-    if (old + v < old) atomicAdd(&w[1], 1u);
+    unsigned *w = reinterpret_cast<unsigned *>(node);  // w[0] low part, w[1] high part
+    atomicAdd(&w[0], v & ((1u << SPLIT_BITS) - 1u));
+    atomicAdd(&w[1], v >> SPLIT_BITS);
 }
-__device__ __forceinline__ void acc64_sub(unsigned long long *node, unsigned v)
+__device__ __forceinline__ void split_sub(unsigned long long *node, unsigned v)
 {
     unsigned *w = reinterpret_cast<unsigned *>(node);
-    const unsigned old = atomicSub(&w[0], v);
-    if (old < v) atomicSub(&w[1], 1u);
+    atomicSub(&w[0], v & ((1u << SPLIT_BITS) - 1u));
+    atomicSub(&w[1], v >> SPLIT_BITS);
+}
+__host__ __device__ __forceinline__ unsigned long long split_value(unsigned long long node)
+{
+    const long long lo = (int)(unsigned)(node & 0xFFFFFFFFull);
+    const long long hi = (int)(unsigned)(node >> 32);
+    return (unsigned long long)(hi * (1LL << SPLIT_BITS) + lo);
 }
 
+__device__ __forceinline__ unsigned long long acc_value(unsigned long long node) { return split_value(node); }
+__device__ __forceinline__ double acc_value(double node) { return node; }
+
 // removal of one particle deposited in phase A (it died in a collision):
-// the same fixed-point weights, so the accumulator returns exactly
+// the same fixed-point weights, so the node value returns exactly
 __device__ __forceinline__ void deposit_shared_remove(unsigned long long *sAcc, int c, float off)
 {
     const unsigned w1 = __float2uint_rn(off * (float)(1 << FIX_BITS));
     const unsigned w0 = (1u << FIX_BITS) - w1;
-    acc64_sub(&sAcc[c], w0);
-    acc64_sub(&sAcc[c + 1], w1);
+    split_sub(&sAcc[c], w0);
+    split_sub(&sAcc[c + 1], w1);
 }
 __device__ __forceinline__ void deposit_shared_remove(double *sAcc, int c, double off)
 {
@@ -399,22 +422,22 @@ __device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep
         const unsigned sa = __reduce_add_sync(0xffffffffu, a);
         const unsigned sb = __reduce_add_sync(0xffffffffu, b);
         if (lane == 0) {
-            acc64_add(&sAcc[c0], sa);
-            acc64_add(&sAcc[c0 + 1], sb);
+            split_add(&sAcc[c0], sa);
+            split_add(&sAcc[c0 + 1], sb);
         }
         return;
     }
     if (same) {
-        acc64_add(&sAcc[dep[0]], a);
-        acc64_add(&sAcc[dep[0] + 1], b);
+        split_add(&sAcc[dep[0]], a);
+        split_add(&sAcc[dep[0] + 1], b);
         return;
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (dep[k] >= 0) {
-            acc64_add(&sAcc[dep[k]], w0[k]);
-            acc64_add(&sAcc[dep[k] + 1], w1[k]);
-        }
+        // an empty slot adds zero weights to node 0
+        const int ck = dep[k] >= 0 ? dep[k] : 0;
+        split_add(&sAcc[ck], w0[k]);
+        split_add(&sAcc[ck + 1], w1[k]);
     }
 }
 __device__ __forceinline__ void deposit4(double *sAcc, const int dep[4], const double off[4])
@@ -467,7 +490,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     const unsigned lt_mask = (1u << lane) - 1u;
     BirthStage<Real> B{bCell, bTag, bOff, bVx, bVy, bVz, &s_wnb[w]};
 
-    int ds = -1, d = -1;
+    int ds = -1, d = -1, run_tk = 0;
     for (int q = tid; q < C_NCOUNT; q += PUSH_THREADS) s_cnt[q] = 0;
     if (lane == 0) s_wnb[w] = 0;
 
@@ -477,7 +500,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         __syncthreads();
         Acc *g = accG + (size_t)fs * W.total_nodes + Dd.gbase;
         for (int i = tid; i <= Dd.N; i += PUSH_THREADS) {
-            Acc v = sAcc[i];
+            const Acc v = acc_value(sAcc[i]);
             if (v != Acc(0)) acc_add(&g[i], v);
         }
         for (int q = tid; q < C_NCOUNT; q += PUSH_THREADS) {
@@ -506,7 +529,8 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         int nx = ds < 0 ? 0 : ds;
         while (nx < nds && !(tbeg >= W.cnt[nx].chunk0 && tbeg < W.cnt[nx].chunk0 + W.cnt[nx].nchunk)) ++nx;
         if (nx >= nds) continue;
-        if (nx != ds) {
+        // a new (d, s), or the FP32 split sums at their bound: flush
+        if (nx != ds || (sizeof(Real) == 4 && run_tk >= FLUSH_TICKETS)) {
             if (ds >= 0) flush(ds);
             const int nd = nx / NSP;
             const Disc &Dn = W.disc[nd];
@@ -522,8 +546,10 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 for (int i = tid; i < fm_max; i += PUSH_THREADS) sFm[i] = 0;
             }
             ds = nx;
+            run_tk = 0;
             __syncthreads();
         }
+        ++run_tk;
         const int s = ds % NSP;
         const Disc &Dd = W.disc[d];
         const SpeciesC &S = Dd.sp[s];
@@ -624,63 +650,37 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             if (c[0] >= 0 || c[1] >= 0 || c[2] >= 0 || c[3] >= 0)
                 w4 = rng_block(Dd.seed, Dd.discharge, s, 0, 0, 0, step, (unsigned)((i0 - pb) >> 2));
             const unsigned wk[4] = {w4.x, w4.y, w4.z, w4.w};
-            unsigned nslots = 0, nlive = 0;
+            // each slot is pushed without branches; absorptions are noted in
+            // a mask and handled after the four slots
+            unsigned nslots = 0, nlive = 0, outm = 0, wallm = 0;
             int dep[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int ck = c[k];
-                dep[k] = -1;
-                bool cand = false;
-                if (ck >= -1) ++nslots;
-                if (ck >= 0) {
-                    ++nlive;
-                    const Real e0 = sE[ck], e1 = sE[ck + 1];
-                    const Real ep = e0 + off[k] * (e1 - e0);
-                    const Real v = vx[k] + qm * ep;
-                    Real o = off[k] + v;
-                    const Real fl = floor(o);
-                    const bool bad = !(fl > Real(-2 * N - 4) && fl < Real(2 * N + 4));
-                    int cn = bad ? (v < Real(0) ? -1 : N) : ck + (int)fl;
-                    o -= fl;
-                    if (o >= Real(1)) { o -= Real(1); cn += 1; }
-                    vx[k] = v;
-                    if (cn < 0 || cn >= N) {
-                        const int wall = cn < 0 ? 0 : 1;
-                        atomicAdd(&s_cnt[C_ABS + 2 * s + wall], 1u);
-                        if (s == 2 && Dd.iedf_bins > 0) {
-                            const Real vy = vyA[i0 + k], vz = vzA[i0 + k];
-                            const Real Ei = pick<Real>(S.ke_eV, S.ke_eV_f) * (v * v + vy * vy + vz * vz);
-                            const Real bb = floor(Ei * pick<Real>(Dd.iedf_scale, Dd.iedf_scale_f));
-                            if (bb >= Real(0) && bb < Real(Dd.iedf_bins))
-                                atomicAdd(&W.iedf[Dd.iedf_base + wall * Dd.iedf_bins + (int)bb], 1u);
-                        }
-                        c[k] = -1;
-                    } else {
-                        off[k] = o;
-                        c[k] = cn;
-                        dep[k] = cn;
-                        cand = wk[k] < tnull;
-                        if (DIAG) {
-                            // distributions after the free flight, before collisions
-                            if (s == 0 && cn == N / 2 && Dd.eedf_bins > 0) {
-                                const Real vy = vyA[i0 + k], vz = vzA[i0 + k];
-                                const Real Ee = pick<Real>(S.ke_eV, S.ke_eV_f) * (v * v + vy * vy + vz * vz);
-                                const Real bb = floor(Ee * pick<Real>(Dd.eedf_scale, Dd.eedf_scale_f));
-                                if (bb >= Real(0) && bb < Real(Dd.eedf_bins)) atomicAdd(&sEedf[(int)bb], 1u);
-                            }
-                            if (s == 1 && Dd.fm_bins > 0) {
-                                Real Es = pick<Real>(S.ke_eV, S.ke_eV_f) * v * v;
-                                if (v < Real(0)) Es = -Es;
-                                const Real bb = floor((Es + pick<Real>(Dd.fm_emax, Dd.fm_emax_f)) *
-                                                      pick<Real>(Dd.fm_scale, Dd.fm_scale_f));
-                                if (bb >= Real(0) && bb < Real(Dd.fm_bins)) {
-                                    const int xb = (int)(((long long)cn * Dd.fm_xbins) / N);
-                                    atomicAdd(&sFm[xb * Dd.fm_bins + (int)bb], 1u);
-                                }
-                            }
-                        }
-                    }
-                }
+                const bool was = ck >= 0;
+                nslots += ck >= -1 ? 1u : 0u;
+                nlive += was ? 1u : 0u;
+                const int cc = was ? ck : 0;
+                const Real e0 = sE[cc], e1 = sE[cc + 1];
+                const Real ep = e0 + off[k] * (e1 - e0);
+                const Real v = vx[k] + qm * ep;
+                Real o = off[k] + v;
+                const Real fl = floor(o);
+                const bool bad = !(fl > Real(-2 * N - 4) && fl < Real(2 * N + 4));
+                int cn = bad ? (v < Real(0) ? -1 : N) : cc + (int)fl;
+                o -= fl;
+                const bool wrap = o >= Real(1);
+                o = wrap ? o - Real(1) : o;
+                cn += wrap ? 1 : 0;
+                const bool out = was && (cn < 0 || cn >= N);
+                const bool live = was && !out;
+                outm |= out ? 1u << k : 0u;
+                wallm |= cn >= N ? 1u << k : 0u;
+                vx[k] = was ? v : vx[k];
+                off[k] = live ? o : off[k];
+                c[k] = was ? (out ? -1 : cn) : ck;
+                dep[k] = live ? cn : -1;
+                const bool cand = live && wk[k] < tnull;
                 const unsigned m = __ballot_sync(0xffffffffu, cand);
                 if (cand) {
                     const int pos = qn + __popc(m & lt_mask);
@@ -688,6 +688,46 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                     qVx[pos] = vx[k];
                 }
                 qn += __popc(m);
+            }
+            if (outm) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!((outm >> k) & 1u)) continue;
+                    const int wall = (wallm >> k) & 1u;
+                    atomicAdd(&s_cnt[C_ABS + 2 * s + wall], 1u);
+                    if (s == 2 && Dd.iedf_bins > 0) {
+                        const Real v = vx[k], vy = vyA[i0 + k], vz = vzA[i0 + k];
+                        const Real Ei = pick<Real>(S.ke_eV, S.ke_eV_f) * (v * v + vy * vy + vz * vz);
+                        const Real bb = floor(Ei * pick<Real>(Dd.iedf_scale, Dd.iedf_scale_f));
+                        if (bb >= Real(0) && bb < Real(Dd.iedf_bins))
+                            atomicAdd(&W.iedf[Dd.iedf_base + wall * Dd.iedf_bins + (int)bb], 1u);
+                    }
+                }
+            }
+            if (DIAG) {
+                // distributions after the free flight, before collisions
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int cn = dep[k];
+                    if (cn < 0) continue;
+                    const Real v = vx[k];
+                    if (s == 0 && cn == N / 2 && Dd.eedf_bins > 0) {
+                        const Real vy = vyA[i0 + k], vz = vzA[i0 + k];
+                        const Real Ee = pick<Real>(S.ke_eV, S.ke_eV_f) * (v * v + vy * vy + vz * vz);
+                        const Real bb = floor(Ee * pick<Real>(Dd.eedf_scale, Dd.eedf_scale_f));
+                        if (bb >= Real(0) && bb < Real(Dd.eedf_bins)) atomicAdd(&sEedf[(int)bb], 1u);
+                    }
+                    if (s == 1 && Dd.fm_bins > 0) {
+                        Real Es = pick<Real>(S.ke_eV, S.ke_eV_f) * v * v;
+                        if (v < Real(0)) Es = -Es;
+                        const Real bb = floor((Es + pick<Real>(Dd.fm_emax, Dd.fm_emax_f)) *
+                                              pick<Real>(Dd.fm_scale, Dd.fm_scale_f));
+                        if (bb >= Real(0) && bb < Real(Dd.fm_bins)) {
+                            const int xb = (int)(((long long)cn * Dd.fm_xbins) / N);
+                            atomicAdd(&sFm[xb * Dd.fm_bins + (int)bb], 1u);
+                        }
+                    }
+                }
             }
             deposit4(sAcc, dep, off);
             {
