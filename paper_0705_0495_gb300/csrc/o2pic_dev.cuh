@@ -97,7 +97,11 @@ struct PairC {          // particle-target reaction of one discharge
     double Ek;          // (1/2) mu (dx/dt)^2 / e
     double mfrac, Mfrac;// m/(m+M), M/(m+M) of the pair
     double dloss;       // 2 dE/mu (dt/dx)^2
+    // bound on sigma(E) u_n over the table: sigma u_n <= max(bnd_g, bnd_s * u_n)
+    // (u_n relative speed in cells per step; margins included)
+    double bnd_g, bnd_s;
     float Ek_f, mfrac_f, Mfrac_f, dloss_f, coef_f, pad_f;
+    float bnd_g_f, bnd_s_f;
 };
 
 struct Disc {
@@ -190,6 +194,7 @@ struct WsPtrs {
     int *pair_bcount;         // [total cells] births of (19) per cell
     int *cell_disc;           // [total cells] discharge of each global cell
     int *pair_first;          // [total cells] first flagged projectile of the current reaction
+    unsigned *vmax2;          // [D * 3] largest speed^2 (cells/step, float bits) at the last sort
     int *pair_kills;          // [total cells * 3] particles killed per species in this pass
     void *pair_births;        // [total cells * PAIR_BIRTH_CAP] records
     int total_nodes;

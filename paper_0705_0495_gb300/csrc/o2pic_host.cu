@@ -76,7 +76,7 @@ struct Bump {
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
+    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
         counters, eedf, iedf, fm, tables, lutE, lutS, lutEf, lutSf, sort_counts, cell_start,
         sort_live, pair_bcount, cell_disc, pair_births, sort_tab, ninit, vt;
     size_t cell[2], off[2], vx[2], vy[2], vz[2];
@@ -304,6 +304,7 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.pair_bcount = B.take(4ull * tc);
     L.cell_disc = B.take(4ull * tc);
     L.pair_first = B.take(4ull * tc);
+    L.vmax2 = B.take(4ull * 3 * D);
     L.pair_kills = B.take(4ull * 3 * tc);
     for (int s = 0; s < 3; ++s) {
         long long tiles = 0;
@@ -524,6 +525,24 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
         P.Mfrac_f = (float)P.Mfrac;
         P.dloss_f = (float)P.dloss;
         P.coef_f = (float)P.coef;
+        // Bound on sigma(E) u over the table, u in cells per step: on a
+        // segment [E_k, E_k+1] sigma is at most the larger end value and
+        // u <= U_k+1 = sqrt(E_k+1 / Ek); below the grid sigma is the first
+        // value and u < U_0; above it sigma is the last value, so sigma u
+        // grows as bnd_s * u.  A relative margin covers the rounding of the
+        // device's sigma, u and E.
+        P.bnd_g = P.bnd_s = 0.0;
+        if (P.table >= 0) {
+            const HostTable &t = h->tabs[P.table];
+            const int n = (int)t.E.size();
+            double g = t.S[0] * std::sqrt(t.E[0] / P.Ek);
+            for (int q = 0; q + 1 < n; ++q)
+                g = std::max(g, std::max(t.S[q], t.S[q + 1]) * std::sqrt(t.E[q + 1] / P.Ek));
+            P.bnd_g = g * 1.001;
+            P.bnd_s = t.S[n - 1] * 1.001;
+        }
+        P.bnd_g_f = (float)(P.bnd_g * 1.0001);
+        P.bnd_s_f = (float)(P.bnd_s * 1.0001);
     }
     h->disc[d] = D;
 }
@@ -600,6 +619,7 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.pair_bcount = reinterpret_cast<int *>(b + L.pair_bcount);
     W.cell_disc = reinterpret_cast<int *>(b + L.cell_disc);
     W.pair_first = reinterpret_cast<int *>(b + L.pair_first);
+    W.vmax2 = reinterpret_cast<unsigned *>(b + L.vmax2);
     W.pair_kills = reinterpret_cast<int *>(b + L.pair_kills);
     W.pair_births = b + L.pair_births;
     W.total_nodes = L.total_nodes;

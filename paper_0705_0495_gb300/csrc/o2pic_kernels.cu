@@ -386,6 +386,7 @@ k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
     const Disc &Dd = W.disc[d];
     const int N = Dd.N, n = W.cnt[ds].n;
     const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
+    if (bi == 0 && threadIdx.x == 0) W.vmax2[ds] = 0u;  // raised by the scatter
     if (bi >= G) return;
     for (int i = threadIdx.x; i <= N; i += blockDim.x) ssm[i] = 0;
     __syncthreads();
@@ -555,6 +556,7 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
     Real *offD = P.off[nxt] + pb, *vxD = P.vx[nxt] + pb, *vyD = P.vy[nxt] + pb,
          *vzD = P.vz[nxt] + pb;
     const unsigned lt = (1u << lane) - 1u;
+    float vm2 = 0.f;  // largest speed^2 of the live particles this lane moves
     for (int i0 = lo; i0 < hi; i0 += 32 * SORT_ILP) {
         int b[SORT_ILP];
         int dst[SORT_ILP];
@@ -599,6 +601,7 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
                 rx[r] = __ldg(&vxS[i]);
                 ry[r] = __ldg(&vyS[i]);
                 rz[r] = __ldg(&vzS[i]);
+                vm2 = fmaxf(vm2, (float)(rx[r] * rx[r] + ry[r] * ry[r] + rz[r] * rz[r]));
             }
         }
 #pragma unroll
@@ -613,6 +616,10 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
             }
         }
     }
+    // speed bound of the species for the particle-target pass (float bits of
+    // a non-negative number order like unsigned integers)
+    const unsigned vb = __reduce_max_sync(0xffffffffu, __float_as_uint(vm2));
+    if (lane == 0 && vb) atomicMax(&W.vmax2[ds], vb);
 }
 
 __global__ void k_sort_finish(WsPtrs W)
@@ -707,6 +714,19 @@ k_pair_eval(WsPtrs W, Pools<Real> P, int par, int k, const int *tab)
     const int rx = k == 0 ? 13 : (k == 1 ? 14 : 19);
     const unsigned long long step = W.ctl->step[par];
     const uint4 d0 = rng_block(Dd.seed, Dd.discharge, ps, 2, rx, 0, step, (unsigned)i);
+    {
+        // Exact skip: P = n sigma u tau is at most liveT * coef *
+        // max(bnd_g, bnd_s * u) with u below the sum of the two species'
+        // largest speeds at the sort, so a draw at or above that bound
+        // rejects whatever partner is drawn; the partner is not read.
+        const float vP = sqrtf(__uint_as_float(W.vmax2[d * NSP + ps]));
+        const float vT = sqrtf(__uint_as_float(W.vmax2[d * NSP + pt]));
+        const Real ub = Real((vP + vT) * 1.00001f);
+        const Real bg = pick<Real>(pc.bnd_g, pc.bnd_g_f), bs = pick<Real>(pc.bnd_s, pc.bnd_s_f);
+        const Real M = bg > bs * ub ? bg : bs * ub;
+        const Real Bd = Real(liveT) * pick<Real>(pc.coef, pc.coef_f) * M;
+        if (Bd < Real(1) && !(unif<Real>(d0.y) < Bd)) return;
+    }
     int j = t0 + (int)__umulhi(d0.x, (unsigned)range);
     int walked = 0;
     const int *cellA = P.cell[cur];

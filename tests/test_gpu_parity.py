@@ -197,6 +197,51 @@ def test_fp64_ragged_small_and_degenerate_sizes():
     assert ex < TOL64 and ev < TOL64
 
 
+def _scaled_pair_tables(factor):
+    tabs = inputs.xs_tables()
+    for t in tabs:
+        if t["reaction"] in (13, 14, 19):
+            t["sigma_m2"] = t["sigma_m2"] * factor
+    return tabs
+
+
+def test_fp64_pair_pass_with_frequent_events():
+    # particle-target cross sections scaled up so that (13), (14) and (19)
+    # fire in every pass: the exact skip of the pair evaluation (a bound on
+    # n sigma u tau) must leave the same events, kills and births as the
+    # oracle, which evaluates every projectile
+    d = inputs.cfg1(n_op=6000)
+    tabs = _scaled_pair_tables(3e6)
+    sim, orc, (ex, ev) = _run_pair(d, [10, 11, 20, 30], tabs)
+    assert ex < TOL64 and ev < TOL64, (ex, ev)
+    g, o = sim.diagnostics(0), orc.counters()
+    assert np.array_equal(g["events"], o["events"])
+    assert g["events"][13] > 0 and g["events"][14] > 0 and g["events"][19] > 0, g["events"]
+
+
+def test_fp32_pair_pass_with_frequent_events():
+    d = inputs.cfg1(fp64=False, n_op=6000)
+    tabs = _scaled_pair_tables(3e6)
+    sim = _sim(d, tabs)
+    orc = oracle.Oracle(d, tabs)
+    orc.step(9)
+    compared = flips = 0
+    worst = 0.0
+    for n in range(9, 21):
+        for s in range(3):
+            st = orc.get(s)
+            sim.set_state(0, s, st["x"], st["vx"], st["vy"], st["vz"], st["alive"])
+        sim.set_step(n)
+        sim.step(1)
+        orc.step(1)
+        for s in range(3):
+            c, f, w = _matched(d, sim.get_state(0, s), orc.get(s), s, TOL32)
+            compared, flips, worst = compared + c, flips + f, max(worst, w)
+    assert worst < TOL32
+    assert flips <= 1e-3 * compared, (flips, compared)
+    assert sim.diagnostics(0)["events"][[13, 14, 19]].sum() > 0
+
+
 def test_fp64_empty_discharge():
     d = inputs.cfg1(n_op=0)
     sim, orc, _ = _run_pair(d, [5])
