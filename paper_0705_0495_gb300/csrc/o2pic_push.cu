@@ -37,67 +37,6 @@ template <typename Real> struct PushOcc {
     static constexpr int blocks = sizeof(Real) == 4 ? O2_PUSH_BLOCKS_F32 : 2;
 };
 
-// FP32 path: each warp keeps the cell, offset and vx of its next 128-slot
-// sub-tile in flight (one stage in shared memory, filled by bulk
-// asynchronous copies) while it works on the current one, and reads E
-// through the read-only cache, which leaves the shared memory for the stage
-// at three blocks per SM.  The FP64 path loads directly and keeps E in
-// shared memory.
-#ifndef O2_PUSH_STAGES_F32
-#define O2_PUSH_STAGES_F32 1
-#endif
-template <typename Real> struct PushStages { static constexpr int value = sizeof(Real) == 4 ? O2_PUSH_STAGES_F32 : 0; };
-template <typename Real> struct PushFieldGlobal { static constexpr bool value = sizeof(Real) == 4; };
-template <typename Real> struct StageBytes {
-    static constexpr unsigned value = SUBTILE * (sizeof(int) + 2 * sizeof(Real));
-};
-
-// ---- bulk asynchronous copies global -> shared, completed on an mbarrier
-__device__ __forceinline__ unsigned smem_addr(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
-{
-    unsigned done;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(done)
-                 : "r"(smem_addr(bar)), "r"(parity)
-                 : "memory");
-    return done != 0;
-}
-// bytes: a multiple of 16; both addresses 16-byte aligned
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-// orders this thread's earlier generic accesses of shared memory before its
-// later asynchronous-proxy accesses (a stage is refilled after it was read)
-__device__ __forceinline__ void fence_proxy_async_shared()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-constexpr long long MBAR_SPIN_LIMIT = 1LL << 20;
-
-
 template <typename Real> struct AccT;
 template <> struct AccT<float> { using T = unsigned long long; };
 template <> struct AccT<double> { using T = double; };
@@ -518,33 +457,26 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
 {
     using Acc = typename AccT<Real>::T;
     constexpr int NW = PUSH_THREADS / 32;
-    constexpr int ST = PushStages<Real>::value;
-    constexpr int STQ = ST > 0 ? ST : 1;
-    constexpr unsigned SB = StageBytes<Real>::value;
-    constexpr bool GE = PushFieldGlobal<Real>::value;
     extern __shared__ __align__(16) unsigned char smem[];
-    // [stages of every warp][charge grid][field (FP64)][queues][births][histograms]
-    Acc *sAcc = reinterpret_cast<Acc *>(smem + (size_t)NW * ST * SB);
+    Acc *sAcc = reinterpret_cast<Acc *>(smem);
     Real *sE = reinterpret_cast<Real *>(sAcc + (Nmax + 2));
-    Real *qR = sE + (GE ? 0 : Nmax + 2);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     // per-warp candidate queue (index, vx after the push) and staged births
-    Real *qVx = qR + w * QCAP;
-    Real *bOff = qR + NW * QCAP + w * BSTAGE;
+    Real *qVx = sE + (Nmax + 2) + w * QCAP;
+    Real *bOff = sE + (Nmax + 2) + NW * QCAP + w * BSTAGE;
     Real *bVx = bOff + NW * BSTAGE;
     Real *bVy = bVx + NW * BSTAGE;
     Real *bVz = bVy + NW * BSTAGE;
-    int *ibase = reinterpret_cast<int *>(qR + NW * QCAP + 4 * NW * BSTAGE);
+    int *ibase = reinterpret_cast<int *>(sE + (Nmax + 2) + NW * QCAP + 4 * NW * BSTAGE);
     int *qIdx = ibase + w * QCAP;
     int *bCell = ibase + NW * QCAP + w * BSTAGE;
     int *bTag = ibase + NW * QCAP + NW * BSTAGE + w * BSTAGE;
     unsigned *sEedf = reinterpret_cast<unsigned *>(ibase + NW * QCAP + 2 * NW * BSTAGE);
     unsigned *sFm = sEedf + eedf_max;
 
-    __shared__ int s_tk[3];  // tickets of iterations it, it + 1, it + 2 (ring)
+    __shared__ int s_ticket[2];
     __shared__ int s_wnb[NW];
     __shared__ unsigned s_cnt[C_NCOUNT];
-    __shared__ __align__(8) unsigned long long s_bar[NW][STQ];
 
     Ctl *ctl = W.ctl;
     const int cur = ctl->cur;
@@ -559,58 +491,8 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     BirthStage<Real> B{bCell, bTag, bOff, bVx, bVy, bVz, &s_wnb[w]};
 
     int ds = -1, d = -1, run_tk = 0;
-    const Real *Ef = sE;  // E of the current discharge (shared, or global in the FP32 path)
     for (int q = tid; q < C_NCOUNT; q += PUSH_THREADS) s_cnt[q] = 0;
     if (lane == 0) s_wnb[w] = 0;
-    if (ST > 0 && lane == 0) {
-        for (int q = 0; q < ST; ++q) mbar_init(&s_bar[w][q], 1);
-        mbar_init_fence();
-    }
-    if (tid == 0) {
-        s_tk[0] = (int)atomicAdd(&ctl->ticket, (unsigned)TILES_PER_TICKET);
-        s_tk[1] = (int)atomicAdd(&ctl->ticket, (unsigned)TILES_PER_TICKET);
-    }
-    // (d, s) of a ticket: tiles of one (discharge, species) start at a
-    // multiple of TILES_PER_TICKET, so a ticket belongs to one (d, s) or to
-    // padding (returns nds); tickets of a block increase, so the search
-    // starts at the last (d, s) found
-    auto ticket_ds = [&](int tb, int from) {
-        int nx = from < 0 ? 0 : from;
-        while (nx < nds && !(tb >= W.cnt[nx].chunk0 && tb < W.cnt[nx].chunk0 + W.cnt[nx].nchunk)) ++nx;
-        return nx;
-    };
-
-    // ---- one-stage prefetch (FP32): `pf` is the first slot of the sub-tile
-    // whose copy is in flight (-1: none).  It is always the next sub-tile
-    // this warp consumes, so every issued copy is consumed; the one rule
-    // "copy iff the sub-tile starts below the live end" is used on both sides.
-    int pf = -1;
-    unsigned spar = 0;  // parity of the stage's next completion
-    bool broken = false;
-    auto issue = [&](int sb) {
-        if (lane == 0) {
-            unsigned char *st = smem + (size_t)w * SB;
-            mbar_arrive_expect_tx(&s_bar[w][0], SB);
-            bulk_load(st, cellA + sb, SUBTILE * sizeof(int), &s_bar[w][0]);
-            bulk_load(st + SUBTILE * sizeof(int), offA + sb, SUBTILE * sizeof(Real), &s_bar[w][0]);
-            bulk_load(st + SUBTILE * (sizeof(int) + sizeof(Real)), vxA + sb, SUBTILE * sizeof(Real), &s_bar[w][0]);
-        }
-        pf = sb;
-    };
-    auto wait_stage = [&]() {
-        long long spins = 0;
-        bool ok = true;
-        while (!mbar_try_wait(&s_bar[w][0], spar)) {
-            if (++spins > MBAR_SPIN_LIMIT) {
-                set_status(ctl, ST_TIMEOUT);
-                ok = false;
-                break;
-            }
-        }
-        broken = broken || __any_sync(0xffffffffu, !ok);
-        spar ^= 1u;
-        pf = -1;
-    };
 
     auto flush = [&](int fds) {
         const int fd = fds / NSP, fs = fds % NSP;
@@ -636,14 +518,16 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     };
 
     for (int it = 0;; ++it) {
-        // ring of three ticket slots: slot (it + 2) % 3 was last read in
-        // iteration it - 1, before this barrier
+        // two ticket buffers: a buffer is rewritten only after the barrier
+        // that every reader of its previous value has passed
+        if (tid == 0) s_ticket[it & 1] = (int)atomicAdd(&ctl->ticket, (unsigned)TILES_PER_TICKET);
         __syncthreads();
-        const int tbeg = s_tk[it % 3];
-        const int tnext = s_tk[(it + 1) % 3];
-        if (tid == 0) s_tk[(it + 2) % 3] = (int)atomicAdd(&ctl->ticket, (unsigned)TILES_PER_TICKET);
+        const int tbeg = s_ticket[it & 1];
         if (tbeg >= total) break;
-        const int nx = ticket_ds(tbeg, ds);
+        // tiles of one (discharge, species) start at a multiple of
+        // TILES_PER_TICKET, so a ticket belongs to one (d, s) or to padding
+        int nx = ds < 0 ? 0 : ds;
+        while (nx < nds && !(tbeg >= W.cnt[nx].chunk0 && tbeg < W.cnt[nx].chunk0 + W.cnt[nx].nchunk)) ++nx;
         if (nx >= nds) continue;
         // a new (d, s), or the FP32 split sums at their bound: flush
         if (nx != ds || (sizeof(Real) == 4 && run_tk >= FLUSH_TICKETS)) {
@@ -652,11 +536,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             const Disc &Dn = W.disc[nd];
             if (nd != d) {
                 const Real *Eg = reinterpret_cast<const Real *>(W.Ereal) + Dn.gbase;
-                if (GE) {
-                    Ef = Eg;
-                } else {
-                    for (int i = tid; i <= Dn.N; i += PUSH_THREADS) sE[i] = Eg[i];
-                }
+                for (int i = tid; i <= Dn.N; i += PUSH_THREADS) sE[i] = Eg[i];
                 d = nd;
             }
             for (int i = tid; i <= Dn.N + 1; i += PUSH_THREADS) sAcc[i] = Acc(0);
@@ -681,17 +561,6 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         const Real qm = pick<Real>(S.qm, S.qm_f);
         const unsigned tnull = S.tnull;
         const int wbase0 = pb + (tbeg - C.chunk0) * CHUNK + w * SUBTILE;  // warp's first sub-tile
-        // this warp's first sub-tile of the next ticket, if it holds live slots
-        int nfirst = -1;
-        if (ST > 0 && tnext < total) {
-            const int nn = ticket_ds(tnext, ds);
-            if (nn < nds) {
-                const Counts &Cn = W.cnt[nn];
-                const int pbn = W.disc[nn / NSP].pbase[nn % NSP];
-                const int sb = pbn + (tnext - Cn.chunk0) * CHUNK + w * SUBTILE;
-                if (sb < pbn + Cn.n_snap) nfirst = sb;
-            }
-        }
         int qn = 0;  // warp-uniform queue length
 
         // ---- phase B: the queued candidates of this warp, one per lane;
@@ -764,37 +633,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             int c[4];
             Real off[4], vx[4];
             const bool full = i0 + 3 < end;
-            if (ST > 0) {
-                bool have = sbase < end && !broken;
-                if (have) {
-                    if (pf >= 0 && pf != sbase) wait_stage();  // (never: pf is the next sub-tile)
-                    if (pf != sbase) issue(sbase);
-                    wait_stage();
-                    have = !broken;
-                }
-                if (have) {
-                    const unsigned char *stg = smem + (size_t)w * SB;
-                    ld4(reinterpret_cast<const int *>(stg) + 4 * lane, c);
-                    ld4(reinterpret_cast<const Real *>(stg + SUBTILE * sizeof(int)) + 4 * lane, off);
-                    ld4(reinterpret_cast<const Real *>(stg + SUBTILE * (sizeof(int) + sizeof(Real))) + 4 * lane, vx);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (i0 + k >= end) c[k] = -2;
-                    __syncwarp();
-                    if (lane == 0) fence_proxy_async_shared();
-                    // the next sub-tile this warp consumes: the next tile of
-                    // this ticket, else its first of the next ticket
-                    const int nb = t + 1 < tend ? sbase + CHUNK : nfirst;
-                    if (nb >= 0 && (t + 1 >= tend || nb < end)) issue(nb);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        c[k] = -2;
-                        off[k] = Real(0);
-                        vx[k] = Real(0);
-                    }
-                }
-            } else if (full) {
+            if (full) {
                 ld4(cellA + i0, c);
                 ld4(offA + i0, off);
                 ld4(vxA + i0, vx);
@@ -822,7 +661,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 nslots += ck >= -1 ? 1u : 0u;
                 nlive += was ? 1u : 0u;
                 const int cc = was ? ck : 0;
-                const Real e0 = GE ? __ldg(&Ef[cc]) : Ef[cc], e1 = GE ? __ldg(&Ef[cc + 1]) : Ef[cc + 1];
+                const Real e0 = sE[cc], e1 = sE[cc + 1];
                 const Real ep = e0 + off[k] * (e1 - e0);
                 const Real v = vx[k] + qm * ep;
                 Real o = off[k] + v;
@@ -899,10 +738,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                     if (wl) atomicAdd(&s_cnt[C_LIVE], wl);
                 }
             }
-            if (broken) {
-                // a copy never arrived: the sub-tile is left as it was (the
-                // host sees the timeout status)
-            } else if (full) {
+            if (full) {
                 st4(cellA + i0, c);
                 st4(offA + i0, off);
                 st4(vxA + i0, vx);
@@ -1078,8 +914,7 @@ static size_t push_smem_bytes(int Nmax, int eedf_max, int fm_max)
 {
     using Acc = typename AccT<Real>::T;
     constexpr int NW = PUSH_THREADS / 32;
-    size_t b = (size_t)NW * PushStages<Real>::value * StageBytes<Real>::value;
-    b += sizeof(Acc) * (Nmax + 2) + (PushFieldGlobal<Real>::value ? 0 : sizeof(Real) * (Nmax + 2));
+    size_t b = sizeof(Acc) * (Nmax + 2) + sizeof(Real) * (Nmax + 2);
     b += sizeof(Real) * NW * QCAP + sizeof(int) * NW * QCAP;
     b += 4 * sizeof(Real) * NW * BSTAGE + 2 * sizeof(int) * NW * BSTAGE;
     b += sizeof(unsigned) * (eedf_max + fm_max);
