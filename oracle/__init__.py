@@ -47,7 +47,7 @@ class _Cfg(C.Structure):
         ("n_cells", C.c_int), ("n1", C.c_int), ("sort_interval", C.c_int),
         ("diag_every", C.c_int), ("eedf_bins", C.c_int), ("iedf_bins", C.c_int),
         ("fm_bins", C.c_int), ("fm_xbins", C.c_int), ("discharge", C.c_int),
-        ("cx_isotropic", C.c_int),
+        ("cx_isotropic", C.c_int), ("numax_bins", C.c_int),
     ]
 
 
@@ -86,6 +86,10 @@ def lib():
         l.orc_set.argtypes = [C.c_void_p, C.c_int, C.c_longlong, dp, dp, dp, dp, ip]
         l.orc_numax.restype = C.c_double
         l.orc_numax.argtypes = [C.c_void_p, C.c_int]
+        l.orc_numax_bin.restype = C.c_double
+        l.orc_numax_bin.argtypes = [C.c_void_p, C.c_int]
+        l.orc_bin_of.restype = C.c_int
+        l.orc_bin_of.argtypes = [C.c_void_p, C.c_double]
         l.orc_fields.argtypes = [C.c_void_p, dp, dp, dp]
         l.orc_counters.argtypes = [C.c_void_p, lp, lp, lp, lp]
         l.orc_diag.restype = C.c_longlong
@@ -154,6 +158,7 @@ class Oracle:
         cfg.fm_xbins = d.fm_xbins
         cfg.discharge = discharge
         cfg.cx_isotropic = int(d.cx_isotropic)
+        cfg.numax_bins = int(d.numax_bins)
         self._keep = []
         xs = (_Xs * len(tables))()
         for i, t in enumerate(tables):
@@ -192,6 +197,12 @@ class Oracle:
 
     def numax(self, s):
         return lib().orc_numax(self.h, s)
+
+    def numax_bin(self, b):
+        return lib().orc_numax_bin(self.h, b)
+
+    def bin_of(self, K_eV):
+        return lib().orc_bin_of(self.h, float(K_eV))
 
     def get(self, s):
         n = self.count(s)

@@ -19,7 +19,10 @@
  * Gas-target channels use the null-collision test, candidate probability
  * 1 - exp(-nu_max dt), then a channel walk with the running sum of
  * n_j sigma_j(E) u; particle-target reactions (13), (14), (19) use Eq. 1 with
- * tau = n1 dt in a per-cell pass after the sort.
+ * tau = n1 dt in a per-cell pass after the sort.  For electrons nu_max may
+ * depend on the electron's lab energy (bins of a quarter octave): the
+ * null-collision method gives the same collision statistics for any bound
+ * that is at least the true frequency.
  *
  * Readings of points the paper leaves open (each restated where used):
  *   x = 0 driven, x = L grounded; a particle with x < 0 or x >= L is absorbed.
@@ -93,6 +96,8 @@ struct orc_sim {
     int pair_tab[20];
     double numax[3];
     double pnull[3];
+    double nubin[64];   /* electrons: bound per lab-energy bin */
+    double pbin[64];
     parts_t p[3];
     long long step;
     double *rho, *phi, *E, *dens[3];
@@ -265,6 +270,63 @@ static double compute_numax(const orc_sim *s, int sp)
     return best * s->c.numax_safety;
 }
 
+/* Electron energy bins: bin b holds lab energies K with
+ * 4 (log2 K + 6) in [b, b + 1) when K is written m 2^e, m in [1, 2), as
+ * 4 (e + 6) + floor(4 (m - 1)) (quarter octaves split linearly in m), K in
+ * eV; bins below 0 join bin 0 and bins above the last join the last. */
+#define BIN_LOG2_E0 (-6)
+int orc_bin_of(const orc_sim *s, double K)
+{
+    int nb = s->c.numax_bins;
+    if (nb <= 0) return 0;
+    if (!(K > 0.0)) return 0;
+    if (!(K < 1e300)) return nb - 1;
+    int ex;
+    double mh = frexp(K, &ex);     /* K = mh 2^ex, mh in [0.5, 1) */
+    double m = 2.0 * mh;           /* K = m 2^(ex - 1) */
+    int e = ex - 1;
+    long long b = 4LL * (e - BIN_LOG2_E0) + (long long)((m - 1.0) * 4.0);
+    if (b < 0) return 0;
+    if (b > nb - 1) return nb - 1;
+    return (int)b;
+}
+
+/* Upper lab energy of bin b: 2^(e0 + q) (1 + (r + 1)/4) with b = 4q + r. */
+static double bin_top(int b)
+{
+    return ldexp(1.0 + (double)(b % 4 + 1) / 4.0, BIN_LOG2_E0 + b / 4);
+}
+
+/* Bound of bin b (not the last): relative speed at most the bin's top
+ * electron speed plus 7 thermal speeds of the gas molecule (a Maxwellian
+ * sample beyond that, chance 1e-10, is counted as a violation); the same
+ * node scan as compute_numax up to the matching centre-of-mass energy. */
+static double compute_numax_bin(const orc_sim *s, int b)
+{
+    const int sp = 0;
+    double mu = reduced_mass(MASS[sp], M_O2);
+    double vtop = sqrt(2.0 * bin_top(b) * QE / MASS[sp]);
+    double vg = sqrt(KB * s->c.T_gas / M_O2);
+    double urel = vtop + 7.0 * vg;
+    double cap = 0.5 * mu * urel * urel / QE;
+    double best = 0.0;
+    for (int a = 0; a < s->n_gas_ch[sp]; ++a) {
+        const table_t *ta = &s->t[s->gas_ch[sp][a]];
+        for (int k = 0; k <= ta->n; ++k) {
+            double E = (k < ta->n) ? ta->E[k] : cap;
+            if (E > cap || E <= 0.0) continue;
+            double u = sqrt(2.0 * E * QE / mu);
+            double nu = 0.0;
+            for (int c = 0; c < s->n_gas_ch[sp]; ++c) {
+                const table_t *tb = &s->t[s->gas_ch[sp][c]];
+                nu += tb->ndens * sigma_of(tb, E) * u;
+            }
+            if (nu > best) best = nu;
+        }
+    }
+    return best * s->c.numax_safety;
+}
+
 static void load_species(orc_sim *s, int sp)
 {
     parts_t *p = &s->p[sp];
@@ -320,6 +382,12 @@ orc_sim *orc_create(const orc_cfg *cfg, const orc_xs *xs, int n_xs, int load)
     for (int sp = 0; sp < 3; ++sp) {
         s->numax[sp] = compute_numax(s, sp);
         s->pnull[sp] = 1.0 - exp(-s->numax[sp] * cfg->dt);
+    }
+    if (s->c.numax_bins > 64) s->c.numax_bins = 64;
+    for (int b = 0; b < s->c.numax_bins; ++b) {
+        /* the last bin has no upper energy: it keeps the species' bound */
+        s->nubin[b] = (b < s->c.numax_bins - 1) ? compute_numax_bin(s, b) : s->numax[0];
+        s->pbin[b] = 1.0 - exp(-s->nubin[b] * cfg->dt);
     }
     s->rho = calloc(N + 1, sizeof(double));
     s->phi = calloc(N + 1, sizeof(double));
@@ -664,7 +732,7 @@ static void sample_histograms(orc_sim *s, int sp, double x, const double v[3])
 }
 
 /* null-collision test, channel choice and kinematics for one gas candidate */
-static void gas_collision(orc_sim *s, int sp, long long i, blist_t *bl)
+static void gas_collision(orc_sim *s, int sp, long long i, double numax, blist_t *bl)
 {
     parts_t *p = &s->p[sp];
     uint32_t a[4], b[4], c2[4];
@@ -679,7 +747,7 @@ static void gas_collision(orc_sim *s, int sp, long long i, blist_t *bl)
     double g0 = v[0] - V[0], g1 = v[1] - V[1], g2 = v[2] - V[2];
     double u = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
     double E = 0.5 * reduced_mass(MASS[sp], M_O2) * u * u / QE;
-    double target = unif(b[0]) * s->numax[sp];
+    double target = unif(b[0]) * numax;
     double cum = 0.0;
     int chosen = -1;
     for (int k = 0; k < s->n_gas_ch[sp]; ++k) {
@@ -687,7 +755,7 @@ static void gas_collision(orc_sim *s, int sp, long long i, blist_t *bl)
         cum += t->ndens * sigma_of(t, E) * u;
         if (chosen < 0 && target < cum) chosen = s->gas_ch[sp][k];
     }
-    if (cum > s->numax[sp]) s->viol[0]++;
+    if (cum > numax) s->viol[0]++;
     if (chosen < 0) return; /* null event */
     const table_t *t = &s->t[chosen];
     double r4[4] = {unif(b[0]), unif(b[1]), unif(b[2]), unif(b[3])};
@@ -876,7 +944,15 @@ static void step_once(orc_sim *s)
                 last_blk = i >> 2;
                 rng(s, sp, 0, 0, 0, s->step, (uint32_t)(i >> 2), w0);
             }
-            if (unif(w0[i & 3]) < s->pnull[sp]) gas_collision(s, sp, i, bl);
+            double pc = s->pnull[sp], nu = s->numax[sp];
+            if (sp == 0 && s->c.numax_bins > 0) {
+                /* electrons: the bound of their lab-energy bin */
+                double v2 = p->vx[i] * p->vx[i] + p->vy[i] * p->vy[i] + p->vz[i] * p->vz[i];
+                int b = orc_bin_of(s, 0.5 * MASS[0] * v2 / QE);
+                pc = s->pbin[b];
+                nu = s->nubin[b];
+            }
+            if (unif(w0[i & 3]) < pc) gas_collision(s, sp, i, nu, bl);
         }
     }
     append_births(s, bl);
@@ -917,6 +993,10 @@ long long orc_particle_steps(const orc_sim *s) { return s->psteps; }
 void orc_set_step(orc_sim *s, long long step) { s->step = step; }
 long long orc_count(const orc_sim *s, int sp) { return s->p[sp].n; }
 double orc_numax(const orc_sim *s, int sp) { return s->numax[sp]; }
+double orc_numax_bin(const orc_sim *s, int b)
+{
+    return (b >= 0 && b < s->c.numax_bins) ? s->nubin[b] : 0.0;
+}
 
 void orc_get(const orc_sim *s, int sp, double *x, double *vx, double *vy,
              double *vz, int *alive)

@@ -43,6 +43,8 @@ typedef struct {
     int fm_xbins;        /* f_-(E, x): equal regions of (0, L) */
     int discharge;       /* discharge index, enters the random counter */
     int cx_isotropic;    /* reaction (6): 0 = velocity swap, 1 = isotropic */
+    int numax_bins;      /* electrons: collision-frequency bounds per quarter
+                            octave of lab energy from 2^-6 eV (0 = one bound) */
 } orc_cfg;
 
 typedef struct {
@@ -68,6 +70,9 @@ int orc_set(orc_sim *s, int sp, long long n, const double *x, const double *vx,
             const double *vy, const double *vz, const int *alive);
 void orc_set_step(orc_sim *s, long long step);
 double orc_numax(const orc_sim *s, int sp);
+/* electrons: bound of energy bin b, and the bin of a lab energy K [eV] */
+double orc_numax_bin(const orc_sim *s, int b);
+int orc_bin_of(const orc_sim *s, double K_eV);
 void orc_fields(orc_sim *s, double *rho, double *phi, double *E);
 /* counters: absorbed[3][2], events[20], violations[2] (gas, pair), births[3] */
 void orc_counters(const orc_sim *s, long long *absorbed, long long *events,

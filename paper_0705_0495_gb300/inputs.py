@@ -167,6 +167,7 @@ class Discharge:
     fm_xbins: int = 64
     fm_emax: float = 4.0
     numax_safety: float = 1.05
+    numax_bins: int = 64            # electrons: bounds per quarter octave of lab energy
     cx_isotropic: bool = False
     capacity_factor: float = 1.5
     capacity_extra: int = 4096

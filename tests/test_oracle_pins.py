@@ -260,7 +260,7 @@ def test_cold_plasma_oscillation_frequency():
 
 def test_null_collision_real_event_fraction():
     sig, E0, cap = 1e-19, 10.0, 40.0
-    d = _disch(ecap_override=cap, dt_override=5e-11)
+    d = _disch(ecap_override=cap, dt_override=5e-11, numax_bins=0)
     o = oracle.Oracle(d, [_flat(4, sig)])
     n = 200000
     rs = np.random.default_rng(11)
@@ -276,6 +276,75 @@ def test_null_collision_real_event_fraction():
     numax = d.numax_safety * ngas * sig * math.sqrt(2 * cap * QE / mu)
     nu = ngas * sig * math.sqrt(2 * E0 * QE / mu)  # gas motion is negligible here
     p = (1 - math.exp(-numax * d.dt)) * nu / numax
+    assert abs(ev - n * p) < 4 * math.sqrt(n * p * (1 - p))
+
+
+def test_electron_energy_bin_index():
+    # quarter octaves of the lab energy from 2^-6 eV: K = m 2^e, m in [1, 2),
+    # bin = 4 (e + 6) + floor(4 (m - 1)), clamped to [0, 63]
+    o = oracle.Oracle(_disch(), [_flat(4, 1e-19)])
+    cases = {2.0 ** -6: 0, 2.0 ** -7: 0, 0.0: 0, 1.0: 24, 1.3: 25, 1.5: 26, 1.75: 27,
+             1.99: 27, 2.0: 28, 10.0: 37, 700.0: 61, 800.0: 62, 1000.0: 63, 1e6: 63}
+    for K, b in cases.items():
+        assert o.bin_of(K) == b, (K, o.bin_of(K), b)
+
+
+def test_electron_bin_bounds_cover_the_collision_frequency():
+    # every bin's bound is at least sum_j n_j sigma_j(E_cm) u for electrons of
+    # that bin against gas molecules within 7 thermal speeds, and, the point
+    # of the bins, not much larger than the largest such frequency
+    d = _disch(p_Pa=20.0, ecap_override=1250.0)
+    tabs = [t for t in inputs.xs_tables() if t["reaction"] in (4, 7, 8, 9, 10, 11, 12, 15, 18)]
+    o = oracle.Oracle(d, tabs)
+    ngas = d.p_Pa / (KB * d.T_gas)
+    mu = ME * M_O2 / (ME + M_O2)
+    vg = math.sqrt(KB * d.T_gas / M_O2)
+    rs = np.random.default_rng(21)
+    gas_tabs = list(range(len(tabs)))
+    for b in range(0, 63, 3):
+        lo = 2.0 ** (-6 + b // 4) * (1 + (b % 4) / 4)
+        hi = 2.0 ** (-6 + b // 4) * (1 + (b % 4 + 1) / 4)
+        K = rs.uniform(lo, hi, size=400)
+        dirs = rs.normal(size=(400, 3))
+        dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+        v = np.sqrt(2 * K * QE / ME)[:, None] * dirs
+        V = rs.normal(size=(400, 3)) * vg
+        V *= np.minimum(1.0, 7.0 / np.linalg.norm(V / vg, axis=1))[:, None]
+        u = np.linalg.norm(v - V, axis=1)
+        Ecm = 0.5 * mu * u * u / QE
+        nu = np.zeros(400)
+        for k in gas_tabs:
+            nu += ngas * np.array([o.sigma(k, e) for e in Ecm]) * u
+        bound = o.numax_bin(b)
+        assert np.all(nu <= bound), (b, nu.max(), bound)
+        assert bound <= o.numax(0) * 1.0000001 or hi > 1000.0
+        if nu.max() > 0 and b >= 8:
+            assert bound < 2.0 * nu.max(), (b, bound, nu.max())
+
+
+def test_binned_null_collision_real_event_fraction():
+    # with an energy-dependent bound the real-event probability is
+    # (1 - exp(-nu_b dt)) nu / nu_b for the bin's bound nu_b (the rejection
+    # step of the null-collision method), and the bound is far below the
+    # single bound at the cap
+    sig, E0, cap = 1e-19, 10.0, 400.0
+    d = _disch(ecap_override=cap, dt_override=5e-11, numax_bins=64)
+    o = oracle.Oracle(d, [_flat(4, sig)])
+    n = 200000
+    rs = np.random.default_rng(13)
+    dirs = rs.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    v = math.sqrt(2 * E0 * QE / ME) * dirs
+    o.set(0, np.full(n, 0.5), v[:, 0], v[:, 1], v[:, 2])
+    _empty_others(o, [0])
+    o.step(1)
+    ev = o.counters()["events"][4]
+    ngas = d.p_Pa / (KB * d.T_gas)
+    mu = ME * M_O2 / (ME + M_O2)
+    nu = ngas * sig * math.sqrt(2 * E0 * QE / mu)
+    nub = o.numax_bin(o.bin_of(E0))
+    assert nu < nub < 1.2 * nu and nub < 0.2 * o.numax(0)
+    p = (1 - math.exp(-nub * d.dt)) * nu / nub
     assert abs(ev - n * p) < 4 * math.sqrt(n * p * (1 - p))
 
 
