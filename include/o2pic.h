@@ -115,6 +115,13 @@ typedef struct {
  *                  (-fm_emax, fm_emax)
  *   cx_isotropic   reaction (6): 0 = the ion takes the gas molecule's velocity
  *                  (resonant exchange), 1 = isotropic elastic scattering
+ *   numax_bins     electrons only, 0..64: the collision-frequency bound is
+ *                  taken per bin of the electron's lab energy K after the push
+ *                  (K = m 2^e with m in [1, 2): bin 4 (e + 6) + floor(4 (m - 1)),
+ *                  clamped to [0, numax_bins - 1]); bin b < numax_bins - 1 uses
+ *                  the bound up to the centre-of-mass energy of relative speed
+ *                  (top electron speed of the bin + 7 sqrt(kT/M_O2)), the last
+ *                  bin the species' bound; 0 = one bound for all energies
  *   precision      pic_precision; all discharges of one handle share it
  */
 typedef struct {
@@ -130,6 +137,7 @@ typedef struct {
     int n_cells, n1, sort_interval, diag_every;
     int eedf_bins, iedf_bins, fm_bins, fm_xbins;
     int cx_isotropic;
+    int numax_bins;
     int precision;
 } pic_config;
 

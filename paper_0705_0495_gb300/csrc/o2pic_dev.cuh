@@ -69,6 +69,15 @@ struct GasChan {
     float coef_f, dloss_f;
 };
 
+// one energy bin of a collision-frequency bound
+constexpr int NUBIN_MAX = 64;
+constexpr int NUBIN_LOG2_E0 = -6;  // bins are quarter octaves of lab energy from 2^-6 eV
+struct NuBin {
+    unsigned tnull;     // null-collision threshold on a 32-bit word
+    float numax_n_f;    // nu_max dt
+    double numax_n;
+};
+
 struct SpeciesC {
     double qm;          // (q/m) dt^2 / dx : normalised acceleration per V/m
     double numax_n;     // nu_max * dt
@@ -84,6 +93,8 @@ struct SpeciesC {
     int table_lo;       // first table of the shared grid (for the index)
     int gtab_ld;        // row length of the node-major gas table (multiple of 4)
     int gtab_off;       // first element of this (discharge, species) gas table
+    int nbins;          // energy bins of the collision-frequency bound (0: one bound)
+    int bin_off;        // first entry of this species' bins in WsPtrs::nubin
     // FP32 copies (the FP32 path never converts from FP64 on the device)
     float qm_f, numax_n_f, vgas_n_f, Ek_f, mfrac_f, Mfrac_f, ke_eV_f, pad_f;
     GasChan ch[MAX_GAS_CH];
@@ -195,6 +206,7 @@ struct WsPtrs {
     int *cell_disc;           // [total cells] discharge of each global cell
     int *pair_first;          // [total cells] first flagged projectile of the current reaction
     unsigned *vmax2;          // [D * 3] largest speed^2 (cells/step, float bits) at the last sort
+    struct NuBin *nubin;      // [D * NUBIN_MAX] electron collision-frequency bounds per energy bin
     int *pair_kills;          // [total cells * 3] particles killed per species in this pass
     void *pair_births;        // [total cells * PAIR_BIRTH_CAP] records
     int total_nodes;

@@ -76,7 +76,7 @@ struct Bump {
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
+    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, nubin, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
         counters, eedf, iedf, fm, tables, lutE, lutS, lutEf, lutSf, sort_counts, cell_start,
         sort_live, pair_bcount, cell_disc, pair_births, sort_tab, ninit, vt;
     size_t cell[2], off[2], vx[2], vy[2], vz[2];
@@ -97,9 +97,10 @@ bool validate(const pic_config *c, int D, const pic_xs_table *xs, int n_xs, std:
         const pic_config &q = c[d];
         char b[256];
         if (!(q.L_m > 0) || !(q.dt_s > 0) || q.n_cells < 2 || q.n_cells > 4096 || !(q.weight_m2 >= 0) ||
-            !(q.p_Pa >= 0) || !(q.T_gas_K > 0) || !(q.numax_safety >= 1.0)) {
+            !(q.p_Pa >= 0) || !(q.T_gas_K > 0) || !(q.numax_safety >= 1.0) || q.numax_bins < 0 ||
+            q.numax_bins > NUBIN_MAX) {
             snprintf(b, sizeof b, "discharge %d: need L > 0, dt > 0, 2 <= n_cells <= 4096, weight >= 0, "
-                                  "p >= 0, T > 0, numax_safety >= 1", d);
+                                  "p >= 0, T > 0, numax_safety >= 1, 0 <= numax_bins <= 64", d);
             why = b;
             return false;
         }
@@ -305,6 +306,7 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.cell_disc = B.take(4ull * tc);
     L.pair_first = B.take(4ull * tc);
     L.vmax2 = B.take(4ull * 3 * D);
+    L.nubin = B.take(sizeof(NuBin) * NUBIN_MAX * (size_t)D);
     L.pair_kills = B.take(4ull * 3 * tc);
     for (int s = 0; s < 3; ++s) {
         long long tiles = 0;
@@ -343,6 +345,7 @@ struct pic_handle {
     int *sort_tab = nullptr;
     long long step = 0;
     std::vector<Disc> disc;
+    std::vector<NuBin> nubin;   // [D * NUBIN_MAX]
     std::vector<double> numax;  // [D*3]
     std::string err;
     // graph of one period
@@ -474,26 +477,47 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
             S.ch[j].th = t.th;
             S.ch[j].th_f = (float)t.th;
         }
-        // nu_max: largest sum_j n_j sigma_j(E) sqrt(2E/mu) over the nodes up to
-        // the cap and the cap itself, times the safety factor
-        double best = 0.0;
-        const double capE = q.ecap_eV[s];
-        for (int a = 0; a < S.nch; ++a) {
-            const HostTable &ta = h->tabs[S.ch[a].table];
-            for (int k = 0; k <= ta.n; ++k) {
-                const double E = k < ta.n ? ta.E[k] : capE;
-                if (E > capE || E <= 0.0) continue;
-                const double u = std::sqrt(2.0 * E * QE / mu);
-                double nu = 0.0;
-                for (int b = 0; b < S.nch; ++b) {
-                    const HostTable &tb = h->tabs[S.ch[b].table];
-                    const double nj = (tb.reaction == 17) ? q.C_delta * ngas : ngas;
-                    nu += nj * sigma_host(tb, E) * u;
+        // nu_max up to a centre-of-mass energy: largest sum_j n_j sigma_j(E)
+        // sqrt(2E/mu) over the nodes up to it and at it, times the safety factor
+        auto numax_upto = [&](double capE) {
+            double best = 0.0;
+            for (int a = 0; a < S.nch; ++a) {
+                const HostTable &ta = h->tabs[S.ch[a].table];
+                for (int k = 0; k <= ta.n; ++k) {
+                    const double E = k < ta.n ? ta.E[k] : capE;
+                    if (E > capE || E <= 0.0) continue;
+                    const double u = std::sqrt(2.0 * E * QE / mu);
+                    double nu = 0.0;
+                    for (int b = 0; b < S.nch; ++b) {
+                        const HostTable &tb = h->tabs[S.ch[b].table];
+                        const double nj = (tb.reaction == 17) ? q.C_delta * ngas : ngas;
+                        nu += nj * sigma_host(tb, E) * u;
+                    }
+                    best = std::max(best, nu);
                 }
-                best = std::max(best, nu);
             }
+            return best * q.numax_safety;
+        };
+        S.numax = numax_upto(q.ecap_eV[s]);
+        // electrons: one bound per quarter octave of lab energy; a bin's
+        // relative speed is at most its top electron speed plus 7 thermal
+        // speeds of the gas molecule; the last bin keeps the species' bound
+        S.nbins = (s == 0) ? q.numax_bins : 0;
+        S.bin_off = d * NUBIN_MAX;
+        for (int b = 0; b < S.nbins; ++b) {
+            NuBin &nb = h->nubin[(size_t)d * NUBIN_MAX + b];
+            double nu = S.numax;
+            if (b < S.nbins - 1) {
+                const double Ktop = std::ldexp(1.0 + (b % 4 + 1) / 4.0, NUBIN_LOG2_E0 + b / 4);
+                const double urel = std::sqrt(2.0 * Ktop * QE / m) + 7.0 * std::sqrt(KB * q.T_gas_K / M_O2);
+                nu = numax_upto(0.5 * mu * urel * urel / QE);
+            }
+            const double pb = 1.0 - std::exp(-nu * q.dt_s);
+            const double tb = std::ceil(pb * 4294967296.0 - 0.5);
+            nb.tnull = tb <= 0.0 ? 0u : (tb >= 4294967295.0 ? 0xFFFFFFFFu : (unsigned)tb);
+            nb.numax_n = nu * q.dt_s;
+            nb.numax_n_f = (float)nb.numax_n;
         }
-        S.numax = best * q.numax_safety;
         S.numax_n = S.numax * q.dt_s;
         const double pnull = 1.0 - std::exp(-S.numax * q.dt_s);
         const double thr = std::ceil(pnull * 4294967296.0 - 0.5);
@@ -620,6 +644,7 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.cell_disc = reinterpret_cast<int *>(b + L.cell_disc);
     W.pair_first = reinterpret_cast<int *>(b + L.pair_first);
     W.vmax2 = reinterpret_cast<unsigned *>(b + L.vmax2);
+    W.nubin = reinterpret_cast<NuBin *>(b + L.nubin);
     W.pair_kills = reinterpret_cast<int *>(b + L.pair_kills);
     W.pair_births = b + L.pair_births;
     W.total_nodes = L.total_nodes;
@@ -671,6 +696,7 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
         }
     }
     h->disc.resize(n_discharges);
+    h->nubin.assign((size_t)n_discharges * NUBIN_MAX, NuBin{});
     h->numax.assign(3 * n_discharges, 0.0);
     for (int d = 0; d < n_discharges; ++d) build_disc(h, d, gas, gcount, pair_tab);
     // node-major gas tables: row k of (d, s) holds n_j dx sigma_j(E_k), j < nch
@@ -738,6 +764,7 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     CK(cudaMemsetAsync(h->ws, 0, L.total, st));
     CK(cudaMemcpyAsync(W.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(W.disc, h->disc.data(), sizeof(Disc) * n_discharges, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(W.nubin, h->nubin.data(), sizeof(NuBin) * h->nubin.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(W.cnt, cnt.data(), sizeof(Counts) * cnt.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(W.gtab, gt.data(), 8 * gt.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(W.gtabf, gtf.data(), 4 * gtf.size(), cudaMemcpyHostToDevice, st));

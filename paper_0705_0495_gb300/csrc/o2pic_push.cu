@@ -212,12 +212,31 @@ __device__ __forceinline__ void stage_birth(const BirthStage<Real> &B, Ctl *ctl,
     B.vz[pos] = v[2];
 }
 
+// Energy bin of an electron's lab energy K [eV] for the collision-frequency
+// bound: with K = m 2^e, m in [1, 2), bin 4 (e + 6) + floor(4 (m - 1)) (the
+// exponent and the top two mantissa bits), clamped to [0, nb - 1]; K <= 0
+// or NaN gives bin 0.
+__device__ __forceinline__ int energy_bin(float K, int nb)
+{
+    if (!(K > 0.f)) return 0;
+    const unsigned u = __float_as_uint(K);
+    const int b = 4 * ((int)((u >> 23) & 0xFFu) - 127 - NUBIN_LOG2_E0) + (int)((u >> 21) & 3u);
+    return b < 0 ? 0 : (b > nb - 1 ? nb - 1 : b);
+}
+__device__ __forceinline__ int energy_bin(double K, int nb)
+{
+    if (!(K > 0.0)) return 0;
+    const unsigned long long u = (unsigned long long)__double_as_longlong(K);
+    const int b = 4 * ((int)((u >> 52) & 0x7FFull) - 1023 - NUBIN_LOG2_E0) + (int)((u >> 50) & 3ull);
+    return b < 0 ? 0 : (b > nb - 1 ? nb - 1 : b);
+}
+
 // One gas-target candidate (null-collision method).  Returns false if the
 // particle died.  v is updated in place; products are staged.
 template <typename Real>
 __device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int s, unsigned idx,
-                                         unsigned long long step, Real &vx, Real &vy, Real &vz,
-                                         int c, Real off, int tag, const BirthStage<Real> &B,
+                                         unsigned long long step, Real numax_n, Real &vx, Real &vy,
+                                         Real &vz, int c, Real off, int tag, const BirthStage<Real> &B,
                                          unsigned *s_cnt, int &staged)
 {
     const SpeciesC &S = Dd.sp[s];
@@ -235,7 +254,6 @@ __device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int
     Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
     Real u = sqrt(u2);
     Real E = pick<Real>(S.Ek, S.Ek_f) * u2;
-    const Real numax_n = pick<Real>(S.numax_n, S.numax_n_f);
     Real target = unif<Real>(b.x) * numax_n;
     const TableDesc &T0 = W.tables[S.table_lo];
     XsPoint<Real> pt = xs_locate<Real>(T0, lutE, E);
@@ -473,10 +491,13 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     int *bTag = ibase + NW * QCAP + NW * BSTAGE + w * BSTAGE;
     unsigned *sEedf = reinterpret_cast<unsigned *>(ibase + NW * QCAP + 2 * NW * BSTAGE);
     unsigned *sFm = sEedf + eedf_max;
+    unsigned char *qBin = reinterpret_cast<unsigned char *>(sFm + fm_max) + w * QCAP;  // energy bin
 
     __shared__ int s_ticket[2];
     __shared__ int s_wnb[NW];
     __shared__ unsigned s_cnt[C_NCOUNT];
+    __shared__ unsigned s_btn[NUBIN_MAX];  // electron bounds per energy bin: thresholds
+    __shared__ Real s_bnu[NUBIN_MAX];      // and nu_max dt
 
     Ctl *ctl = W.ctl;
     const int cur = ctl->cur;
@@ -540,6 +561,14 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 d = nd;
             }
             for (int i = tid; i <= Dn.N + 1; i += PUSH_THREADS) sAcc[i] = Acc(0);
+            {
+                const SpeciesC &Sn = Dn.sp[nx % NSP];
+                for (int b = tid; b < Sn.nbins; b += PUSH_THREADS) {
+                    const NuBin &nb = W.nubin[Sn.bin_off + b];
+                    s_btn[b] = nb.tnull;
+                    s_bnu[b] = pick<Real>(nb.numax_n, nb.numax_n_f);
+                }
+            }
             for (int q = tid; q < C_NCOUNT; q += PUSH_THREADS) s_cnt[q] = 0;
             if (DIAG) {
                 for (int i = tid; i < eedf_max; i += PUSH_THREADS) sEedf[i] = 0;
@@ -560,6 +589,9 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         const int tend = min(tbeg + TILES_PER_TICKET, C.chunk0 + C.nchunk);
         const Real qm = pick<Real>(S.qm, S.qm_f);
         const unsigned tnull = S.tnull;
+        const int nbins = S.nbins;
+        const bool binned = nbins > 0;  // electrons: bound per lab-energy bin
+        const Real ke = pick<Real>(S.ke_eV, S.ke_eV_f);
         const int wbase0 = pb + (tbeg - C.chunk0) * CHUNK + w * SUBTILE;  // warp's first sub-tile
         int qn = 0;  // warp-uniform queue length
 
@@ -575,8 +607,9 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 Real ux = qVx[q], vy = vyA[i], vz = vzA[i];
                 const int rel = i - wbase0;  // (tile offset) * CHUNK + slot in sub-tile
                 const int tag = (((rel / CHUNK) << 7) | (rel % CHUNK)) << 1;
-                const bool alive = gas_collide<Real>(W, Dd, s, (unsigned)(i - pb), step, ux, vy, vz, cq, oq,
-                                                     tag, B, s_cnt, staged);
+                const Real nun = binned ? s_bnu[qBin[q]] : pick<Real>(S.numax_n, S.numax_n_f);
+                const bool alive = gas_collide<Real>(W, Dd, s, (unsigned)(i - pb), step, nun, ux, vy, vz, cq,
+                                                     oq, tag, B, s_cnt, staged);
                 if (alive) {
                     vxA[i] = ux;
                     vyA[i] = vy;
@@ -646,6 +679,20 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                     vx[k] = in ? vxA[i0 + k] : Real(0);
                 }
             }
+            Real vyl[4], vzl[4];  // binned species only: the lab energy needs vy, vz
+            if (binned) {
+                if (full) {
+                    ld4(vyA + i0, vyl);
+                    ld4(vzA + i0, vzl);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const bool in = i0 + k < end;
+                        vyl[k] = in ? vyA[i0 + k] : Real(0);
+                        vzl[k] = in ? vzA[i0 + k] : Real(0);
+                    }
+                }
+            }
             uint4 w4 = make_uint4(0, 0, 0, 0);
             if (c[0] >= 0 || c[1] >= 0 || c[2] >= 0 || c[3] >= 0)
                 w4 = rng_block(Dd.seed, Dd.discharge, s, 0, 0, 0, step, (unsigned)((i0 - pb) >> 2));
@@ -680,12 +727,19 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 off[k] = live ? o : off[k];
                 c[k] = was ? (out ? -1 : cn) : ck;
                 dep[k] = live ? cn : -1;
-                const bool cand = live && wk[k] < tnull;
+                int bin = 0;
+                unsigned thr = tnull;
+                if (binned) {
+                    bin = energy_bin(ke * (v * v + vyl[k] * vyl[k] + vzl[k] * vzl[k]), nbins);
+                    thr = s_btn[bin];
+                }
+                const bool cand = live && wk[k] < thr;
                 const unsigned m = __ballot_sync(0xffffffffu, cand);
                 if (cand) {
                     const int pos = qn + __popc(m & lt_mask);
                     qIdx[pos] = i0 + k;
                     qVx[pos] = vx[k];
+                    qBin[pos] = (unsigned char)bin;
                 }
                 qn += __popc(m);
             }
@@ -918,6 +972,7 @@ static size_t push_smem_bytes(int Nmax, int eedf_max, int fm_max)
     b += sizeof(Real) * NW * QCAP + sizeof(int) * NW * QCAP;
     b += 4 * sizeof(Real) * NW * BSTAGE + 2 * sizeof(int) * NW * BSTAGE;
     b += sizeof(unsigned) * (eedf_max + fm_max);
+    b += (size_t)NW * QCAP;  // queue energy bins
     return (b + 15) & ~size_t(15);
 }
 

@@ -43,7 +43,7 @@ class pic_config(C.Structure):
         ("n_init", C.c_longlong * 3), ("capacity", C.c_longlong * 3), ("seed", C.c_ulonglong),
         ("n_cells", C.c_int), ("n1", C.c_int), ("sort_interval", C.c_int), ("diag_every", C.c_int),
         ("eedf_bins", C.c_int), ("iedf_bins", C.c_int), ("fm_bins", C.c_int), ("fm_xbins", C.c_int),
-        ("cx_isotropic", C.c_int), ("precision", C.c_int),
+        ("cx_isotropic", C.c_int), ("numax_bins", C.c_int), ("precision", C.c_int),
     ]
 
 
@@ -123,6 +123,7 @@ def make_config(d: "_inputs.Discharge", fp64: bool | None = None) -> pic_config:
     c.n_cells, c.n1, c.sort_interval, c.diag_every = d.n_cells, d.n1, d.sort_interval, d.diag_every
     c.eedf_bins, c.iedf_bins, c.fm_bins, c.fm_xbins = d.eedf_bins, d.iedf_bins, d.fm_bins, d.fm_xbins
     c.cx_isotropic = int(d.cx_isotropic)
+    c.numax_bins = int(d.numax_bins)
     use64 = d.fp64 if fp64 is None else fp64
     c.precision = PIC_FP64 if use64 else PIC_FP32_MIXED
     return c
