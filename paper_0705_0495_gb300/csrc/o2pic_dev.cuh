@@ -45,7 +45,9 @@ enum {
     C_SLOTS = 28,       // slots processed by the push (all species)
     C_CANDS = 29,       // null-collision candidates
     C_LIVE = 30,        // live particles pushed (particle-steps)
-    C_NCOUNT = 32
+    C_BSLOTS = 31,      // slots of species with an energy-binned bound (vy, vz read)
+    C_BCANDS = 32,      // candidates of those species
+    C_NCOUNT = 34
 };
 
 struct TableDesc {

@@ -359,7 +359,7 @@ struct pic_handle {
     long long push_launches = 0, launches = 0;
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
-    unsigned long long slots0 = 0, cands0 = 0;
+    unsigned long long slots0 = 0, cands0 = 0, bslots0 = 0, bcands0 = 0;
     const void *pools() const { return fp64 ? (const void *)&Pd : (const void *)&Pf; }
 };
 
@@ -1193,16 +1193,22 @@ extern "C" pic_status pic_timing(pic_handle *h, double *push_ms, long long *push
     std::vector<unsigned long long> c((size_t)h->D * C_NCOUNT);
     CK(cudaMemcpyAsync(c.data(), h->W.counters, 8 * c.size(), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    unsigned long long slots = 0, cands = 0;
+    unsigned long long slots = 0, cands = 0, bslots = 0, bcands = 0;
     for (int d = 0; d < h->D; ++d) {
         slots += c[(size_t)d * C_NCOUNT + C_SLOTS];
         cands += c[(size_t)d * C_NCOUNT + C_CANDS];
+        bslots += c[(size_t)d * C_NCOUNT + C_BSLOTS];
+        bcands += c[(size_t)d * C_NCOUNT + C_BCANDS];
     }
     // algorithmic bytes of the push: cell, offset and vx read and written for
-    // every slot; vy, vz read and written for null-collision candidates
+    // every slot; vy, vz read for every slot of a species whose bound depends
+    // on the lab energy; vy, vz read and written for null-collision
+    // candidates (a candidate of a binned species only writes them)
     const double R = h->fp64 ? 8.0 : 4.0;
     const double bytes = (double)(slots - h->slots0) * 2.0 * (4.0 + 2.0 * R) +
-                         (double)(cands - h->cands0) * 2.0 * (2.0 * R);
+                         (double)(bslots - h->bslots0) * 2.0 * R +
+                         (double)(cands - h->cands0) * 2.0 * (2.0 * R) -
+                         (double)(bcands - h->bcands0) * 2.0 * R;
     if (push_ms) *push_ms = h->push_ms;
     if (push_launches) *push_launches = h->push_launches;
     if (launches) *launches = h->launches;
@@ -1213,6 +1219,8 @@ extern "C" pic_status pic_timing(pic_handle *h, double *push_ms, long long *push
         h->launches = 0;
         h->slots0 = slots;
         h->cands0 = cands;
+        h->bslots0 = bslots;
+        h->bcands0 = bcands;
     }
     return PIC_OK;
 }

@@ -601,13 +601,13 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
                 rx[r] = __ldg(&vxS[i]);
                 ry[r] = __ldg(&vyS[i]);
                 rz[r] = __ldg(&vzS[i]);
-                vm2 = fmaxf(vm2, (float)(rx[r] * rx[r] + ry[r] * ry[r] + rz[r] * rz[r]));
             }
         }
 #pragma unroll
         for (int r = 0; r < SORT_ILP; ++r) {
             if (gd[r] >= 0) {
                 const int g = gd[r];
+                vm2 = fmaxf(vm2, (float)(rx[r] * rx[r] + ry[r] * ry[r] + rz[r] * rz[r]));
                 cellD[g] = b[r];
                 offD[g] = ro[r];
                 vxD[g] = rx[r];

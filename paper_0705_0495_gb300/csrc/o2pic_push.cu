@@ -599,6 +599,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         // births grouped by sub-tile and written in parent order
         auto drain = [&]() {
             if (lane == 0) atomicAdd(&s_cnt[C_CANDS], (unsigned)qn);
+            if (lane == 0 && binned) atomicAdd(&s_cnt[C_BCANDS], (unsigned)qn);
             int staged = 0;
             for (int q = lane; q < qn; q += 32) {
                 const int i = qIdx[q];
@@ -789,6 +790,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 const unsigned wl = __reduce_add_sync(0xffffffffu, nlive);
                 if (lane == 0) {
                     if (ws) atomicAdd(&s_cnt[C_SLOTS], ws);
+                    if (ws && binned) atomicAdd(&s_cnt[C_BSLOTS], ws);
                     if (wl) atomicAdd(&s_cnt[C_LIVE], wl);
                 }
             }
