@@ -137,6 +137,20 @@ bool validate(const pic_config *c, int D, const pic_xs_table *xs, int n_xs, std:
             }
         }
     }
+    {
+        // slot indices are int and the births' tags carry the tile index in
+        // 21 bits: all slots, with the alignment padding, below 2^31
+        long long slots = 0;
+        for (int d = 0; d < D; ++d) {
+            for (int s = 0; s < 3; ++s)
+                slots += ((std::max(1LL, c[d].capacity[s]) + CHUNK - 1) / CHUNK) * (long long)CHUNK;
+            slots += (long long)(TILE_ALIGN + 3 * TILES_PER_TICKET) * CHUNK;
+        }
+        if (slots >= (1LL << 31)) {
+            why = "the capacities of all discharges together must stay below 2^31 slots";
+            return false;
+        }
+    }
     if (n_xs < 0 || (n_xs > 0 && !xs)) {
         why = "bad table list";
         return false;

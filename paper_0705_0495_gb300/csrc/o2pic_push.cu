@@ -494,6 +494,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     unsigned char *qBin = reinterpret_cast<unsigned char *>(sFm + fm_max) + w * QCAP;  // energy bin
 
     __shared__ int s_ticket[2];
+    __shared__ int s_qn[2][NW];  // queue lengths published at each ticket barrier (by parity)
     __shared__ int s_wnb[NW];
     __shared__ unsigned s_cnt[C_NCOUNT];
     __shared__ unsigned s_btn[NUBIN_MAX];  // electron bounds per energy bin: thresholds
@@ -538,13 +539,94 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         __syncthreads();
     };
 
+    // ---- phase B: the queued candidates of this warp, one per lane; the
+    // queue holds candidates of the current (discharge, species) only and
+    // outlives tickets (it is emptied at 32 and before every flush); births
+    // are grouped by sub-tile and written in parent order
+    int qn = 0;  // warp-uniform queue length
+    const Disc *Dq = nullptr;       // the queue's discharge and species
+    int sq = 0, pbq = 0, ch0q = 0;
+    auto drain = [&]() {
+        const Disc &Dd = *Dq;
+        const SpeciesC &S = Dd.sp[sq];
+        const bool binned = S.nbins > 0;
+        if (lane == 0) atomicAdd(&s_cnt[C_CANDS], (unsigned)qn);
+        if (lane == 0 && binned) atomicAdd(&s_cnt[C_BCANDS], (unsigned)qn);
+        int staged = 0;
+        for (int q = lane; q < qn; q += 32) {
+            const int i = qIdx[q];
+            const int cq = cellA[i];
+            const Real oq = offA[i];
+            Real ux = qVx[q], vy = vyA[i], vz = vzA[i];
+            // tag: (tile << 7 | slot in this warp's sub-tile) << 1
+            const int rel = i - pbq;
+            const int tag = (((ch0q + rel / CHUNK) << 7) | (rel % CHUNK - w * SUBTILE)) << 1;
+            const Real nun = binned ? s_bnu[qBin[q]] : pick<Real>(S.numax_n, S.numax_n_f);
+            const bool alive = gas_collide<Real>(W, Dd, sq, (unsigned)rel, step, nun, ux, vy, vz, cq, oq, tag,
+                                                 B, s_cnt, staged);
+            if (alive) {
+                vxA[i] = ux;
+                vyA[i] = vy;
+                vzA[i] = vz;
+            } else {
+                cellA[i] = -1;
+                deposit_shared_remove(sAcc, cq, oq);
+            }
+        }
+        qn = 0;
+        if (!__any_sync(0xffffffffu, staged != 0)) return;
+        __syncwarp();
+        const int nb = min(s_wnb[w], BSTAGE);
+        for (int r = lane; r < nb; r += 32) {
+            const int tg = bTag[r];  // ((tile << 7 | slot) << 1 | product) << 2 | species
+            const int tile = tg >> 10, sp = tg & 3;
+            int rank = 0, count = 0, below = 0;
+            for (int q = 0; q < nb; ++q) {
+                const int tq = bTag[q];
+                if ((tq >> 10) != tile) continue;
+                const int spq = tq & 3;
+                if (spq == sp) {
+                    ++count;
+                    rank += tq < tg;
+                } else if (spq < sp) {
+                    ++below;
+                }
+            }
+            const int sub = tile * SUBTILES + w;
+            if (below + rank < BIRTH_CAP_W) {
+                BirthRec<Real> &rec = stage[(size_t)sub * BIRTH_CAP_W + below + rank];
+                rec.c = bCell[r];
+                rec.off = bOff[r];
+                rec.vx = bVx[r];
+                rec.vy = bVy[r];
+                rec.vz = bVz[r];
+            } else {
+                set_status(ctl, ST_BIRTHBUF);
+            }
+            if (rank == 0) W.tile_cnt[(size_t)sub * NSP + sp] = count;
+        }
+        __syncwarp();
+        if (lane == 0) s_wnb[w] = 0;
+        __syncwarp();
+    };
+
     for (int it = 0;; ++it) {
         // two ticket buffers: a buffer is rewritten only after the barrier
         // that every reader of its previous value has passed
         if (tid == 0) s_ticket[it & 1] = (int)atomicAdd(&ctl->ticket, (unsigned)TILES_PER_TICKET);
+        if (lane == 0) s_qn[it & 1][w] = qn;
         __syncthreads();
         const int tbeg = s_ticket[it & 1];
         if (tbeg >= total) break;
+        {
+            // collisions run in all warps of the block at once (their latency
+            // is paid once, not once per warp at the next barrier), as soon as
+            // one warp has a full round of candidates
+            int qmax = 0;
+#pragma unroll
+            for (int q = 0; q < NW; ++q) qmax = max(qmax, s_qn[it & 1][q]);
+            if (qmax >= 32 && qn > 0) drain();
+        }
         // tiles of one (discharge, species) start at a multiple of
         // TILES_PER_TICKET, so a ticket belongs to one (d, s) or to padding
         int nx = ds < 0 ? 0 : ds;
@@ -552,6 +634,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         if (nx >= nds) continue;
         // a new (d, s), or the FP32 split sums at their bound: flush
         if (nx != ds || (sizeof(Real) == 4 && run_tk >= FLUSH_TICKETS)) {
+            if (qn > 0) drain();
             if (ds >= 0) flush(ds);
             const int nd = nx / NSP;
             const Disc &Dn = W.disc[nd];
@@ -576,6 +659,10 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             }
             ds = nx;
             run_tk = 0;
+            Dq = &W.disc[nd];
+            sq = nx % NSP;
+            pbq = Dn.pbase[sq];
+            ch0q = W.cnt[nx].chunk0;
             __syncthreads();
         }
         ++run_tk;
@@ -593,70 +680,6 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         const bool binned = nbins > 0;  // electrons: bound per lab-energy bin
         const Real ke = pick<Real>(S.ke_eV, S.ke_eV_f);
         const int wbase0 = pb + (tbeg - C.chunk0) * CHUNK + w * SUBTILE;  // warp's first sub-tile
-        int qn = 0;  // warp-uniform queue length
-
-        // ---- phase B: the queued candidates of this warp, one per lane;
-        // births grouped by sub-tile and written in parent order
-        auto drain = [&]() {
-            if (lane == 0) atomicAdd(&s_cnt[C_CANDS], (unsigned)qn);
-            if (lane == 0 && binned) atomicAdd(&s_cnt[C_BCANDS], (unsigned)qn);
-            int staged = 0;
-            for (int q = lane; q < qn; q += 32) {
-                const int i = qIdx[q];
-                const int cq = cellA[i];
-                const Real oq = offA[i];
-                Real ux = qVx[q], vy = vyA[i], vz = vzA[i];
-                const int rel = i - wbase0;  // (tile offset) * CHUNK + slot in sub-tile
-                const int tag = (((rel / CHUNK) << 7) | (rel % CHUNK)) << 1;
-                const Real nun = binned ? s_bnu[qBin[q]] : pick<Real>(S.numax_n, S.numax_n_f);
-                const bool alive = gas_collide<Real>(W, Dd, s, (unsigned)(i - pb), step, nun, ux, vy, vz, cq,
-                                                     oq, tag, B, s_cnt, staged);
-                if (alive) {
-                    vxA[i] = ux;
-                    vyA[i] = vy;
-                    vzA[i] = vz;
-                } else {
-                    cellA[i] = -1;
-                    deposit_shared_remove(sAcc, cq, oq);
-                }
-            }
-            qn = 0;
-            if (!__any_sync(0xffffffffu, staged != 0)) return;
-            __syncwarp();
-            const int nb = min(s_wnb[w], BSTAGE);
-            for (int r = lane; r < nb; r += 32) {
-                const int tg = bTag[r];  // ((tile offset << 7 | slot) << 1 | product) << 2 | species
-                const int tile_off = tg >> 10, sp = tg & 3;
-                int rank = 0, count = 0, below = 0;
-                for (int q = 0; q < nb; ++q) {
-                    const int tq = bTag[q];
-                    if ((tq >> 10) != tile_off) continue;
-                    const int sq = tq & 3;
-                    if (sq == sp) {
-                        ++count;
-                        rank += tq < tg;
-                    } else if (sq < sp) {
-                        ++below;
-                    }
-                }
-                const int sub = (tbeg + tile_off) * SUBTILES + w;
-                if (below + rank < BIRTH_CAP_W) {
-                    BirthRec<Real> &rec = stage[(size_t)sub * BIRTH_CAP_W + below + rank];
-                    rec.c = bCell[r];
-                    rec.off = bOff[r];
-                    rec.vx = bVx[r];
-                    rec.vy = bVy[r];
-                    rec.vz = bVz[r];
-                } else {
-                    set_status(ctl, ST_BIRTHBUF);
-                }
-                if (rank == 0) W.tile_cnt[(size_t)sub * NSP + sp] = count;
-            }
-            __syncwarp();
-            if (lane == 0) s_wnb[w] = 0;
-            __syncwarp();
-        };
-
         for (int t = tbeg; t < tend; ++t) {
             const int sbase = wbase0 + (t - tbeg) * CHUNK;
             const int i0 = sbase + 4 * lane;
@@ -809,10 +832,10 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 }
             }
             __syncwarp();
-            if (qn >= 32) drain();
+            if (qn > QCAP - SUBTILE) drain();  // the next sub-tile might not fit
         }
-        if (qn > 0) drain();
     }
+    if (qn > 0) drain();
     if (ds >= 0) flush(ds);
 }
 
