@@ -14,7 +14,7 @@ constexpr int SUBTILE = 128;           // slots of one warp in a tile (32 lanes 
 constexpr int SUBTILES = 1024 / SUBTILE;
 constexpr int BIRTH_CAP_W = 32;        // births staged per sub-tile
 constexpr int QCAP = 160;              // candidate queue of one warp (< 32 left + one sub-tile)
-constexpr int BSTAGE = 48;             // births staged by one warp between write-outs
+constexpr int COLLIDE_THREADS = 256;   // threads per block of the collision kernel
 constexpr int TILES_PER_TICKET = 8;    // tiles taken per atomic ticket by a push block
 constexpr int BIRTHS_THREADS = 512;    // block of the birth-append kernel (sub-tiles)
 constexpr int TILE_ALIGN = BIRTHS_THREADS / (1024 / 128);  // tiles per birth-append block
@@ -155,6 +155,7 @@ struct Ctl {
     int total_chunks;             // chunks in the current push
     int D;                        // discharges
     unsigned int births_ticket;   // block order of the birth-append kernel
+    unsigned int cand_n;          // collision candidates listed by the push this step
 };
 
 // Per (discharge, species) dynamic counts.
@@ -209,6 +210,8 @@ struct WsPtrs {
     int *pair_first;          // [total cells] first flagged projectile of the current reaction
     unsigned *vmax2;          // [D * 3] largest speed^2 (cells/step, float bits) at the last sort
     struct NuBin *nubin;      // [D * NUBIN_MAX] electron collision-frequency bounds per energy bin
+    int2 *cand;               // [cand_cap] collision candidates: (slot, ds << 8 | energy bin)
+    int cand_cap;
     int *pair_kills;          // [total cells * 3] particles killed per species in this pass
     void *pair_births;        // [total cells * PAIR_BIRTH_CAP] records
     int total_nodes;

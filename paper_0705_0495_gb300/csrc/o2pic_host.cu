@@ -76,12 +76,12 @@ struct Bump {
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, nubin, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
+    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, nubin, cand, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
         counters, eedf, iedf, fm, tables, lutE, lutS, lutEf, lutSf, sort_counts, cell_start,
         sort_live, pair_bcount, cell_disc, pair_births, sort_tab, ninit, vt;
     size_t cell[2], off[2], vx[2], vy[2], vz[2];
     size_t total;
-    int total_nodes, total_cells, max_chunks, total_cap, sort_blocks, n_lut, maxN, eedf_max, fm_max;
+    int total_nodes, total_cells, max_chunks, total_cap, sort_blocks, n_lut, maxN, eedf_max, fm_max, cand_cap;
     long long gtab_n;  // elements of the node-major gas tables
     std::vector<int> pbase, capr, gbase, ccell, sort_cbase, sort_gmax, cs_base, eedf_base, iedf_base,
         fm_base;
@@ -321,6 +321,10 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.pair_first = B.take(4ull * tc);
     L.vmax2 = B.take(4ull * 3 * D);
     L.nubin = B.take(sizeof(NuBin) * NUBIN_MAX * (size_t)D);
+    // collision candidates of one step: a quarter of all slots (a candidate
+    // probability up to 1/4 on average); more is reported as PIC_ECAPACITY
+    L.cand_cap = (int)std::min<long long>((long long)cap / 4 + 65536, (1LL << 31) - 1);
+    L.cand = B.take(8ull * (size_t)L.cand_cap);
     L.pair_kills = B.take(4ull * 3 * tc);
     for (int s = 0; s < 3; ++s) {
         long long tiles = 0;
@@ -659,6 +663,8 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.pair_first = reinterpret_cast<int *>(b + L.pair_first);
     W.vmax2 = reinterpret_cast<unsigned *>(b + L.vmax2);
     W.nubin = reinterpret_cast<NuBin *>(b + L.nubin);
+    W.cand = reinterpret_cast<int2 *>(b + L.cand);
+    W.cand_cap = L.cand_cap;
     W.pair_kills = reinterpret_cast<int *>(b + L.pair_kills);
     W.pair_births = b + L.pair_births;
     W.total_nodes = L.total_nodes;
@@ -842,6 +848,9 @@ static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool time_p
         if (e) return e;
         h->ev_used += 2;
     }
+    e = launch_collide(h->fp64, h->W, h->pools(), par, h->L.collide_blocks, st);
+    if (e) return e;
+    ++nk;
     e = launch_births(h->fp64, h->W, h->pools(), par, h->W.max_chunks / TILE_ALIGN + 1, st);
     if (e) return e;
     ++nk;
@@ -1216,13 +1225,11 @@ extern "C" pic_status pic_timing(pic_handle *h, double *push_ms, long long *push
     }
     // algorithmic bytes of the push: cell, offset and vx read and written for
     // every slot; vy, vz read for every slot of a species whose bound depends
-    // on the lab energy; vy, vz read and written for null-collision
-    // candidates (a candidate of a binned species only writes them)
+    // on the lab energy; one 8-byte list entry per collision candidate (the
+    // collisions themselves run in the next kernel)
     const double R = h->fp64 ? 8.0 : 4.0;
     const double bytes = (double)(slots - h->slots0) * 2.0 * (4.0 + 2.0 * R) +
-                         (double)(bslots - h->bslots0) * 2.0 * R +
-                         (double)(cands - h->cands0) * 2.0 * (2.0 * R) -
-                         (double)(bcands - h->bcands0) * 2.0 * R;
+                         (double)(bslots - h->bslots0) * 2.0 * R + (double)(cands - h->cands0) * 8.0;
     if (push_ms) *push_ms = h->push_ms;
     if (push_launches) *push_launches = h->push_launches;
     if (launches) *launches = h->launches;

@@ -350,6 +350,7 @@ k_field(WsPtrs W, int par, int diag, int mode)
         ctl->total_chunks = chunk;
         ctl->ticket = 0u;
         ctl->births_ticket = 0u;
+        ctl->cand_n = 0u;
         ctl->step[par ^ 1] = step + 1ull;
     }
     __syncthreads();

@@ -8,6 +8,7 @@ namespace o2 {
 
 struct LaunchCfg {
     int push_blocks;      // persistent grid of the push
+    int collide_blocks;   // grid of the collision kernel (loops over the candidates)
     size_t push_smem;     // dynamic shared memory of the push (non-diag)
     size_t push_smem_diag;
     int sort_blocks;      // sum over (d, s) of sort blocks
@@ -27,6 +28,7 @@ cudaError_t launch_push(bool fp64, bool diag, const WsPtrs &W, const void *pools
                         int par, const LaunchCfg &L, cudaStream_t s);
 cudaError_t push_configure(bool fp64, LaunchCfg &L, int num_sms);
 // births of the push appended in parent order
+cudaError_t launch_collide(bool fp64, const WsPtrs &W, const void *pools, int par, int blocks, cudaStream_t st);
 cudaError_t launch_births(bool fp64, const WsPtrs &W, const void *pools, int par, int max_blocks,
                           cudaStream_t s);
 

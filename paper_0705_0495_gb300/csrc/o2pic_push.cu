@@ -181,35 +181,37 @@ __device__ __forceinline__ void ee_elastic(Real a[3], Real b[3], const Real n[3]
 }
 
 template <typename Real>
-struct BirthStage {
-    int *cell, *tag;
-    Real *off, *vx, *vy, *vz;
-    int *nb;
-};
-
-template <typename Real>
 struct BirthRec {
     int c;
-    int pad;
+    int tag;    // (slot in the sub-tile << 1 | product) << 2 | species
     Real off, vx, vy, vz;
 };
 
+// Births of one candidate go straight to its sub-tile's records, in any
+// order; the tag restores parent order when they are appended.
 template <typename Real>
-__device__ __forceinline__ void stage_birth(const BirthStage<Real> &B, Ctl *ctl, int tag,
-                                            int sp, int c, Real off, const Real v[3], int &staged)
+struct BirthSink {
+    BirthRec<Real> *rec;  // the sub-tile's BIRTH_CAP_W records
+    int *n;               // the sub-tile's record count
+    Ctl *ctl;
+};
+
+template <typename Real>
+__device__ __forceinline__ void stage_birth(const BirthSink<Real> &B, int tag, int sp, int c, Real off,
+                                            const Real v[3])
 {
-    ++staged;
-    int pos = atomicAdd(B.nb, 1);
-    if (pos >= BSTAGE) {
-        set_status(ctl, ST_BIRTHBUF);
+    const int pos = atomicAdd(B.n, 1);
+    if (pos >= BIRTH_CAP_W) {
+        set_status(B.ctl, ST_BIRTHBUF);
         return;
     }
-    B.cell[pos] = c;
-    B.tag[pos] = (tag << 2) | sp;
-    B.off[pos] = off;
-    B.vx[pos] = v[0];
-    B.vy[pos] = v[1];
-    B.vz[pos] = v[2];
+    BirthRec<Real> &r = B.rec[pos];
+    r.c = c;
+    r.tag = (tag << 2) | sp;
+    r.off = off;
+    r.vx = v[0];
+    r.vy = v[1];
+    r.vz = v[2];
 }
 
 // Energy bin of an electron's lab energy K [eV] for the collision-frequency
@@ -233,11 +235,16 @@ __device__ __forceinline__ int energy_bin(double K, int nb)
 
 // One gas-target candidate (null-collision method).  Returns false if the
 // particle died.  v is updated in place; products are staged.
+struct Outcome {
+    bool alive;     // the particle survives
+    bool viol;      // sum_j n_j sigma_j u exceeded the bound
+    int reaction;   // reaction number, -1 for a null event
+};
+
 template <typename Real>
-__device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int s, unsigned idx,
-                                         unsigned long long step, Real numax_n, Real &vx, Real &vy,
-                                         Real &vz, int c, Real off, int tag, const BirthStage<Real> &B,
-                                         unsigned *s_cnt, int &staged)
+__device__ __forceinline__ Outcome gas_collide(const WsPtrs &W, const Disc &Dd, int s, unsigned idx,
+                                            unsigned long long step, Real numax_n, Real &vx, Real &vy,
+                                            Real &vz, int c, Real off, int tag, const BirthSink<Real> &B)
 {
     const SpeciesC &S = Dd.sp[s];
     const Real *lutE = Lut<Real>::E(W);
@@ -281,11 +288,10 @@ __device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int
             chosen = (chosen < 0 && target < cum) ? j : chosen;
         }
     }
-    if (cum > numax_n) atomicAdd(&s_cnt[C_VIOL_GAS], 1u);
-    if (chosen < 0) return true;  // null event
+    const bool viol = cum > numax_n;
+    if (chosen < 0) return Outcome{true, viol, -1};  // null event
     const GasChan &ch = S.ch[chosen];
     const int r = ch.reaction;
-    atomicAdd(&s_cnt[C_EVENTS + r], 1u);
     Real nd[3];
     iso_dir<Real>(unif<Real>(b.y), unif<Real>(b.z), nd);
     const Real mf = pick<Real>(S.mfrac, S.mfrac_f), Mf = pick<Real>(S.Mfrac, S.Mfrac_f);
@@ -308,12 +314,12 @@ __device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int
         iso_dir<Real>(unif<Real>(e.x), unif<Real>(e.y), n2v);
         Real e2[3] = {Vo[0], Vo[1], Vo[2]};
         ee_elastic<Real>(vo, e2, n2v);
-        stage_birth<Real>(B, W.ctl, tag, 0, c, off, e2, staged);
-        stage_birth<Real>(B, W.ctl, tag | 1, 2, c, off, Vo, staged);
+        stage_birth<Real>(B, tag, 0, c, off, e2);
+        stage_birth<Real>(B, tag | 1, 2, c, off, Vo);
     }
     if (!dies) {
         vx = vo[0]; vy = vo[1]; vz = vo[2];
-        return true;
+        return Outcome{true, viol, r};
     }
     // (15) attachment: O- with the CM velocity plus half the relative
     // energy above threshold shared back to back with O; (16) detachment:
@@ -337,8 +343,8 @@ __device__ __forceinline__ bool gas_collide(const WsPtrs &W, const Disc &Dd, int
     Real pv[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) pv[q] = A * (mf * v[q] + Mf * V[q]) + w * nd[q];
-    stage_birth<Real>(B, W.ctl, tag, r == 15 ? 1 : 0, c, off, pv, staged);
-    return false;
+    stage_birth<Real>(B, tag, r == 15 ? 1 : 0, c, off, pv);
+    return Outcome{false, viol, r};
 }
 
 template <typename Acc> __device__ __forceinline__ void acc_add(Acc *a, Acc v);
@@ -469,6 +475,12 @@ __device__ __forceinline__ void deposit4(double *sAcc, const int dep[4], const d
     }
 }
 
+// the species of (discharge, species) index ds has an energy-binned bound
+__device__ __forceinline__ bool Dd_binned(const WsPtrs &W, int ds)
+{
+    return W.disc[ds / NSP].sp[ds % NSP].nbins > 0;
+}
+
 template <typename Real, bool DIAG>
 __global__ void __launch_bounds__(PUSH_THREADS, PushOcc<Real>::blocks)
 k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
@@ -479,26 +491,16 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     Acc *sAcc = reinterpret_cast<Acc *>(smem);
     Real *sE = reinterpret_cast<Real *>(sAcc + (Nmax + 2));
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    // per-warp candidate queue (index, vx after the push) and staged births
-    Real *qVx = sE + (Nmax + 2) + w * QCAP;
-    Real *bOff = sE + (Nmax + 2) + NW * QCAP + w * BSTAGE;
-    Real *bVx = bOff + NW * BSTAGE;
-    Real *bVy = bVx + NW * BSTAGE;
-    Real *bVz = bVy + NW * BSTAGE;
-    int *ibase = reinterpret_cast<int *>(sE + (Nmax + 2) + NW * QCAP + 4 * NW * BSTAGE);
-    int *qIdx = ibase + w * QCAP;
-    int *bCell = ibase + NW * QCAP + w * BSTAGE;
-    int *bTag = ibase + NW * QCAP + NW * BSTAGE + w * BSTAGE;
-    unsigned *sEedf = reinterpret_cast<unsigned *>(ibase + NW * QCAP + 2 * NW * BSTAGE);
+    // per-warp list of collision candidates (slot, energy bin) before it is
+    // written out, and the histograms
+    int *qIdx = reinterpret_cast<int *>(sE + (Nmax + 2)) + w * QCAP;
+    unsigned *sEedf = reinterpret_cast<unsigned *>(sE + (Nmax + 2)) + NW * QCAP;
     unsigned *sFm = sEedf + eedf_max;
-    unsigned char *qBin = reinterpret_cast<unsigned char *>(sFm + fm_max) + w * QCAP;  // energy bin
+    unsigned char *qBin = reinterpret_cast<unsigned char *>(sFm + fm_max) + w * QCAP;
 
     __shared__ int s_ticket[2];
-    __shared__ int s_qn[2][NW];  // queue lengths published at each ticket barrier (by parity)
-    __shared__ int s_wnb[NW];
     __shared__ unsigned s_cnt[C_NCOUNT];
     __shared__ unsigned s_btn[NUBIN_MAX];  // electron bounds per energy bin: thresholds
-    __shared__ Real s_bnu[NUBIN_MAX];      // and nu_max dt
 
     Ctl *ctl = W.ctl;
     const int cur = ctl->cur;
@@ -508,14 +510,10 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     int *cellA = P.cell[cur];
     Real *offA = P.off[cur], *vxA = P.vx[cur], *vyA = P.vy[cur], *vzA = P.vz[cur];
     Acc *accG = acc_global<Real>(W);
-    BirthRec<Real> *stage = reinterpret_cast<BirthRec<Real> *>(W.births);
     const unsigned lt_mask = (1u << lane) - 1u;
-    BirthStage<Real> B{bCell, bTag, bOff, bVx, bVy, bVz, &s_wnb[w]};
 
     int ds = -1, d = -1, run_tk = 0;
     for (int q = tid; q < C_NCOUNT; q += PUSH_THREADS) s_cnt[q] = 0;
-    if (lane == 0) s_wnb[w] = 0;
-
     auto flush = [&](int fds) {
         const int fd = fds / NSP, fs = fds % NSP;
         const Disc &Dd = W.disc[fd];
@@ -539,94 +537,33 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         __syncthreads();
     };
 
-    // ---- phase B: the queued candidates of this warp, one per lane; the
-    // queue holds candidates of the current (discharge, species) only and
-    // outlives tickets (it is emptied at 32 and before every flush); births
-    // are grouped by sub-tile and written in parent order
-    int qn = 0;  // warp-uniform queue length
-    const Disc *Dq = nullptr;       // the queue's discharge and species
-    int sq = 0, pbq = 0, ch0q = 0;
-    auto drain = [&]() {
-        const Disc &Dd = *Dq;
-        const SpeciesC &S = Dd.sp[sq];
-        const bool binned = S.nbins > 0;
-        if (lane == 0) atomicAdd(&s_cnt[C_CANDS], (unsigned)qn);
-        if (lane == 0 && binned) atomicAdd(&s_cnt[C_BCANDS], (unsigned)qn);
-        int staged = 0;
+    // ---- the warp's candidates go to the step's list (one reservation per
+    // batch); the collision kernel takes them from there
+    int qn = 0;  // warp-uniform
+    auto list_out = [&]() {
+        int base = 0;
+        if (lane == 0) {
+            base = (int)atomicAdd(&ctl->cand_n, (unsigned)qn);
+            atomicAdd(&s_cnt[C_CANDS], (unsigned)qn);
+            if (Dd_binned(W, ds)) atomicAdd(&s_cnt[C_BCANDS], (unsigned)qn);
+            if ((long long)base + qn > W.cand_cap) set_status(ctl, ST_BIRTHBUF);
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
         for (int q = lane; q < qn; q += 32) {
-            const int i = qIdx[q];
-            const int cq = cellA[i];
-            const Real oq = offA[i];
-            Real ux = qVx[q], vy = vyA[i], vz = vzA[i];
-            // tag: (tile << 7 | slot in this warp's sub-tile) << 1
-            const int rel = i - pbq;
-            const int tag = (((ch0q + rel / CHUNK) << 7) | (rel % CHUNK - w * SUBTILE)) << 1;
-            const Real nun = binned ? s_bnu[qBin[q]] : pick<Real>(S.numax_n, S.numax_n_f);
-            const bool alive = gas_collide<Real>(W, Dd, sq, (unsigned)rel, step, nun, ux, vy, vz, cq, oq, tag,
-                                                 B, s_cnt, staged);
-            if (alive) {
-                vxA[i] = ux;
-                vyA[i] = vy;
-                vzA[i] = vz;
-            } else {
-                cellA[i] = -1;
-                deposit_shared_remove(sAcc, cq, oq);
-            }
+            const long long at = (long long)base + q;
+            if (at < W.cand_cap) W.cand[at] = make_int2(qIdx[q], (ds << 8) | qBin[q]);
         }
+        __syncwarp();
         qn = 0;
-        if (!__any_sync(0xffffffffu, staged != 0)) return;
-        __syncwarp();
-        const int nb = min(s_wnb[w], BSTAGE);
-        for (int r = lane; r < nb; r += 32) {
-            const int tg = bTag[r];  // ((tile << 7 | slot) << 1 | product) << 2 | species
-            const int tile = tg >> 10, sp = tg & 3;
-            int rank = 0, count = 0, below = 0;
-            for (int q = 0; q < nb; ++q) {
-                const int tq = bTag[q];
-                if ((tq >> 10) != tile) continue;
-                const int spq = tq & 3;
-                if (spq == sp) {
-                    ++count;
-                    rank += tq < tg;
-                } else if (spq < sp) {
-                    ++below;
-                }
-            }
-            const int sub = tile * SUBTILES + w;
-            if (below + rank < BIRTH_CAP_W) {
-                BirthRec<Real> &rec = stage[(size_t)sub * BIRTH_CAP_W + below + rank];
-                rec.c = bCell[r];
-                rec.off = bOff[r];
-                rec.vx = bVx[r];
-                rec.vy = bVy[r];
-                rec.vz = bVz[r];
-            } else {
-                set_status(ctl, ST_BIRTHBUF);
-            }
-            if (rank == 0) W.tile_cnt[(size_t)sub * NSP + sp] = count;
-        }
-        __syncwarp();
-        if (lane == 0) s_wnb[w] = 0;
-        __syncwarp();
     };
 
     for (int it = 0;; ++it) {
         // two ticket buffers: a buffer is rewritten only after the barrier
         // that every reader of its previous value has passed
         if (tid == 0) s_ticket[it & 1] = (int)atomicAdd(&ctl->ticket, (unsigned)TILES_PER_TICKET);
-        if (lane == 0) s_qn[it & 1][w] = qn;
         __syncthreads();
         const int tbeg = s_ticket[it & 1];
         if (tbeg >= total) break;
-        {
-            // collisions run in all warps of the block at once (their latency
-            // is paid once, not once per warp at the next barrier), as soon as
-            // one warp has a full round of candidates
-            int qmax = 0;
-#pragma unroll
-            for (int q = 0; q < NW; ++q) qmax = max(qmax, s_qn[it & 1][q]);
-            if (qmax >= 32 && qn > 0) drain();
-        }
         // tiles of one (discharge, species) start at a multiple of
         // TILES_PER_TICKET, so a ticket belongs to one (d, s) or to padding
         int nx = ds < 0 ? 0 : ds;
@@ -634,7 +571,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         if (nx >= nds) continue;
         // a new (d, s), or the FP32 split sums at their bound: flush
         if (nx != ds || (sizeof(Real) == 4 && run_tk >= FLUSH_TICKETS)) {
-            if (qn > 0) drain();
+            if (qn > 0) list_out();
             if (ds >= 0) flush(ds);
             const int nd = nx / NSP;
             const Disc &Dn = W.disc[nd];
@@ -649,7 +586,6 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 for (int b = tid; b < Sn.nbins; b += PUSH_THREADS) {
                     const NuBin &nb = W.nubin[Sn.bin_off + b];
                     s_btn[b] = nb.tnull;
-                    s_bnu[b] = pick<Real>(nb.numax_n, nb.numax_n_f);
                 }
             }
             for (int q = tid; q < C_NCOUNT; q += PUSH_THREADS) s_cnt[q] = 0;
@@ -659,10 +595,6 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             }
             ds = nx;
             run_tk = 0;
-            Dq = &W.disc[nd];
-            sq = nx % NSP;
-            pbq = Dn.pbase[sq];
-            ch0q = W.cnt[nx].chunk0;
             __syncthreads();
         }
         ++run_tk;
@@ -684,7 +616,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             const int sbase = wbase0 + (t - tbeg) * CHUNK;
             const int i0 = sbase + 4 * lane;
             const int sub = t * SUBTILES + w;
-            if (lane < NSP) W.tile_cnt[(size_t)sub * NSP + lane] = 0;
+            if (lane == 0) W.tile_cnt[(size_t)sub * NSP] = 0;  // births recorded by the collision kernel
 
             // ---- phase A: push, absorb, null test, deposit, candidate queue
             int c[4];
@@ -762,7 +694,6 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 if (cand) {
                     const int pos = qn + __popc(m & lt_mask);
                     qIdx[pos] = i0 + k;
-                    qVx[pos] = vx[k];
                     qBin[pos] = (unsigned char)bin;
                 }
                 qn += __popc(m);
@@ -832,11 +763,78 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 }
             }
             __syncwarp();
-            if (qn > QCAP - SUBTILE) drain();  // the next sub-tile might not fit
+            if (qn >= 32) list_out();
         }
     }
-    if (qn > 0) drain();
+    if (qn > 0) list_out();
     if (ds >= 0) flush(ds);
+}
+
+
+// Collisions of the step's candidates (null-collision method, Sec. III
+// kinematics): one thread per candidate, in list order; a dying particle's
+// charge leaves the global grid, births go to its sub-tile's records.  Event
+// counts are summed per block for the discharge of the block's first
+// candidate (the list holds runs of one discharge), others go straight to
+// the global counters.
+template <typename Real>
+__global__ void __launch_bounds__(COLLIDE_THREADS)
+k_collide(WsPtrs W, Pools<Real> P, int par)
+{
+    using Acc = typename AccT<Real>::T;
+    __shared__ unsigned s_ev[C_NCOUNT];
+    Ctl *ctl = W.ctl;
+    const int n = (int)min((long long)ctl->cand_n, (long long)W.cand_cap);
+    const unsigned long long step = ctl->step[par];
+    const int cur = ctl->cur;
+    int *cellA = P.cell[cur];
+    Real *offA = P.off[cur], *vxA = P.vx[cur], *vyA = P.vy[cur], *vzA = P.vz[cur];
+    BirthRec<Real> *stage = reinterpret_cast<BirthRec<Real> *>(W.births);
+    Acc *accG = acc_global<Real>(W);
+    for (int base = blockIdx.x * COLLIDE_THREADS; base < n; base += gridDim.x * COLLIDE_THREADS) {
+        for (int q = threadIdx.x; q < C_NCOUNT; q += COLLIDE_THREADS) s_ev[q] = 0;
+        __syncthreads();
+        const int dblk = (W.cand[base].y >> 8) / NSP;
+        const int q = base + threadIdx.x;
+        if (q < n) {
+            const int2 e = W.cand[q];
+            const int i = e.x, ds = e.y >> 8, bin = e.y & 0xFF;
+            const int d = ds / NSP, s = ds % NSP;
+            const Disc &Dd = W.disc[d];
+            const SpeciesC &S = Dd.sp[s];
+            const int rel = i - Dd.pbase[s];
+            const int sub = (W.cnt[ds].chunk0 + rel / CHUNK) * SUBTILES + (rel % CHUNK) / SUBTILE;
+            const int slot = rel % SUBTILE;
+            const int c = cellA[i];
+            const Real off = offA[i];
+            Real vx = vxA[i], vy = vyA[i], vz = vzA[i];
+            const Real nun = S.nbins > 0 ? pick<Real>(W.nubin[S.bin_off + bin].numax_n, W.nubin[S.bin_off + bin].numax_n_f)
+                                         : pick<Real>(S.numax_n, S.numax_n_f);
+            const BirthSink<Real> B{stage + (size_t)sub * BIRTH_CAP_W, W.tile_cnt + (size_t)sub * NSP, ctl};
+            const Outcome o = gas_collide<Real>(W, Dd, s, (unsigned)rel, step, nun, vx, vy, vz, c, off,
+                                                slot << 1, B);
+            if (o.alive) {
+                vxA[i] = vx;
+                vyA[i] = vy;
+                vzA[i] = vz;
+            } else {
+                cellA[i] = -1;
+                deposit_global(accG + (size_t)s * W.total_nodes + Dd.gbase, c, off, -1);
+            }
+            if (d == dblk) {
+                if (o.viol) atomicAdd(&s_ev[C_VIOL_GAS], 1u);
+                if (o.reaction >= 0) atomicAdd(&s_ev[C_EVENTS + o.reaction], 1u);
+            } else {
+                unsigned long long *g = W.counters + (size_t)d * C_NCOUNT;
+                if (o.viol) atomicAdd(&g[C_VIOL_GAS], 1ull);
+                if (o.reaction >= 0) atomicAdd(&g[C_EVENTS + o.reaction], 1ull);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < C_NCOUNT; k += COLLIDE_THREADS)
+            if (s_ev[k]) atomicAdd(&W.counters[(size_t)dblk * C_NCOUNT + k], (unsigned long long)s_ev[k]);
+        __syncthreads();
+    }
 }
 
 // Births of one step appended after the survivors, per discharge and
@@ -887,10 +885,11 @@ k_births(WsPtrs W, Pools<Real> P, int par)
     const int T1 = (W.cnt[d * NSP + 2].chunk0 + W.cnt[d * NSP + 2].nchunk) * SUBTILES;
     int mine[NSP] = {0, 0, 0};
     const bool in = t < total && t < T1;
+    const BirthRec<Real> *rec = reinterpret_cast<const BirthRec<Real> *>(W.births) + (size_t)t * BIRTH_CAP_W;
+    int nrec = 0;  // records of this sub-tile (any order; the tag gives species and parent order)
     if (in) {
-        const int *tc = W.tile_cnt + (size_t)t * NSP;
-#pragma unroll
-        for (int q = 0; q < NSP; ++q) mine[q] = tc[q];
+        nrec = min(W.tile_cnt[(size_t)t * NSP], BIRTH_CAP_W);
+        for (int r = 0; r < nrec; ++r) ++mine[rec[r].tag & 3];
     }
     int excl[NSP];
 #pragma unroll
@@ -958,33 +957,32 @@ k_births(WsPtrs W, Pools<Real> P, int par)
         }
     }
     __syncthreads();
-    if (!in) return;
-    int nsum = mine[0] + mine[1] + mine[2];
-    if (nsum == 0) return;
+    if (!in || nrec == 0) return;
     const Disc &Dd = W.disc[d];
     const int cur = ctl->cur;
-    const BirthRec<Real> *stage = reinterpret_cast<const BirthRec<Real> *>(W.births);
     Acc *accG = acc_global<Real>(W);
-    int off0 = 0;
-    for (int q = 0; q < NSP; ++q) {
-        const int n0 = W.cnt[d * NSP + q].n_snap;
-        const int start = s_excl[q] + excl[q];
-        for (int r = 0; r < mine[q]; ++r) {
-            const BirthRec<Real> &b = stage[(size_t)t * BIRTH_CAP_W + off0 + r];
-            const long long dst = (long long)n0 + start + r;
-            if (dst >= Dd.cap[q]) {
-                set_status(ctl, ST_CAPACITY);
-                continue;
-            }
-            const int g = Dd.pbase[q] + (int)dst;
-            P.cell[cur][g] = b.c;
-            P.off[cur][g] = b.off;
-            P.vx[cur][g] = b.vx;
-            P.vy[cur][g] = b.vy;
-            P.vz[cur][g] = b.vz;
-            deposit_global(accG + (size_t)q * W.total_nodes + Dd.gbase, b.c, b.off, 1);
+    // a record's place among its species: the number of that species'
+    // records with a smaller tag (parent slot, then product)
+    for (int r = 0; r < nrec; ++r) {
+        const BirthRec<Real> &b = rec[r];
+        const int q = b.tag & 3;
+        int rank = 0;
+        for (int k = 0; k < nrec; ++k) {
+            const int tk = rec[k].tag;
+            rank += (tk & 3) == q && tk < b.tag;
         }
-        off0 += mine[q];
+        const long long dst = (long long)W.cnt[d * NSP + q].n_snap + s_excl[q] + excl[q] + rank;
+        if (dst >= Dd.cap[q]) {
+            set_status(ctl, ST_CAPACITY);
+            continue;
+        }
+        const int g = Dd.pbase[q] + (int)dst;
+        P.cell[cur][g] = b.c;
+        P.off[cur][g] = b.off;
+        P.vx[cur][g] = b.vx;
+        P.vy[cur][g] = b.vy;
+        P.vz[cur][g] = b.vz;
+        deposit_global(accG + (size_t)q * W.total_nodes + Dd.gbase, b.c, b.off, 1);
     }
 }
 
@@ -994,10 +992,9 @@ static size_t push_smem_bytes(int Nmax, int eedf_max, int fm_max)
     using Acc = typename AccT<Real>::T;
     constexpr int NW = PUSH_THREADS / 32;
     size_t b = sizeof(Acc) * (Nmax + 2) + sizeof(Real) * (Nmax + 2);
-    b += sizeof(Real) * NW * QCAP + sizeof(int) * NW * QCAP;
-    b += 4 * sizeof(Real) * NW * BSTAGE + 2 * sizeof(int) * NW * BSTAGE;
+    b += sizeof(int) * NW * QCAP;  // candidate slots
     b += sizeof(unsigned) * (eedf_max + fm_max);
-    b += (size_t)NW * QCAP;  // queue energy bins
+    b += (size_t)NW * QCAP;        // candidate energy bins
     return (b + 15) & ~size_t(15);
 }
 
@@ -1031,6 +1028,7 @@ cudaError_t push_configure(bool fp64, LaunchCfg &L, int num_sms)
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     L.push_blocks = num_sms * per_sm;
+    L.collide_blocks = num_sms * 8;
     return cudaSuccess;
 }
 
@@ -1052,6 +1050,15 @@ cudaError_t launch_push(bool fp64, bool diag, const WsPtrs &W, const void *pools
         else
             k_push<float, false><<<L.push_blocks, PUSH_THREADS, sm, st>>>(W, P, par, L.maxN, em, fm);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collide(bool fp64, const WsPtrs &W, const void *pools, int par, int blocks, cudaStream_t st)
+{
+    if (fp64)
+        k_collide<double><<<blocks, COLLIDE_THREADS, 0, st>>>(W, *static_cast<const Pools<double> *>(pools), par);
+    else
+        k_collide<float><<<blocks, COLLIDE_THREADS, 0, st>>>(W, *static_cast<const Pools<float> *>(pools), par);
     return cudaGetLastError();
 }
 
