@@ -570,6 +570,23 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
                 b[r] = c < 0 ? N : c;
             }
         }
+        // every load of the rows' data (read-only path) before the ranks are
+        // worked out, so that their latency overlaps that work; the source
+        // and destination arrays never overlap
+        Real ro[SORT_ILP], rx[SORT_ILP], ry[SORT_ILP], rz[SORT_ILP];
+        int gb[SORT_ILP];
+#pragma unroll
+        for (int r = 0; r < SORT_ILP; ++r) {
+            gb[r] = 0;
+            if (b[r] >= 0 && b[r] < N) {
+                const int i = i0 + r * 32 + lane;
+                gb[r] = __ldg(&cstart[b[r]]) + __ldg(&base[b[r]]);
+                ro[r] = __ldg(&offS[i]);
+                rx[r] = __ldg(&vxS[i]);
+                ry[r] = __ldg(&vyS[i]);
+                rz[r] = __ldg(&vzS[i]);
+            }
+        }
 #pragma unroll
         for (int r = 0; r < SORT_ILP; ++r) {
             dst[r] = -1;
@@ -588,26 +605,10 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
             if (b[r] >= 0 && lane == __ffs(peers) - 1) hw[b[r]] += (unsigned short)__popc(peers);
             __syncwarp();
         }
-        // every load of the rows first (read-only path), then the stores: the
-        // source and destination arrays never overlap
-        Real ro[SORT_ILP], rx[SORT_ILP], ry[SORT_ILP], rz[SORT_ILP];
-        int gd[SORT_ILP];
 #pragma unroll
         for (int r = 0; r < SORT_ILP; ++r) {
-            gd[r] = -1;
             if (dst[r] >= 0) {
-                const int i = i0 + r * 32 + lane;
-                gd[r] = __ldg(&cstart[b[r]]) + __ldg(&base[b[r]]) + dst[r];
-                ro[r] = __ldg(&offS[i]);
-                rx[r] = __ldg(&vxS[i]);
-                ry[r] = __ldg(&vyS[i]);
-                rz[r] = __ldg(&vzS[i]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < SORT_ILP; ++r) {
-            if (gd[r] >= 0) {
-                const int g = gd[r];
+                const int g = gb[r] + dst[r];
                 vm2 = fmaxf(vm2, (float)(rx[r] * rx[r] + ry[r] * ry[r] + rz[r] * rz[r]));
                 cellD[g] = b[r];
                 offD[g] = ro[r];

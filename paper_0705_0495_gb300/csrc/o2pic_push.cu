@@ -920,40 +920,55 @@ k_births(WsPtrs W, Pools<Real> P, int par)
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < NSP; ++q) excl[q] += warp > 0 ? wsum[q][warp - 1] : 0;
-    // look-back over the earlier blocks of this discharge
-    if (tid < NSP) {
-        const int q = tid;
+    // look-back over the earlier blocks of this discharge, one warp per
+    // species, 32 predecessors per round: the nearest one that has published
+    // its inclusive prefix ends the walk (a ballot finds it, a warp sum adds
+    // the aggregates of the blocks in between)
+    if (warp < NSP) {
+        const int q = warp;
         const unsigned long long epoch = (ctl->step[par] + 1ull) & 0xFFFFFFFFull;
         const int first_blk = W.cnt[d * NSP].chunk0 * SUBTILES / BIRTHS_THREADS;
         unsigned long long *lb = W.births_lb + (size_t)blk * NSP + q;
         const unsigned own = (unsigned)s_tot[q];
         unsigned ex = 0;
         if (blk > first_blk) {
-            st_release_u64(lb, (epoch << 32) | own);
-            int j = blk - 1;
+            if (lane == 0) st_release_u64(lb, (epoch << 32) | own);
+            int jhi = blk - 1;
             long long spins = 0;
-            while (j >= first_blk) {
-                const unsigned long long v = ld_acquire_u64(W.births_lb + (size_t)j * NSP + q);
-                if ((v >> 32) != epoch) {
+            for (;;) {
+                const int j = jhi - lane;
+                bool ready = true, incl = true;  // before the first block: an empty prefix
+                unsigned val = 0;
+                if (j >= first_blk) {
+                    const unsigned long long v = ld_acquire_u64(W.births_lb + (size_t)j * NSP + q);
+                    ready = (v >> 32) == epoch;
+                    incl = ready && (v & 0x80000000ull);
+                    val = (unsigned)(v & 0x7FFFFFFFull);
+                }
+                const unsigned im = __ballot_sync(0xffffffffu, incl);
+                const int k = im ? __ffs(im) - 1 : 31;  // lanes 0..k are needed
+                if (__ballot_sync(0xffffffffu, !ready && lane <= k)) {
                     if (++spins > SPIN_LIMIT) {
-                        set_status(ctl, ST_TIMEOUT);
+                        if (lane == 0) set_status(ctl, ST_TIMEOUT);
                         break;
                     }
                     __nanosleep(64);
                     continue;
                 }
-                ex += (unsigned)(v & 0x7FFFFFFFull);
-                if (v & 0x80000000ull) break;
-                --j;
+                ex += __reduce_add_sync(0xffffffffu, lane <= k ? val : 0u);
+                if (im) break;
+                jhi -= 32;
             }
         }
-        st_release_u64(lb, (epoch << 32) | 0x80000000ull | (unsigned long long)(ex + own));
-        s_excl[q] = (int)ex;
-        // the block holding the last tile of the discharge sets the counts
-        if (tfirst_blk <= T1 - 1 && T1 - 1 < tfirst_blk + BIRTHS_THREADS) {
-            Counts &cs = W.cnt[d * NSP + q];
-            const long long nn = (long long)cs.n_snap + ex + own;
-            cs.n = (int)(nn < W.disc[d].cap[q] ? nn : W.disc[d].cap[q]);
+        if (lane == 0) {
+            st_release_u64(lb, (epoch << 32) | 0x80000000ull | (unsigned long long)(ex + own));
+            s_excl[q] = (int)ex;
+            // the block holding the last tile of the discharge sets the counts
+            if (tfirst_blk <= T1 - 1 && T1 - 1 < tfirst_blk + BIRTHS_THREADS) {
+                Counts &cs = W.cnt[d * NSP + q];
+                const long long nn = (long long)cs.n_snap + ex + own;
+                cs.n = (int)(nn < W.disc[d].cap[q] ? nn : W.disc[d].cap[q]);
+            }
         }
     }
     __syncthreads();
