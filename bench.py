@@ -42,6 +42,8 @@ def _args():
                    help="fraction of the workload's superparticles (same plasma density)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the FP64 and batched-sweep figures reported beside the main one")
     return p.parse_args()
 
 
@@ -204,6 +206,54 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reduce_over_ranks(values, ops, device):
+    """Combine per-rank numbers: 'max' (the job's time is its slowest rank's)
+    or 'sum' (work adds up over ranks).  Without a process group it is the
+    identity."""
+    import torch
+    import torch.distributed as tdist
+    out = []
+    for v, op in zip(values, ops):
+        t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+        if tdist.is_available() and tdist.is_initialized():
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX if op == "max" else tdist.ReduceOp.SUM)
+        out.append(float(t.item()))
+    return out
+
+
+def measure_variant(name, discharges, warm_steps, timed_steps):
+    """Particle-steps/s and the push's HBM fraction of another configuration
+    (the FP64 path, the batched sweep), timed with CUDA events like the main
+    figure; the state of each is far larger than L2."""
+    import torch
+
+    from paper_0705_0495_gb300 import o2pic
+    sim = o2pic.Simulation(discharges, inputs.xs_tables())
+    try:
+        sim.step(warm_steps)
+        sim.set_timing(True)
+        sim.timing(reset=True)
+        g0 = [sim.diagnostics(k) for k in range(len(discharges))]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(timed_steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ps = sum(sim.diagnostics(k)["particle_steps"] - g0[k]["particle_steps"] for k in range(len(discharges)))
+        tm = sim.timing()
+        peak, _ = _peaks()
+        launches = max(1, tm["push_launches"])
+        achieved = tm["push_bytes"] / launches / (tm["push_ms"] / 1e3 / launches) / 1e9 if tm["push_ms"] > 0 else 0.0
+        return {"workload": name, "value": ps / (ms / 1e3), "unit": UNIT, "time_steps": timed_steps,
+                "warmup_time_steps": warm_steps, "ms_per_time_step": ms / timed_steps,
+                "push_hbm_frac": achieved / peak}
+    finally:
+        sim.close()
+
+
 def run_ours(a, rank, world, local_rank):
     import numpy as np
     import torch
@@ -255,13 +305,8 @@ def run_ours(a, rank, world, local_rank):
     g1 = sim.diagnostics(0)
     tm = sim.timing()
     psteps = g1["particle_steps"] - g0["particle_steps"]
-    ms = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    ps_t = torch.tensor([float(psteps)], dtype=torch.float64, device="cuda")
-    if dist:
-        tdist.all_reduce(ms, op=tdist.ReduceOp.MAX)
-        tdist.all_reduce(ps_t, op=tdist.ReduceOp.SUM)
-    total_ms_max = float(ms.item())
-    value = float(ps_t.item()) / (total_ms_max / 1e3)
+    total_ms_max, psteps_all = reduce_over_ranks([total_ms, psteps], ["max", "sum"], "cuda")
+    value = psteps_all / (total_ms_max / 1e3)
 
     # roofline of the dominant kernel (the fused push), CUDA events on its stream
     peak, peak_kind = _peaks()
@@ -309,12 +354,8 @@ def run_ours(a, rank, world, local_rank):
             ps_e2e += gd1["particle_steps"] - gd0["particle_steps"]
         barrier()
         te = time.perf_counter() - t0
-        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-        pe = torch.tensor([float(ps_e2e)], dtype=torch.float64, device="cuda")
-        if dist:
-            tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-            tdist.all_reduce(pe, op=tdist.ReduceOp.SUM)
-        e2e = {"value": float(pe.item()) / float(tt.item()), "unit": UNIT,
+        te_max, ps_e2e_all = reduce_over_ranks([te, ps_e2e], ["max", "sum"], "cuda")
+        e2e = {"value": ps_e2e_all / te_max, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "path": "pic_set_state from pinned host arrays + pic_step(one RF cycle) + "
                        "pic_diagnostics read back, per step"}
@@ -329,6 +370,25 @@ def run_ours(a, rank, world, local_rank):
         except Exception as ex:  # the baseline is reported, not required
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"failed: {ex}"}
+
+    variants = None
+    if rank == 0 and world == 1 and not a.no_variants:
+        sim.close()
+        sim = None
+        variants = {}
+        try:
+            d64 = _workload(a.workload, fp64=True, scale=a.scale)
+            variants["fp64"] = measure_variant(f"{a.workload} in FP64: {_describe(d64)}", [d64], 200, 400)
+        except Exception as ex:
+            variants["fp64"] = {"error": str(ex)}
+        try:
+            sweep = inputs.cfg3_sweep()
+            variants["batched"] = measure_variant(
+                "cfg3: 64 discharges (100-600 V x 5-50 Pa, 2.5-4 cm, 256/512 cells, 1e4-2e6 superparticles "
+                f"each, {sum(sum(x.n_init) for x in sweep):.3g} total), FP32 mixed, one launch per kernel "
+                "for all discharges", sweep, 200, sweep[0].steps_per_cycle)
+        except Exception as ex:
+            variants["batched"] = {"error": str(ex)}
 
     if rank == 0:
         line = {
@@ -353,9 +413,11 @@ def run_ours(a, rank, world, local_rank):
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": tm["launches"],
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
 
 
 def main():
