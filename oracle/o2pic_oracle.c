@@ -19,7 +19,7 @@
  * Gas-target channels use the null-collision test, candidate probability
  * 1 - exp(-nu_max dt), then a channel walk with the running sum of
  * n_j sigma_j(E) u; particle-target reactions (13), (14), (19) use Eq. 1 with
- * tau = n1 dt in a per-cell pass after the sort.  For electrons nu_max may
+ * tau = n1 dt in a per-cell pass after the sort, thinned by a bound on P.  For electrons nu_max may
  * depend on the electron's lab energy (bins of a quarter octave): the
  * null-collision method gives the same collision statistics for any bound
  * that is at least the true frequency.
@@ -139,7 +139,8 @@ void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
     out[3] = c3;
 }
 
-/* stream: 0 null test, 1 gas collision, 2 pair reaction, 3 initial load */
+/* stream: 0 null test, 1 gas collision, 2 pair reaction, 3 initial load,
+ * 4 pair candidates of a cell */
 static void rng(const orc_sim *s, int sp, int stream, int sub, uint32_t draw,
                 long long step, uint32_t index, uint32_t out[4])
 {
@@ -836,6 +837,30 @@ static void sort_species(orc_sim *s, int sp, long long *start)
 }
 
 /* per-cell particle-target pass of one reaction (Eq. 1 with tau = n1 dt) */
+/* Bound on sigma(E) u over a particle-target table for relative speeds up
+ * to u_cap (SI): on a segment [E_k, E_k+1] sigma is at most the larger end
+ * value and u at most the speed of E_k+1; below the grid sigma is the first
+ * value; above it sigma is the last value, so sigma u <= sigma_last u_cap;
+ * with a relative margin of 1e-3. */
+static double pair_bound(const table_t *t, double mu, double u_cap)
+{
+    double g = t->s[0] * sqrt(2.0 * t->E[0] * QE / mu);
+    for (int k = 0; k + 1 < t->n; ++k) {
+        double sk = t->s[k] > t->s[k + 1] ? t->s[k] : t->s[k + 1];
+        double gk = sk * sqrt(2.0 * t->E[k + 1] * QE / mu);
+        if (gk > g) g = gk;
+    }
+    double tail = t->s[t->n - 1] * u_cap;
+    return 1.001 * (g > tail ? g : tail);
+}
+
+/* Particle-target reaction in one cell (Eq. 1), by thinning: B bounds
+ * P = n_T sigma u tau for every pair below the cap speed (the relative speed
+ * of the projectile's cap energy), candidates are drawn among the cell's
+ * projectiles with probability B each (geometric gaps, a random stream per
+ * cell), and a candidate reacts with probability P/B, so every projectile
+ * reacts with probability P; with B >= 1 every projectile is a candidate and
+ * reacts with probability min(P, 1). */
 static void pair_channel(orc_sim *s, int reaction, int c, long long **start, blist_t *bl)
 {
     int tab = s->pair_tab[reaction];
@@ -853,7 +878,23 @@ static void pair_channel(orc_sim *s, int reaction, int c, long long **start, bli
     double nT = (double)live * s->c.weight / s->dx;
     double tau = s->c.n1 * s->c.dt;
     double mp = MASS[ps], mt = MASS[ts];
-    for (long long i = p0; i < p1; ++i) {
+    double mu = reduced_mass(mp, mt);
+    double u_cap = sqrt(2.0 * s->c.ecap_eV[ps] * QE / mu);
+    double B = nT * pair_bound(t, mu, u_cap) * tau;
+    double lq = B < 1.0 ? log1p(-B) : 0.0;
+    long long i = p0 - 1;
+    uint32_t draw = 0;
+    for (;;) {
+        if (B >= 1.0) {
+            ++i;
+        } else {
+            uint32_t g[4];
+            rng(s, ps, 4, reaction, draw++, s->step, (uint32_t)c, g);
+            double G = floor(log(unif(g[0])) / lq);
+            if (G >= (double)(p1 - i)) break;
+            i += 1 + (long long)G;
+        }
+        if (i >= p1) break;
         if (!P->alive[i]) continue;
         uint32_t d0[4];
         rng(s, ps, 2, reaction, 0, s->step, (uint32_t)i, d0);
@@ -870,11 +911,12 @@ static void pair_channel(orc_sim *s, int reaction, int c, long long **start, bli
         double u = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
         double E = 0.5 * reduced_mass(mp, mt) * u * u / QE;
         double P_ = nT * sigma_of(t, E) * u * tau;
-        if (P_ > 1.0) {
+        double Bc = B < 1.0 ? B : 1.0;
+        if (P_ > Bc) {  /* above the cap speed, or beyond 1 */
             s->viol[1]++;
-            P_ = 1.0;
+            P_ = Bc;
         }
-        if (!(unif(d0[1]) < P_)) continue;
+        if (!(unif(d0[1]) * Bc < P_)) continue;
         s->events[reaction]++;
         if (reaction == 13 || reaction == 14) {
             P->alive[i] = 0;

@@ -534,13 +534,16 @@ def test_sort_is_stable_by_cell_and_drops_dead():
 
 # ----------------------------------------------------------- pair pass
 
-def test_neutralisation_rate_matches_eq1():
-    # all O- and O2+ in one cell, zero net charge, one pass of (14)
+@pytest.mark.parametrize("weight", [2e14, 1e13])
+def test_neutralisation_rate_matches_eq1(weight):
+    # all O- and O2+ in one cell, zero net charge, one pass of (14); at the
+    # smaller weight the bound B on P is below 1, so candidates are thinned
+    # (probability B each) and accepted with P/B: the rate is Eq. 1's either way
     L, N = 0.064, 64
     dx = L / N
     n = 8000
     dt = 1e-9
-    d = _disch(L=L, n_cells=N, n1=1, dt_override=dt, weight_override=2e14)
+    d = _disch(L=L, n_cells=N, n1=1, dt_override=dt, weight_override=weight)
     o = oracle.Oracle(d, [_table(14)])
     rs = np.random.default_rng(31)
     x = rs.uniform(10 * dx + 0.3 * dx, 10 * dx + 0.7 * dx, n)
@@ -560,7 +563,7 @@ def test_neutralisation_rate_matches_eq1():
     sig = 0.8 * (1 + 2.85 / E) * 1e-18
     p = np.minimum(nT * sig * u * dt, 1.0).mean()
     expect = n * p
-    assert 500 < expect < 4000
+    assert 40 < expect < 4000
     assert abs(ev - expect) < 4 * math.sqrt(expect) + 0.02 * expect
 
 
