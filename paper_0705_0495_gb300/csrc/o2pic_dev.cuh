@@ -113,6 +113,7 @@ struct PairC {          // particle-target reaction of one discharge
     // bound on sigma(E) u_n over the table: sigma u_n <= max(bnd_g, bnd_s * u_n)
     // (u_n relative speed in cells per step; margins included)
     double bnd_g, bnd_s;
+    double ucap_n;      // relative speed (cells per step) of the projectile's cap energy
     float Ek_f, mfrac_f, Mfrac_f, dloss_f, coef_f, pad_f;
     float bnd_g_f, bnd_s_f;
 };

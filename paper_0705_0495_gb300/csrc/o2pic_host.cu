@@ -583,6 +583,7 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
             P.bnd_g = g * 1.001;
             P.bnd_s = t.S[n - 1] * 1.001;
         }
+        P.ucap_n = std::sqrt(2.0 * q.ecap_eV[P.proj] * QE / mu) * tdx;
         P.bnd_g_f = (float)(P.bnd_g * 1.0001);
         P.bnd_s_f = (float)(P.bnd_s * 1.0001);
     }

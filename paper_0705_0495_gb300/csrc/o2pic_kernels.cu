@@ -691,63 +691,51 @@ constexpr int NO_FLAG = 0x7F7F7F7F;  // larger than any slot index
 // P > 1 is recorded, and the sequential pass of that cell restarts there.
 // Before it, every projectile's outcome is exactly that of the sequential
 // pass, because no earlier projectile of the cell changed anything.
+// Particle-target reaction k by thinning (Eq. 1): B bounds P = n sigma u tau
+// for every pair below the projectile's cap speed (the same definition as the
+// oracle's), the cell's candidates are its projectiles at geometric gaps of
+// rate B (a random stream per cell), and a candidate reacts with probability
+// P / B; with B >= 1 every projectile is a candidate.
+__device__ __forceinline__ double pair_bound_B(const PairC &pc, int liveT)
+{
+    return (double)liveT * pc.coef * fmax(pc.bnd_g, pc.bnd_s * pc.ucap_n);
+}
+// gap before the next candidate: floor(ln U / ln(1 - B)) for the draw-th word
+// of the cell's stream (B < 1, lq = ln(1 - B)), at most 2^30
+__device__ __forceinline__ long long pair_gap(const Disc &Dd, int ps, int rx, unsigned draw,
+                                              unsigned long long step, int c, double lq)
+{
+    const uint4 g = rng_block(Dd.seed, Dd.discharge, ps, 4, rx, draw, step, (unsigned)c);
+    const double G = floor(log(unif<double>(g.x)) / lq);
+    return G < 1073741824.0 ? (long long)G : 1073741824LL;
+}
+
+// One thread per cell: does reaction k have a candidate in it?
 template <typename Real>
 __global__ void __launch_bounds__(256)
-k_pair_eval(WsPtrs W, Pools<Real> P, int par, int k, const int *tab)
+k_pair_eval(WsPtrs W, Pools<Real> P, int par, int k)
 {
-    const int d = tab[2 * blockIdx.x], tile = tab[2 * blockIdx.x + 1];
+    const int gw = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gw >= W.total_cells) return;
+    const int d = W.cell_disc[gw];
     const Disc &Dd = W.disc[d];
     const PairC &pc = Dd.pair[k];
     if (pc.table < 0) return;
-    const int ps = pc.proj, pt = pc.targ;
-    const int i = tile * 256 + threadIdx.x;
-    if (i >= W.cnt[d * NSP + ps].n) return;
-    const int cur = W.ctl->cur;
-    const int pbp = Dd.pbase[ps], pbt = Dd.pbase[pt];
-    const int c = P.cell[cur][pbp + i];
-    if (c < 0) return;
-    const int N = Dd.N;
+    const int ps = pc.proj, pt = pc.targ, N = Dd.N, c = gw - Dd.ccell_base;
     const int *cs = W.cell_start + Dd.cs_base;
-    const int t0 = cs[pt * (N + 2) + c], t1 = cs[pt * (N + 2) + c + 1];
-    const int range = t1 - t0;
+    const int p0 = cs[ps * (N + 2) + c], p1 = cs[ps * (N + 2) + c + 1];
+    if (p1 <= p0) return;
+    const int range = cs[pt * (N + 2) + c + 1] - cs[pt * (N + 2) + c];
     if (range <= 0) return;
-    const int liveT = range - W.pair_kills[(size_t)(Dd.ccell_base + c) * NSP + pt];
+    const int liveT = range - W.pair_kills[(size_t)gw * NSP + pt];
     if (liveT <= 0) return;
-    const int rx = k == 0 ? 13 : (k == 1 ? 14 : 19);
-    const unsigned long long step = W.ctl->step[par];
-    const uint4 d0 = rng_block(Dd.seed, Dd.discharge, ps, 2, rx, 0, step, (unsigned)i);
-    {
-        // Exact skip: P = n sigma u tau is at most liveT * coef *
-        // max(bnd_g, bnd_s * u) with u below the sum of the two species'
-        // largest speeds at the sort, so a draw at or above that bound
-        // rejects whatever partner is drawn; the partner is not read.
-        const float vP = sqrtf(__uint_as_float(W.vmax2[d * NSP + ps]));
-        const float vT = sqrtf(__uint_as_float(W.vmax2[d * NSP + pt]));
-        const Real ub = Real((vP + vT) * 1.00001f);
-        const Real bg = pick<Real>(pc.bnd_g, pc.bnd_g_f), bs = pick<Real>(pc.bnd_s, pc.bnd_s_f);
-        const Real M = bg > bs * ub ? bg : bs * ub;
-        const Real Bd = Real(liveT) * pick<Real>(pc.coef, pc.coef_f) * M;
-        if (Bd < Real(1) && !(unif<Real>(d0.y) < Bd)) return;
+    const double B = pair_bound_B(pc, liveT);
+    long long first = 0;
+    if (B < 1.0) {
+        const int rx = k == 0 ? 13 : (k == 1 ? 14 : 19);
+        first = pair_gap(Dd, ps, rx, 0u, W.ctl->step[par], c, log1p(-B));
     }
-    int j = t0 + (int)__umulhi(d0.x, (unsigned)range);
-    int walked = 0;
-    const int *cellA = P.cell[cur];
-    while (cellA[pbt + j] < 0 && walked < range) {
-        j = (j + 1 < t1) ? j + 1 : t0;
-        ++walked;
-    }
-    bool flag = cellA[pbt + j] < 0;
-    if (!flag) {
-        const Real g0 = P.vx[cur][pbp + i] - P.vx[cur][pbt + j];
-        const Real g1 = P.vy[cur][pbp + i] - P.vy[cur][pbt + j];
-        const Real g2 = P.vz[cur][pbp + i] - P.vz[cur][pbt + j];
-        const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
-        const Real u = sqrt(u2);
-        const Real E = pick<Real>(pc.Ek, pc.Ek_f) * u2;
-        const Real Pc = Real(liveT) * pick<Real>(pc.coef, pc.coef_f) * pair_sigma<Real>(W, W.tables[pc.table], E) * u;
-        flag = Pc > Real(1) || unif<Real>(d0.y) < Pc;
-    }
-    if (flag) atomicMin(&W.pair_first[Dd.ccell_base + c], i);
+    if (first < (long long)(p1 - p0)) W.pair_first[gw] = p0 + (int)first;
 }
 
 // Sequential pass of reaction k over one flagged cell (one warp), from its
@@ -779,18 +767,36 @@ k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
     const int rx = k == 0 ? 13 : (k == 1 ? 14 : 19);
     const PairC &pc = Dd.pair[k];
     const int ps = pc.proj, pt = pc.targ;
-    const int p1 = cs[ps * (N + 2) + c + 1];
+    const int p0 = cs[ps * (N + 2) + c], p1 = cs[ps * (N + 2) + c + 1];
     const int t0 = cs[pt * (N + 2) + c], t1 = cs[pt * (N + 2) + c + 1];
     const int range = t1 - t0;
     const int liveT = range - kills[pt];
     const TableDesc &T = W.tables[pc.table];
     const Real coefP = Real(liveT) * pick<Real>(pc.coef, pc.coef_f);
     const int pbp = Dd.pbase[ps], pbt = Dd.pbase[pt];
+    // candidates of the thinning, 32 at a time: each lane draws its gap, a
+    // warp scan of (1 + gap) places them (the gaps do not depend on events)
+    const double B = pair_bound_B(pc, liveT);
+    const bool thin = B < 1.0;
+    const double lq = thin ? log1p(-B) : 0.0;
+    const Real Bc = thin ? Real(B) : Real(1);
+    long long pos = p0 - 1;  // last candidate placed (warp-uniform)
+    unsigned draw = 0;
     bool stop = false;
     unsigned nviol = 0;
     int nkp = 0, nkt = 0;
-    for (int b0 = first; b0 < p1 && !stop; b0 += 32) {
-        const int i = b0 + lane;
+    (void)first;
+    while (!stop && pos + 1 < p1) {
+        long long inc = 1 + (thin ? pair_gap(Dd, ps, rx, draw + (unsigned)lane, step, c, lq) : 0LL);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long x = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += x;
+        }
+        const long long ipos = pos + inc;
+        const int i = ipos < p1 ? (int)ipos : p1;  // p1: no candidate for this lane
+        pos = __shfl_sync(0xffffffffu, ipos, 31);
+        draw += 32;
         int from = 0;
         for (;;) {
             bool ev = false, ex = false, viol = false;
@@ -814,11 +820,11 @@ k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
                     const Real u = sqrt(u2);
                     const Real E = pick<Real>(pc.Ek, pc.Ek_f) * u2;
                     Real Pc = coefP * pair_sigma<Real>(W, T, E) * u;
-                    if (Pc > Real(1)) {
+                    if (Pc > Bc) {  // above the cap speed, or beyond 1
                         viol = true;
-                        Pc = Real(1);
+                        Pc = Bc;
                     }
-                    ev = unif<Real>(d0.y) < Pc;
+                    ev = unif<Real>(d0.y) * Bc < Pc;
                 }
             }
             const unsigned m = __ballot_sync(0xffffffffu, ev || ex);
@@ -1078,18 +1084,15 @@ cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par, 
                         cudaStream_t st)
 {
     const int fix_blocks = (W.total_cells * 32 + 255) / 256;
-    const int ps_of[3] = {0, 1, 0};  // projectile species of (13), (14), (19)
+    const int eval_blocks = (W.total_cells + 255) / 256;
     for (int k = 0; k < 3; ++k) {
-        const int ps = ps_of[k];
         if (fp64) {
             const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
-            if (L.pair_blocks_sp[ps] > 0)
-                k_pair_eval<double><<<L.pair_blocks_sp[ps], 256, 0, st>>>(W, P, par, k, L.pair_tab_sp[ps]);
+            k_pair_eval<double><<<eval_blocks, 256, 0, st>>>(W, P, par, k);
             k_pair_fix<double><<<fix_blocks, 256, 0, st>>>(W, P, par, k);
         } else {
             const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
-            if (L.pair_blocks_sp[ps] > 0)
-                k_pair_eval<float><<<L.pair_blocks_sp[ps], 256, 0, st>>>(W, P, par, k, L.pair_tab_sp[ps]);
+            k_pair_eval<float><<<eval_blocks, 256, 0, st>>>(W, P, par, k);
             k_pair_fix<float><<<fix_blocks, 256, 0, st>>>(W, P, par, k);
         }
     }
