@@ -308,6 +308,15 @@ __device__ __forceinline__ void iso_dir(Real r1, Real r2, Real n[3])
     n[2] = cx;
 }
 
+// Kernels of a time step are launched with programmatic dependent launch:
+// the next kernel may be scheduled while the previous one drains, and waits
+// here, before it reads anything, until that one has completed (a no-op
+// when launched without the attribute).
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ void set_status(Ctl *ctl, unsigned bits)
 {
     atomicOr(&ctl->status, bits);

@@ -125,6 +125,7 @@ template <typename Real>
 __global__ void __launch_bounds__(FIELD_THREADS)
 k_field(WsPtrs W, int par, int diag, int mode)
 {
+    pdl_wait();
     extern __shared__ __align__(16) double fsm[];
     __shared__ double warp_tot[FIELD_THREADS / 32];
     __shared__ double s_rho0, s_rhoN, s_D0;
@@ -380,6 +381,7 @@ template <typename Real>
 __global__ void __launch_bounds__(SORT_WARPS * 32)
 k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
 {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned ssm[];
     int ds, bi;
     sort_block(tab, ds, bi);
@@ -429,6 +431,7 @@ k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
 __global__ void __launch_bounds__(256)
 k_sort_colscan(WsPtrs W, const int *warp_base)
 {
+    pdl_wait();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     // warp -> (ds, bucket): the buckets of all (d, s) laid end to end
@@ -467,6 +470,7 @@ k_sort_colscan(WsPtrs W, const int *warp_base)
 __global__ void __launch_bounds__(512)
 k_sort_cellscan(WsPtrs W)
 {
+    pdl_wait();
     extern __shared__ __align__(16) int isx[];
     __shared__ int wsum[32];
     const int ds = blockIdx.x;
@@ -495,6 +499,7 @@ template <typename Real>
 __global__ void __launch_bounds__(SORT_WARPS * 32)
 k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
 {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned short hsm[];
     int ds, bi;
     sort_block(tab, ds, bi);
@@ -626,6 +631,7 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
 
 __global__ void k_sort_finish(WsPtrs W)
 {
+    pdl_wait();
     for (int ds = threadIdx.x; ds < W.D * NSP; ds += blockDim.x) W.cnt[ds].n = W.sort_live[ds];
     __syncthreads();
     if (threadIdx.x == 0) W.ctl->cur ^= 1;
@@ -715,6 +721,7 @@ template <typename Real>
 __global__ void __launch_bounds__(256)
 k_pair_eval(WsPtrs W, Pools<Real> P, int par, int k)
 {
+    pdl_wait();
     const int gw = blockIdx.x * blockDim.x + threadIdx.x;
     if (gw >= W.total_cells) return;
     const int d = W.cell_disc[gw];
@@ -746,6 +753,7 @@ template <typename Real>
 __global__ void __launch_bounds__(256)
 k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
 {
+    pdl_wait();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (gw >= W.total_cells) return;
@@ -915,6 +923,7 @@ template <typename Real>
 __global__ void __launch_bounds__(256)
 k_pair_append(WsPtrs W, Pools<Real> P)
 {
+    pdl_wait();
     extern __shared__ __align__(16) int pre[];
     __shared__ int wsum[32];
     const int d = blockIdx.x;
@@ -1049,9 +1058,9 @@ cudaError_t launch_field(bool fp64, bool diag, int mode, const WsPtrs &W, int pa
                          cudaStream_t st)
 {
     if (fp64)
-        k_field<double><<<W.D, FIELD_THREADS, L.field_smem, st>>>(W, par, diag ? 1 : 0, mode);
+        launch_k(k_field<double>, W.D, FIELD_THREADS, L.field_smem, st, W, par, diag ? 1 : 0, mode);
     else
-        k_field<float><<<W.D, FIELD_THREADS, L.field_smem, st>>>(W, par, diag ? 1 : 0, mode);
+        launch_k(k_field<float>, W.D, FIELD_THREADS, L.field_smem, st, W, par, diag ? 1 : 0, mode);
     return cudaGetLastError();
 }
 
@@ -1065,18 +1074,18 @@ cudaError_t launch_sort(bool fp64, const WsPtrs &W, const void *pools, const int
     const int cs_blocks = (L.sort_col_warps * 32 + 255) / 256;
     if (fp64) {
         const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
-        k_sort_count<double><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
-        k_sort_colscan<<<cs_blocks, 256, 0, st>>>(W, L.sort_warp_base);
-        k_sort_cellscan<<<W.D * NSP, 512, scan_smem, st>>>(W);
-        k_sort_scatter<double><<<L.sort_blocks, SORT_WARPS * 32, L.scatter_smem, st>>>(W, P, tab);
+        launch_k(k_sort_count<double>, L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st, W, P, tab);
+        launch_k(k_sort_colscan, cs_blocks, 256, 0, st, W, L.sort_warp_base);
+        launch_k(k_sort_cellscan, W.D * NSP, 512, scan_smem, st, W);
+        launch_k(k_sort_scatter<double>, L.sort_blocks, SORT_WARPS * 32, L.scatter_smem, st, W, P, tab);
     } else {
         const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
-        k_sort_count<float><<<L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st>>>(W, P, tab);
-        k_sort_colscan<<<cs_blocks, 256, 0, st>>>(W, L.sort_warp_base);
-        k_sort_cellscan<<<W.D * NSP, 512, scan_smem, st>>>(W);
-        k_sort_scatter<float><<<L.sort_blocks, SORT_WARPS * 32, L.scatter_smem, st>>>(W, P, tab);
+        launch_k(k_sort_count<float>, L.sort_blocks, SORT_WARPS * 32, L.sort_smem, st, W, P, tab);
+        launch_k(k_sort_colscan, cs_blocks, 256, 0, st, W, L.sort_warp_base);
+        launch_k(k_sort_cellscan, W.D * NSP, 512, scan_smem, st, W);
+        launch_k(k_sort_scatter<float>, L.sort_blocks, SORT_WARPS * 32, L.scatter_smem, st, W, P, tab);
     }
-    k_sort_finish<<<1, 256, 0, st>>>(W);
+    launch_k(k_sort_finish, 1, 256, 0, st, W);
     return cudaGetLastError();
 }
 
@@ -1088,20 +1097,20 @@ cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par, 
     for (int k = 0; k < 3; ++k) {
         if (fp64) {
             const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
-            k_pair_eval<double><<<eval_blocks, 256, 0, st>>>(W, P, par, k);
-            k_pair_fix<double><<<fix_blocks, 256, 0, st>>>(W, P, par, k);
+            launch_k(k_pair_eval<double>, eval_blocks, 256, 0, st, W, P, par, k);
+            launch_k(k_pair_fix<double>, fix_blocks, 256, 0, st, W, P, par, k);
         } else {
             const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
-            k_pair_eval<float><<<eval_blocks, 256, 0, st>>>(W, P, par, k);
-            k_pair_fix<float><<<fix_blocks, 256, 0, st>>>(W, P, par, k);
+            launch_k(k_pair_eval<float>, eval_blocks, 256, 0, st, W, P, par, k);
+            launch_k(k_pair_fix<float>, fix_blocks, 256, 0, st, W, P, par, k);
         }
     }
     if (fp64)
-        k_pair_append<double><<<W.D, 256, sizeof(int) * (L.maxN + 1), st>>>(
-            W, *static_cast<const Pools<double> *>(pools));
+        launch_k(k_pair_append<double>, W.D, 256, sizeof(int) * (L.maxN + 1), st, W,
+                 *static_cast<const Pools<double> *>(pools));
     else
-        k_pair_append<float><<<W.D, 256, sizeof(int) * (L.maxN + 1), st>>>(
-            W, *static_cast<const Pools<float> *>(pools));
+        launch_k(k_pair_append<float>, W.D, 256, sizeof(int) * (L.maxN + 1), st, W,
+                 *static_cast<const Pools<float> *>(pools));
     return cudaGetLastError();
 }
 

@@ -6,6 +6,28 @@
 
 namespace o2 {
 
+// Launch of a time-step kernel with programmatic stream serialization (the
+// kernel itself waits for its predecessor with pdl_wait()).
+#ifndef O2_PDL
+#define O2_PDL 1
+#endif
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args &&...args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = O2_PDL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 struct LaunchCfg {
     int push_blocks;      // persistent grid of the push
     int collide_blocks;   // grid of the collision kernel (loops over the candidates)

@@ -485,6 +485,7 @@ template <typename Real, bool DIAG>
 __global__ void __launch_bounds__(PUSH_THREADS, PushOcc<Real>::blocks)
 k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
 {
+    pdl_wait();
     using Acc = typename AccT<Real>::T;
     constexpr int NW = PUSH_THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -777,10 +778,14 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
 // counts are summed per block for the discharge of the block's first
 // candidate (the list holds runs of one discharge), others go straight to
 // the global counters.
+#ifndef O2_COLLIDE_MIN_BLOCKS
+#define O2_COLLIDE_MIN_BLOCKS 1
+#endif
 template <typename Real>
-__global__ void __launch_bounds__(COLLIDE_THREADS)
+__global__ void __launch_bounds__(COLLIDE_THREADS, O2_COLLIDE_MIN_BLOCKS)
 k_collide(WsPtrs W, Pools<Real> P, int par)
 {
+    pdl_wait();
     using Acc = typename AccT<Real>::T;
     __shared__ unsigned s_ev[C_NCOUNT];
     Ctl *ctl = W.ctl;
@@ -859,6 +864,7 @@ template <typename Real>
 __global__ void __launch_bounds__(BIRTHS_THREADS)
 k_births(WsPtrs W, Pools<Real> P, int par)
 {
+    pdl_wait();
     using Acc = typename AccT<Real>::T;
     __shared__ int wsum[NSP][BIRTHS_THREADS / 32];
     __shared__ int s_blk, s_excl[NSP], s_tot[NSP];
@@ -1055,15 +1061,15 @@ cudaError_t launch_push(bool fp64, bool diag, const WsPtrs &W, const void *pools
     if (fp64) {
         const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
         if (diag)
-            k_push<double, true><<<L.push_blocks, PUSH_THREADS, sm, st>>>(W, P, par, L.maxN, em, fm);
+            launch_k(k_push<double, true>, L.push_blocks, PUSH_THREADS, sm, st, W, P, par, L.maxN, em, fm);
         else
-            k_push<double, false><<<L.push_blocks, PUSH_THREADS, sm, st>>>(W, P, par, L.maxN, em, fm);
+            launch_k(k_push<double, false>, L.push_blocks, PUSH_THREADS, sm, st, W, P, par, L.maxN, em, fm);
     } else {
         const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
         if (diag)
-            k_push<float, true><<<L.push_blocks, PUSH_THREADS, sm, st>>>(W, P, par, L.maxN, em, fm);
+            launch_k(k_push<float, true>, L.push_blocks, PUSH_THREADS, sm, st, W, P, par, L.maxN, em, fm);
         else
-            k_push<float, false><<<L.push_blocks, PUSH_THREADS, sm, st>>>(W, P, par, L.maxN, em, fm);
+            launch_k(k_push<float, false>, L.push_blocks, PUSH_THREADS, sm, st, W, P, par, L.maxN, em, fm);
     }
     return cudaGetLastError();
 }
@@ -1071,9 +1077,9 @@ cudaError_t launch_push(bool fp64, bool diag, const WsPtrs &W, const void *pools
 cudaError_t launch_collide(bool fp64, const WsPtrs &W, const void *pools, int par, int blocks, cudaStream_t st)
 {
     if (fp64)
-        k_collide<double><<<blocks, COLLIDE_THREADS, 0, st>>>(W, *static_cast<const Pools<double> *>(pools), par);
+        launch_k(k_collide<double>, blocks, COLLIDE_THREADS, 0, st, W, *static_cast<const Pools<double> *>(pools), par);
     else
-        k_collide<float><<<blocks, COLLIDE_THREADS, 0, st>>>(W, *static_cast<const Pools<float> *>(pools), par);
+        launch_k(k_collide<float>, blocks, COLLIDE_THREADS, 0, st, W, *static_cast<const Pools<float> *>(pools), par);
     return cudaGetLastError();
 }
 
@@ -1081,9 +1087,9 @@ cudaError_t launch_births(bool fp64, const WsPtrs &W, const void *pools, int par
                           cudaStream_t st)
 {
     if (fp64)
-        k_births<double><<<max_blocks, BIRTHS_THREADS, 0, st>>>(W, *static_cast<const Pools<double> *>(pools), par);
+        launch_k(k_births<double>, max_blocks, BIRTHS_THREADS, 0, st, W, *static_cast<const Pools<double> *>(pools), par);
     else
-        k_births<float><<<max_blocks, BIRTHS_THREADS, 0, st>>>(W, *static_cast<const Pools<float> *>(pools), par);
+        launch_k(k_births<float>, max_blocks, BIRTHS_THREADS, 0, st, W, *static_cast<const Pools<float> *>(pools), par);
     return cudaGetLastError();
 }
 
