@@ -47,7 +47,8 @@ class _Cfg(C.Structure):
         ("n_cells", C.c_int), ("n1", C.c_int), ("sort_interval", C.c_int),
         ("diag_every", C.c_int), ("eedf_bins", C.c_int), ("iedf_bins", C.c_int),
         ("fm_bins", C.c_int), ("fm_xbins", C.c_int), ("discharge", C.c_int),
-        ("cx_isotropic", C.c_int), ("numax_bins", C.c_int),
+        ("cx_isotropic", C.c_int), ("numax_bins", C.c_int), ("n2", C.c_int),
+        ("coulomb_log", C.c_double),
     ]
 
 
@@ -86,6 +87,16 @@ def lib():
         l.orc_set.argtypes = [C.c_void_p, C.c_int, C.c_longlong, dp, dp, dp, dp, ip]
         l.orc_numax.restype = C.c_double
         l.orc_numax.argtypes = [C.c_void_p, C.c_int]
+        l.orc_coulomb_pair.restype = None
+        l.orc_coulomb_pair.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double,
+                                       C.c_double, C.c_double, C.c_double]
+        l.orc_coulomb_pairing.restype = C.c_longlong
+        l.orc_coulomb_pairing.argtypes = [C.c_void_p, C.c_int, C.c_longlong, C.c_longlong,
+                                          C.c_uint32, C.c_void_p, C.c_void_p]
+        l.orc_coulomb_cell.restype = None
+        l.orc_coulomb_cell.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_longlong, C.c_double, C.c_double, C.c_longlong,
+                                       C.c_uint32]
         l.orc_numax_bin.restype = C.c_double
         l.orc_numax_bin.argtypes = [C.c_void_p, C.c_int]
         l.orc_bin_of.restype = C.c_int
@@ -159,6 +170,8 @@ class Oracle:
         cfg.discharge = discharge
         cfg.cx_isotropic = int(d.cx_isotropic)
         cfg.numax_bins = int(d.numax_bins)
+        cfg.n2 = int(d.n2)
+        cfg.coulomb_log = float(d.coulomb_log)
         self._keep = []
         xs = (_Xs * len(tables))()
         for i, t in enumerate(tables):
@@ -197,6 +210,26 @@ class Oracle:
 
     def numax(self, s):
         return lib().orc_numax(self.h, s)
+
+    def coulomb_pair(self, s, v1, v2, n, tau, xi, r):
+        a = np.ascontiguousarray(v1, dtype=np.float64).copy()
+        b = np.ascontiguousarray(v2, dtype=np.float64).copy()
+        lib().orc_coulomb_pair(self.h, s, _dp(a), _dp(b), float(n), float(tau), float(xi), float(r))
+        return a, b
+
+    def coulomb_cell(self, s, vx, vy, vz, dens, tau, step, cell):
+        """the Coulomb collisions of one cell's particles; returns new copies"""
+        a = [np.ascontiguousarray(v, dtype=np.float64).copy() for v in (vx, vy, vz)]
+        lib().orc_coulomb_cell(self.h, s, _dp(a[0]), _dp(a[1]), _dp(a[2]), len(a[0]),
+                               float(dens), float(tau), int(step), int(cell))
+        return a
+
+    def coulomb_pairing(self, s, n, step, cell):
+        """partners of each Coulomb collision of a cell of n particles"""
+        pi = np.zeros(n // 2 + 2, dtype=np.int64)
+        pj = np.zeros(n // 2 + 2, dtype=np.int64)
+        k = lib().orc_coulomb_pairing(self.h, s, int(n), int(step), int(cell), _dp(pi), _dp(pj))
+        return pi[:k], pj[:k]
 
     def numax_bin(self, b):
         return lib().orc_numax_bin(self.h, b)

@@ -16,6 +16,8 @@
  *            inelastic speed rule (Eq. 5), charge exchange, reactions
  *            (13)-(19) with the rules of Sec. III C, associative detachment
  *            with target density C n_O2.
+ *   Sec. III A intra-species Coulomb collisions (1)-(3), the binary model of
+ *            Takizuka and Abe with the variance of Eq. 2, every n2 steps.
  * Gas-target channels use the null-collision test, candidate probability
  * 1 - exp(-nu_max dt), then a channel walk with the running sum of
  * n_j sigma_j(E) u; particle-target reactions (13), (14), (19) use Eq. 1 with
@@ -36,6 +38,10 @@
  *   (18), (19): inelastic binary collision, split of the heavy partner into
  *            a charged pair sharing its velocity, then an elastic collision
  *            between the two electrons.
+ *   Coulomb: every n2 steps on the sorted cells (before a particle-target
+ *            pass due in the same step), tau = n2 dt, eps0 squared in Eq. 2,
+ *            pairs from a random affine permutation of the cell (a triangle
+ *            for an odd count), ln Gamma a configuration value.
  *   Random numbers: Philox4x32-10 (Salmon et al., SC'11) on a counter made of
  *   (step, index, stream/sub/draw, discharge/species), uniforms (w+0.5)/2^32,
  *   normals by Box-Muller.
@@ -140,7 +146,7 @@ void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
 }
 
 /* stream: 0 null test, 1 gas collision, 2 pair reaction, 3 initial load,
- * 4 pair candidates of a cell */
+ * 4 pair candidates of a cell, 5 Coulomb pairing and scattering of a cell */
 static void rng(const orc_sim *s, int sp, int stream, int sub, uint32_t draw,
                 long long step, uint32_t index, uint32_t out[4])
 {
@@ -937,6 +943,147 @@ static void pair_channel(orc_sim *s, int reaction, int c, long long **start, bli
     }
 }
 
+/* ------------------------------------------------------ Coulomb (1)-(3) */
+
+/* One binary Coulomb collision between two particles of species sp (Sec.
+ * III A, Eq. 2, the binary model of Takizuka and Abe): tan(chi/2) is normal
+ * with variance q^4 n lnGamma tau / (8 pi eps0^2 mu^2 u^3) (eps0 squared: the
+ * printed Eq. 2 is not dimensionless without it), mu = m/2 the reduced mass,
+ * u the relative speed; the azimuth is uniform.  The relative velocity g is
+ * turned by chi about itself (azimuth measured from the plane of g and the z
+ * axis), and each particle takes half of its change (equal masses). */
+void orc_coulomb_pair(const orc_sim *s, int sp, double v1[3], double v2[3],
+                      double n, double tau, double xi, double r)
+{
+    double g[3] = {v1[0] - v2[0], v1[1] - v2[1], v1[2] - v2[2]};
+    double u = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (!(u > 0.0)) return;
+    double q = CHARGE[sp], mu = 0.5 * MASS[sp];
+    double var = q * q * q * q * n * s->c.coulomb_log * tau /
+                 (8.0 * PI * EPS0 * EPS0 * mu * mu * u * u * u);
+    double d = sqrt(var) * xi; /* tan(chi/2) */
+    /* sin(chi) = 2d/(1+d^2), 1 - cos(chi) = 2d^2/(1+d^2); for |d| > 1 the
+     * same in e = 1/d, which stays finite as d grows without bound */
+    double sn, om;
+    if (fabs(d) <= 1.0) {
+        sn = 2.0 * d / (1.0 + d * d);
+        om = 2.0 * d * d / (1.0 + d * d);
+    } else {
+        double e = 1.0 / d;
+        sn = 2.0 * e / (1.0 + e * e);
+        om = 2.0 / (1.0 + e * e);
+    }
+    double phi = 2.0 * PI * r;
+    double cp = cos(phi), spn = sin(phi);
+    double up = sqrt(g[0] * g[0] + g[1] * g[1]);
+    double dg[3];
+    if (up > 0.0) {
+        dg[0] = (g[0] / up) * g[2] * sn * cp - (g[1] / up) * u * sn * spn - g[0] * om;
+        dg[1] = (g[1] / up) * g[2] * sn * cp + (g[0] / up) * u * sn * spn - g[1] * om;
+        dg[2] = -up * sn * cp - g[2] * om;
+    } else {
+        dg[0] = u * sn * cp;
+        dg[1] = u * sn * spn;
+        dg[2] = -g[2] * om;
+    }
+    for (int k = 0; k < 3; ++k) {
+        v1[k] += 0.5 * dg[k];
+        v2[k] -= 0.5 * dg[k];
+    }
+}
+
+static long long gcd_ll(long long a, long long b)
+{
+    while (b) {
+        long long t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+/* random numbers of the k-th collision of a cell's Coulomb pass: stream 5,
+ * draw counter k split over the sub-stream (high bits) and draw fields */
+static void coulomb_rng(const orc_sim *s, int sp, long long step, uint32_t cell,
+                        long long k, uint32_t out[4])
+{
+    rng(s, sp, 5, (int)(k >> 20), (uint32_t)(k & 0xFFFFF), step, cell, out);
+}
+
+static void coulomb_one(const orc_sim *s, int sp, double *vx, double *vy, double *vz,
+                        long long i, long long j, double dens, double tau,
+                        long long step, uint32_t cell, long long k)
+{
+    uint32_t d[4];
+    coulomb_rng(s, sp, step, cell, k, d);
+    double n0, n1;
+    box_muller(d[0], d[1], &n0, &n1);
+    double v1[3] = {vx[i], vy[i], vz[i]}, v2[3] = {vx[j], vy[j], vz[j]};
+    orc_coulomb_pair(s, sp, v1, v2, dens, tau, n0, unif(d[2]));
+    vx[i] = v1[0]; vy[i] = v1[1]; vz[i] = v1[2];
+    vx[j] = v2[0]; vy[j] = v2[1]; vz[j] = v2[2];
+}
+
+/* The Coulomb pairing of a cell of n >= 2 particles: a random affine
+ * permutation k -> (a k + b) mod n, a coprime to n (a and b from draw 0 of the
+ * cell's stream 5), pairs pi(0) with pi(1), pi(2) with pi(3), ...; for odd n
+ * the last three, A, B, C, collide as (A, B), (B, C), (C, A), each with half
+ * the collision time, so that every particle scatters over tau once.  Writes
+ * the collisions in draw order (collision k takes draw 1 + k) and returns
+ * their number; the last three are the triangle's when n is odd. */
+long long orc_coulomb_pairing(const orc_sim *s, int sp, long long n, long long step,
+                              uint32_t cell, long long *pi, long long *pj)
+{
+    if (n < 2) return 0;
+    uint32_t w[4];
+    coulomb_rng(s, sp, step, cell, 0, w);
+    long long a = 1 + (long long)(w[0] % (uint64_t)(n - 1));
+    while (gcd_ll(a, n) != 1) a = (a % (n - 1)) + 1;
+    long long b = (long long)(w[1] % (uint64_t)n);
+    long long pairs = (n % 2 == 0) ? n / 2 : (n - 3) / 2, k = 0;
+    for (long long m = 0; m < pairs; ++m, ++k) {
+        pi[k] = (a * (2 * m) + b) % n;
+        pj[k] = (a * (2 * m + 1) + b) % n;
+    }
+    if (n % 2 == 1)
+        for (int t = 0; t < 3; ++t, ++k) {
+            pi[k] = (a * (n - 3 + t) + b) % n;
+            pj[k] = (a * (n - 3 + (t + 1) % 3) + b) % n;
+        }
+    return k;
+}
+
+/* Coulomb collisions among the n particles (velocities vx, vy, vz) of one
+ * cell, paired as orc_coulomb_pairing */
+void orc_coulomb_cell(const orc_sim *s, int sp, double *vx, double *vy, double *vz,
+                      long long n, double dens, double tau, long long step, uint32_t cell)
+{
+    if (n < 2) return;
+    long long cap = n / 2 + 2;
+    long long *pi = malloc(cap * sizeof(long long)), *pj = malloc(cap * sizeof(long long));
+    long long nc = orc_coulomb_pairing(s, sp, n, step, cell, pi, pj);
+    for (long long k = 0; k < nc; ++k) {
+        double t = (n % 2 == 1 && k >= nc - 3) ? 0.5 * tau : tau;
+        coulomb_one(s, sp, vx, vy, vz, pi[k], pj[k], dens, t, step, cell, 1 + k);
+    }
+    free(pi);
+    free(pj);
+}
+
+/* Coulomb pass of species sp over the sorted cells: the density of Eq. 2 is
+ * the species' own count in the cell times the weight over the cell volume,
+ * the collision time tau = n2 dt */
+static void coulomb_species(orc_sim *s, int sp, const long long *start)
+{
+    parts_t *p = &s->p[sp];
+    double tau = s->c.n2 * s->c.dt;
+    for (int c = 0; c < s->c.n_cells; ++c) {
+        long long p0 = start[c], n = start[c + 1] - start[c];
+        orc_coulomb_cell(s, sp, p->vx + p0, p->vy + p0, p->vz + p0, n,
+                         (double)n * s->c.weight / s->dx, tau, s->step, (uint32_t)c);
+    }
+}
+
 static void step_once(orc_sim *s)
 {
     int N = s->c.n_cells;
@@ -1001,13 +1148,18 @@ static void step_once(orc_sim *s)
 
     long long next = s->step + 1;
     int pair = s->c.n1 > 0 && (next % s->c.n1) == 0;
-    int sort = pair || (s->c.sort_interval > 0 && (next % s->c.sort_interval) == 0);
+    int coul = s->c.n2 > 0 && (next % s->c.n2) == 0;
+    int sort = pair || coul || (s->c.sort_interval > 0 && (next % s->c.sort_interval) == 0);
     if (sort) {
         long long *start[3];
         for (int sp = 0; sp < 3; ++sp) {
             start[sp] = malloc((N + 1) * sizeof(long long));
             sort_species(s, sp, start[sp]);
         }
+        /* Coulomb collisions (1)-(3) every n2 steps on the sorted cells,
+         * then the particle-target reactions every n1 steps */
+        if (coul)
+            for (int sp = 0; sp < 3; ++sp) coulomb_species(s, sp, start[sp]);
         if (pair) {
             for (int c = 0; c < N; ++c) {
                 pair_channel(s, 13, c, start, bl);

@@ -45,6 +45,9 @@ typedef struct {
     int cx_isotropic;    /* reaction (6): 0 = velocity swap, 1 = isotropic */
     int numax_bins;      /* electrons: collision-frequency bounds per quarter
                             octave of lab energy from 2^-6 eV (0 = one bound) */
+    int n2;              /* intra-species Coulomb collisions every n2 steps,
+                            tau = n2 dt (0 = none) */
+    double coulomb_log;  /* ln Gamma of Eq. 2 */
 } orc_cfg;
 
 typedef struct {
@@ -97,6 +100,21 @@ int orc_gas_event(const orc_sim *s, int sp, int reaction, int table,
                   const double v[3], const double V[3], const double r4[4],
                   const double r2[2], double vout[3], int *alive_out,
                   int *prod_sp, double *prod_v, double *Vout);
+/* one intra-species Coulomb collision of species sp (Eq. 2): velocities
+ * v1, v2 [m/s] in place, n the species' density, tau the collision time,
+ * xi a standard normal and r a uniform in (0, 1) */
+void orc_coulomb_pair(const orc_sim *s, int sp, double v1[3], double v2[3],
+                      double n, double tau, double xi, double r);
+/* the Coulomb pairing of a cell of n particles of species sp at step `step`:
+ * writes the partners of every collision in draw order (n/2 + 2 entries
+ * suffice) and returns their number (the last three form the triangle of an
+ * odd n) */
+long long orc_coulomb_pairing(const orc_sim *s, int sp, long long n, long long step,
+                              uint32_t cell, long long *pi, long long *pj);
+/* the Coulomb collisions of one cell's n particles of species sp at step
+ * `step` (velocities in place; pairing and draws as the Coulomb pass) */
+void orc_coulomb_cell(const orc_sim *s, int sp, double *vx, double *vy, double *vz,
+                      long long n, double dens, double tau, long long step, uint32_t cell);
 /* reaction 19 pair event: electron v, O- target vt; returns e1 and e2 */
 void orc_pair19_event(const orc_sim *s, int table, const double v[3],
                       const double vt[3], const double rc[2], const double r2[2],

@@ -168,6 +168,8 @@ class Discharge:
     fm_emax: float = 4.0
     numax_safety: float = 1.05
     numax_bins: int = 64            # electrons: bounds per quarter octave of lab energy
+    n2: int = 0                     # intra-species Coulomb collisions every n2 steps (0: none)
+    coulomb_log: float = 10.0       # ln Gamma of Eq. 2 (not given in the paper)
     cx_isotropic: bool = False
     capacity_factor: float = 1.5
     capacity_extra: int = 4096
