@@ -42,8 +42,10 @@ def _args():
                    help="fraction of the workload's superparticles (same plasma density)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--n2", type=int, default=None,
+                   help="intra-species Coulomb collisions every n2 steps on the workload (default: none)")
     p.add_argument("--no-variants", action="store_true",
-                   help="skip the FP64 and batched-sweep figures reported beside the main one")
+                   help="skip the FP64, batched-sweep and Coulomb figures reported beside the main one")
     return p.parse_args()
 
 
@@ -244,14 +246,22 @@ def measure_variant(name, discharges, warm_steps, timed_steps):
         # the push's duration per launch, in the library's timing mode
         sim.set_timing(True)
         sim.timing(reset=True)
+        sim.kernel_timing("coulomb", reset=True)
         sim.step(min(timed_steps, 200))
         tm = sim.timing()
         peak, _ = _peaks()
         launches = max(1, tm["push_launches"])
         achieved = tm["push_bytes"] / launches / (tm["push_ms"] / 1e3 / launches) / 1e9 if tm["push_ms"] > 0 else 0.0
-        return {"workload": name, "value": ps / (ms / 1e3), "unit": UNIT, "time_steps": timed_steps,
-                "warmup_time_steps": warm_steps, "ms_per_time_step": ms / timed_steps,
-                "push_hbm_frac": achieved / peak}
+        out = {"workload": name, "value": ps / (ms / 1e3), "unit": UNIT, "time_steps": timed_steps,
+               "warmup_time_steps": warm_steps, "ms_per_time_step": ms / timed_steps,
+               "push_hbm_frac": achieved / peak}
+        kc = sim.kernel_timing("coulomb")
+        if kc["launches"] > 0 and kc["ms"] > 0:
+            # the Coulomb pass: device time per launch and its HBM fraction
+            # (vx, vy, vz read and written per particle of the pass)
+            out["coulomb_ms_per_launch"] = kc["ms"] / kc["launches"]
+            out["coulomb_hbm_frac"] = kc["bytes"] / (kc["ms"] / 1e3) / 1e9 / peak
+        return out
     finally:
         sim.close()
 
@@ -272,6 +282,8 @@ def run_ours(a, rank, world, local_rank):
     if dist:
         tdist.barrier()
     d = _workload(a.workload, rank, a.fp64, a.scale)
+    if a.n2 is not None:
+        d.n2 = a.n2
     tabs = inputs.xs_tables()
     sim = o2pic.Simulation([d], tabs)
     spc = d.steps_per_cycle
@@ -410,6 +422,14 @@ def run_ours(a, rank, world, local_rank):
                 "for all discharges", sweep, 200, sweep[0].steps_per_cycle)
         except Exception as ex:
             variants["batched"] = {"error": str(ex)}
+        try:
+            dc = _workload(a.workload, scale=a.scale)
+            dc.n2 = dc.n1 if dc.n1 > 0 else 10
+            variants["coulomb"] = measure_variant(
+                f"{a.workload} with intra-species Coulomb collisions (1)-(3) every {dc.n2} steps "
+                f"(ln Gamma {dc.coulomb_log:g}): {_describe(dc)}", [dc], 200, 400)
+        except Exception as ex:
+            variants["coulomb"] = {"error": str(ex)}
 
     if rank == 0:
         line = {
@@ -420,7 +440,8 @@ def run_ours(a, rank, world, local_rank):
             "config": {
                 "workload": f"{a.workload}: {_describe(d)}",
                 "step": f"one RF cycle = {spc} time steps (sort and pair pass every "
-                        f"{d.sort_interval}/{d.n1} steps, diagnostics every {d.diag_every})",
+                        f"{d.sort_interval}/{d.n1} steps, diagnostics every {d.diag_every}"
+                        + (f", Coulomb collisions every {d.n2}" if d.n2 > 0 else "") + ")",
                 "precision": ("FP64 throughout" if d.fp64 else
                               "FP32 particles, push and collisions; exact fixed-point charge "
                               "accumulation; FP64 Poisson, field and diagnostics"),

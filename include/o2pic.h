@@ -123,6 +123,18 @@ typedef struct {
  *                  (top electron speed of the bin + 7 sqrt(kT/M_O2)), the last
  *                  bin the species' bound; 0 = one bound for all energies
  *   precision      pic_precision; all discharges of one handle share it
+ *   n2             interval of the intra-species Coulomb collisions (1)-(3)
+ *                  (Sec. III A): every n2 steps, after the cell sort of that
+ *                  step and before a particle-target pass due in the same
+ *                  step, the particles of each species in each cell are
+ *                  paired by a random affine permutation (odd counts end in
+ *                  a triangle with half the time) and scattered by the
+ *                  binary model with <tan^2(chi/2)> = q^4 n lnGamma tau /
+ *                  (8 pi eps0^2 mu^2 u^3) (Eq. 2), tau = n2 dt, mu = m/2, n
+ *                  the species' density in the cell; 0 disables them; all
+ *                  discharges of one handle share it.  A cell may hold at most
+ *                  2^29 particles of a species.
+ *   coulomb_log    ln Gamma of Eq. 2 (> 0 when n2 > 0)
  */
 typedef struct {
     double L_m, p_Pa, T_gas_K, U_rf_V, f_rf_Hz, rf_phase, dt_s;
@@ -138,7 +150,9 @@ typedef struct {
     int eedf_bins, iedf_bins, fm_bins, fm_xbins;
     int cx_isotropic;
     int numax_bins;
+    int n2;
     int precision;
+    double coulomb_log;
 } pic_config;
 
 typedef struct pic_handle pic_handle;
@@ -187,7 +201,8 @@ pic_status pic_step(pic_handle *h, long long n_steps);
  *              (including dead slots not yet compacted), 31 steps taken,
  *              32 particle-steps (live particles pushed, summed over steps),
  *              33 null-collision candidates, 34 slots visited by the push,
- *              35-39 reserved (0)
+ *              35 particles through the Coulomb pass (summed over passes),
+ *              36-39 reserved (0)
  *   n_samples  number of diagnostic samples accumulated
  * reset != 0 clears the sums and histograms after copying.
  */
@@ -236,6 +251,17 @@ double pic_numax(const pic_handle *h, int discharge, int species);
 pic_status pic_set_timing(pic_handle *h, int on);
 pic_status pic_timing(pic_handle *h, double *push_ms, long long *push_launches,
                       long long *launches, double *push_bytes, int reset);
+
+/*
+ * The same for one kernel kind (timing mode on): PIC_KERNEL_PUSH gives what
+ * pic_timing gives; PIC_KERNEL_COULOMB the Coulomb pass of collisions
+ * (1)-(3): device ms, launches and algorithmic bytes (vx, vy, vz read and
+ * written for every particle of a cell holding at least two of its species)
+ * since its last reset.  Unknown kinds return PIC_EINVAL.
+ */
+typedef enum { PIC_KERNEL_PUSH = 0, PIC_KERNEL_COULOMB = 1 } pic_kernel;
+pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, long long *launches,
+                             double *bytes, int reset);
 
 /*
  * pic_field_solve_static -- charge deposit, Poisson solve and field of ONE

@@ -47,6 +47,7 @@ enum {
     C_LIVE = 30,        // live particles pushed (particle-steps)
     C_BSLOTS = 31,      // slots of species with an energy-binned bound (vy, vz read)
     C_BCANDS = 32,      // candidates of those species
+    C_COUL = 33,        // particles through the Coulomb pass (cells with >= 2 of a species)
     C_NCOUNT = 34
 };
 
@@ -90,6 +91,7 @@ struct SpeciesC {
     double Mfrac;       // M_O2/(m+M_O2)
     double ke_eV;       // (1/2) m (dx/dt)^2 / e: lab kinetic energy per u_n^2
     double vscale;      // dx/dt: normalised -> m/s
+    double coul_k;      // Coulomb: <tan^2(chi/2)> u_n^3 per particle of the cell (Eq. 2)
     unsigned int tnull; // null-collision threshold on a 32-bit word
     int nch;
     int table_lo;       // first table of the shared grid (for the index)
@@ -98,7 +100,7 @@ struct SpeciesC {
     int nbins;          // energy bins of the collision-frequency bound (0: one bound)
     int bin_off;        // first entry of this species' bins in WsPtrs::nubin
     // FP32 copies (the FP32 path never converts from FP64 on the device)
-    float qm_f, numax_n_f, vgas_n_f, Ek_f, mfrac_f, Mfrac_f, ke_eV_f, pad_f;
+    float qm_f, numax_n_f, vgas_n_f, Ek_f, mfrac_f, Mfrac_f, ke_eV_f, coul_k_f;
     GasChan ch[MAX_GAS_CH];
 };
 
@@ -139,7 +141,7 @@ struct Disc {
     double eedf_scale, iedf_scale, fm_scale, fm_emax;
     float f15_f, f16_f, f17_f, eedf_scale_f, iedf_scale_f, fm_scale_f, fm_emax_f, pad_f;
     int eedf_bins, iedf_bins, fm_bins, fm_xbins;
-    int diag_every, n1, sort_interval, pad;
+    int diag_every, n1, sort_interval, n2;
     int eedf_base, iedf_base, fm_base, pad2;
     unsigned long long seed;
     int discharge;

@@ -21,6 +21,7 @@ constexpr double ME = 9.1093837015e-31;
 constexpr double AMU = 1.66053906660e-27;
 constexpr double KB = 1.380649e-23;
 constexpr double PI = 3.14159265358979323846;
+constexpr double EPS0 = 8.8541878128e-12;
 constexpr double M_O = 16.0 * AMU;
 constexpr double M_O2 = 32.0 * AMU;
 // O- carries the extra electron and O2+ lacks one, so that every reaction of
@@ -105,8 +106,12 @@ bool validate(const pic_config *c, int D, const pic_xs_table *xs, int n_xs, std:
             return false;
         }
         if (q.precision != c[0].precision || q.diag_every != c[0].diag_every || q.n1 != c[0].n1 ||
-            q.sort_interval != c[0].sort_interval) {
-            why = "all discharges of one handle must share precision, diag_every, n1 and sort_interval";
+            q.sort_interval != c[0].sort_interval || q.n2 != c[0].n2) {
+            why = "all discharges of one handle must share precision, diag_every, n1, n2 and sort_interval";
+            return false;
+        }
+        if (q.n2 < 0 || (q.n2 > 0 && !(q.coulomb_log > 0))) {
+            why = "n2 must be >= 0 and coulomb_log > 0 when n2 > 0";
             return false;
         }
         if (q.precision != PIC_FP64 && q.precision != PIC_FP32_MIXED) {
@@ -373,11 +378,13 @@ struct pic_handle {
     bool graph_failed = false;
     // timing
     bool timing = false;
-    double push_ms = 0.0;
-    long long push_launches = 0, launches = 0;
+    double kms[2] = {0.0, 0.0};        // device ms per timed kernel kind (push, Coulomb)
+    long long kl[2] = {0, 0};          // timed launches per kind
+    long long launches = 0;
     std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;          // kind of each event pair
     int ev_used = 0;
-    unsigned long long slots0 = 0, cands0 = 0, bslots0 = 0, bcands0 = 0;
+    unsigned long long slots0 = 0, cands0 = 0, bslots0 = 0, bcands0 = 0, coul0 = 0;
     const void *pools() const { return fp64 ? (const void *)&Pd : (const void *)&Pf; }
 };
 
@@ -465,6 +472,7 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
     D.diag_every = q.diag_every;
     D.n1 = q.n1;
     D.sort_interval = q.sort_interval;
+    D.n2 = q.n2;
     D.seed = q.seed;
     D.discharge = d;
     D.cx_iso = q.cx_isotropic;
@@ -480,6 +488,12 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
         S.mfrac = m / (m + M_O2);
         S.Mfrac = M_O2 / (m + M_O2);
         S.vscale = xdt;
+        // Eq. 2 (eps0 squared, reduced mass m/2 of a like pair) with the
+        // cell density count * weight / dx and tau = n2 dt, in units of u_n^3
+        const double mc = 0.5 * m, q2 = CHARGE[s] * CHARGE[s];
+        S.coul_k = q.n2 > 0 ? q2 * q2 * q.coulomb_log * (q.n2 * q.dt_s) * q.weight_m2 /
+                                  (8.0 * PI * EPS0 * EPS0 * mc * mc * D.dx) / (xdt * xdt * xdt)
+                            : 0.0;
         S.nch = gas_count[s];
         S.table_lo = S.nch > 0 ? gas_tabs_by_sp_flat[s * MAX_GAS_CH] : 0;
         for (int j = 0; j < S.nch; ++j) {
@@ -547,6 +561,7 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
         S.mfrac_f = (float)S.mfrac;
         S.Mfrac_f = (float)S.Mfrac;
         S.ke_eV_f = (float)S.ke_eV;
+        S.coul_k_f = (float)S.coul_k;
         h->numax[3 * d + s] = S.numax;
     }
     const int rx[3] = {13, 14, 19};
@@ -827,7 +842,25 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
 static long long lcm_ll(long long a, long long b) { return a / std::gcd(a, b) * b; }
 
 // Kernels of one step; returns the number launched.
-static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool time_push)
+// events around one kernel launch in timing mode (kind 0 push, 1 Coulomb)
+static cudaError_t time_open(pic_handle *h, bool on, cudaStream_t st)
+{
+    if (!on) return cudaSuccess;
+    if (h->ev_used + 2 > (int)h->ev.size()) return cudaErrorNotReady;
+    return cudaEventRecord(h->ev[h->ev_used], st);
+}
+
+static cudaError_t time_close(pic_handle *h, bool on, cudaStream_t st, int kind)
+{
+    if (!on) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(h->ev[h->ev_used + 1], st);
+    if (e) return e;
+    h->ev_kind[h->ev_used / 2] = kind;
+    h->ev_used += 2;
+    return cudaSuccess;
+}
+
+static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool timed)
 {
     const pic_config &q = h->cfg[0];
     const int par = (int)(n & 1);
@@ -836,19 +869,11 @@ static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool time_p
     cudaError_t e = launch_field(h->fp64, diag, 0, h->W, par, h->L, st);
     if (e) return e;
     ++nk;
-    if (time_push) {
-        if (h->ev_used + 2 > (int)h->ev.size()) return cudaErrorNotReady;
-        e = cudaEventRecord(h->ev[h->ev_used], st);
-        if (e) return e;
-    }
+    if ((e = time_open(h, timed, st))) return e;
     e = launch_push(h->fp64, diag, h->W, h->pools(), par, h->L, st);
     if (e) return e;
     ++nk;
-    if (time_push) {
-        e = cudaEventRecord(h->ev[h->ev_used + 1], st);
-        if (e) return e;
-        h->ev_used += 2;
-    }
+    if ((e = time_close(h, timed, st, 0))) return e;
     e = launch_collide(h->fp64, h->W, h->pools(), par, h->L.collide_blocks, st);
     if (e) return e;
     ++nk;
@@ -857,11 +882,19 @@ static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool time_p
     ++nk;
     const long long next = n + 1;
     const bool pair = q.n1 > 0 && next % q.n1 == 0;
-    const bool sort = pair || (q.sort_interval > 0 && next % q.sort_interval == 0);
+    const bool coul = q.n2 > 0 && next % q.n2 == 0;
+    const bool sort = pair || coul || (q.sort_interval > 0 && next % q.sort_interval == 0);
     if (sort) {
         e = launch_sort(h->fp64, h->W, h->pools(), h->sort_tab, h->L, st);
         if (e) return e;
         nk += kernels_per_sort();
+    }
+    if (coul) {
+        if ((e = time_open(h, timed, st))) return e;
+        e = launch_coulomb(h->fp64, h->W, h->pools(), par, st);
+        if (e) return e;
+        ++nk;
+        if ((e = time_close(h, timed, st, 1))) return e;
     }
     if (pair) {
         e = launch_pair(h->fp64, h->W, h->pools(), par, h->L, st);
@@ -878,8 +911,9 @@ static pic_status harvest_events(pic_handle *h)
     for (int i = 0; i < h->ev_used; i += 2) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]));
-        h->push_ms += ms;
-        h->push_launches += 1;
+        const int k = h->ev_kind[i / 2];
+        h->kms[k] += ms;
+        h->kl[k] += 1;
     }
     h->ev_used = 0;
     return PIC_OK;
@@ -914,6 +948,7 @@ extern "C" pic_status pic_step(pic_handle *h, long long n_steps)
     if (h->period == 0) {
         long long P = 2;
         if (q.n1 > 0) P = lcm_ll(P, q.n1);
+        if (q.n2 > 0) P = lcm_ll(P, q.n2);
         if (q.sort_interval > 0) P = lcm_ll(P, q.sort_interval);
         if (q.diag_every > 0) P = lcm_ll(P, q.diag_every);
         h->period = P;
@@ -953,7 +988,7 @@ extern "C" pic_status pic_step(pic_handle *h, long long n_steps)
             continue;
         }
         int nk = 0;
-        if (h->timing && h->ev_used + 2 > (int)h->ev.size()) {
+        if (h->timing && h->ev_used + 4 > (int)h->ev.size()) {
             pic_status s = harvest_events(h);
             if (s != PIC_OK) return s;
         }
@@ -1051,7 +1086,8 @@ extern "C" pic_status pic_diagnostics(pic_handle *h, int d, double *dens_sum, do
         counters[32] = (long long)c[C_LIVE];
         counters[33] = (long long)c[C_CANDS];
         counters[34] = (long long)c[C_SLOTS];
-        for (int k = 35; k < 40; ++k) counters[k] = 0;
+        counters[35] = (long long)c[C_COUL];
+        for (int k = 36; k < 40; ++k) counters[k] = 0;
     }
     if (n_samples) *n_samples = (long long)ns;
     if (reset) {
@@ -1204,6 +1240,7 @@ extern "C" pic_status pic_set_timing(pic_handle *h, int on)
     if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
     if (on && h->ev.empty()) {
         h->ev.resize(4096);
+        h->ev_kind.assign(2048, 0);
         for (auto &e : h->ev) CK(cudaEventCreate(&e));
     }
     h->timing = on != 0;
@@ -1231,18 +1268,46 @@ extern "C" pic_status pic_timing(pic_handle *h, double *push_ms, long long *push
     const double R = h->fp64 ? 8.0 : 4.0;
     const double bytes = (double)(slots - h->slots0) * 2.0 * (4.0 + 2.0 * R) +
                          (double)(bslots - h->bslots0) * 2.0 * R + (double)(cands - h->cands0) * 8.0;
-    if (push_ms) *push_ms = h->push_ms;
-    if (push_launches) *push_launches = h->push_launches;
+    if (push_ms) *push_ms = h->kms[0];
+    if (push_launches) *push_launches = h->kl[0];
     if (launches) *launches = h->launches;
     if (push_bytes) *push_bytes = bytes;
     if (reset) {
-        h->push_ms = 0.0;
-        h->push_launches = 0;
+        h->kms[0] = 0.0;
+        h->kl[0] = 0;
         h->launches = 0;
         h->slots0 = slots;
         h->cands0 = cands;
         h->bslots0 = bslots;
         h->bcands0 = bcands;
+    }
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, long long *launches,
+                                        double *bytes, int reset)
+{
+    if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
+    if (kernel == PIC_KERNEL_PUSH) {
+        long long all = 0;
+        return pic_timing(h, ms, launches, &all, bytes, reset);
+    }
+    if (kernel != PIC_KERNEL_COULOMB) return fail(h, PIC_EINVAL, "unknown kernel kind");
+    std::vector<unsigned long long> c((size_t)h->D * C_NCOUNT);
+    CK(cudaMemcpyAsync(c.data(), h->W.counters, 8 * c.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    unsigned long long coul = 0;
+    for (int d = 0; d < h->D; ++d) coul += c[(size_t)d * C_NCOUNT + C_COUL];
+    // algorithmic bytes of the Coulomb pass: vx, vy, vz read and written for
+    // every particle of a cell holding at least two of its species
+    const double R = h->fp64 ? 8.0 : 4.0;
+    if (ms) *ms = h->kms[1];
+    if (launches) *launches = h->kl[1];
+    if (bytes) *bytes = (double)(coul - h->coul0) * 6.0 * R;
+    if (reset) {
+        h->kms[1] = 0.0;
+        h->kl[1] = 0;
+        h->coul0 = coul;
     }
     return PIC_OK;
 }

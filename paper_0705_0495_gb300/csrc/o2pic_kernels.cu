@@ -917,6 +917,245 @@ k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
     }
 }
 
+// ------------------------------------------------------------ Coulomb (1)-(3)
+
+// Arithmetic of the Coulomb collision.  FP64: correctly rounded functions.
+// FP32: the hardware approximations (rsqrtf, __fdividef, __logf, __sincosf,
+// each documented within a few units of 2^-22), whose errors change a
+// velocity by far less than the FP32 path's tolerance of 1e-5 of the thermal
+// speed; sin and cos of 2 pi r come from pi (2 r - 1) in [-pi, pi) with the
+// signs of both flipped.
+template <typename Real> struct CoulMath;
+template <> struct CoulMath<double> {
+    static __device__ __forceinline__ double inv_u32(double kn_sqrt, double u2, double u)
+    {
+        (void)kn_sqrt;
+        return 1.0 / (u2 * u);
+    }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ void normal(unsigned a, unsigned b, double &n0)
+    {
+        double n1;
+        box_muller<double>(a, b, n0, n1);
+    }
+    static __device__ __forceinline__ void sincos2pi(double r, double *s, double *c) { sincospi(2.0 * r, s, c); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+};
+template <> struct CoulMath<float> {
+    static __device__ __forceinline__ float inv_u32(float, float u2, float u)
+    {
+        (void)u2;
+        const float r = rsqrtf(u);
+        return r * r * r * r * r * r;  // u^-3
+    }
+    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ void normal(unsigned a, unsigned b, float &n0)
+    {
+        const float x = -2.0f * __logf(unif<float>(a));
+        float s, c;
+        __sincosf(3.14159265358979f * (2.0f * unif<float>(b) - 1.0f), &s, &c);
+        n0 = -(x * rsqrtf(x)) * c;
+    }
+    static __device__ __forceinline__ void sincos2pi(float r, float *s, float *c)
+    {
+        __sincosf(3.14159265358979f * (2.0f * r - 1.0f), s, c);
+        *s = -*s;
+        *c = -*c;
+    }
+    static __device__ __forceinline__ float sqrt_(float x) { return x * rsqrtf(x); }
+};
+
+// One binary Coulomb collision of two like particles i, j (Sec. III A, the
+// model of Takizuka and Abe): tan(chi/2) = sqrt(kn / u^3) * xi with kn the
+// Eq. 2 variance times u^3 for this cell, xi a standard normal; the azimuth
+// phi = 2 pi r is measured from the plane of g and the z axis (the x-y plane
+// when g is along z).  Each particle takes half of the change of g.
+template <typename Real>
+__device__ __forceinline__ void coulomb_pair(Real *vx, Real *vy, Real *vz, int i, int j, Real kn,
+                                             uint4 w)
+{
+    using M = CoulMath<Real>;
+    const Real g0 = vx[i] - vx[j], g1 = vy[i] - vy[j], g2 = vz[i] - vz[j];
+    const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
+    if (!(u2 > Real(0))) return;
+    const Real u = M::sqrt_(u2);
+    Real xi;
+    M::normal(w.x, w.y, xi);
+    const Real d = M::sqrt_(kn * M::inv_u32(Real(0), u2, u)) * xi;  // tan(chi/2)
+    Real sn, om;                                                     // sin(chi), 1 - cos(chi)
+    if (fabs(d) <= Real(1)) {
+        const Real r = M::rcp(Real(1) + d * d);
+        sn = Real(2) * d * r;
+        om = Real(2) * d * d * r;
+    } else {                                  // the same in 1/d (finite for any d)
+        const Real e = M::rcp(d);
+        const Real r = M::rcp(Real(1) + e * e);
+        sn = Real(2) * e * r;
+        om = Real(2) * r;
+    }
+    Real sp, cp;
+    M::sincos2pi(unif<Real>(w.z), &sp, &cp);
+    const Real up2 = g0 * g0 + g1 * g1;
+    Real d0, d1, d2;
+    if (up2 > Real(0)) {
+        const Real up = M::sqrt_(up2), rp = M::rcp(up);
+        const Real ex = g0 * rp, ey = g1 * rp;
+        const Real a = g2 * sn * cp, b = u * sn * sp;
+        d0 = ex * a - ey * b - g0 * om;
+        d1 = ey * a + ex * b - g1 * om;
+        d2 = -up * sn * cp - g2 * om;
+    } else {
+        d0 = u * sn * cp;
+        d1 = u * sn * sp;
+        d2 = -g2 * om;
+    }
+    vx[i] += Real(0.5) * d0;
+    vy[i] += Real(0.5) * d1;
+    vz[i] += Real(0.5) * d2;
+    vx[j] -= Real(0.5) * d0;
+    vy[j] -= Real(0.5) * d1;
+    vz[j] -= Real(0.5) * d2;
+}
+
+// random numbers of collision k of a cell's pass: stream 5, the draw
+// counter split over the sub-stream (high bits) and draw fields
+__device__ __forceinline__ uint4 coulomb_rng(unsigned long long seed, int disc, int s,
+                                             unsigned long long step, int c, unsigned k)
+{
+    return rng_block(seed, disc, s, 5, (int)(k >> 20), k & 0xFFFFFu, step, (unsigned)c);
+}
+
+// Copy n values of each component, COUL_COPY elements per thread in flight.
+constexpr int COUL_COPY = 4;
+template <typename Real>
+__device__ __forceinline__ void coulomb_copy(Real *__restrict__ dx, Real *__restrict__ dy, Real *__restrict__ dz,
+                                             const Real *__restrict__ sx, const Real *__restrict__ sy,
+                                             const Real *__restrict__ sz, int n)
+{
+    for (int k0 = threadIdx.x; k0 < n; k0 += COUL_COPY * COUL_THREADS) {
+        Real ax[COUL_COPY], ay[COUL_COPY], az[COUL_COPY];
+#pragma unroll
+        for (int q = 0; q < COUL_COPY; ++q) {
+            const int k = k0 + q * COUL_THREADS;
+            if (k < n) {
+                ax[q] = sx[k];
+                ay[q] = sy[k];
+                az[q] = sz[k];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < COUL_COPY; ++q) {
+            const int k = k0 + q * COUL_THREADS;
+            if (k < n) {
+                dx[k] = ax[q];
+                dy[k] = ay[q];
+                dz[k] = az[q];
+            }
+        }
+    }
+}
+
+// The collisions of one cell: pi(2m) for m = threadIdx.x is (b + m (2a mod
+// n)) mod n, advanced by T (2a mod n) mod n per iteration; pi(2m+1) = pi(2m)
+// + a mod n.  prm holds a, b and 2a mod n.
+template <typename Real>
+__device__ __forceinline__ void coulomb_cell_pairs(Real *vx, Real *vy, Real *vz, unsigned un,
+                                                   const unsigned *prm, Real kn, unsigned long long seed,
+                                                   int disc, int s, unsigned long long step, int c)
+{
+    const unsigned a = prm[0], b = prm[1], a2 = prm[2];
+    const unsigned pairs = (un & 1u) ? (un - 3u) / 2u : un / 2u;
+    const unsigned t = threadIdx.x;
+    unsigned x = un <= (1u << 22) ? (b + (t * a2) % un) % un
+                                  : (unsigned)(((unsigned long long)t * a2 + b) % un);
+    const unsigned stepA = (unsigned)(((unsigned long long)COUL_THREADS * a2) % un);
+    for (unsigned m = t; m < pairs; m += COUL_THREADS) {
+        unsigned y = x + a;
+        if (y >= un) y -= un;
+        coulomb_pair<Real>(vx, vy, vz, (int)x, (int)y, kn, coulomb_rng(seed, disc, s, step, c, 1u + m));
+        x += stepA;
+        if (x >= un) x -= un;
+    }
+    if ((un & 1u) && t == 0) {
+        const int A = (int)(((unsigned long long)a * (un - 3u) + b) % un);
+        const int B = (int)(((unsigned long long)a * (un - 2u) + b) % un);
+        const int C = (int)(((unsigned long long)a * (un - 1u) + b) % un);
+        const Real kh = Real(0.5) * kn;
+        coulomb_pair<Real>(vx, vy, vz, A, B, kh, coulomb_rng(seed, disc, s, step, c, 1u + pairs));
+        coulomb_pair<Real>(vx, vy, vz, B, C, kh, coulomb_rng(seed, disc, s, step, c, 2u + pairs));
+        coulomb_pair<Real>(vx, vy, vz, C, A, kh, coulomb_rng(seed, disc, s, step, c, 3u + pairs));
+    }
+}
+
+// Coulomb pass of one species in one cell per block, right after the sort
+// (every slot of the cell is live).  Blocks run the O2+ cells first, then
+// O-, then electrons (the largest cells first).  The n particles are paired
+// by the affine permutation pi(k) = (a k + b) mod n, a coprime to n, from
+// draw 0 of the cell's stream 5: thread t takes the pairs m = t, t + T, ...
+// as (pi(2m), pi(2m+1)) with the random numbers of draw 1 + m; for odd n
+// thread 0 then runs the triangle of the last three, (A, B), (B, C), (C, A),
+// with half the time each.  The pairs are disjoint, so no ordering is needed
+// between threads.  A cell of at most `cap` particles is staged in shared
+// memory (coalesced copies in and out); a larger one is worked on in place.
+template <typename Real>
+__global__ void __launch_bounds__(COUL_THREADS, 2)
+k_coulomb(WsPtrs W, Pools<Real> P, int par, int cap)
+{
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char coul_smem[];
+    const int gw = blockIdx.x % W.total_cells, s = NSP - 1 - (int)(blockIdx.x / W.total_cells);
+    const int d = W.cell_disc[gw];
+    const Disc &Dd = W.disc[d];
+    const int N = Dd.N, c = gw - Dd.ccell_base;
+    const int *cs = W.cell_start + Dd.cs_base;
+    const int p0 = cs[s * (N + 2) + c], p1 = cs[s * (N + 2) + c + 1];
+    const int n = p1 - p0;
+    if (n < 2) return;
+    if (n >= (1 << 29)) {
+        if (threadIdx.x == 0) set_status(W.ctl, ST_BADSTATE);
+        return;
+    }
+    if (threadIdx.x == 0) atomicAdd(&W.counters[(size_t)d * C_NCOUNT + C_COUL], (unsigned long long)n);
+    const unsigned long long step = W.ctl->step[par];
+    const unsigned long long seed = Dd.seed;
+    const int disc = Dd.discharge;
+    const int cur = W.ctl->cur;
+    const int base = Dd.pbase[s] + p0;
+    Real *gx = P.vx[cur] + base, *gy = P.vy[cur] + base, *gz = P.vz[cur] + base;
+    const unsigned un = (unsigned)n;
+    __shared__ unsigned prm[3];  // a, b, 2a mod n of the cell's permutation
+    if (threadIdx.x == 0) {
+        const uint4 w0 = coulomb_rng(seed, disc, s, step, c, 0u);
+        unsigned a = 1u + w0.x % (un - 1u);
+        for (;;) {  // a -> a mod (n-1) + 1 until coprime; a = 1 always is
+            unsigned x = a, y = un;
+            while (y) {
+                const unsigned t = x % y;
+                x = y;
+                y = t;
+            }
+            if (x == 1u) break;
+            a = a % (un - 1u) + 1u;
+        }
+        prm[0] = a;
+        prm[1] = w0.y % un;
+        prm[2] = (unsigned)((2ull * a) % un);
+    }
+    const SpeciesC &S = Dd.sp[s];
+    const Real kn = pick<Real>(S.coul_k, S.coul_k_f) * Real(n);
+    if (n <= cap) {
+        Real *sx = reinterpret_cast<Real *>(coul_smem), *sy = sx + cap, *sz = sy + cap;
+        coulomb_copy<Real>(sx, sy, sz, gx, gy, gz, n);
+        __syncthreads();
+        coulomb_cell_pairs<Real>(sx, sy, sz, un, prm, kn, seed, disc, s, step, c);
+        __syncthreads();
+        coulomb_copy<Real>(gx, gy, gz, sx, sy, sz, n);
+    } else {
+        __syncthreads();
+        coulomb_cell_pairs<Real>(gx, gy, gz, un, prm, kn, seed, disc, s, step, c);
+    }
+}
+
 // Births of (19) appended to the electron array of each discharge in cell
 // order (the order of the sequential pass).
 template <typename Real>
@@ -1042,12 +1281,18 @@ cudaError_t configure_kernels(bool fp64, LaunchCfg &L)
         if (e) return e;
         e = cudaFuncSetAttribute(k_sort_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.scatter_smem);
         if (e) return e;
+        e = cudaFuncSetAttribute(k_coulomb<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)coulomb_smem_bytes(true));
+        if (e) return e;
     } else {
         e = cudaFuncSetAttribute(k_field<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.field_smem);
         if (e) return e;
         e = cudaFuncSetAttribute(k_sort_count<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sort_smem);
         if (e) return e;
         e = cudaFuncSetAttribute(k_sort_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.scatter_smem);
+        if (e) return e;
+        e = cudaFuncSetAttribute(k_coulomb<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)coulomb_smem_bytes(false));
         if (e) return e;
     }
     return cudaFuncSetAttribute(k_sort_cellscan, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1088,6 +1333,22 @@ cudaError_t launch_sort(bool fp64, const WsPtrs &W, const void *pools, const int
     launch_k(k_sort_finish, 1, 256, 0, st, W);
     return cudaGetLastError();
 }
+
+size_t coulomb_smem_bytes(bool fp64) { return (size_t)COUL_STAGE * 3 * (fp64 ? 8 : 4); }
+
+cudaError_t launch_coulomb(bool fp64, const WsPtrs &W, const void *pools, int par, cudaStream_t st)
+{
+    const int grid = W.total_cells * NSP;
+    const size_t smem = coulomb_smem_bytes(fp64);
+    if (fp64)
+        launch_k(k_coulomb<double>, grid, COUL_THREADS, smem, st, W, *static_cast<const Pools<double> *>(pools),
+                 par, COUL_STAGE);
+    else
+        launch_k(k_coulomb<float>, grid, COUL_THREADS, smem, st, W, *static_cast<const Pools<float> *>(pools),
+                 par, COUL_STAGE);
+    return cudaGetLastError();
+}
+
 
 cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par, const LaunchCfg &L,
                         cudaStream_t st)

@@ -61,6 +61,18 @@ cudaError_t launch_field(bool fp64, bool diag, int mode, const WsPtrs &W, int pa
 
 cudaError_t launch_sort(bool fp64, const WsPtrs &W, const void *pools,
                         const int *sort_block_ds, const LaunchCfg &L, cudaStream_t s);
+// Coulomb pass: a block per (cell, species) of COUL_THREADS threads; cells of
+// at most COUL_STAGE particles are staged in shared memory
+#ifndef O2_COUL_THREADS
+#define O2_COUL_THREADS 384
+#endif
+#ifndef O2_COUL_STAGE
+#define O2_COUL_STAGE 8192
+#endif
+constexpr int COUL_THREADS = O2_COUL_THREADS;
+constexpr int COUL_STAGE = O2_COUL_STAGE;
+size_t coulomb_smem_bytes(bool fp64);
+cudaError_t launch_coulomb(bool fp64, const WsPtrs &W, const void *pools, int par, cudaStream_t st);
 cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par,
                         const LaunchCfg &L, cudaStream_t s);
 cudaError_t launch_load(bool fp64, const WsPtrs &W, const void *pools, const long long *d_ninit,

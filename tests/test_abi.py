@@ -62,3 +62,37 @@ def test_batched_workspace_grows_with_discharges(lib):
     two = o2pic.workspace_size([inputs.cfg1(n_op=1000), inputs.cfg1(n_op=1000, n_cells=64)],
                                inputs.xs_tables())
     assert two > one
+
+
+def _c_layout(tmp_path, struct, fields, header="o2pic.h", incdir=os.path.join(ROOT, "include")):
+    """offsetof of each field and sizeof, as the C compiler lays out the
+    struct declared in the header"""
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', f'#include "{header}"', "int main(void) {"]
+    for f in fields:
+        lines.append(f'    printf("%zu\\n", offsetof({struct}, {f}));')
+    lines += [f'    printf("%zu\\n", sizeof({struct}));', "    return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", incdir, str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return [int(v) for v in out]
+
+
+@pytest.mark.parametrize("cls", [o2pic.pic_config, o2pic.pic_xs_table])
+def test_binding_struct_layout_matches_the_header(tmp_path, cls):
+    names = [f[0] for f in cls._fields_]
+    c = _c_layout(tmp_path, cls.__name__, names)
+    py = [getattr(cls, n).offset for n in names] + [C.sizeof(cls)]
+    assert c == py, list(zip(names + ["sizeof"], c, py))
+
+
+def test_oracle_binding_config_layout_matches_its_header(tmp_path):
+    import oracle
+    cls = oracle._Cfg
+    names = [f[0] for f in cls._fields_]
+    c = _c_layout(tmp_path, "orc_cfg", names, "o2pic_oracle.h", os.path.join(ROOT, "oracle"))
+    py = [getattr(cls, n).offset for n in names] + [C.sizeof(cls)]
+    assert c == py, list(zip(names + ["sizeof"], c, py))

@@ -96,6 +96,37 @@ def _matched(d, g, o, s, tol):
     return best
 
 
+def _matched_by_cell(d, g, o, s, tol):
+    """After a Coulomb pass: a decision that changes the number of particles
+    of a species in a cell (a birth, a death or a cell crossing decided
+    differently in FP32) changes that cell's random pairing, so all of its
+    particles scatter with other partners.  Cells whose counts agree are
+    compared slot by slot; the others are counted.  Returns (particles
+    compared, bad particles, cells with different counts, worst error of the
+    good ones)."""
+    N = d.n_cells
+    dx = d.L / N
+    side = []
+    for st in (g, o):
+        m = st["alive"]
+        c = np.clip(np.floor(st["x"][m] / dx).astype(np.int64), 0, N - 1)
+        order = np.argsort(c, kind="stable")
+        side.append(({k: st[k][m][order] for k in ("x", "vx", "vy", "vz")},
+                     np.bincount(c, minlength=N)))
+    (ga, gc), (oa, oc) = side
+    gs = np.concatenate([[0], np.cumsum(gc)])
+    os_ = np.concatenate([[0], np.cumsum(oc)])
+    same = gc == oc
+    gi = np.concatenate([np.arange(gs[k], gs[k + 1]) for k in np.flatnonzero(same)] + [np.zeros(0, int)])
+    oi = np.concatenate([np.arange(os_[k], os_[k + 1]) for k in np.flatnonzero(same)] + [np.zeros(0, int)])
+    vt = _vth(d, s)
+    err = np.abs(ga["x"][gi] - oa["x"][oi]) / d.L
+    for k in ("vx", "vy", "vz"):
+        err = np.maximum(err, np.abs(ga[k][gi] - oa[k][oi]) / vt)
+    bad = err > tol
+    return len(gi), int(bad.sum()), int((~same).sum()), float(np.max(err[~bad], initial=0.0))
+
+
 # ------------------------------------------------------------------ load
 
 @pytest.mark.parametrize("fp64", [True, False])
@@ -242,6 +273,51 @@ def test_fp32_pair_pass_with_frequent_events():
     assert sim.diagnostics(0)["events"][[13, 14, 19]].sum() > 0
 
 
+# ------------------------------------------------ Coulomb collisions (1)-(3)
+
+def _no_coulomb_run(d, steps):
+    import dataclasses
+    sim = _sim(dataclasses.replace(d, n2=0))
+    sim.step(steps)
+    return sim
+
+
+@pytest.mark.parametrize("n2", [1, 3])
+def test_fp64_coulomb_step_by_step(n2):
+    # every n2 steps a Coulomb pass over all cells and species; the Coulomb
+    # logarithm is raised so that the scattering is far above the tolerance
+    d = inputs.cfg1(n2=n2, coulomb_log=1e4)
+    sim, orc, (ex, ev) = _run_pair(d, [1, 2, 3, 10, 11, 30, 60])
+    assert ex < TOL64 and ev < TOL64, (ex, ev)
+    ref = _no_coulomb_run(d, 60)
+    g, r = sim.get_state(0, 2), ref.get_state(0, 2)
+    n = min(len(g["vx"]), len(r["vx"]))
+    assert np.max(np.abs(g["vx"][:n] - r["vx"][:n])) > 1e-3 * _vth(d, 2)
+
+
+def test_fp64_coulomb_ragged_cells_with_pair_pass():
+    # 7 cells, odd and even populations, cells with 0, 1, 2 and 3 particles
+    # of a species, Coulomb and particle-target passes on common steps; 3
+    # cells of about 10^4 particles of a species (more than a block stages in
+    # shared memory: the pass works in place)
+    for n_cells, n_op in ((7, 2 * 1237 + 2), (7, 22), (3, 60002)):
+        d = inputs.cfg1(n_cells=n_cells, n_op=n_op, sort_interval=3, n1=6, n2=2, coulomb_log=1e4)
+        # frequent particle-target events, except in the large cells (whose
+        # per-cell birth buffers they would overflow)
+        tabs = _scaled_pair_tables(3e6 if n_cells > 3 else 1.0)
+        sim, orc, (ex, ev) = _run_pair(d, [1, 2, 5, 6, 12, 18], tabs)
+        assert ex < TOL64 and ev < TOL64, (n_cells, n_op, ex, ev)
+        assert np.array_equal(sim.diagnostics(0)["events"], orc.counters()["events"])
+        assert sim.diagnostics(0)["coulomb_particles"] > 0
+
+
+def test_fp32_coulomb_replay():
+    d = inputs.cfg1(fp64=False, n2=1, coulomb_log=1e4)
+    compared, flips, worst = _replay(d, 30)
+    assert worst < TOL32, worst
+    assert flips <= 1e-4 * compared, (flips, compared)
+
+
 def test_fp64_empty_discharge():
     d = inputs.cfg1(n_op=0)
     sim, orc, _ = _run_pair(d, [5])
@@ -310,11 +386,13 @@ def test_fp32_replay_ragged_multi_tile_cfg2_geometry():
 
 # ------------------------------------------------- full-size, one step
 
-@pytest.mark.parametrize("name", ["cfg2", "cfg4"])
-def test_full_size_one_step_replay(name):
-    # BASELINE sizes in the bench's launch configuration: the GPU's loaded
-    # state is handed to the oracle and both take one step
-    d = inputs.WORKLOADS[name]()
+@pytest.mark.parametrize("name,n2", [("cfg2", 0), ("cfg4", 0), ("cfg4", 1)])
+def test_full_size_one_step_replay(name, n2):
+    # full sizes in the bench's launch configuration: the GPU's loaded state
+    # is handed to the oracle and both take one step (n2 = 1: with a Coulomb
+    # pass over every cell and species)
+    import dataclasses
+    d = dataclasses.replace(inputs.WORKLOADS[name](), n2=n2)
     tabs = inputs.xs_tables()
     sim = _sim(d, tabs)
     orc = oracle.Oracle(d, tabs, load=False)
@@ -324,14 +402,23 @@ def test_full_size_one_step_replay(name):
         del st
     sim.step(1)
     orc.step(1)
-    compared = flips = 0
+    compared = flips = cells = 0
     worst = 0.0
     for s in range(3):
-        c, f, w = _matched(d, sim.get_state(0, s), orc.get(s), s, TOL32)
+        if n2:
+            c, f, nc, w = _matched_by_cell(d, sim.get_state(0, s), orc.get(s), s, TOL32)
+            cells += nc
+        else:
+            c, f, w = _matched(d, sim.get_state(0, s), orc.get(s), s, TOL32)
         compared, flips, worst = compared + c, flips + f, max(worst, w)
-    assert compared > 0.99 * sum(d.n_init)
+    # a count-changing FP32 decision re-pairs a whole cell: at most one such
+    # decision in 1e6 particles, and the cells left out hold under 2% of them;
+    # any other flipped particle drags its Coulomb partner along, which
+    # doubles the decision-flip budget
+    assert cells <= 10 + 1e-6 * sum(d.n_init), cells
+    assert compared > (0.98 if n2 else 0.99) * sum(d.n_init), compared
     assert worst < TOL32
-    assert flips <= 1e-4 * compared, (flips, compared)
+    assert flips <= (2e-4 if n2 else 1e-4) * compared, (flips, compared)
     g, o = sim.diagnostics(0), orc.counters()
     # reaction counts: equal up to flipped decisions
     assert np.abs(g["events"] - o["events"]).sum() <= max(10, 1e-4 * compared)
