@@ -1010,16 +1010,19 @@ static void coulomb_rng(const orc_sim *s, int sp, long long step, uint32_t cell,
     rng(s, sp, 5, (int)(k >> 20), (uint32_t)(k & 0xFFFFF), step, cell, out);
 }
 
+/* collision k of a cell takes draw 1 + k/2 of the cell's stream: the normal
+ * is the first (k even) or second (k odd) of that draw's Box-Muller pair,
+ * the azimuth its third or fourth word */
 static void coulomb_one(const orc_sim *s, int sp, double *vx, double *vy, double *vz,
                         long long i, long long j, double dens, double tau,
                         long long step, uint32_t cell, long long k)
 {
     uint32_t d[4];
-    coulomb_rng(s, sp, step, cell, k, d);
+    coulomb_rng(s, sp, step, cell, 1 + k / 2, d);
     double n0, n1;
     box_muller(d[0], d[1], &n0, &n1);
     double v1[3] = {vx[i], vy[i], vz[i]}, v2[3] = {vx[j], vy[j], vz[j]};
-    orc_coulomb_pair(s, sp, v1, v2, dens, tau, n0, unif(d[2]));
+    orc_coulomb_pair(s, sp, v1, v2, dens, tau, (k % 2) ? n1 : n0, unif(d[2 + k % 2]));
     vx[i] = v1[0]; vy[i] = v1[1]; vz[i] = v1[2];
     vx[j] = v2[0]; vy[j] = v2[1]; vz[j] = v2[2];
 }
@@ -1029,8 +1032,8 @@ static void coulomb_one(const orc_sim *s, int sp, double *vx, double *vy, double
  * cell's stream 5), pairs pi(0) with pi(1), pi(2) with pi(3), ...; for odd n
  * the last three, A, B, C, collide as (A, B), (B, C), (C, A), each with half
  * the collision time, so that every particle scatters over tau once.  Writes
- * the collisions in draw order (collision k takes draw 1 + k) and returns
- * their number; the last three are the triangle's when n is odd. */
+ * the collisions in draw order (collisions 2m and 2m+1 share draw 1 + m) and
+ * returns their number; the last three are the triangle's when n is odd. */
 long long orc_coulomb_pairing(const orc_sim *s, int sp, long long n, long long step,
                               uint32_t cell, long long *pi, long long *pj)
 {
@@ -1064,7 +1067,7 @@ void orc_coulomb_cell(const orc_sim *s, int sp, double *vx, double *vy, double *
     long long nc = orc_coulomb_pairing(s, sp, n, step, cell, pi, pj);
     for (long long k = 0; k < nc; ++k) {
         double t = (n % 2 == 1 && k >= nc - 3) ? 0.5 * tau : tau;
-        coulomb_one(s, sp, vx, vy, vz, pi[k], pj[k], dens, t, step, cell, 1 + k);
+        coulomb_one(s, sp, vx, vy, vz, pi[k], pj[k], dens, t, step, cell, k);
     }
     free(pi);
     free(pj);

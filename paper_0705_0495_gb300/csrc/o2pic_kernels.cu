@@ -933,9 +933,8 @@ template <> struct CoulMath<double> {
         return 1.0 / (u2 * u);
     }
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-    static __device__ __forceinline__ void normal(unsigned a, unsigned b, double &n0)
+    static __device__ __forceinline__ void normal2(unsigned a, unsigned b, double &n0, double &n1)
     {
-        double n1;
         box_muller<double>(a, b, n0, n1);
     }
     static __device__ __forceinline__ void sincos2pi(double r, double *s, double *c) { sincospi(2.0 * r, s, c); }
@@ -949,12 +948,14 @@ template <> struct CoulMath<float> {
         return r * r * r * r * r * r;  // u^-3
     }
     static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-    static __device__ __forceinline__ void normal(unsigned a, unsigned b, float &n0)
+    static __device__ __forceinline__ void normal2(unsigned a, unsigned b, float &n0, float &n1)
     {
         const float x = -2.0f * __logf(unif<float>(a));
+        const float r = x * rsqrtf(x);
         float s, c;
         __sincosf(3.14159265358979f * (2.0f * unif<float>(b) - 1.0f), &s, &c);
-        n0 = -(x * rsqrtf(x)) * c;
+        n0 = -r * c;
+        n1 = -r * s;
     }
     static __device__ __forceinline__ void sincos2pi(float r, float *s, float *c)
     {
@@ -972,15 +973,13 @@ template <> struct CoulMath<float> {
 // when g is along z).  Each particle takes half of the change of g.
 template <typename Real>
 __device__ __forceinline__ void coulomb_pair(Real *vx, Real *vy, Real *vz, int i, int j, Real kn,
-                                             uint4 w)
+                                             Real xi, unsigned wphi)
 {
     using M = CoulMath<Real>;
     const Real g0 = vx[i] - vx[j], g1 = vy[i] - vy[j], g2 = vz[i] - vz[j];
     const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
     if (!(u2 > Real(0))) return;
     const Real u = M::sqrt_(u2);
-    Real xi;
-    M::normal(w.x, w.y, xi);
     const Real d = M::sqrt_(kn * M::inv_u32(Real(0), u2, u)) * xi;  // tan(chi/2)
     Real sn, om;                                                     // sin(chi), 1 - cos(chi)
     if (fabs(d) <= Real(1)) {
@@ -994,7 +993,7 @@ __device__ __forceinline__ void coulomb_pair(Real *vx, Real *vy, Real *vz, int i
         om = Real(2) * r;
     }
     Real sp, cp;
-    M::sincos2pi(unif<Real>(w.z), &sp, &cp);
+    M::sincos2pi(unif<Real>(wphi), &sp, &cp);
     const Real up2 = g0 * g0 + g1 * g1;
     Real d0, d1, d2;
     if (up2 > Real(0)) {
@@ -1055,24 +1054,50 @@ __device__ __forceinline__ void coulomb_copy(Real *__restrict__ dx, Real *__rest
     }
 }
 
-// The collisions of one cell: pi(2m) for m = threadIdx.x is (b + m (2a mod
-// n)) mod n, advanced by T (2a mod n) mod n per iteration; pi(2m+1) = pi(2m)
-// + a mod n.  prm holds a, b and 2a mod n.
+// Collision k of a cell with the random numbers of draw 1 + k/2: the normal
+// is the first (k even) or second (k odd) of the Box-Muller pair, the
+// azimuth word 2 or 3.
+template <typename Real>
+__device__ __forceinline__ void coulomb_one(Real *vx, Real *vy, Real *vz, int i, int j, Real kn,
+                                            unsigned long long seed, int disc, int s,
+                                            unsigned long long step, int c, unsigned k)
+{
+    const uint4 w = coulomb_rng(seed, disc, s, step, c, 1u + (k >> 1));
+    Real n0, n1;
+    CoulMath<Real>::normal2(w.x, w.y, n0, n1);
+    coulomb_pair<Real>(vx, vy, vz, i, j, kn, (k & 1u) ? n1 : n0, (k & 1u) ? w.w : w.z);
+}
+
+// The collisions of one cell.  Thread t takes collisions 2q and 2q + 1 for
+// q = t, t + T, ..., which share one draw: pi(4q) = (b + q (4a mod n)) mod n,
+// advanced by T (4a mod n) mod n per iteration; pi(4q+2) = pi(4q) + 2a mod
+// n and pi(k+1) = pi(k) + a mod n.  prm holds a, b, 2a mod n and 4a mod n.
 template <typename Real>
 __device__ __forceinline__ void coulomb_cell_pairs(Real *vx, Real *vy, Real *vz, unsigned un,
                                                    const unsigned *prm, Real kn, unsigned long long seed,
                                                    int disc, int s, unsigned long long step, int c)
 {
-    const unsigned a = prm[0], b = prm[1], a2 = prm[2];
+    using M = CoulMath<Real>;
+    const unsigned a = prm[0], b = prm[1], a2 = prm[2], a4 = prm[3];
     const unsigned pairs = (un & 1u) ? (un - 3u) / 2u : un / 2u;
     const unsigned t = threadIdx.x;
-    unsigned x = un <= (1u << 22) ? (b + (t * a2) % un) % un
-                                  : (unsigned)(((unsigned long long)t * a2 + b) % un);
-    const unsigned stepA = (unsigned)(((unsigned long long)COUL_THREADS * a2) % un);
-    for (unsigned m = t; m < pairs; m += COUL_THREADS) {
+    unsigned x = un <= (1u << 22) ? (b + (t * a4) % un) % un
+                                  : (unsigned)(((unsigned long long)t * a4 + b) % un);
+    const unsigned stepA = (unsigned)(((unsigned long long)COUL_THREADS * a4) % un);
+    for (unsigned q = t; 2u * q < pairs; q += COUL_THREADS) {
+        const uint4 w = coulomb_rng(seed, disc, s, step, c, 1u + q);
+        Real n0, n1;
+        M::normal2(w.x, w.y, n0, n1);
         unsigned y = x + a;
         if (y >= un) y -= un;
-        coulomb_pair<Real>(vx, vy, vz, (int)x, (int)y, kn, coulomb_rng(seed, disc, s, step, c, 1u + m));
+        coulomb_pair<Real>(vx, vy, vz, (int)x, (int)y, kn, n0, w.z);
+        if (2u * q + 1u < pairs) {
+            unsigned x1 = x + a2;
+            if (x1 >= un) x1 -= un;
+            unsigned y1 = x1 + a;
+            if (y1 >= un) y1 -= un;
+            coulomb_pair<Real>(vx, vy, vz, (int)x1, (int)y1, kn, n1, w.w);
+        }
         x += stepA;
         if (x >= un) x -= un;
     }
@@ -1081,9 +1106,9 @@ __device__ __forceinline__ void coulomb_cell_pairs(Real *vx, Real *vy, Real *vz,
         const int B = (int)(((unsigned long long)a * (un - 2u) + b) % un);
         const int C = (int)(((unsigned long long)a * (un - 1u) + b) % un);
         const Real kh = Real(0.5) * kn;
-        coulomb_pair<Real>(vx, vy, vz, A, B, kh, coulomb_rng(seed, disc, s, step, c, 1u + pairs));
-        coulomb_pair<Real>(vx, vy, vz, B, C, kh, coulomb_rng(seed, disc, s, step, c, 2u + pairs));
-        coulomb_pair<Real>(vx, vy, vz, C, A, kh, coulomb_rng(seed, disc, s, step, c, 3u + pairs));
+        coulomb_one<Real>(vx, vy, vz, A, B, kh, seed, disc, s, step, c, pairs);
+        coulomb_one<Real>(vx, vy, vz, B, C, kh, seed, disc, s, step, c, pairs + 1u);
+        coulomb_one<Real>(vx, vy, vz, C, A, kh, seed, disc, s, step, c, pairs + 2u);
     }
 }
 
@@ -1091,10 +1116,10 @@ __device__ __forceinline__ void coulomb_cell_pairs(Real *vx, Real *vy, Real *vz,
 // (every slot of the cell is live).  Blocks run the O2+ cells first, then
 // O-, then electrons (the largest cells first).  The n particles are paired
 // by the affine permutation pi(k) = (a k + b) mod n, a coprime to n, from
-// draw 0 of the cell's stream 5: thread t takes the pairs m = t, t + T, ...
-// as (pi(2m), pi(2m+1)) with the random numbers of draw 1 + m; for odd n
-// thread 0 then runs the triangle of the last three, (A, B), (B, C), (C, A),
-// with half the time each.  The pairs are disjoint, so no ordering is needed
+// draw 0 of the cell's stream 5; collision m is (pi(2m), pi(2m+1)) with the
+// random numbers of draw 1 + m/2 (two collisions per draw); for odd n thread
+// 0 then runs the triangle of the last three, (A, B), (B, C), (C, A), with
+// half the time each.  The pairs are disjoint, so no ordering is needed
 // between threads.  A cell of at most `cap` particles is staged in shared
 // memory (coalesced copies in and out); a larger one is worked on in place.
 template <typename Real>
@@ -1123,7 +1148,7 @@ k_coulomb(WsPtrs W, Pools<Real> P, int par, int cap)
     const int base = Dd.pbase[s] + p0;
     Real *gx = P.vx[cur] + base, *gy = P.vy[cur] + base, *gz = P.vz[cur] + base;
     const unsigned un = (unsigned)n;
-    __shared__ unsigned prm[3];  // a, b, 2a mod n of the cell's permutation
+    __shared__ unsigned prm[4];  // a, b, 2a mod n, 4a mod n of the cell's permutation
     if (threadIdx.x == 0) {
         const uint4 w0 = coulomb_rng(seed, disc, s, step, c, 0u);
         unsigned a = 1u + w0.x % (un - 1u);
@@ -1140,6 +1165,7 @@ k_coulomb(WsPtrs W, Pools<Real> P, int par, int cap)
         prm[0] = a;
         prm[1] = w0.y % un;
         prm[2] = (unsigned)((2ull * a) % un);
+        prm[3] = (unsigned)((4ull * a) % un);
     }
     const SpeciesC &S = Dd.sp[s];
     const Real kn = pick<Real>(S.coul_k, S.coul_k_f) * Real(n);
