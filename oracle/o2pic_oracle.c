@@ -784,6 +784,107 @@ static void gas_collision(orc_sim *s, int sp, long long i, double numax, blist_t
     for (int k = 0; k < np; ++k) blist_push(&bl[psp[k]], psp[k], p->x[i], &pv[3 * k]);
 }
 
+/* ------------------------------------------- sequential gas channels */
+
+/* The gas-target channels in the order of Table I (reaction number, then
+ * table order): the list the sequential scheme walks.  Returns its length. */
+static int dsmc_list(const orc_sim *s, int *list)
+{
+    int n = 0;
+    for (int r = 4; r <= 18; ++r)
+        for (int i = 0; i < s->nt; ++i)
+            if (s->t[i].reaction == r && s->t[i].target < 0) list[n++] = i;
+    return n;
+}
+
+/* Channel k of the list for a particle of species sp with velocity v, the
+ * chain of root (root_sp, root) in generation gen (Sec. II and Eq. 1): a gas
+ * molecule from the Maxwellian at T_gas, u the relative speed, E the centre-
+ * of-mass energy; the channel takes place with P = n sigma(E) u tau, tau =
+ * n1 dt, clamped at 1 (and counted).  Random numbers: stream 6 of the root,
+ * sub-stream k, draws 4 gen (gas molecule), 4 gen + 1 (test and direction),
+ * 4 gen + 2 (the second direction of (18)).  Returns -1 if nothing happens,
+ * else the number of products (orc_gas_event). */
+static int dsmc_channel(orc_sim *s, int root_sp, long long root, int gen, int k, int tabi,
+                        int sp, const double v[3], double vo[3], int *alive, int *psp,
+                        double *pv)
+{
+    const table_t *t = &s->t[tabi];
+    uint32_t a[4], b[4], c2[4];
+    rng(s, root_sp, 6, k, (uint32_t)(4 * gen), s->step, (uint32_t)root, a);
+    rng(s, root_sp, 6, k, (uint32_t)(4 * gen + 1), s->step, (uint32_t)root, b);
+    double n0, n1, n2, n3;
+    box_muller(a[0], a[1], &n0, &n1);
+    box_muller(a[2], a[3], &n2, &n3);
+    double vg = sqrt(KB * s->c.T_gas / M_O2);
+    double V[3] = {vg * n0, vg * n1, vg * n2};
+    double g0 = v[0] - V[0], g1 = v[1] - V[1], g2 = v[2] - V[2];
+    double u = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+    double E = 0.5 * reduced_mass(MASS[sp], M_O2) * u * u / QE;
+    double P = t->ndens * sigma_of(t, E) * u * (s->c.n1 * s->c.dt);
+    if (P > 1.0) {
+        s->viol[1]++;
+        P = 1.0;
+    }
+    if (!(unif(b[0]) < P)) return -1;
+    double r4[4] = {unif(b[0]), unif(b[1]), unif(b[2]), unif(b[3])};
+    double r2[2] = {0.5, 0.5};
+    if (t->reaction == 18) {
+        rng(s, root_sp, 6, k, (uint32_t)(4 * gen + 2), s->step, (uint32_t)root, c2);
+        r2[0] = unif(c2[0]);
+        r2[1] = unif(c2[1]);
+    }
+    s->events[t->reaction]++;
+    return orc_gas_event(s, sp, t->reaction, tabi, v, V, r4, r2, vo, alive, psp, pv, NULL);
+}
+
+/* One pass of the sequential scheme over the channels of the list numbered
+ * below 13 (part 0) or above 14 (part 1): roots in species order, then slot
+ * order.  A particle meets the channels of its species in list order; one
+ * that dies in (15), (16) or (17) is replaced by its product, which meets the
+ * later channels of the list ("readmitted for the next collision"); products
+ * of (18) meet no later gas channel.  Births are appended in root order:
+ * (18)'s electron and O2+ when they occur, the product that ends a chain
+ * after the chain. */
+static void dsmc_pass(orc_sim *s, int part, blist_t *bl)
+{
+    int list[64];
+    int nl = dsmc_list(s, list);
+    for (int sp = 0; sp < 3; ++sp) {
+        parts_t *p = &s->p[sp];
+        for (long long i = 0; i < p->n; ++i) {
+            if (!p->alive[i]) continue;
+            int cs = sp, gen = 0;
+            double v[3] = {p->vx[i], p->vy[i], p->vz[i]};
+            for (int k = 0; k < nl; ++k) {
+                const table_t *t = &s->t[list[k]];
+                if (t->proj != cs) continue;
+                if (part == 0 ? t->reaction > 12 : t->reaction < 15) continue;
+                double vo[3], pv[6];
+                int alive, psp[2];
+                int np = dsmc_channel(s, sp, i, gen, k, list[k], cs, v, vo, &alive, psp, pv);
+                if (np < 0) continue;
+                if (alive) {
+                    for (int q = 0; q < 3; ++q) v[q] = vo[q];
+                    for (int q = 0; q < np; ++q) blist_push(&bl[psp[q]], psp[q], p->x[i], &pv[3 * q]);
+                } else {
+                    cs = psp[0];
+                    for (int q = 0; q < 3; ++q) v[q] = pv[q];
+                    ++gen;
+                }
+            }
+            if (gen == 0) {
+                p->vx[i] = v[0];
+                p->vy[i] = v[1];
+                p->vz[i] = v[2];
+            } else {
+                p->alive[i] = 0;
+                blist_push(&bl[cs], cs, p->x[i], v);
+            }
+        }
+    }
+}
+
 static void append_births(orc_sim *s, blist_t *bl)
 {
     for (int sp = 0; sp < 3; ++sp) {
@@ -1144,7 +1245,7 @@ static void step_once(orc_sim *s)
                 pc = s->pbin[b];
                 nu = s->nubin[b];
             }
-            if (unif(w0[i & 3]) < pc) gas_collision(s, sp, i, nu, bl);
+            if (s->c.gas_scheme == 0 && unif(w0[i & 3]) < pc) gas_collision(s, sp, i, nu, bl);
         }
     }
     append_births(s, bl);
@@ -1163,7 +1264,22 @@ static void step_once(orc_sim *s)
          * then the particle-target reactions every n1 steps */
         if (coul)
             for (int sp = 0; sp < 3; ++sp) coulomb_species(s, sp, start[sp]);
-        if (pair) {
+        if (pair && s->c.gas_scheme == 1) {
+            /* the sequential scheme: the whole list of Table I in order, gas
+             * channels before (13), (13), (14), gas channels after (14) with
+             * their products readmitted, a new sort (particles were born and
+             * removed), (19) */
+            dsmc_pass(s, 0, bl);
+            for (int c = 0; c < N; ++c) {
+                pair_channel(s, 13, c, start, bl);
+                pair_channel(s, 14, c, start, bl);
+            }
+            dsmc_pass(s, 1, bl);
+            append_births(s, bl);
+            for (int sp = 0; sp < 3; ++sp) sort_species(s, sp, start[sp]);
+            for (int c = 0; c < N; ++c) pair_channel(s, 19, c, start, bl);
+            append_births(s, bl);
+        } else if (pair) {
             for (int c = 0; c < N; ++c) {
                 pair_channel(s, 13, c, start, bl);
                 pair_channel(s, 14, c, start, bl);

@@ -47,6 +47,8 @@ typedef struct {
                             octave of lab energy from 2^-6 eV (0 = one bound) */
     int n2;              /* intra-species Coulomb collisions every n2 steps,
                             tau = n2 dt (0 = none) */
+    int gas_scheme;      /* gas targets: 0 null collision every step, 1 the
+                            sequential channel test every n1 steps (Sec. II) */
     double coulomb_log;  /* ln Gamma of Eq. 2 */
 } orc_cfg;
 

@@ -170,6 +170,7 @@ class Discharge:
     numax_bins: int = 64            # electrons: bounds per quarter octave of lab energy
     n2: int = 0                     # intra-species Coulomb collisions every n2 steps (0: none)
     coulomb_log: float = 10.0       # ln Gamma of Eq. 2 (not given in the paper)
+    gas_scheme: int = 0             # gas targets: 0 null collision, 1 sequential test every n1 steps
     cx_isotropic: bool = False
     capacity_factor: float = 1.5
     capacity_extra: int = 4096
