@@ -44,8 +44,10 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--n2", type=int, default=None,
                    help="intra-species Coulomb collisions every n2 steps on the workload (default: none)")
+    p.add_argument("--gas-scheme", type=int, default=None, choices=[0, 1],
+                   help="gas targets: 0 null-collision test (default), 1 the sequential scheme every n1 steps")
     p.add_argument("--no-variants", action="store_true",
-                   help="skip the FP64, batched-sweep and Coulomb figures reported beside the main one")
+                   help="skip the FP64, batched-sweep, Coulomb and sequential-gas figures beside the main one")
     return p.parse_args()
 
 
@@ -247,6 +249,7 @@ def measure_variant(name, discharges, warm_steps, timed_steps):
         sim.set_timing(True)
         sim.timing(reset=True)
         sim.kernel_timing("coulomb", reset=True)
+        sim.kernel_timing("sequential_gas", reset=True)
         sim.step(min(timed_steps, 200))
         tm = sim.timing()
         peak, _ = _peaks()
@@ -255,12 +258,13 @@ def measure_variant(name, discharges, warm_steps, timed_steps):
         out = {"workload": name, "value": ps / (ms / 1e3), "unit": UNIT, "time_steps": timed_steps,
                "warmup_time_steps": warm_steps, "ms_per_time_step": ms / timed_steps,
                "push_hbm_frac": achieved / peak}
-        kc = sim.kernel_timing("coulomb")
-        if kc["launches"] > 0 and kc["ms"] > 0:
-            # the Coulomb pass: device time per launch and its HBM fraction
-            # (vx, vy, vz read and written per particle of the pass)
-            out["coulomb_ms_per_launch"] = kc["ms"] / kc["launches"]
-            out["coulomb_hbm_frac"] = kc["bytes"] / (kc["ms"] / 1e3) / 1e9 / peak
+        for kind in ("coulomb", "sequential_gas"):
+            kc = sim.kernel_timing(kind)
+            if kc["launches"] > 0 and kc["ms"] > 0:
+                # the Coulomb pass or the sequential gas scheme: device time per
+                # launch and the HBM fraction of its algorithmic bytes
+                out[f"{kind}_ms_per_launch"] = kc["ms"] / kc["launches"]
+                out[f"{kind}_hbm_frac"] = kc["bytes"] / (kc["ms"] / 1e3) / 1e9 / peak
         return out
     finally:
         sim.close()
@@ -284,6 +288,8 @@ def run_ours(a, rank, world, local_rank):
     d = _workload(a.workload, rank, a.fp64, a.scale)
     if a.n2 is not None:
         d.n2 = a.n2
+    if a.gas_scheme is not None:
+        d.gas_scheme = a.gas_scheme
     tabs = inputs.xs_tables()
     sim = o2pic.Simulation([d], tabs)
     spc = d.steps_per_cycle
@@ -430,6 +436,14 @@ def run_ours(a, rank, world, local_rank):
                 f"(ln Gamma {dc.coulomb_log:g}): {_describe(dc)}", [dc], 200, 400)
         except Exception as ex:
             variants["coulomb"] = {"error": str(ex)}
+        try:
+            dq = _workload(a.workload, scale=a.scale)
+            dq.gas_scheme = 1
+            variants["sequential_gas"] = measure_variant(
+                f"{a.workload} with the sequential gas scheme (Table I in order every {dq.n1} steps, Eq. 1 "
+                f"per channel) instead of the null-collision test: {_describe(dq)}", [dq], 200, 400)
+        except Exception as ex:
+            variants["sequential_gas"] = {"error": str(ex)}
 
     if rank == 0:
         line = {
@@ -441,7 +455,9 @@ def run_ours(a, rank, world, local_rank):
                 "workload": f"{a.workload}: {_describe(d)}",
                 "step": f"one RF cycle = {spc} time steps (sort and pair pass every "
                         f"{d.sort_interval}/{d.n1} steps, diagnostics every {d.diag_every}"
-                        + (f", Coulomb collisions every {d.n2}" if d.n2 > 0 else "") + ")",
+                        + (f", Coulomb collisions every {d.n2}" if d.n2 > 0 else "")
+                        + (", sequential gas scheme instead of the null-collision test" if d.gas_scheme else "")
+                        + ")",
                 "precision": ("FP64 throughout" if d.fp64 else
                               "FP32 particles, push and collisions; exact fixed-point charge "
                               "accumulation; FP64 Poisson, field and diagnostics"),

@@ -135,6 +135,16 @@ typedef struct {
  *                  discharges of one handle share it.  A cell may hold at most
  *                  2^29 particles of a species.
  *   coulomb_log    ln Gamma of Eq. 2 (> 0 when n2 > 0)
+ *   gas_scheme     gas-target channels: 0 = null-collision test every step
+ *                  (one candidate draw against nu_max, then the channel walk);
+ *                  1 = the paper's sequential scheme (Sec. II): no test
+ *                  between particle-target steps; every n1 steps, after the
+ *                  sort, the channels of Table I in order, each with Eq. 1's
+ *                  P = n sigma u n1 dt (clamped at 1 and counted as a P > 1
+ *                  clamp): gas channels below (13), (13), (14), gas channels
+ *                  above (14) (a product of (15), (16), (17) meets the later
+ *                  channels of the list), a new sort, (19).  Needs n1 > 0;
+ *                  all discharges of one handle share it.
  */
 typedef struct {
     double L_m, p_Pa, T_gas_K, U_rf_V, f_rf_Hz, rf_phase, dt_s;
@@ -151,6 +161,7 @@ typedef struct {
     int cx_isotropic;
     int numax_bins;
     int n2;
+    int gas_scheme;
     int precision;
     double coulomb_log;
 } pic_config;
@@ -197,12 +208,14 @@ pic_status pic_step(pic_handle *h, long long n_steps);
  *   fm         [fm_xbins][fm_bins] O-, E = sign(vx) M vx^2 / 2
  *   counters   [40]: 0-5 absorbed (species*2 + wall), 6-25 events per
  *              reaction 0..19 (index 6 + reaction), 26 gas nu_max
- *              violations, 27 pair P > 1 clamps, 28-30 slots per species
+ *              violations, 27 Eq. 1 P > 1 clamps (particle-target pass and
+ *              sequential gas scheme), 28-30 slots per species
  *              (including dead slots not yet compacted), 31 steps taken,
  *              32 particle-steps (live particles pushed, summed over steps),
  *              33 null-collision candidates, 34 slots visited by the push,
  *              35 particles through the Coulomb pass (summed over passes),
- *              36-39 reserved (0)
+ *              36 live slots through the sequential gas scheme (summed over
+ *              its two parts and passes), 37-39 reserved (0)
  *   n_samples  number of diagnostic samples accumulated
  * reset != 0 clears the sums and histograms after copying.
  */
@@ -257,9 +270,11 @@ pic_status pic_timing(pic_handle *h, double *push_ms, long long *push_launches,
  * pic_timing gives; PIC_KERNEL_COULOMB the Coulomb pass of collisions
  * (1)-(3): device ms, launches and algorithmic bytes (vx, vy, vz read and
  * written for every particle of a cell holding at least two of its species)
- * since its last reset.  Unknown kinds return PIC_EINVAL.
+ * since its last reset; PIC_KERNEL_SEQUENTIAL_GAS the two parts of the
+ * sequential gas scheme (cell, offset, vx, vy, vz read and vx, vy, vz written
+ * per live slot and part).  Unknown kinds return PIC_EINVAL.
  */
-typedef enum { PIC_KERNEL_PUSH = 0, PIC_KERNEL_COULOMB = 1 } pic_kernel;
+typedef enum { PIC_KERNEL_PUSH = 0, PIC_KERNEL_COULOMB = 1, PIC_KERNEL_SEQUENTIAL_GAS = 2 } pic_kernel;
 pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, long long *launches,
                              double *bytes, int reset);
 

@@ -48,7 +48,8 @@ enum {
     C_BSLOTS = 31,      // slots of species with an energy-binned bound (vy, vz read)
     C_BCANDS = 32,      // candidates of those species
     C_COUL = 33,        // particles through the Coulomb pass (cells with >= 2 of a species)
-    C_NCOUNT = 34
+    C_DSMC = 34,        // live slots visited by the sequential gas scheme (both parts)
+    C_NCOUNT = 35
 };
 
 struct TableDesc {
@@ -120,6 +121,15 @@ struct PairC {          // particle-target reaction of one discharge
     float bnd_g_f, bnd_s_f;
 };
 
+// one gas channel of the sequential scheme's list (Table I order)
+constexpr int MAX_DSMC = 3 * MAX_GAS_CH;
+struct DsmcCh {
+    int sp;        // projectile species
+    int j;         // index in the species' channel list (SpeciesC::ch)
+    int reaction;
+    int pad;
+};
+
 struct Disc {
     int N;                   // cells
     int gbase;               // first node of this discharge in grid arrays
@@ -146,6 +156,9 @@ struct Disc {
     unsigned long long seed;
     int discharge;
     int cx_iso;
+    int gas_scheme;          // 0 null collision, 1 the sequential channel list every n1 steps
+    int ndsmc;               // gas channels of the sequential list
+    DsmcCh dsmc[MAX_DSMC];   // in the order of Table I
     SpeciesC sp[NSP];
     PairC pair[3];           // 13, 14, 19
 };

@@ -114,6 +114,18 @@ bool validate(const pic_config *c, int D, const pic_xs_table *xs, int n_xs, std:
             why = "n2 must be >= 0 and coulomb_log > 0 when n2 > 0";
             return false;
         }
+        if (q.gas_scheme != 0 && q.gas_scheme != 1) {
+            why = "gas_scheme must be 0 (null collision) or 1 (sequential list)";
+            return false;
+        }
+        if (q.gas_scheme == 1 && q.n1 <= 0) {
+            why = "the sequential gas scheme (gas_scheme = 1) needs n1 > 0";
+            return false;
+        }
+        if (q.gas_scheme != c[0].gas_scheme) {
+            why = "all discharges of one handle must share gas_scheme";
+            return false;
+        }
         if (q.precision != PIC_FP64 && q.precision != PIC_FP32_MIXED) {
             why = "precision must be PIC_FP64 or PIC_FP32_MIXED";
             return false;
@@ -378,13 +390,13 @@ struct pic_handle {
     bool graph_failed = false;
     // timing
     bool timing = false;
-    double kms[2] = {0.0, 0.0};        // device ms per timed kernel kind (push, Coulomb)
-    long long kl[2] = {0, 0};          // timed launches per kind
+    double kms[3] = {0.0, 0.0, 0.0};   // device ms per timed kernel kind (push, Coulomb, sequential gas)
+    long long kl[3] = {0, 0, 0};       // timed launches per kind
     long long launches = 0;
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kind;          // kind of each event pair
     int ev_used = 0;
-    unsigned long long slots0 = 0, cands0 = 0, bslots0 = 0, bcands0 = 0, coul0 = 0;
+    unsigned long long slots0 = 0, cands0 = 0, bslots0 = 0, bcands0 = 0, coul0 = 0, dsmc0 = 0;
     const void *pools() const { return fp64 ? (const void *)&Pd : (const void *)&Pf; }
 };
 
@@ -476,6 +488,7 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
     D.seed = q.seed;
     D.discharge = d;
     D.cx_iso = q.cx_isotropic;
+    D.gas_scheme = q.gas_scheme;
     const double ngas = q.p_Pa / (KB * q.T_gas_K);
     for (int s = 0; s < 3; ++s) {
         SpeciesC &S = D.sp[s];
@@ -547,6 +560,7 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
             const double pb = 1.0 - std::exp(-nu * q.dt_s);
             const double tb = std::ceil(pb * 4294967296.0 - 0.5);
             nb.tnull = tb <= 0.0 ? 0u : (tb >= 4294967295.0 ? 0xFFFFFFFFu : (unsigned)tb);
+            if (q.gas_scheme == 1) nb.tnull = 0u;  // no null-collision candidates
             nb.numax_n = nu * q.dt_s;
             nb.numax_n_f = (float)nb.numax_n;
         }
@@ -554,6 +568,7 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
         const double pnull = 1.0 - std::exp(-S.numax * q.dt_s);
         const double thr = std::ceil(pnull * 4294967296.0 - 0.5);
         S.tnull = thr <= 0.0 ? 0u : (thr >= 4294967295.0 ? 0xFFFFFFFFu : (unsigned)thr);
+        if (q.gas_scheme == 1) S.tnull = 0u;  // no null-collision candidates
         S.qm_f = (float)S.qm;
         S.numax_n_f = (float)S.numax_n;
         S.vgas_n_f = (float)S.vgas_n;
@@ -564,6 +579,16 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
         S.coul_k_f = (float)S.coul_k;
         h->numax[3 * d + s] = S.numax;
     }
+    // the sequential scheme's list: gas channels in the order of Table I
+    // (reaction number, then table order)
+    D.ndsmc = 0;
+    for (int r = 4; r <= 18; ++r)
+        for (size_t ti = 0; ti < h->tabs.size(); ++ti) {
+            if (h->tabs[ti].reaction != r) continue;
+            for (int s = 0; s < 3; ++s)
+                for (int j = 0; j < D.sp[s].nch; ++j)
+                    if (D.sp[s].ch[j].table == (int)ti && D.ndsmc < MAX_DSMC) D.dsmc[D.ndsmc++] = DsmcCh{s, j, r, 0};
+        }
     const int rx[3] = {13, 14, 19};
     for (int k = 0; k < 3; ++k) {
         PairC &P = D.pair[k];
@@ -896,7 +921,26 @@ static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool timed)
         ++nk;
         if ((e = time_close(h, timed, st, 1))) return e;
     }
-    if (pair) {
+    if (pair && q.gas_scheme == 1) {
+        // the sequential scheme (R22): gas channels below (13), (13), (14),
+        // gas channels above (14), their births, a new sort, (19)
+        if ((e = launch_retile(h->W, par, st))) return e;
+        if ((e = time_open(h, timed, st))) return e;
+        if ((e = launch_dsmc(h->fp64, h->W, h->pools(), par, 0, st))) return e;
+        if ((e = time_close(h, timed, st, 2))) return e;
+        if ((e = launch_pair_reaction(h->fp64, h->W, h->pools(), par, 0, st))) return e;
+        if ((e = launch_pair_reaction(h->fp64, h->W, h->pools(), par, 1, st))) return e;
+        if ((e = time_open(h, timed, st))) return e;
+        if ((e = launch_dsmc(h->fp64, h->W, h->pools(), par, 1, st))) return e;
+        if ((e = time_close(h, timed, st, 2))) return e;
+        if ((e = launch_births(h->fp64, h->W, h->pools(), par, h->W.max_chunks / TILE_ALIGN + 1, st, 1))) return e;
+        if ((e = launch_sort(h->fp64, h->W, h->pools(), h->sort_tab, h->L, st))) return e;
+        // the kill counts of (13), (14) refer to the cells before the sort
+        if ((e = cudaMemsetAsync(h->W.pair_kills, 0, sizeof(int) * NSP * (size_t)h->W.total_cells, st))) return e;
+        if ((e = launch_pair_reaction(h->fp64, h->W, h->pools(), par, 2, st))) return e;
+        if ((e = launch_pair_append(h->fp64, h->W, h->pools(), h->L, st))) return e;
+        nk += 1 + 2 + 2 * 3 + 1 + kernels_per_sort() + 1;
+    } else if (pair) {
         e = launch_pair(h->fp64, h->W, h->pools(), par, h->L, st);
         if (e) return e;
         nk += kernels_per_pair();
@@ -988,7 +1032,7 @@ extern "C" pic_status pic_step(pic_handle *h, long long n_steps)
             continue;
         }
         int nk = 0;
-        if (h->timing && h->ev_used + 4 > (int)h->ev.size()) {
+        if (h->timing && h->ev_used + 8 > (int)h->ev.size()) {
             pic_status s = harvest_events(h);
             if (s != PIC_OK) return s;
         }
@@ -1087,7 +1131,8 @@ extern "C" pic_status pic_diagnostics(pic_handle *h, int d, double *dens_sum, do
         counters[33] = (long long)c[C_CANDS];
         counters[34] = (long long)c[C_SLOTS];
         counters[35] = (long long)c[C_COUL];
-        for (int k = 36; k < 40; ++k) counters[k] = 0;
+        counters[36] = (long long)c[C_DSMC];
+        for (int k = 37; k < 40; ++k) counters[k] = 0;
     }
     if (n_samples) *n_samples = (long long)ns;
     if (reset) {
@@ -1292,22 +1337,28 @@ extern "C" pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, l
         long long all = 0;
         return pic_timing(h, ms, launches, &all, bytes, reset);
     }
-    if (kernel != PIC_KERNEL_COULOMB) return fail(h, PIC_EINVAL, "unknown kernel kind");
+    if (kernel != PIC_KERNEL_COULOMB && kernel != PIC_KERNEL_SEQUENTIAL_GAS)
+        return fail(h, PIC_EINVAL, "unknown kernel kind");
     std::vector<unsigned long long> c((size_t)h->D * C_NCOUNT);
     CK(cudaMemcpyAsync(c.data(), h->W.counters, 8 * c.size(), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    unsigned long long coul = 0;
-    for (int d = 0; d < h->D; ++d) coul += c[(size_t)d * C_NCOUNT + C_COUL];
-    // algorithmic bytes of the Coulomb pass: vx, vy, vz read and written for
-    // every particle of a cell holding at least two of its species
+    const int slot = kernel == PIC_KERNEL_COULOMB ? C_COUL : C_DSMC;
+    unsigned long long units = 0;
+    for (int d = 0; d < h->D; ++d) units += c[(size_t)d * C_NCOUNT + slot];
+    unsigned long long &base = kernel == PIC_KERNEL_COULOMB ? h->coul0 : h->dsmc0;
+    // algorithmic bytes.  Coulomb pass: vx, vy, vz read and written for every
+    // particle of a cell holding at least two of its species.  Sequential gas
+    // scheme: per live slot and part, cell and offset read, vx, vy, vz read
+    // and written
     const double R = h->fp64 ? 8.0 : 4.0;
-    if (ms) *ms = h->kms[1];
-    if (launches) *launches = h->kl[1];
-    if (bytes) *bytes = (double)(coul - h->coul0) * 6.0 * R;
+    const double per = kernel == PIC_KERNEL_COULOMB ? 6.0 * R : 4.0 + 7.0 * R;
+    if (ms) *ms = h->kms[kernel];
+    if (launches) *launches = h->kl[kernel];
+    if (bytes) *bytes = (double)(units - base) * per;
     if (reset) {
-        h->kms[1] = 0.0;
-        h->kl[1] = 0;
-        h->coul0 = coul;
+        h->kms[kernel] = 0.0;
+        h->kl[kernel] = 0;
+        base = units;
     }
     return PIC_OK;
 }

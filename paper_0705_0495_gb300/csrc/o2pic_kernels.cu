@@ -121,6 +121,8 @@ __device__ int block_scan_exclusive_int(int *a, int M, int *wsum)
 // is solved exactly by two prefix sums: with s_i = rho_i dx^2/eps0,
 // S1_i = sum_{k<=i} s_k and S2_i = sum_{m<=i} S1_m (i >= 1),
 // phi_i = phi_0 + i D0 - S2_{i-1}, D0 fixed by phi_N = 0.
+__device__ void tile_table(const WsPtrs &W, int par, unsigned long long step, bool advance);
+
 template <typename Real>
 __global__ void __launch_bounds__(FIELD_THREADS)
 k_field(WsPtrs W, int par, int diag, int mode)
@@ -329,6 +331,19 @@ k_field(WsPtrs W, int par, int diag, int mode)
     if (mode != 0 || blockIdx.x != 0) return;
     // block 0: tile table of this step's push and the step counter
     __syncthreads();
+    tile_table(W, par, step, true);
+}
+
+// Tile table of the current counts: tiles of each discharge start at a
+// multiple of TILE_ALIGN, so that the birth-append blocks (BIRTHS_THREADS
+// sub-tiles) never span two, and those of each species at a multiple of
+// TILES_PER_TICKET, so that a push ticket never spans two; the birth counts
+// of the padding tiles after each species (never pushed) are cleared.  With
+// `advance` the next step's counter is set and the candidate list emptied.
+__device__ void tile_table(const WsPtrs &W, int par, unsigned long long step, bool advance)
+{
+    Ctl *ctl = W.ctl;
+    const int tid = threadIdx.x;
     if (tid == 0) {
         // tiles of each discharge start at a multiple of TILE_ALIGN, so that the
         // birth-append blocks (BIRTHS_THREADS sub-tiles) never span two, and
@@ -351,18 +366,25 @@ k_field(WsPtrs W, int par, int diag, int mode)
         ctl->total_chunks = chunk;
         ctl->ticket = 0u;
         ctl->births_ticket = 0u;
-        ctl->cand_n = 0u;
-        ctl->step[par ^ 1] = step + 1ull;
+        if (advance) {
+            ctl->cand_n = 0u;
+            ctl->step[par ^ 1] = step + 1ull;
+        }
     }
     __syncthreads();
-    // birth counts of the padding tiles after each species (never pushed)
     for (int ds = 0; ds < W.D * NSP; ++ds) {
         const Counts &C = W.cnt[ds];
         const int t0 = C.chunk0 + C.nchunk;
         const int t1 = (t0 + TILES_PER_TICKET - 1) / TILES_PER_TICKET * TILES_PER_TICKET;
         const int n = (t1 - t0) * SUBTILES * NSP;
-        for (int k = tid; k < n; k += FIELD_THREADS) W.tile_cnt[(size_t)t0 * SUBTILES * NSP + k] = 0;
+        for (int k = tid; k < n; k += blockDim.x) W.tile_cnt[(size_t)t0 * SUBTILES * NSP + k] = 0;
     }
+}
+
+__global__ void __launch_bounds__(256) k_retile(WsPtrs W, int par)
+{
+    pdl_wait();
+    tile_table(W, par, 0ull, false);
 }
 
 // ------------------------------------------------------------- sort
@@ -1376,28 +1398,46 @@ cudaError_t launch_coulomb(bool fp64, const WsPtrs &W, const void *pools, int pa
 }
 
 
-cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par, const LaunchCfg &L,
-                        cudaStream_t st)
+cudaError_t launch_pair_reaction(bool fp64, const WsPtrs &W, const void *pools, int par, int k, cudaStream_t st)
 {
     const int fix_blocks = (W.total_cells * 32 + 255) / 256;
     const int eval_blocks = (W.total_cells + 255) / 256;
-    for (int k = 0; k < 3; ++k) {
-        if (fp64) {
-            const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
-            launch_k(k_pair_eval<double>, eval_blocks, 256, 0, st, W, P, par, k);
-            launch_k(k_pair_fix<double>, fix_blocks, 256, 0, st, W, P, par, k);
-        } else {
-            const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
-            launch_k(k_pair_eval<float>, eval_blocks, 256, 0, st, W, P, par, k);
-            launch_k(k_pair_fix<float>, fix_blocks, 256, 0, st, W, P, par, k);
-        }
+    if (fp64) {
+        const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
+        launch_k(k_pair_eval<double>, eval_blocks, 256, 0, st, W, P, par, k);
+        launch_k(k_pair_fix<double>, fix_blocks, 256, 0, st, W, P, par, k);
+    } else {
+        const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
+        launch_k(k_pair_eval<float>, eval_blocks, 256, 0, st, W, P, par, k);
+        launch_k(k_pair_fix<float>, fix_blocks, 256, 0, st, W, P, par, k);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_append(bool fp64, const WsPtrs &W, const void *pools, const LaunchCfg &L, cudaStream_t st)
+{
     if (fp64)
         launch_k(k_pair_append<double>, W.D, 256, sizeof(int) * (L.maxN + 1), st, W,
                  *static_cast<const Pools<double> *>(pools));
     else
         launch_k(k_pair_append<float>, W.D, 256, sizeof(int) * (L.maxN + 1), st, W,
                  *static_cast<const Pools<float> *>(pools));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par, const LaunchCfg &L,
+                        cudaStream_t st)
+{
+    for (int k = 0; k < 3; ++k) {
+        const cudaError_t e = launch_pair_reaction(fp64, W, pools, par, k, st);
+        if (e) return e;
+    }
+    return launch_pair_append(fp64, W, pools, L, st);
+}
+
+cudaError_t launch_retile(const WsPtrs &W, int par, cudaStream_t st)
+{
+    launch_k(k_retile, 1, 256, 0, st, W, par);
     return cudaGetLastError();
 }
 

@@ -51,8 +51,16 @@ cudaError_t launch_push(bool fp64, bool diag, const WsPtrs &W, const void *pools
 cudaError_t push_configure(bool fp64, LaunchCfg &L, int num_sms);
 // births of the push appended in parent order
 cudaError_t launch_collide(bool fp64, const WsPtrs &W, const void *pools, int par, int blocks, cudaStream_t st);
+// salt: 0 for the append after the collisions, 1 for the one after the
+// sequential gas scheme in the same step
 cudaError_t launch_births(bool fp64, const WsPtrs &W, const void *pools, int par, int max_blocks,
-                          cudaStream_t s);
+                          cudaStream_t s, int salt = 0);
+// the sequential gas scheme, part 0 (channels below (13)) or 1 (above (14))
+constexpr int DSMC_THREADS = 256;
+cudaError_t launch_dsmc(bool fp64, const WsPtrs &W, const void *pools, int par, int part, cudaStream_t st);
+// tile table of the current particle counts (after a sort), for the
+// sequential scheme and its birth append
+cudaError_t launch_retile(const WsPtrs &W, int par, cudaStream_t st);
 
 // charge density -> Poisson -> field; per-step bookkeeping (mode 0), or a
 // read-only evaluation of the fields of the current state (mode 1)
@@ -75,6 +83,12 @@ size_t coulomb_smem_bytes(bool fp64);
 cudaError_t launch_coulomb(bool fp64, const WsPtrs &W, const void *pools, int par, cudaStream_t st);
 cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par,
                         const LaunchCfg &L, cudaStream_t s);
+// one reaction of the particle-target pass (k = 0, 1, 2 for (13), (14),
+// (19)), and the append of (19)'s births
+cudaError_t launch_pair_reaction(bool fp64, const WsPtrs &W, const void *pools, int par, int k,
+                                 cudaStream_t s);
+cudaError_t launch_pair_append(bool fp64, const WsPtrs &W, const void *pools, const LaunchCfg &L,
+                               cudaStream_t s);
 cudaError_t launch_load(bool fp64, const WsPtrs &W, const void *pools, const long long *d_ninit,
                         const double *d_vt, int max_n, cudaStream_t s);
 cudaError_t launch_deposit_all(bool fp64, const WsPtrs &W, const void *pools, int disc,

@@ -241,6 +241,82 @@ struct Outcome {
     int reaction;   // reaction number, -1 for a null event
 };
 
+// Products of one gas event: species, product index (the tag's product
+// bit) and velocity
+template <typename Real>
+struct GasProducts {
+    int n;
+    int sp[2], prod[2];
+    Real v[2][3];
+};
+
+// Kinematics of gas channel ch for a particle of species s with velocity v
+// that meets a gas molecule of velocity V at centre-of-mass energy E; nd is
+// an isotropic direction, nd2 a second one used by (18).  Returns whether
+// the particle lives on (with velocity vo) and its products.  One centre-of-
+// mass scattering serves every channel that scatters: elastic (4), (5),
+// isotropic (6) with no loss, (7)-(12) and (18) with the loss of Eq. 5; its
+// result is unused by (15)-(17) and resonant (6).
+template <typename Real>
+__device__ __forceinline__ bool gas_event(const WsPtrs &W, const Disc &Dd, const SpeciesC &S, const GasChan &ch,
+                                          const Real v[3], const Real V[3], Real E, const Real nd[3],
+                                          const Real nd2[3], Real vo[3], GasProducts<Real> &pr)
+{
+    const int r = ch.reaction;
+    const Real mf = pick<Real>(S.mfrac, S.mfrac_f), Mf = pick<Real>(S.Mfrac, S.Mfrac_f);
+    const bool elastic = r <= 6;
+    const bool dies = r >= 15 && r <= 17;
+    Real Vo[3];
+    cm_scatter<Real>(mf, Mf, v, V, elastic ? Real(0) : pick<Real>(ch.dloss, ch.dloss_f), nd, vo, Vo);
+    const bool swap = r == 6 && !Dd.cx_iso;  // resonant exchange: the ion takes the gas velocity
+#pragma unroll
+    for (int q = 0; q < 3; ++q) vo[q] = swap ? V[q] : vo[q];
+    pr.n = 0;
+    if (r == 18) {
+        // ionisation: the O2 splits into O2+ and a second electron with the
+        // post-collision O2 velocity, then the two electrons collide
+        // elastically (isotropic in their centre of mass)
+        Real e2[3] = {Vo[0], Vo[1], Vo[2]};
+        ee_elastic<Real>(vo, e2, nd2);
+        pr.n = 2;
+        pr.sp[0] = 0;
+        pr.prod[0] = 0;
+        pr.sp[1] = 2;
+        pr.prod[1] = 1;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            pr.v[0][q] = e2[q];
+            pr.v[1][q] = Vo[q];
+        }
+    }
+    if (!dies) return true;
+    // (15) attachment: O- with the CM velocity plus half the relative
+    // energy above threshold shared back to back with O; (16) detachment:
+    // electron with a tenth of the O- energy, isotropic; (17) associative
+    // detachment: electron with the CM energy about the CM velocity
+    Real w;
+    if (r == 16) {
+        w = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * pick<Real>(Dd.f16, Dd.f16_f);
+    } else {
+        Real arg;
+        if (r == 15) {
+            const TableDesc &Tc = W.tables[ch.table];
+            const Real Ea = E - pick<Real>(Tc.th, Tc.th_f);
+            arg = (Ea > Real(0) ? Ea : Real(0)) * pick<Real>(Dd.f15, Dd.f15_f);
+        } else {
+            arg = E * pick<Real>(Dd.f17, Dd.f17_f);
+        }
+        w = sqrt(arg);
+    }
+    const Real A = r == 16 ? Real(0) : Real(1);
+    pr.n = 1;
+    pr.sp[0] = r == 15 ? 1 : 0;
+    pr.prod[0] = 0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) pr.v[0][q] = A * (mf * v[q] + Mf * V[q]) + w * nd[q];
+    return false;
+}
+
 template <typename Real>
 __device__ __forceinline__ Outcome gas_collide(const WsPtrs &W, const Disc &Dd, int s, unsigned idx,
                                             unsigned long long step, Real numax_n, Real &vx, Real &vy,
@@ -292,59 +368,20 @@ __device__ __forceinline__ Outcome gas_collide(const WsPtrs &W, const Disc &Dd, 
     if (chosen < 0) return Outcome{true, viol, -1};  // null event
     const GasChan &ch = S.ch[chosen];
     const int r = ch.reaction;
-    Real nd[3];
+    Real nd[3], nd2[3] = {Real(0), Real(0), Real(1)};
     iso_dir<Real>(unif<Real>(b.y), unif<Real>(b.z), nd);
-    const Real mf = pick<Real>(S.mfrac, S.mfrac_f), Mf = pick<Real>(S.Mfrac, S.Mfrac_f);
-    // one centre-of-mass scattering serves every channel that scatters:
-    // elastic (4), (5), isotropic (6) with no loss, (7)-(12) and (18) with
-    // the loss of Eq. 5; its result is unused by (15)-(17) and resonant (6)
-    const bool elastic = r <= 6;
-    const bool dies = r >= 15 && r <= 17;
-    Real vo[3], Vo[3];
-    cm_scatter<Real>(mf, Mf, v, V, elastic ? Real(0) : pick<Real>(ch.dloss, ch.dloss_f), nd, vo, Vo);
-    const bool swap = r == 6 && !Dd.cx_iso;  // resonant exchange: the ion takes the gas velocity
-#pragma unroll
-    for (int q = 0; q < 3; ++q) vo[q] = swap ? V[q] : vo[q];
     if (r == 18) {
-        // ionisation: the O2 splits into O2+ and a second electron with the
-        // post-collision O2 velocity, then the two electrons collide
-        // elastically (isotropic in their centre of mass)
         uint4 e = rng_block(Dd.seed, Dd.discharge, s, 1, 0, 2, step, idx);
-        Real n2v[3];
-        iso_dir<Real>(unif<Real>(e.x), unif<Real>(e.y), n2v);
-        Real e2[3] = {Vo[0], Vo[1], Vo[2]};
-        ee_elastic<Real>(vo, e2, n2v);
-        stage_birth<Real>(B, tag, 0, c, off, e2);
-        stage_birth<Real>(B, tag | 1, 2, c, off, Vo);
+        iso_dir<Real>(unif<Real>(e.x), unif<Real>(e.y), nd2);
     }
-    if (!dies) {
+    GasProducts<Real> pr;
+    Real vo[3];
+    const bool alive = gas_event<Real>(W, Dd, S, ch, v, V, E, nd, nd2, vo, pr);
+    for (int q = 0; q < pr.n; ++q) stage_birth<Real>(B, tag | pr.prod[q], pr.sp[q], c, off, pr.v[q]);
+    if (alive) {
         vx = vo[0]; vy = vo[1]; vz = vo[2];
-        return Outcome{true, viol, r};
     }
-    // (15) attachment: O- with the CM velocity plus half the relative
-    // energy above threshold shared back to back with O; (16) detachment:
-    // electron with a tenth of the O- energy, isotropic; (17) associative
-    // detachment: electron with the CM energy about the CM velocity
-    Real w;
-    if (r == 16) {
-        w = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * pick<Real>(Dd.f16, Dd.f16_f);
-    } else {
-        Real arg;
-        if (r == 15) {
-            const TableDesc &Tc = W.tables[ch.table];
-            const Real Ea = E - pick<Real>(Tc.th, Tc.th_f);
-            arg = (Ea > Real(0) ? Ea : Real(0)) * pick<Real>(Dd.f15, Dd.f15_f);
-        } else {
-            arg = E * pick<Real>(Dd.f17, Dd.f17_f);
-        }
-        w = sqrt(arg);
-    }
-    const Real A = r == 16 ? Real(0) : Real(1);
-    Real pv[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) pv[q] = A * (mf * v[q] + Mf * V[q]) + w * nd[q];
-    stage_birth<Real>(B, tag, r == 15 ? 1 : 0, c, off, pv);
-    return Outcome{false, viol, r};
+    return Outcome{alive, viol, r};
 }
 
 template <typename Acc> __device__ __forceinline__ void acc_add(Acc *a, Acc v);
@@ -842,6 +879,125 @@ k_collide(WsPtrs W, Pools<Real> P, int par)
     }
 }
 
+// The paper's sequential scheme for the gas channels (Sec. II, Eq. 1),
+// every n1 steps after the sort: part 0 walks the gas channels of the list
+// numbered below (13), part 1 those above (14).  One block per tile of the
+// table rebuilt after the sort, four slots per thread.  A particle meets the
+// channels of its species in list order; channel k takes place with P =
+// n sigma(E) u n1 dt (clamped at 1 and counted) against a gas molecule drawn
+// from the Maxwellian; one that dies in (15), (16) or (17) is replaced by
+// its product, which meets the later channels ("readmitted").  Random
+// numbers: stream 6 of the chain's first particle, sub-stream k, draws 4g,
+// 4g + 1, 4g + 2 in generation g.  Products are recorded in the first
+// particle's sub-tile: (18)'s with product bits 0 (electron) and 1 (O2+),
+// the one that ends a chain with bit 1.
+template <typename Real>
+__global__ void __launch_bounds__(DSMC_THREADS)
+k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
+{
+    pdl_wait();
+    using Acc = typename AccT<Real>::T;
+    __shared__ unsigned s_ev[C_NCOUNT];
+    Ctl *ctl = W.ctl;
+    const int chunk = blockIdx.x;
+    if (chunk >= ctl->total_chunks) return;
+    int lo = 0, hi = W.D * NSP;  // (discharge, species) of the tile
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (W.cnt[mid].chunk0 <= chunk) lo = mid; else hi = mid;
+    }
+    const int ds = lo;
+    const Counts &C = W.cnt[ds];
+    if (chunk >= C.chunk0 + C.nchunk) return;  // padding between species
+    const int d = ds / NSP, s = ds % NSP;
+    const Disc &Dd = W.disc[d];
+    for (int q = threadIdx.x; q < C_NCOUNT; q += DSMC_THREADS) s_ev[q] = 0;
+    if (part == 1 && threadIdx.x < SUBTILES) W.tile_cnt[(size_t)(chunk * SUBTILES + threadIdx.x) * NSP] = 0;
+    __syncthreads();
+    const unsigned long long step = ctl->step[par];
+    const int cur = ctl->cur;
+    int *cellA = P.cell[cur];
+    Real *offA = P.off[cur], *vxA = P.vx[cur], *vyA = P.vy[cur], *vzA = P.vz[cur];
+    BirthRec<Real> *stage = reinterpret_cast<BirthRec<Real> *>(W.births);
+    const Real *lutE = Lut<Real>::E(W);
+    const Real n1 = Real(Dd.n1);
+    for (int k4 = 0; k4 < CHUNK / DSMC_THREADS; ++k4) {
+        const int local = threadIdx.x + k4 * DSMC_THREADS;
+        const int rel = (chunk - C.chunk0) * CHUNK + local;
+        if (rel >= C.n) break;
+        const int i = Dd.pbase[s] + rel;
+        const int c = cellA[i];
+        if (c < 0) continue;
+        atomicAdd(&s_ev[C_DSMC], 1u);
+        const Real off = offA[i];
+        Real v[3] = {vxA[i], vyA[i], vzA[i]};
+        int cs = s, gen = 0;
+        const int sub = chunk * SUBTILES + local / SUBTILE;
+        const int tag = (local % SUBTILE) << 1;
+        const BirthSink<Real> B{stage + (size_t)sub * BIRTH_CAP_W, W.tile_cnt + (size_t)sub * NSP, ctl};
+        for (int kk = 0; kk < Dd.ndsmc; ++kk) {
+            const DsmcCh &e = Dd.dsmc[kk];
+            if (e.sp != cs || (part == 0 ? e.reaction > 12 : e.reaction < 15)) continue;
+            const SpeciesC &S = Dd.sp[cs];
+            const GasChan &ch = S.ch[e.j];
+            const uint4 a = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen, step, (unsigned)rel);
+            const uint4 b = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen + 1u, step, (unsigned)rel);
+            Real n0, nn1, n2, n3;
+            box_muller<Real>(a.x, a.y, n0, nn1);
+            box_muller<Real>(a.z, a.w, n2, n3);
+            const Real vg = pick<Real>(S.vgas_n, S.vgas_n_f);
+            const Real V[3] = {vg * n0, vg * nn1, vg * n2};
+            const Real g0 = v[0] - V[0], g1 = v[1] - V[1], g2 = v[2] - V[2];
+            const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
+            const Real u = sqrt(u2);
+            const Real E = pick<Real>(S.Ek, S.Ek_f) * u2;
+            // n_j dx sigma_j(E) from the species' node-major table
+            const XsPoint<Real> pt = xs_locate<Real>(W.tables[S.table_lo], lutE, E);
+            const Real *ra = GasTab<Real>::ptr(W) + S.gtab_off + (size_t)pt.k * S.gtab_ld;
+            const Real xa = ra[e.j], xb = ra[S.gtab_ld + e.j];
+            Real xs = pt.region == 2 ? xb : xa + pt.f * (xb - xa);
+            xs = E < pick<Real>(ch.th, ch.th_f) ? Real(0) : xs;
+            Real Pj = xs * u * n1;
+            if (Pj > Real(1)) {
+                atomicAdd(&s_ev[C_VIOL_PAIR], 1u);
+                Pj = Real(1);
+            }
+            if (!(unif<Real>(b.x) < Pj)) continue;
+            atomicAdd(&s_ev[C_EVENTS + ch.reaction], 1u);
+            Real nd[3], nd2[3] = {Real(0), Real(0), Real(1)};
+            iso_dir<Real>(unif<Real>(b.y), unif<Real>(b.z), nd);
+            if (ch.reaction == 18) {
+                const uint4 e2 = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen + 2u, step, (unsigned)rel);
+                iso_dir<Real>(unif<Real>(e2.x), unif<Real>(e2.y), nd2);
+            }
+            GasProducts<Real> pr;
+            Real vo[3];
+            if (gas_event<Real>(W, Dd, S, ch, v, V, E, nd, nd2, vo, pr)) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) v[q] = vo[q];
+                for (int q = 0; q < pr.n; ++q) stage_birth<Real>(B, tag | pr.prod[q], pr.sp[q], c, off, pr.v[q]);
+            } else {
+                cs = pr.sp[0];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) v[q] = pr.v[0][q];
+                ++gen;
+            }
+        }
+        if (gen == 0) {
+            vxA[i] = v[0];
+            vyA[i] = v[1];
+            vzA[i] = v[2];
+        } else {
+            cellA[i] = -1;
+            deposit_global(acc_global<Real>(W) + (size_t)s * W.total_nodes + Dd.gbase, c, off, -1);
+            stage_birth<Real>(B, tag | 1, cs, c, off, v);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < C_NCOUNT; k += DSMC_THREADS)
+        if (s_ev[k]) atomicAdd(&W.counters[(size_t)d * C_NCOUNT + k], (unsigned long long)s_ev[k]);
+}
+
 // Births of one step appended after the survivors, per discharge and
 // product species in tile order (tiles are numbered in (parent species,
 // slot) order), i.e. in parent order; their charge is deposited.  Each block
@@ -862,7 +1018,7 @@ __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned l
 
 template <typename Real>
 __global__ void __launch_bounds__(BIRTHS_THREADS)
-k_births(WsPtrs W, Pools<Real> P, int par)
+k_births(WsPtrs W, Pools<Real> P, int par, int salt)
 {
     pdl_wait();
     using Acc = typename AccT<Real>::T;
@@ -932,7 +1088,9 @@ k_births(WsPtrs W, Pools<Real> P, int par)
     // the aggregates of the blocks in between)
     if (warp < NSP) {
         const int q = warp;
-        const unsigned long long epoch = (ctl->step[par] + 1ull) & 0xFFFFFFFFull;
+        // look-back words carry the step and which append of the step wrote
+        // them (0 after the collisions, 1 after the sequential gas scheme)
+        const unsigned long long epoch = (((ctl->step[par] + 1ull) << 1) | (unsigned)salt) & 0xFFFFFFFFull;
         const int first_blk = W.cnt[d * NSP].chunk0 * SUBTILES / BIRTHS_THREADS;
         unsigned long long *lb = W.births_lb + (size_t)blk * NSP + q;
         const unsigned own = (unsigned)s_tot[q];
@@ -1084,12 +1242,25 @@ cudaError_t launch_collide(bool fp64, const WsPtrs &W, const void *pools, int pa
 }
 
 cudaError_t launch_births(bool fp64, const WsPtrs &W, const void *pools, int par, int max_blocks,
-                          cudaStream_t st)
+                          cudaStream_t st, int salt)
 {
     if (fp64)
-        launch_k(k_births<double>, max_blocks, BIRTHS_THREADS, 0, st, W, *static_cast<const Pools<double> *>(pools), par);
+        launch_k(k_births<double>, max_blocks, BIRTHS_THREADS, 0, st, W, *static_cast<const Pools<double> *>(pools), par,
+                 salt);
     else
-        launch_k(k_births<float>, max_blocks, BIRTHS_THREADS, 0, st, W, *static_cast<const Pools<float> *>(pools), par);
+        launch_k(k_births<float>, max_blocks, BIRTHS_THREADS, 0, st, W, *static_cast<const Pools<float> *>(pools), par,
+                 salt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dsmc(bool fp64, const WsPtrs &W, const void *pools, int par, int part, cudaStream_t st)
+{
+    if (fp64)
+        launch_k(k_dsmc<double>, W.max_chunks, DSMC_THREADS, 0, st, W, *static_cast<const Pools<double> *>(pools), par,
+                 part);
+    else
+        launch_k(k_dsmc<float>, W.max_chunks, DSMC_THREADS, 0, st, W, *static_cast<const Pools<float> *>(pools), par,
+                 part);
     return cudaGetLastError();
 }
 

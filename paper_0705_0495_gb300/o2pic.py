@@ -43,7 +43,8 @@ class pic_config(C.Structure):
         ("n_init", C.c_longlong * 3), ("capacity", C.c_longlong * 3), ("seed", C.c_ulonglong),
         ("n_cells", C.c_int), ("n1", C.c_int), ("sort_interval", C.c_int), ("diag_every", C.c_int),
         ("eedf_bins", C.c_int), ("iedf_bins", C.c_int), ("fm_bins", C.c_int), ("fm_xbins", C.c_int),
-        ("cx_isotropic", C.c_int), ("numax_bins", C.c_int), ("n2", C.c_int), ("precision", C.c_int),
+        ("cx_isotropic", C.c_int), ("numax_bins", C.c_int), ("n2", C.c_int), ("gas_scheme", C.c_int),
+        ("precision", C.c_int),
         ("coulomb_log", C.c_double),
     ]
 
@@ -52,7 +53,7 @@ EXPORTS = ["pic_workspace_size", "pic_init", "pic_step", "pic_diagnostics", "pic
            "pic_set_state", "pic_set_step", "pic_fields", "pic_numax", "pic_set_timing",
            "pic_timing", "pic_kernel_timing", "pic_destroy", "pic_last_error",
            "pic_field_solve_static"]
-KERNELS = {"push": 0, "coulomb": 1}
+KERNELS = {"push": 0, "coulomb": 1, "sequential_gas": 2}
 
 _lib = None
 
@@ -131,6 +132,7 @@ def make_config(d: "_inputs.Discharge", fp64: bool | None = None) -> pic_config:
     c.numax_bins = int(d.numax_bins)
     c.n2 = int(d.n2)
     c.coulomb_log = float(d.coulomb_log)
+    c.gas_scheme = int(d.gas_scheme)
     use64 = d.fp64 if fp64 is None else fp64
     c.precision = PIC_FP64 if use64 else PIC_FP32_MIXED
     return c
@@ -258,7 +260,8 @@ class Simulation:
                 "events": cnt[6:26].copy(), "violations": cnt[26:28].copy(),
                 "slots": cnt[28:31].copy(), "steps": int(cnt[31]),
                 "particle_steps": int(cnt[32]), "candidates": int(cnt[33]),
-                "slots_visited": int(cnt[34]), "coulomb_particles": int(cnt[35])}
+                "slots_visited": int(cnt[34]), "coulomb_particles": int(cnt[35]),
+                "sequential_gas_slots": int(cnt[36])}
 
     def set_timing(self, on=True):
         self._check(self.lib.pic_set_timing(self.h, 1 if on else 0))
@@ -273,7 +276,7 @@ class Simulation:
 
     def kernel_timing(self, kernel, reset=False):
         """device ms, launches and algorithmic bytes of one kernel kind
-        ("push" or "coulomb") in timing mode"""
+        ("push", "coulomb" or "sequential_gas") in timing mode"""
         ms, bts, n = C.c_double(), C.c_double(), C.c_longlong()
         self._check(self.lib.pic_kernel_timing(self.h, KERNELS[kernel], C.byref(ms), C.byref(n),
                                                C.byref(bts), 1 if reset else 0))

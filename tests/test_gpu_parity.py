@@ -318,6 +318,45 @@ def test_fp32_coulomb_replay():
     assert flips <= 1e-4 * compared, (flips, compared)
 
 
+# ------------------------------------- the sequential gas scheme (R22)
+
+def _scaled_tables(factors):
+    tabs = inputs.xs_tables()
+    for t in tabs:
+        if t["reaction"] in factors:
+            t["sigma_m2"] = t["sigma_m2"] * factors[t["reaction"]]
+    return tabs
+
+
+def test_fp64_sequential_scheme_step_by_step():
+    d = inputs.cfg1(gas_scheme=1)
+    sim, orc, (ex, ev) = _run_pair(d, [1, 9, 10, 11, 20, 30, 60, 100])
+    assert ex < TOL64 and ev < TOL64, (ex, ev)
+    g, o = sim.diagnostics(0), orc.counters()
+    assert np.array_equal(g["events"], o["events"])
+    assert g["events"][4] > 0 and g["events"][6] > 0 and g["candidates"] == 0
+
+
+def test_fp64_sequential_scheme_chains_and_pair_events():
+    # attachment and both detachments scaled up so that chains (15) -> (16)
+    # or (17) -> (18) occur in a pass, and the particle-target reactions
+    # scaled up so that (19) meets the re-sorted cells with new particles
+    d = inputs.cfg1(n_op=6000, gas_scheme=1, U_rf=300.0)
+    tabs = _scaled_tables({15: 1e3, 16: 3e3, 17: 300.0, 13: 3e6, 14: 3e6, 19: 3e6})
+    sim, orc, (ex, ev) = _run_pair(d, [10, 20, 30, 40], tabs)
+    assert ex < TOL64 and ev < TOL64, (ex, ev)
+    g, o = sim.diagnostics(0), orc.counters()
+    assert np.array_equal(g["events"], o["events"])
+    assert all(g["events"][r] > 0 for r in (13, 14, 15, 16, 17, 19)), g["events"]
+
+
+def test_fp32_sequential_scheme_replay():
+    d = inputs.cfg1(fp64=False, gas_scheme=1)
+    compared, flips, worst = _replay(d, 30)
+    assert worst < TOL32, worst
+    assert flips <= 1e-4 * compared, (flips, compared)
+
+
 def test_fp64_empty_discharge():
     d = inputs.cfg1(n_op=0)
     sim, orc, _ = _run_pair(d, [5])
@@ -386,13 +425,14 @@ def test_fp32_replay_ragged_multi_tile_cfg2_geometry():
 
 # ------------------------------------------------- full-size, one step
 
-@pytest.mark.parametrize("name,n2", [("cfg2", 0), ("cfg4", 0), ("cfg4", 1)])
-def test_full_size_one_step_replay(name, n2):
+@pytest.mark.parametrize("name,n2,gas", [("cfg2", 0, 0), ("cfg4", 0, 0), ("cfg4", 1, 0), ("cfg4", 0, 1)])
+def test_full_size_one_step_replay(name, n2, gas):
     # full sizes in the bench's launch configuration: the GPU's loaded state
     # is handed to the oracle and both take one step (n2 = 1: with a Coulomb
-    # pass over every cell and species)
+    # pass over every cell and species; gas = 1: the sequential gas scheme,
+    # from step 9 so that the step ends with its pass)
     import dataclasses
-    d = dataclasses.replace(inputs.WORKLOADS[name](), n2=n2)
+    d = dataclasses.replace(inputs.WORKLOADS[name](), n2=n2, gas_scheme=gas)
     tabs = inputs.xs_tables()
     sim = _sim(d, tabs)
     orc = oracle.Oracle(d, tabs, load=False)
@@ -400,6 +440,9 @@ def test_full_size_one_step_replay(name, n2):
         st = sim.get_state(0, s)
         orc.set(s, st["x"], st["vx"], st["vy"], st["vz"], st["alive"])
         del st
+    if gas:
+        sim.set_step(d.n1 - 1)
+        orc.set_step(d.n1 - 1)
     sim.step(1)
     orc.step(1)
     compared = flips = cells = 0
