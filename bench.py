@@ -437,6 +437,14 @@ def run_ours(a, rank, world, local_rank):
         except Exception as ex:
             variants["coulomb"] = {"error": str(ex)}
         try:
+            sw = inputs.sweep_13p8()
+            variants["sweep_13p8"] = measure_variant(
+                "the 13.8 Pa sweep of Sec. IV: 7 discharges (2.5 cm, 128 cells, 75-300 V with C = 1/6, "
+                "150 V with C = 0), 2e4 O2+ + 2e4 e/O- superparticles each at load, Coulomb every 10 "
+                "steps, FP32 mixed, one launch per kernel for all", sw, 200, 2000)
+        except Exception as ex:
+            variants["sweep_13p8"] = {"error": str(ex)}
+        try:
             dq = _workload(a.workload, scale=a.scale)
             dq.gas_scheme = 1
             variants["sequential_gas"] = measure_variant(

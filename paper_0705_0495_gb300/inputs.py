@@ -272,4 +272,22 @@ def cfg3_sweep(total=30_000_000, seed=1, **kw) -> List[Discharge]:
     return out
 
 
+SWEEP_13P8_VOLTS = (75.0, 100.0, 150.0, 200.0, 250.0, 300.0)
+
+
+def sweep_13p8(n_op=20000, seed=1, fp64=False, rf_cycles=1000.0, **kw) -> List[Discharge]:
+    """The voltage sweep of Sec. IV (Fig. Central): L = 2.5 cm, p = 13.8 Pa,
+    f = 13.6 MHz, U = 75-300 V with C = 1/6, plus the discharge of Fig.
+    Profiles at 150 V without associative detachment (C = 0); 128 cells,
+    dt = T/1000, intra-species Coulomb collisions every 10 steps (kept in all
+    of the paper's runs), load n0 = 1e15 m^-3 with n_op O2+ superparticles and
+    room for the densities to grow sixteenfold."""
+    base = dict(L=0.025, n_cells=128, p_Pa=13.8, f_rf=13.6e6, steps_per_cycle=1000, n0_m3=1e15,
+                n_op=n_op, seed=seed, fp64=fp64, rf_cycles=rf_cycles, n2=10, capacity_factor=16.0)
+    base.update(kw)
+    out = [Discharge(U_rf=u, **base) for u in SWEEP_13P8_VOLTS]
+    out.append(Discharge(U_rf=150.0, **dict(base, C_delta=0.0)))
+    return out
+
+
 WORKLOADS = {"cfg1": cfg1, "cfg2": cfg2, "cfg4": cfg4, "cfg5": cfg5}

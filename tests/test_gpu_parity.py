@@ -380,6 +380,25 @@ def test_fp64_batched_discharges_each_match_their_oracle():
                 assert ex < TOL64 and ev < TOL64, (k, s, ex, ev)
 
 
+def test_fp64_sweep_13p8_batched_matches_oracles():
+    # the seven discharges of the 13.8 Pa sweep (75-300 V, and C = 0 at 150
+    # V) in one handle, with Coulomb collisions every 10 steps
+    ds = inputs.sweep_13p8(n_op=4000, fp64=True)
+    sim = _sim(ds)
+    tabs = inputs.xs_tables()
+    orcs = [oracle.Oracle(d, tabs, discharge=k) for k, d in enumerate(ds)]
+    for steps in (1, 10, 20, 30):
+        done = sim.diagnostics(0)["steps"]
+        sim.step(steps - done)
+        for k, d in enumerate(ds):
+            orcs[k].step(steps - done)
+            for s in range(3):
+                ex, ev = _cmp_slots(d, sim.get_state(k, s), orcs[k].get(s), s)
+                assert ex < TOL64 and ev < TOL64, (k, s, ex, ev)
+    for k in range(len(ds)):
+        assert np.array_equal(sim.diagnostics(k)["events"], orcs[k].counters()["events"])
+
+
 # ----------------------------------------------------- FP32 replay parity
 
 def _replay(d, steps, start=0, orc=None):
