@@ -445,6 +445,15 @@ def run_ours(a, rank, world, local_rank):
         except Exception as ex:
             variants["sweep_13p8"] = {"error": str(ex)}
         try:
+            dk = _workload(a.workload, scale=a.scale)
+            dk.ion_subcycle = 5
+            variants["ion_subcycle"] = measure_variant(
+                f"{a.workload} with O- and O2+ pushed every {dk.ion_subcycle} steps over {dk.ion_subcycle} dt "
+                f"(a throughput variant, not in the paper; value counts pushed particles, compare "
+                f"ms_per_time_step): {_describe(dk)}", [dk], 200, 400)
+        except Exception as ex:
+            variants["ion_subcycle"] = {"error": str(ex)}
+        try:
             dq = _workload(a.workload, scale=a.scale)
             dq.gas_scheme = 1
             variants["sequential_gas"] = measure_variant(

@@ -145,6 +145,12 @@ typedef struct {
  *                  above (14) (a product of (15), (16), (17) meets the later
  *                  channels of the list), a new sort, (19).  Needs n1 > 0;
  *                  all discharges of one handle share it.
+ *   ion_subcycle   k > 1: O- and O2+ are pushed, and tested for gas
+ *                  collisions, only on steps n = 0 mod k, over k dt (null-
+ *                  collision probability 1 - exp(-nu_max k dt)); in between
+ *                  they rest and their charge stays in the grid.  Not in the
+ *                  paper: a throughput variant.  0 or 1: every step.
+ *                  diag_every must then be a multiple of k.
  */
 typedef struct {
     double L_m, p_Pa, T_gas_K, U_rf_V, f_rf_Hz, rf_phase, dt_s;
@@ -162,6 +168,7 @@ typedef struct {
     int numax_bins;
     int n2;
     int gas_scheme;
+    int ion_subcycle;
     int precision;
     double coulomb_log;
 } pic_config;

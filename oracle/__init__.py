@@ -48,7 +48,7 @@ class _Cfg(C.Structure):
         ("diag_every", C.c_int), ("eedf_bins", C.c_int), ("iedf_bins", C.c_int),
         ("fm_bins", C.c_int), ("fm_xbins", C.c_int), ("discharge", C.c_int),
         ("cx_isotropic", C.c_int), ("numax_bins", C.c_int), ("n2", C.c_int),
-        ("gas_scheme", C.c_int), ("coulomb_log", C.c_double),
+        ("gas_scheme", C.c_int), ("ion_subcycle", C.c_int), ("coulomb_log", C.c_double),
     ]
 
 
@@ -173,6 +173,7 @@ class Oracle:
         cfg.n2 = int(d.n2)
         cfg.coulomb_log = float(d.coulomb_log)
         cfg.gas_scheme = int(d.gas_scheme)
+        cfg.ion_subcycle = int(d.ion_subcycle)
         self._keep = []
         xs = (_Xs * len(tables))()
         for i, t in enumerate(tables):

@@ -49,6 +49,8 @@ typedef struct {
                             tau = n2 dt (0 = none) */
     int gas_scheme;      /* gas targets: 0 null collision every step, 1 the
                             sequential channel test every n1 steps (Sec. II) */
+    int ion_subcycle;    /* k > 1: O- and O2+ pushed (and tested for gas
+                            collisions) only on steps n = 0 mod k, with k dt */
     double coulomb_log;  /* ln Gamma of Eq. 2 */
 } orc_cfg;
 

@@ -157,6 +157,7 @@ struct Disc {
     int discharge;
     int cx_iso;
     int gas_scheme;          // 0 null collision, 1 the sequential channel list every n1 steps
+    int ion_sub;             // ions pushed on steps n = 0 mod ion_sub (1: every step)
     int ndsmc;               // gas channels of the sequential list
     DsmcCh dsmc[MAX_DSMC];   // in the order of Table I
     SpeciesC sp[NSP];
@@ -330,6 +331,12 @@ __device__ __forceinline__ void iso_dir(Real r1, Real r2, Real n[3])
 __device__ __forceinline__ void pdl_wait()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// a sub-cycled ion species rests (is not pushed) at this step
+__device__ __forceinline__ bool species_rests(const Disc &Dd, int s, unsigned long long step)
+{
+    return s > 0 && Dd.ion_sub > 1 && step % (unsigned long long)Dd.ion_sub != 0ull;
 }
 
 __device__ __forceinline__ void set_status(Ctl *ctl, unsigned bits)

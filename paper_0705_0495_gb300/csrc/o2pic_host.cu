@@ -122,6 +122,10 @@ bool validate(const pic_config *c, int D, const pic_xs_table *xs, int n_xs, std:
             why = "the sequential gas scheme (gas_scheme = 1) needs n1 > 0";
             return false;
         }
+        if (q.ion_subcycle < 0 || (q.ion_subcycle > 1 && q.diag_every > 0 && q.diag_every % q.ion_subcycle != 0)) {
+            why = "ion_subcycle must be >= 0, and diag_every a multiple of it";
+            return false;
+        }
         if (q.gas_scheme != c[0].gas_scheme) {
             why = "all discharges of one handle must share gas_scheme";
             return false;
@@ -489,6 +493,7 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
     D.discharge = d;
     D.cx_iso = q.cx_isotropic;
     D.gas_scheme = q.gas_scheme;
+    D.ion_sub = q.ion_subcycle > 1 ? q.ion_subcycle : 1;
     const double ngas = q.p_Pa / (KB * q.T_gas_K);
     for (int s = 0; s < 3; ++s) {
         SpeciesC &S = D.sp[s];
@@ -565,7 +570,8 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
             nb.numax_n_f = (float)nb.numax_n;
         }
         S.numax_n = S.numax * q.dt_s;
-        const double pnull = 1.0 - std::exp(-S.numax * q.dt_s);
+        // a sub-cycled ion is tested once per push, over ion_sub steps
+        const double pnull = 1.0 - std::exp(-S.numax * q.dt_s * (s > 0 ? D.ion_sub : 1));
         const double thr = std::ceil(pnull * 4294967296.0 - 0.5);
         S.tnull = thr <= 0.0 ? 0u : (thr >= 4294967295.0 ? 0xFFFFFFFFu : (unsigned)thr);
         if (q.gas_scheme == 1) S.tnull = 0u;  // no null-collision candidates

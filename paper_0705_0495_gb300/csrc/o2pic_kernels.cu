@@ -171,7 +171,7 @@ k_field(WsPtrs W, int par, int diag, int mode)
             for (int s = 0; s < NSP; ++s) {
                 const size_t k = (size_t)s * tn + g + i;
                 a[s] = (long long)acc[k];
-                if (mode == 0) acc[k] = Acc(0);
+                if (mode == 0 && !species_rests(Dd, s, step)) acc[k] = Acc(0);
                 if (diag) W.dens_sum_fix[k] += a[s];  // exact sums; scaled at read-out
             }
             const long long q = a[2] - a[0] - a[1];
@@ -288,7 +288,7 @@ k_field(WsPtrs W, int par, int diag, int mode)
             for (int s = 0; s < NSP; ++s) {
                 const size_t k = (size_t)s * tn + g + i;
                 dn[s] = acc_to_weight(acc[k]) * scale;
-                if (mode == 0) acc[k] = Acc(0);
+                if (mode == 0 && !species_rests(Dd, s, step)) acc[k] = Acc(0);
                 W.dens[k] = dn[s];
                 if (diag) W.dens_sum[k] += dn[s];
             }

@@ -607,6 +607,13 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         int nx = ds < 0 ? 0 : ds;
         while (nx < nds && !(tbeg >= W.cnt[nx].chunk0 && tbeg < W.cnt[nx].chunk0 + W.cnt[nx].nchunk)) ++nx;
         if (nx >= nds) continue;
+        if (species_rests(W.disc[nx / NSP], nx % NSP, step)) {
+            // a resting ion species: nothing to push; its sub-tiles record no births
+            const int te = min(tbeg + TILES_PER_TICKET, W.cnt[nx].chunk0 + W.cnt[nx].nchunk);
+            for (int q = tid; q < (te - tbeg) * SUBTILES; q += PUSH_THREADS)
+                W.tile_cnt[((size_t)tbeg * SUBTILES + q) * NSP] = 0;
+            continue;
+        }
         // a new (d, s), or the FP32 split sums at their bound: flush
         if (nx != ds || (sizeof(Real) == 4 && run_tk >= FLUSH_TICKETS)) {
             if (qn > 0) list_out();
@@ -644,7 +651,9 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         const int pb = Dd.pbase[s];
         const int end = pb + C.n_snap;
         const int tend = min(tbeg + TILES_PER_TICKET, C.chunk0 + C.nchunk);
-        const Real qm = pick<Real>(S.qm, S.qm_f);
+        // a sub-cycled ion species moves over ks steps per push
+        const Real ks = Real(s > 0 ? Dd.ion_sub : 1);
+        const Real qm = pick<Real>(S.qm, S.qm_f) * ks;
         const unsigned tnull = S.tnull;
         const int nbins = S.nbins;
         const bool binned = nbins > 0;  // electrons: bound per lab-energy bin
@@ -705,7 +714,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 const Real e0 = sE[cc], e1 = sE[cc + 1];
                 const Real ep = e0 + off[k] * (e1 - e0);
                 const Real v = vx[k] + qm * ep;
-                Real o = off[k] + v;
+                Real o = off[k] + v * ks;
                 const Real fl = floor(o);
                 const bool bad = !(fl > Real(-2 * N - 4) && fl < Real(2 * N + 4));
                 int cn = bad ? (v < Real(0) ? -1 : N) : cc + (int)fl;

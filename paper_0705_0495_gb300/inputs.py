@@ -171,6 +171,7 @@ class Discharge:
     n2: int = 0                     # intra-species Coulomb collisions every n2 steps (0: none)
     coulomb_log: float = 10.0       # ln Gamma of Eq. 2 (not given in the paper)
     gas_scheme: int = 0             # gas targets: 0 null collision, 1 sequential test every n1 steps
+    ion_subcycle: int = 1           # k > 1: ions pushed every k steps with k dt
     cx_isotropic: bool = False
     capacity_factor: float = 1.5
     capacity_extra: int = 4096

@@ -380,6 +380,26 @@ def test_fp64_batched_discharges_each_match_their_oracle():
                 assert ex < TOL64 and ev < TOL64, (k, s, ex, ev)
 
 
+# ------------------------------------------------------ ion sub-cycling
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_fp64_ion_subcycling_step_by_step(k):
+    d = inputs.cfg1(ion_subcycle=k)
+    sim, orc, (ex, ev) = _run_pair(d, [1, 2, 3, 7, 10, 11, 30, 61, 100])
+    assert ex < TOL64 and ev < TOL64, (ex, ev)
+    g, o = sim.diagnostics(0), orc.counters()
+    assert np.array_equal(g["events"], o["events"])
+    assert np.array_equal(g["absorbed"], o["absorbed"])
+    assert g["particle_steps"] == orc.particle_steps
+
+
+def test_fp32_ion_subcycling_replay():
+    d = inputs.cfg1(fp64=False, ion_subcycle=5)
+    compared, flips, worst = _replay(d, 30)
+    assert worst < TOL32, worst
+    assert flips <= 1e-4 * compared, (flips, compared)
+
+
 def test_fp64_sweep_13p8_batched_matches_oracles():
     # the seven discharges of the 13.8 Pa sweep (75-300 V, and C = 0 at 150
     # V) in one handle, with Coulomb collisions every 10 steps
