@@ -46,6 +46,8 @@ def _args():
                    help="intra-species Coulomb collisions every n2 steps on the workload (default: none)")
     p.add_argument("--gas-scheme", type=int, default=None, choices=[0, 1],
                    help="gas targets: 0 null-collision test (default), 1 the sequential scheme every n1 steps")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the workload's sort interval instead of timing the candidates first")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the FP64, batched-sweep, Coulomb and sequential-gas figures beside the main one")
     return p.parse_args()
@@ -291,6 +293,13 @@ def run_ours(a, rank, world, local_rank):
     if a.gas_scheme is not None:
         d.gas_scheme = a.gas_scheme
     tabs = inputs.xs_tables()
+    tune = None
+    if not a.no_autotune:
+        # the cell-sort interval: each candidate timed on this discharge
+        from paper_0705_0495_gb300 import autotune
+        best, ms = autotune.tune_sort_interval(d, tabs)
+        d.sort_interval = best
+        tune = {"chosen": best, "ms_per_time_step": {str(k): v for k, v in ms.items()}}
     sim = o2pic.Simulation([d], tabs)
     spc = d.steps_per_cycle
     state_bytes = sum(d.n_init) * (12 + (16 if not d.fp64 else 32))
@@ -471,7 +480,7 @@ def run_ours(a, rank, world, local_rank):
             "config": {
                 "workload": f"{a.workload}: {_describe(d)}",
                 "step": f"one RF cycle = {spc} time steps (sort and pair pass every "
-                        f"{d.sort_interval}/{d.n1} steps, diagnostics every {d.diag_every}"
+                        f"{d.sort_interval or d.n1}/{d.n1} steps, diagnostics every {d.diag_every}"
                         + (f", Coulomb collisions every {d.n2}" if d.n2 > 0 else "")
                         + (", sequential gas scheme instead of the null-collision test" if d.gas_scheme else "")
                         + ")",
@@ -482,6 +491,7 @@ def run_ours(a, rank, world, local_rank):
                        f"({state_bytes / 1e6:.0f} MB) exceeds the 129 MB L2"
                        if not flush else "L2 flushed between timed iterations"),
                 "parallelism": f"{world} GPU(s), one independent discharge per GPU",
+                "sort_interval_autotune": tune,
             },
             "roofline": roof,
             "e2e": e2e,
