@@ -48,7 +48,8 @@ class _Cfg(C.Structure):
         ("diag_every", C.c_int), ("eedf_bins", C.c_int), ("iedf_bins", C.c_int),
         ("fm_bins", C.c_int), ("fm_xbins", C.c_int), ("discharge", C.c_int),
         ("cx_isotropic", C.c_int), ("numax_bins", C.c_int), ("n2", C.c_int),
-        ("gas_scheme", C.c_int), ("ion_subcycle", C.c_int), ("coulomb_log", C.c_double),
+        ("gas_scheme", C.c_int), ("ion_subcycle", C.c_int), ("coulomb_inter", C.c_int),
+        ("coulomb_log", C.c_double),
     ]
 
 
@@ -90,6 +91,12 @@ def lib():
         l.orc_coulomb_pair.restype = None
         l.orc_coulomb_pair.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double,
                                        C.c_double, C.c_double, C.c_double]
+        l.orc_coulomb_pair2.restype = None
+        l.orc_coulomb_pair2.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double,
+                                        C.c_double, C.c_double, C.c_double]
+        l.orc_coulomb_inter_pairing.restype = None
+        l.orc_coulomb_inter_pairing.argtypes = [C.c_void_p, C.c_int, C.c_longlong, C.c_longlong,
+                                                C.c_longlong, C.c_uint32, C.c_void_p, C.c_void_p]
         l.orc_coulomb_pairing.restype = C.c_longlong
         l.orc_coulomb_pairing.argtypes = [C.c_void_p, C.c_int, C.c_longlong, C.c_longlong,
                                           C.c_uint32, C.c_void_p, C.c_void_p]
@@ -174,6 +181,7 @@ class Oracle:
         cfg.coulomb_log = float(d.coulomb_log)
         cfg.gas_scheme = int(d.gas_scheme)
         cfg.ion_subcycle = int(d.ion_subcycle)
+        cfg.coulomb_inter = int(d.coulomb_inter)
         self._keep = []
         xs = (_Xs * len(tables))()
         for i, t in enumerate(tables):
@@ -225,6 +233,19 @@ class Oracle:
         lib().orc_coulomb_cell(self.h, s, _dp(a[0]), _dp(a[1]), _dp(a[2]), len(a[0]),
                                float(dens), float(tau), int(step), int(cell))
         return a
+
+    def coulomb_pair2(self, sa, sb, v1, v2, n, tau, xi, r):
+        a = np.ascontiguousarray(v1, dtype=np.float64).copy()
+        b = np.ascontiguousarray(v2, dtype=np.float64).copy()
+        lib().orc_coulomb_pair2(self.h, sa, sb, _dp(a), _dp(b), float(n), float(tau), float(xi), float(r))
+        return a, b
+
+    def coulomb_inter_pairing(self, pair, nA, nB, step, cell):
+        ia = np.zeros(nA, dtype=np.int64)
+        ib = np.zeros(nA, dtype=np.int64)
+        lib().orc_coulomb_inter_pairing(self.h, pair, int(nA), int(nB), int(step), int(cell),
+                                        ia.ctypes.data_as(C.c_void_p), ib.ctypes.data_as(C.c_void_p))
+        return ia, ib
 
     def coulomb_pairing(self, s, n, step, cell):
         """partners of each Coulomb collision of a cell of n particles"""

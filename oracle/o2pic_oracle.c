@@ -1182,6 +1182,123 @@ void orc_coulomb_cell(const orc_sim *s, int sp, double *vx, double *vy, double *
 /* Coulomb pass of species sp over the sorted cells: the density of Eq. 2 is
  * the species' own count in the cell times the weight over the cell volume,
  * the collision time tau = n2 dt */
+/* One Coulomb collision between a particle of species sa (velocity v1) and
+ * one of species sb (v2) (Sec. III A; the binary model of Takizuka and Abe
+ * for unlike particles): tan(chi/2) normal with variance q_a^2 q_b^2 n
+ * lnGamma tau / (8 pi eps0^2 mu^2 u^3), mu = m_a m_b / (m_a + m_b); g turned
+ * as for like particles, particle a takes m_b/(m_a + m_b) of the change of
+ * g, particle b minus m_a/(m_a + m_b) of it. */
+void orc_coulomb_pair2(const orc_sim *s, int sa, int sb, double v1[3], double v2[3],
+                       double n, double tau, double xi, double r)
+{
+    double g[3] = {v1[0] - v2[0], v1[1] - v2[1], v1[2] - v2[2]};
+    double u = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (!(u > 0.0)) return;
+    double ma = MASS[sa], mb = MASS[sb], mu = reduced_mass(ma, mb);
+    double qq = CHARGE[sa] * CHARGE[sb];
+    double var = qq * qq * n * s->c.coulomb_log * tau / (8.0 * PI * EPS0 * EPS0 * mu * mu * u * u * u);
+    double d = sqrt(var) * xi;
+    double sn, om;
+    if (fabs(d) <= 1.0) {
+        sn = 2.0 * d / (1.0 + d * d);
+        om = 2.0 * d * d / (1.0 + d * d);
+    } else {
+        double e = 1.0 / d;
+        sn = 2.0 * e / (1.0 + e * e);
+        om = 2.0 / (1.0 + e * e);
+    }
+    double phi = 2.0 * PI * r;
+    double cp = cos(phi), spn = sin(phi);
+    double up = sqrt(g[0] * g[0] + g[1] * g[1]);
+    double dg[3];
+    if (up > 0.0) {
+        dg[0] = (g[0] / up) * g[2] * sn * cp - (g[1] / up) * u * sn * spn - g[0] * om;
+        dg[1] = (g[1] / up) * g[2] * sn * cp + (g[0] / up) * u * sn * spn - g[1] * om;
+        dg[2] = -up * sn * cp - g[2] * om;
+    } else {
+        dg[0] = u * sn * cp;
+        dg[1] = u * sn * spn;
+        dg[2] = -g[2] * om;
+    }
+    double fa = mb / (ma + mb), fb = ma / (ma + mb);
+    for (int k = 0; k < 3; ++k) {
+        v1[k] += fa * dg[k];
+        v2[k] -= fb * dg[k];
+    }
+}
+
+static const int INTER_PAIR[3][2] = {{SP_E, SP_OM}, {SP_E, SP_OP}, {SP_OM, SP_OP}};
+
+/* an affine permutation k -> (a k + b) mod n with a coprime to n from two
+ * random words (the identity for n = 1) */
+static void affine_of(long long n, uint32_t w0, uint32_t w1, long long *a, long long *b)
+{
+    if (n < 2) {
+        *a = 1;
+        *b = 0;
+        return;
+    }
+    long long x = 1 + (long long)(w0 % (uint64_t)(n - 1));
+    while (gcd_ll(x, n) != 1) x = (x % (n - 1)) + 1;
+    *a = x;
+    *b = (long long)(w1 % (uint64_t)n);
+}
+
+/* Inter-species pairing (Takizuka and Abe for unlike particles): the nA
+ * particles of the more numerous species (A) each collide once, with the
+ * particles of the other (B) taken in turn, so that each B particle collides
+ * about nA/nB times; both lists are shuffled by affine permutations drawn
+ * from draw 0 of stream 5 of the cell with species field 3 + pair (words 0,
+ * 1 for A, 2, 3 for B).  Collision k joins A pi_A(k) with B pi_B(k mod nB)
+ * and takes draw 1 + k/2 like the intra-species collisions. */
+void orc_coulomb_inter_pairing(const orc_sim *s, int pair, long long nA, long long nB,
+                               long long step, uint32_t cell, long long *ia, long long *ib)
+{
+    uint32_t w[4];
+    coulomb_rng(s, 3 + pair, step, cell, 0, w);
+    long long aA, bA, aB, bB;
+    affine_of(nA, w[0], w[1], &aA, &bA);
+    affine_of(nB, w[2], w[3], &aB, &bB);
+    for (long long k = 0; k < nA; ++k) {
+        ia[k] = (aA * k + bA) % nA;
+        ib[k] = (aB * (k % nB) + bB) % nB;
+    }
+}
+
+/* the inter-species Coulomb collisions of one species pair in every cell;
+ * the density of Eq. 2 is that of the less numerous species in the cell
+ * (each A particle meets that density once over tau; each B particle meets
+ * nA/nB of them, the density of A) */
+static void coulomb_inter(orc_sim *s, int pair, long long **start)
+{
+    int s0 = INTER_PAIR[pair][0], s1 = INTER_PAIR[pair][1];
+    double tau = s->c.n2 * s->c.dt;
+    for (int c = 0; c < s->c.n_cells; ++c) {
+        long long n0 = start[s0][c + 1] - start[s0][c], n1 = start[s1][c + 1] - start[s1][c];
+        if (n0 == 0 || n1 == 0) continue;
+        int sA = n0 >= n1 ? s0 : s1, sB = n0 >= n1 ? s1 : s0;
+        long long nA = n0 >= n1 ? n0 : n1, nB = n0 >= n1 ? n1 : n0;
+        parts_t *A = &s->p[sA], *B = &s->p[sB];
+        long long pA = start[sA][c], pB = start[sB][c];
+        long long *ia = malloc(nA * sizeof(long long)), *ib = malloc(nA * sizeof(long long));
+        orc_coulomb_inter_pairing(s, pair, nA, nB, s->step, (uint32_t)c, ia, ib);
+        double dens = (double)nB * s->c.weight / s->dx;
+        for (long long k = 0; k < nA; ++k) {
+            long long i = pA + ia[k], j = pB + ib[k];
+            uint32_t d[4];
+            coulomb_rng(s, 3 + pair, s->step, (uint32_t)c, 1 + k / 2, d);
+            double g0, g1;
+            box_muller(d[0], d[1], &g0, &g1);
+            double v1[3] = {A->vx[i], A->vy[i], A->vz[i]}, v2[3] = {B->vx[j], B->vy[j], B->vz[j]};
+            orc_coulomb_pair2(s, sA, sB, v1, v2, dens, tau, (k % 2) ? g1 : g0, unif(d[2 + k % 2]));
+            A->vx[i] = v1[0]; A->vy[i] = v1[1]; A->vz[i] = v1[2];
+            B->vx[j] = v2[0]; B->vy[j] = v2[1]; B->vz[j] = v2[2];
+        }
+        free(ia);
+        free(ib);
+    }
+}
+
 static void coulomb_species(orc_sim *s, int sp, const long long *start)
 {
     parts_t *p = &s->p[sp];
@@ -1270,8 +1387,13 @@ static void step_once(orc_sim *s)
         }
         /* Coulomb collisions (1)-(3) every n2 steps on the sorted cells,
          * then the particle-target reactions every n1 steps */
-        if (coul)
+        if (coul) {
             for (int sp = 0; sp < 3; ++sp) coulomb_species(s, sp, start[sp]);
+            /* inter-species collisions after the intra-species ones, pairs
+             * e-O-, e-O2+, O- - O2+ in turn */
+            if (s->c.coulomb_inter)
+                for (int pr = 0; pr < 3; ++pr) coulomb_inter(s, pr, start);
+        }
         if (pair && s->c.gas_scheme == 1) {
             /* the sequential scheme: the whole list of Table I in order, gas
              * channels before (13), (13), (14), gas channels after (14) with

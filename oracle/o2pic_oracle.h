@@ -51,6 +51,7 @@ typedef struct {
                             sequential channel test every n1 steps (Sec. II) */
     int ion_subcycle;    /* k > 1: O- and O2+ pushed (and tested for gas
                             collisions) only on steps n = 0 mod k, with k dt */
+    int coulomb_inter;   /* 1: inter-species Coulomb collisions as well */
     double coulomb_log;  /* ln Gamma of Eq. 2 */
 } orc_cfg;
 
@@ -109,6 +110,16 @@ int orc_gas_event(const orc_sim *s, int sp, int reaction, int table,
  * xi a standard normal and r a uniform in (0, 1) */
 void orc_coulomb_pair(const orc_sim *s, int sp, double v1[3], double v2[3],
                       double n, double tau, double xi, double r);
+/* one Coulomb collision between particles of species sa and sb (Eq. 2 with
+ * q_a^2 q_b^2 and the reduced mass of the pair) */
+void orc_coulomb_pair2(const orc_sim *s, int sa, int sb, double v1[3], double v2[3],
+                       double n, double tau, double xi, double r);
+/* the inter-species pairing of a cell with nA particles of the more
+ * numerous species and nB of the other, for species pair `pair` (0: e-O-,
+ * 1: e-O2+, 2: O- - O2+): collision k joins A particle ia[k] with B particle
+ * ib[k], k = 0..nA-1 */
+void orc_coulomb_inter_pairing(const orc_sim *s, int pair, long long nA, long long nB,
+                               long long step, uint32_t cell, long long *ia, long long *ib);
 /* the Coulomb pairing of a cell of n particles of species sp at step `step`:
  * writes the partners of every collision in draw order (n/2 + 2 entries
  * suffice) and returns their number (the last three form the triangle of an

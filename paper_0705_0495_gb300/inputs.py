@@ -172,6 +172,7 @@ class Discharge:
     coulomb_log: float = 10.0       # ln Gamma of Eq. 2 (not given in the paper)
     gas_scheme: int = 0             # gas targets: 0 null collision, 1 sequential test every n1 steps
     ion_subcycle: int = 1           # k > 1: ions pushed every k steps with k dt
+    coulomb_inter: bool = False     # inter-species Coulomb collisions as well (with n2 > 0)
     cx_isotropic: bool = False
     capacity_factor: float = 1.5
     capacity_extra: int = 4096

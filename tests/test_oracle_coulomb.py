@@ -224,3 +224,54 @@ def test_step_applies_the_pass_to_every_sorted_cell():
     assert np.array_equal(vx, rb["vx"]) and np.array_equal(vy, rb["vy"])
     assert np.array_equal(vz, rb["vz"])
     assert not np.array_equal(vx, ra["vx"])
+
+
+# ------------------------------------------------ inter-species collisions
+
+@pytest.mark.parametrize("sa,sb", [(0, 1), (0, 2), (1, 2)])
+def test_unlike_pair_conserves_momentum_and_energy(orc, sa, sb):
+    rs = np.random.default_rng(60 + 3 * sa + sb)
+    ma, mb = MASS[sa], MASS[sb]
+    for k in range(200):
+        v1 = rs.normal(size=3) * (1e6 if sa == 0 else 1e3)
+        v2 = rs.normal(size=3) * 1e3
+        if k % 5 == 0:
+            v2[:2] = v1[:2]
+        xi = rs.normal() * (1.0 if k % 3 else 30.0)
+        a, b = orc.coulomb_pair2(sa, sb, v1, v2, 1e17, 1e-7, xi, rs.uniform())
+        p0 = ma * v1 + mb * v2
+        scale = max(np.abs(ma * v1).max(), np.abs(mb * v2).max())
+        assert np.allclose(ma * a + mb * b, p0, rtol=0, atol=1e-12 * scale)
+        e0 = 0.5 * ma * v1 @ v1 + 0.5 * mb * v2 @ v2
+        assert math.isclose(0.5 * ma * a @ a + 0.5 * mb * b @ b, e0, rel_tol=1e-11)
+        assert math.isclose(np.linalg.norm(a - b), np.linalg.norm(v1 - v2), rel_tol=1e-11)
+
+
+def test_unlike_small_angle_diffusion_matches_rutherford(orc):
+    # an electron against an O2+ ion at rest: the electron's velocity change
+    # over tau, from the Rutherford cross section with the reduced mass mu,
+    # <|dv_e|^2> = n q_e^2 q_i^2 lnL tau / (2 pi eps0^2 m_e^2 u)
+    rs = np.random.default_rng(17)
+    n, u = 1e16, 1.5e6
+    v1, v2 = np.array([0.6, 0.0, 0.8]) * u, np.zeros(3)
+    diff = n * QE ** 4 * LNL / (2 * math.pi * EPS0 ** 2 * ME ** 2 * u)
+    tau = 4e-4 * u * u / diff
+    K = 40000
+    d2 = np.empty(K)
+    for k in range(K):
+        a, _ = orc.coulomb_pair2(0, 2, v1, v2, n, tau, rs.normal(), rs.uniform())
+        d2[k] = np.sum((a - v1) ** 2)
+    # the electron takes mu/m_e of the change of g and the variance carries
+    # 1/mu^2: the reduced mass cancels, as in the Rutherford rate
+    assert d2.mean() == pytest.approx(diff * tau, rel=0.03)
+
+
+@pytest.mark.parametrize("nA,nB", [(7, 7), (10, 3), (1000, 37), (5, 1)])
+def test_inter_pairing_uses_every_A_once_and_B_in_turn(orc, nA, nB):
+    ia, ib = orc.coulomb_inter_pairing(1, nA, nB, 42, 3)
+    assert sorted(ia) == list(range(nA))
+    counts = np.bincount(ib, minlength=nB)
+    assert counts.min() >= nA // nB and counts.max() <= -(-nA // nB)
+    # B's partners in collision order: k and k + nB share a B particle
+    for k in range(nA - nB):
+        assert ib[k] == ib[k + nB]
