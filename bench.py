@@ -446,6 +446,15 @@ def run_ours(a, rank, world, local_rank):
         except Exception as ex:
             variants["coulomb"] = {"error": str(ex)}
         try:
+            dc = _workload(a.workload, scale=a.scale)
+            dc.n2 = dc.n1 if dc.n1 > 0 else 10
+            dc.coulomb_inter = True
+            variants["coulomb_inter"] = measure_variant(
+                f"{a.workload} with intra- and inter-species Coulomb collisions every {dc.n2} steps "
+                f"(the Coulomb figures cover both passes): {_describe(dc)}", [dc], 200, 400)
+        except Exception as ex:
+            variants["coulomb_inter"] = {"error": str(ex)}
+        try:
             sw = inputs.sweep_13p8()
             variants["sweep_13p8"] = measure_variant(
                 "the 13.8 Pa sweep of Sec. IV: 7 discharges (2.5 cm, 128 cells, 75-300 V with C = 1/6, "

@@ -151,6 +151,12 @@ typedef struct {
  *                  they rest and their charge stays in the grid.  Not in the
  *                  paper: a throughput variant.  0 or 1: every step.
  *                  diag_every must then be a multiple of k.
+ *   coulomb_inter  1: inter-species Coulomb collisions as well, after the
+ *                  intra-species ones of a Coulomb step (n2 > 0): pairs
+ *                  e-O-, e-O2+, O- - O2+ in turn; per cell every particle of
+ *                  the more numerous species collides once, those of the
+ *                  other in turn; Eq. 2 with q_a^2 q_b^2, the pair's reduced
+ *                  mass and the density of the less numerous species.
  */
 typedef struct {
     double L_m, p_Pa, T_gas_K, U_rf_V, f_rf_Hz, rf_phase, dt_s;
@@ -169,6 +175,7 @@ typedef struct {
     int n2;
     int gas_scheme;
     int ion_subcycle;
+    int coulomb_inter;
     int precision;
     double coulomb_log;
 } pic_config;

@@ -158,6 +158,12 @@ struct Disc {
     int cx_iso;
     int gas_scheme;          // 0 null collision, 1 the sequential channel list every n1 steps
     int ion_sub;             // ions pushed on steps n = 0 mod ion_sub (1: every step)
+    int coul_inter;          // inter-species Coulomb collisions after the intra-species ones
+    // inter-species Coulomb, pairs e-O-, e-O2+, O- - O2+: <tan^2(chi/2)> u_n^3 per
+    // particle of the less numerous species in the cell, and each member's
+    // share of the change of g (m_other / (m_a + m_b))
+    double ci_k[3], ci_frac[3][2];
+    float ci_k_f[3], ci_frac_f[3][2], pad_ci;
     int ndsmc;               // gas channels of the sequential list
     DsmcCh dsmc[MAX_DSMC];   // in the order of Table I
     SpeciesC sp[NSP];

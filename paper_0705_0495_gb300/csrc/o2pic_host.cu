@@ -126,8 +126,12 @@ bool validate(const pic_config *c, int D, const pic_xs_table *xs, int n_xs, std:
             why = "ion_subcycle must be >= 0, and diag_every a multiple of it";
             return false;
         }
-        if (q.gas_scheme != c[0].gas_scheme) {
-            why = "all discharges of one handle must share gas_scheme";
+        if (q.coulomb_inter != 0 && q.coulomb_inter != 1) {
+            why = "coulomb_inter must be 0 or 1";
+            return false;
+        }
+        if (q.gas_scheme != c[0].gas_scheme || q.coulomb_inter != c[0].coulomb_inter) {
+            why = "all discharges of one handle must share gas_scheme and coulomb_inter";
             return false;
         }
         if (q.precision != PIC_FP64 && q.precision != PIC_FP32_MIXED) {
@@ -494,6 +498,24 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
     D.cx_iso = q.cx_isotropic;
     D.gas_scheme = q.gas_scheme;
     D.ion_sub = q.ion_subcycle > 1 ? q.ion_subcycle : 1;
+    D.coul_inter = (q.n2 > 0 && q.coulomb_inter) ? 1 : 0;
+    {
+        const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        const double tdx_ = q.dt_s / D.dx, xdt_ = D.dx / q.dt_s;
+        (void)tdx_;
+        for (int k = 0; k < 3; ++k) {
+            const double ma = MASS[pr[k][0]], mb = MASS[pr[k][1]], mu = ma * mb / (ma + mb);
+            const double qq = CHARGE[pr[k][0]] * CHARGE[pr[k][1]];
+            D.ci_k[k] = q.n2 > 0 ? qq * qq * q.coulomb_log * (q.n2 * q.dt_s) * q.weight_m2 /
+                                       (8.0 * PI * EPS0 * EPS0 * mu * mu * D.dx) / (xdt_ * xdt_ * xdt_)
+                                 : 0.0;
+            D.ci_frac[k][0] = mb / (ma + mb);
+            D.ci_frac[k][1] = ma / (ma + mb);
+            D.ci_k_f[k] = (float)D.ci_k[k];
+            D.ci_frac_f[k][0] = (float)D.ci_frac[k][0];
+            D.ci_frac_f[k][1] = (float)D.ci_frac[k][1];
+        }
+    }
     const double ngas = q.p_Pa / (KB * q.T_gas_K);
     for (int s = 0; s < 3; ++s) {
         SpeciesC &S = D.sp[s];
@@ -925,6 +947,11 @@ static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool timed)
         e = launch_coulomb(h->fp64, h->W, h->pools(), par, st);
         if (e) return e;
         ++nk;
+        if (q.coulomb_inter) {
+            for (int pr = 0; pr < 3; ++pr)
+                if ((e = launch_coulomb_inter(h->fp64, h->W, h->pools(), par, pr, st))) return e;
+            nk += 3;
+        }
         if ((e = time_close(h, timed, st, 1))) return e;
     }
     if (pair && q.gas_scheme == 1) {

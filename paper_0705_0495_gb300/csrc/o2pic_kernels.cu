@@ -1204,6 +1204,161 @@ k_coulomb(WsPtrs W, Pools<Real> P, int par, int cap)
     }
 }
 
+// One Coulomb collision between particles a (velocity va) and b (vb) of
+// unlike species: as coulomb_pair, with the pair's kn, a taking fa of the
+// change of g = va - vb and b minus fb of it.
+template <typename Real>
+__device__ __forceinline__ void coulomb_pair_ab(Real va[3], Real vb[3], Real kn, Real fa, Real fb, Real xi,
+                                                unsigned wphi)
+{
+    using M = CoulMath<Real>;
+    const Real g0 = va[0] - vb[0], g1 = va[1] - vb[1], g2 = va[2] - vb[2];
+    const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
+    if (!(u2 > Real(0))) return;
+    const Real u = M::sqrt_(u2);
+    const Real d = M::sqrt_(kn * M::inv_u32(Real(0), u2, u)) * xi;
+    Real sn, om;
+    if (fabs(d) <= Real(1)) {
+        const Real r = M::rcp(Real(1) + d * d);
+        sn = Real(2) * d * r;
+        om = Real(2) * d * d * r;
+    } else {
+        const Real e = M::rcp(d);
+        const Real r = M::rcp(Real(1) + e * e);
+        sn = Real(2) * e * r;
+        om = Real(2) * r;
+    }
+    Real sp, cp;
+    M::sincos2pi(unif<Real>(wphi), &sp, &cp);
+    const Real up2 = g0 * g0 + g1 * g1;
+    Real dg[3];
+    if (up2 > Real(0)) {
+        const Real up = M::sqrt_(up2), rp = M::rcp(up);
+        const Real ex = g0 * rp, ey = g1 * rp;
+        const Real a = g2 * sn * cp, b = u * sn * sp;
+        dg[0] = ex * a - ey * b - g0 * om;
+        dg[1] = ey * a + ex * b - g1 * om;
+        dg[2] = -up * sn * cp - g2 * om;
+    } else {
+        dg[0] = u * sn * cp;
+        dg[1] = u * sn * sp;
+        dg[2] = -g2 * om;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        va[q] += fa * dg[q];
+        vb[q] -= fb * dg[q];
+    }
+}
+
+// Inter-species Coulomb collisions of species pair `pair` in one cell per
+// block (Takizuka and Abe for unlike particles), after the intra-species
+// pass: the nA particles of the more numerous species (A) each collide once,
+// those of the other (B) in turn; collision k joins A pi_A(k) with B
+// pi_B(k mod nB) (affine permutations from draw 0 of the cell's stream 5
+// with species field 3 + pair) with the random numbers of draw 1 + k/2.
+// Thread t follows the B particles r = t, t + T, ...: particle pi_B(r) meets
+// A pi_A(r), pi_A(r + nB), ... in that order, its velocity in registers; the
+// A particles are disjoint across threads.  A is staged in shared memory
+// when it has at most `cap` particles.
+template <typename Real>
+__global__ void __launch_bounds__(COUL_THREADS, 2)
+k_coulomb_inter(WsPtrs W, Pools<Real> P, int par, int pair, int cap)
+{
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char coul_smem[];
+    __shared__ unsigned prm[4];  // a, b of A's permutation, a, b of B's
+    const int gw = blockIdx.x;
+    const int d = W.cell_disc[gw];
+    const Disc &Dd = W.disc[d];
+    const int N = Dd.N, c = gw - Dd.ccell_base;
+    const int s0 = pair == 2 ? 1 : 0, s1 = pair == 0 ? 1 : 2;
+    const int *cs = W.cell_start + Dd.cs_base;
+    const int q0 = cs[s0 * (N + 2) + c], n0 = cs[s0 * (N + 2) + c + 1] - q0;
+    const int q1 = cs[s1 * (N + 2) + c], n1 = cs[s1 * (N + 2) + c + 1] - q1;
+    if (n0 <= 0 || n1 <= 0) return;
+    const bool zeroA = n0 >= n1;
+    const int sA = zeroA ? s0 : s1, sB = zeroA ? s1 : s0;
+    const int nA = zeroA ? n0 : n1, nB = zeroA ? n1 : n0;
+    const int pA = zeroA ? q0 : q1, pB = zeroA ? q1 : q0;
+    if (nA >= (1 << 29)) {
+        if (threadIdx.x == 0) set_status(W.ctl, ST_BADSTATE);
+        return;
+    }
+    if (threadIdx.x == 0) atomicAdd(&W.counters[(size_t)d * C_NCOUNT + C_COUL], (unsigned long long)(nA + nB));
+    const unsigned long long step = W.ctl->step[par];
+    const unsigned long long seed = Dd.seed;
+    const int disc = Dd.discharge;
+    const int cur = W.ctl->cur;
+    const int sfield = 3 + pair;
+    if (threadIdx.x == 0) {
+        const uint4 w0 = coulomb_rng(seed, disc, sfield, step, c, 0u);
+        const unsigned w[4] = {w0.x, w0.y, w0.z, w0.w};
+        const unsigned nn[2] = {(unsigned)nA, (unsigned)nB};
+        for (int h = 0; h < 2; ++h) {
+            const unsigned un = nn[h];
+            unsigned a = 1u, b = 0u;
+            if (un >= 2u) {
+                a = 1u + w[2 * h] % (un - 1u);
+                for (;;) {
+                    unsigned x = a, y = un;
+                    while (y) {
+                        const unsigned t = x % y;
+                        x = y;
+                        y = t;
+                    }
+                    if (x == 1u) break;
+                    a = a % (un - 1u) + 1u;
+                }
+                b = w[2 * h + 1] % un;
+            }
+            prm[2 * h] = a;
+            prm[2 * h + 1] = b;
+        }
+    }
+    Real *gax = P.vx[cur] + Dd.pbase[sA] + pA, *gay = P.vy[cur] + Dd.pbase[sA] + pA,
+         *gaz = P.vz[cur] + Dd.pbase[sA] + pA;
+    Real *gbx = P.vx[cur] + Dd.pbase[sB] + pB, *gby = P.vy[cur] + Dd.pbase[sB] + pB,
+         *gbz = P.vz[cur] + Dd.pbase[sB] + pB;
+    const bool staged = nA <= cap;
+    Real *ax = gax, *ay = gay, *az = gaz;
+    if (staged) {
+        ax = reinterpret_cast<Real *>(coul_smem);
+        ay = ax + cap;
+        az = ay + cap;
+        coulomb_copy<Real>(ax, ay, az, gax, gay, gaz, nA);
+    }
+    __syncthreads();
+    const unsigned aA = prm[0], bA = prm[1], aB = prm[2], bB = prm[3];
+    const unsigned uA = (unsigned)nA, uB = (unsigned)nB;
+    const Real kn = pick<Real>(Dd.ci_k[pair], Dd.ci_k_f[pair]) * Real(nB);
+    const int ia = zeroA ? 0 : 1;  // index of A's share
+    const Real fa = pick<Real>(Dd.ci_frac[pair][ia], Dd.ci_frac_f[pair][ia]);
+    const Real fb = pick<Real>(Dd.ci_frac[pair][1 - ia], Dd.ci_frac_f[pair][1 - ia]);
+    for (unsigned r = threadIdx.x; r < uB; r += COUL_THREADS) {
+        const unsigned j = (unsigned)(((unsigned long long)aB * r + bB) % uB);
+        Real vb[3] = {gbx[j], gby[j], gbz[j]};
+        for (unsigned k = r; k < uA; k += uB) {
+            const unsigned i = (unsigned)(((unsigned long long)aA * k + bA) % uA);
+            const uint4 w = coulomb_rng(seed, disc, sfield, step, c, 1u + (k >> 1));
+            Real n0r, n1r;
+            CoulMath<Real>::normal2(w.x, w.y, n0r, n1r);
+            Real va[3] = {ax[i], ay[i], az[i]};
+            coulomb_pair_ab<Real>(va, vb, kn, fa, fb, (k & 1u) ? n1r : n0r, (k & 1u) ? w.w : w.z);
+            ax[i] = va[0];
+            ay[i] = va[1];
+            az[i] = va[2];
+        }
+        gbx[j] = vb[0];
+        gby[j] = vb[1];
+        gbz[j] = vb[2];
+    }
+    if (staged) {
+        __syncthreads();
+        coulomb_copy<Real>(gax, gay, gaz, ax, ay, az, nA);
+    }
+}
+
 // Births of (19) appended to the electron array of each discharge in cell
 // order (the order of the sequential pass).
 template <typename Real>
@@ -1332,6 +1487,9 @@ cudaError_t configure_kernels(bool fp64, LaunchCfg &L)
         e = cudaFuncSetAttribute(k_coulomb<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)coulomb_smem_bytes(true));
         if (e) return e;
+        e = cudaFuncSetAttribute(k_coulomb_inter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)coulomb_smem_bytes(true));
+        if (e) return e;
     } else {
         e = cudaFuncSetAttribute(k_field<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.field_smem);
         if (e) return e;
@@ -1340,6 +1498,9 @@ cudaError_t configure_kernels(bool fp64, LaunchCfg &L)
         e = cudaFuncSetAttribute(k_sort_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.scatter_smem);
         if (e) return e;
         e = cudaFuncSetAttribute(k_coulomb<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)coulomb_smem_bytes(false));
+        if (e) return e;
+        e = cudaFuncSetAttribute(k_coulomb_inter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)coulomb_smem_bytes(false));
         if (e) return e;
     }
@@ -1397,6 +1558,18 @@ cudaError_t launch_coulomb(bool fp64, const WsPtrs &W, const void *pools, int pa
     return cudaGetLastError();
 }
 
+
+cudaError_t launch_coulomb_inter(bool fp64, const WsPtrs &W, const void *pools, int par, int pair, cudaStream_t st)
+{
+    const size_t smem = coulomb_smem_bytes(fp64);
+    if (fp64)
+        launch_k(k_coulomb_inter<double>, W.total_cells, COUL_THREADS, smem, st, W,
+                 *static_cast<const Pools<double> *>(pools), par, pair, COUL_STAGE);
+    else
+        launch_k(k_coulomb_inter<float>, W.total_cells, COUL_THREADS, smem, st, W,
+                 *static_cast<const Pools<float> *>(pools), par, pair, COUL_STAGE);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pair_reaction(bool fp64, const WsPtrs &W, const void *pools, int par, int k, cudaStream_t st)
 {

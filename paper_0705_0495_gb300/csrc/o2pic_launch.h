@@ -81,6 +81,9 @@ constexpr int COUL_THREADS = O2_COUL_THREADS;
 constexpr int COUL_STAGE = O2_COUL_STAGE;
 size_t coulomb_smem_bytes(bool fp64);
 cudaError_t launch_coulomb(bool fp64, const WsPtrs &W, const void *pools, int par, cudaStream_t st);
+// inter-species Coulomb collisions of one species pair (0 e-O-, 1 e-O2+, 2 O- - O2+)
+cudaError_t launch_coulomb_inter(bool fp64, const WsPtrs &W, const void *pools, int par, int pair,
+                                 cudaStream_t st);
 cudaError_t launch_pair(bool fp64, const WsPtrs &W, const void *pools, int par,
                         const LaunchCfg &L, cudaStream_t s);
 // one reaction of the particle-target pass (k = 0, 1, 2 for (13), (14),

@@ -44,7 +44,7 @@ class pic_config(C.Structure):
         ("n_cells", C.c_int), ("n1", C.c_int), ("sort_interval", C.c_int), ("diag_every", C.c_int),
         ("eedf_bins", C.c_int), ("iedf_bins", C.c_int), ("fm_bins", C.c_int), ("fm_xbins", C.c_int),
         ("cx_isotropic", C.c_int), ("numax_bins", C.c_int), ("n2", C.c_int), ("gas_scheme", C.c_int),
-        ("ion_subcycle", C.c_int), ("precision", C.c_int),
+        ("ion_subcycle", C.c_int), ("coulomb_inter", C.c_int), ("precision", C.c_int),
         ("coulomb_log", C.c_double),
     ]
 
@@ -134,6 +134,7 @@ def make_config(d: "_inputs.Discharge", fp64: bool | None = None) -> pic_config:
     c.coulomb_log = float(d.coulomb_log)
     c.gas_scheme = int(d.gas_scheme)
     c.ion_subcycle = int(d.ion_subcycle)
+    c.coulomb_inter = int(d.coulomb_inter)
     use64 = d.fp64 if fp64 is None else fp64
     c.precision = PIC_FP64 if use64 else PIC_FP32_MIXED
     return c

@@ -311,6 +311,24 @@ def test_fp64_coulomb_ragged_cells_with_pair_pass():
         assert sim.diagnostics(0)["coulomb_particles"] > 0
 
 
+@pytest.mark.parametrize("n_cells,n_op", [(128, 20000), (7, 22), (3, 60002)])
+def test_fp64_coulomb_inter_species_step_by_step(n_cells, n_op):
+    # intra- and inter-species collisions every 2 steps; 7 cells of a few
+    # particles (empty species in a cell, one particle of a species); 3 cells
+    # of about 10^4 (the more numerous species is worked on in place)
+    d = inputs.cfg1(n_cells=n_cells, n_op=n_op, n2=2, coulomb_log=1e4, coulomb_inter=True)
+    sim, orc, (ex, ev) = _run_pair(d, [1, 2, 4, 10, 20])
+    assert ex < TOL64 and ev < TOL64, (ex, ev)
+    assert np.array_equal(sim.diagnostics(0)["events"], orc.counters()["events"])
+
+
+def test_fp32_coulomb_inter_species_replay():
+    d = inputs.cfg1(fp64=False, n2=1, coulomb_log=1e4, coulomb_inter=True)
+    compared, flips, worst = _replay(d, 20)
+    assert worst < TOL32, worst
+    assert flips <= 1e-4 * compared, (flips, compared)
+
+
 def test_fp32_coulomb_replay():
     d = inputs.cfg1(fp64=False, n2=1, coulomb_log=1e4)
     compared, flips, worst = _replay(d, 30)
