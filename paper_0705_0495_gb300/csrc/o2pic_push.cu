@@ -30,6 +30,12 @@ namespace o2 {
 
 // three 256-thread blocks per SM in the FP32 path (the rare collision path
 // may spill a little), two in the FP64 path
+// tiles ahead of the current one whose particle data a push block asks the
+// L2 cache to fetch (a bulk prefetch issued by one thread; 0 = none)
+#ifndef O2_PUSH_L2_AHEAD
+#define O2_PUSH_L2_AHEAD 2
+#endif
+
 #ifndef O2_PUSH_BLOCKS_F32
 #define O2_PUSH_BLOCKS_F32 3
 #endif
@@ -195,6 +201,13 @@ struct BirthSink {
     int *n;               // the sub-tile's record count
     Ctl *ctl;
 };
+
+// ask the L2 cache to fetch [p, p + bytes) (16-byte aligned, a multiple of
+// 16 bytes); no completion to wait for
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 template <typename Real>
 __device__ __forceinline__ void stage_birth(const BirthSink<Real> &B, int tag, int sp, int c, Real off,
@@ -664,6 +677,22 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             const int i0 = sbase + 4 * lane;
             const int sub = t * SUBTILES + w;
             if (lane == 0) W.tile_cnt[(size_t)sub * NSP] = 0;  // births recorded by the collision kernel
+            if (O2_PUSH_L2_AHEAD > 0 && tid == 0) {
+                // the tile O2_PUSH_L2_AHEAD ahead in this ticket: its cell,
+                // offset and vx (and vy, vz for a binned species) into L2
+                const int ta = (t == tbeg) ? tbeg + 1 : t + O2_PUSH_L2_AHEAD;
+                const int tb = (t == tbeg) ? min(tbeg + O2_PUSH_L2_AHEAD, tend - 1) : ta;
+                for (int tp = ta; tp <= tb && tp < tend; ++tp) {
+                    const size_t sl = (size_t)pb + (size_t)(tp - C.chunk0) * CHUNK;
+                    l2_prefetch(cellA + sl, CHUNK * sizeof(int));
+                    l2_prefetch(offA + sl, CHUNK * sizeof(Real));
+                    l2_prefetch(vxA + sl, CHUNK * sizeof(Real));
+                    if (binned) {
+                        l2_prefetch(vyA + sl, CHUNK * sizeof(Real));
+                        l2_prefetch(vzA + sl, CHUNK * sizeof(Real));
+                    }
+                }
+            }
 
             // ---- phase A: push, absorb, null test, deposit, candidate queue
             int c[4];
