@@ -15,7 +15,10 @@ constexpr int SUBTILES = 1024 / SUBTILE;
 constexpr int BIRTH_CAP_W = 32;        // births staged per sub-tile
 constexpr int QCAP = 160;              // candidate queue of one warp (< 32 left + one sub-tile)
 constexpr int COLLIDE_THREADS = 256;   // threads per block of the collision kernel
-constexpr int TILES_PER_TICKET = 8;    // tiles taken per atomic ticket by a push block
+#ifndef O2_TILES_PER_TICKET
+#define O2_TILES_PER_TICKET 8
+#endif
+constexpr int TILES_PER_TICKET = O2_TILES_PER_TICKET;  // tiles taken per atomic ticket by a push block
 constexpr int BIRTHS_THREADS = 512;    // block of the birth-append kernel (sub-tiles)
 constexpr int TILE_ALIGN = BIRTHS_THREADS / (1024 / 128);  // tiles per birth-append block
 constexpr int SORT_WARPS = 4;          // warps per sort block

@@ -413,7 +413,7 @@ template <> __device__ __forceinline__ void acc_add(double *a, double v) { atomi
 // below 2^FIX_BITS, so word 1 stays below 2^(FIX_BITS - SPLIT_BITS) per
 // particle and word 0 below 2^SPLIT_BITS per add).
 constexpr int SPLIT_BITS = 12;
-constexpr int FLUSH_TICKETS = 32;
+constexpr int FLUSH_TICKETS = 256 / TILES_PER_TICKET;  // 256 tiles of weights at most
 static_assert((long long)FLUSH_TICKETS * TILES_PER_TICKET * CHUNK * (1LL << (FIX_BITS - SPLIT_BITS)) < (1LL << 31),
               "split sums must stay within int32");
 __device__ __forceinline__ void split_add(unsigned long long *node, unsigned v)
