@@ -227,6 +227,8 @@ struct WsPtrs {
     float *lutEf, *lutSf;     // FP32 copies
     double *gtab;             // node-major gas tables: n_j dx sigma_j(E_k), [k][j] per (d, s)
     float *gtabf;
+    double *gpm;              // same layout: bound on n_j dx sigma_j(E) u_n for E up to E_{k+1}
+    float *gpmf;
     int *sort_counts;         // count matrix
     int *cell_start;          // [sum over d of 3*(N+2)]
     int *sort_live;           // [D*3]

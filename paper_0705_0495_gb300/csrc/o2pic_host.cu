@@ -77,7 +77,7 @@ struct Bump {
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, nubin, cand, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
+    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, gpm, gpmf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, nubin, cand, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
         counters, eedf, iedf, fm, tables, lutE, lutS, lutEf, lutSf, sort_counts, cell_start,
         sort_live, pair_bcount, cell_disc, pair_births, sort_tab, ninit, vt;
     size_t cell[2], off[2], vx[2], vy[2], vz[2];
@@ -336,6 +336,8 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.lutSf = B.take(4ull * std::max(1, nl));
     L.gtab = B.take(8ull * std::max(1LL, gn));
     L.gtabf = B.take(4ull * std::max(1LL, gn));
+    L.gpm = B.take(8ull * std::max(1LL, gn));
+    L.gpmf = B.take(4ull * std::max(1LL, gn));
     L.sort_counts = B.take(4ull * std::max(1LL, sortc));
     L.cell_start = B.take(4ull * csb);
     L.sort_live = B.take(4ull * 3 * D);
@@ -723,6 +725,8 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.lutSf = reinterpret_cast<float *>(b + L.lutSf);
     W.gtab = reinterpret_cast<double *>(b + L.gtab);
     W.gtabf = reinterpret_cast<float *>(b + L.gtabf);
+    W.gpm = reinterpret_cast<double *>(b + L.gpm);
+    W.gpmf = reinterpret_cast<float *>(b + L.gpmf);
     W.sort_counts = reinterpret_cast<int *>(b + L.sort_counts);
     W.cell_start = reinterpret_cast<int *>(b + L.cell_start);
     W.sort_live = reinterpret_cast<int *>(b + L.sort_live);
@@ -791,6 +795,8 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     // node-major gas tables: row k of (d, s) holds n_j dx sigma_j(E_k), j < nch
     std::vector<double> gt(std::max(1LL, L.gtab_n), 0.0);
     std::vector<float> gtf(std::max(1LL, L.gtab_n), 0.0f);
+    std::vector<double> gpm(std::max(1LL, L.gtab_n), 0.0);
+    std::vector<float> gpmf(std::max(1LL, L.gtab_n), 0.0f);
     {
         long long off = 0;
         for (int d = 0; d < n_discharges; ++d)
@@ -806,6 +812,23 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
                         gt[off + (long long)k * ld + j] = v;
                         gtf[off + (long long)k * ld + j] = (float)v;
                     }
+                // bound for the sequential scheme's skip: row k holds the largest
+                // max(v_i, v_{i+1}) u_n(E_{i+1}) over the intervals i <= k (v linear
+                // between nodes, u_n = sqrt(E / Ek) increasing), row nodes-1 repeats
+                // row nodes-2
+                for (int j = 0; j < S.nch; ++j) {
+                    double run = 0.0;
+                    const HostTable &t = h->tabs[S.ch[j].table];
+                    for (int k = 0; k < nodes; ++k) {
+                        if (k + 1 < nodes) {
+                            const double u1 = std::sqrt(t.E[k + 1] / S.Ek);
+                            const double a = gt[off + (long long)k * ld + j], c2 = gt[off + (long long)(k + 1) * ld + j];
+                            run = std::max(run, std::max(a, c2) * u1);
+                        }
+                        gpm[off + (long long)k * ld + j] = run;
+                        gpmf[off + (long long)k * ld + j] = (float)run;
+                    }
+                }
                 off += (long long)nodes * ld + 4;
             }
     }
@@ -857,6 +880,8 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     CK(cudaMemcpyAsync(W.cnt, cnt.data(), sizeof(Counts) * cnt.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(W.gtab, gt.data(), 8 * gt.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(W.gtabf, gtf.data(), 4 * gtf.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(W.gpm, gpm.data(), 8 * gpm.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(W.gpmf, gpmf.data(), 4 * gpmf.size(), cudaMemcpyHostToDevice, st));
     if (n_xs > 0) {
         CK(cudaMemcpyAsync(W.tables, td.data(), sizeof(TableDesc) * n_xs, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(W.lutE, lE.data(), 8 * lE.size(), cudaMemcpyHostToDevice, st));

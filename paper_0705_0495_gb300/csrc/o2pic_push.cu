@@ -51,6 +51,7 @@ template <typename Real> struct GasTab;
 template <> struct GasTab<float> {
     static constexpr int VEC = 4;
     static __device__ __forceinline__ const float *ptr(const WsPtrs &W) { return W.gtabf; }
+    static __device__ __forceinline__ const float *bound(const WsPtrs &W) { return W.gpmf; }
     static __device__ __forceinline__ void load(const float *p, float v[4])
     {
         const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
@@ -60,6 +61,7 @@ template <> struct GasTab<float> {
 template <> struct GasTab<double> {
     static constexpr int VEC = 2;
     static __device__ __forceinline__ const double *ptr(const WsPtrs &W) { return W.gtab; }
+    static __device__ __forceinline__ const double *bound(const WsPtrs &W) { return W.gpm; }
     static __device__ __forceinline__ void load(const double *p, double v[2])
     {
         const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
@@ -973,13 +975,40 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
         const int sub = chunk * SUBTILES + local / SUBTILE;
         const int tag = (local % SUBTILE) << 1;
         const BirthSink<Real> B{stage + (size_t)sub * BIRTH_CAP_W, W.tile_cnt + (size_t)sub * NSP, ctl};
+        // bound on a channel's n dx sigma u_n over every gas molecule Box-
+        // Muller can give (|V| < 10 thermal speeds), from the particle's speed;
+        // refreshed when the chain changes species
+        int bsp = -1, bk = 0, breg = 0;
+        Real umax = Real(0);
         for (int kk = 0; kk < Dd.ndsmc; ++kk) {
             const DsmcCh &e = Dd.dsmc[kk];
             if (e.sp != cs || (part == 0 ? e.reaction > 12 : e.reaction < 15)) continue;
             const SpeciesC &S = Dd.sp[cs];
             const GasChan &ch = S.ch[e.j];
-            const uint4 a = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen, step, (unsigned)rel);
             const uint4 b = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen + 1u, step, (unsigned)rel);
+            if (bsp != cs) {
+                umax = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) + Real(10) * pick<Real>(S.vgas_n, S.vgas_n_f);
+                const XsPoint<Real> pm = xs_locate<Real>(W.tables[S.table_lo], lutE, pick<Real>(S.Ek, S.Ek_f) * umax * umax);
+                bk = pm.k;
+                breg = pm.region;
+                bsp = cs;
+            }
+            {
+                // P = n dx sigma u_n n1 <= the bound times n1 (1e-3 margin for rounding):
+                // a draw at or above it cannot collide, whatever the molecule
+                const Real *tb = GasTab<Real>::ptr(W) + S.gtab_off;
+                const Real *pmr = GasTab<Real>::bound(W) + S.gtab_off;
+                Real bnd;
+                if (breg == 0) bnd = tb[e.j] * umax;
+                else if (breg == 1) bnd = pmr[(size_t)bk * S.gtab_ld + e.j];
+                else {
+                    const Real last = tb[(size_t)(bk + 1) * S.gtab_ld + e.j] * umax;
+                    const Real pmv = pmr[(size_t)bk * S.gtab_ld + e.j];
+                    bnd = last > pmv ? last : pmv;
+                }
+                if (unif<Real>(b.x) >= bnd * n1 * Real(1.001)) continue;
+            }
+            const uint4 a = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen, step, (unsigned)rel);
             Real n0, nn1, n2, n3;
             box_muller<Real>(a.x, a.y, n0, nn1);
             box_muller<Real>(a.z, a.w, n2, n3);
@@ -1020,6 +1049,7 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
                 for (int q = 0; q < 3; ++q) v[q] = pr.v[0][q];
                 ++gen;
             }
+            bsp = -1;  // the speed changed: a new bound
         }
         if (gen == 0) {
             vxA[i] = v[0];
