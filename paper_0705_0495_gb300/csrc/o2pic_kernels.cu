@@ -1335,11 +1335,19 @@ k_coulomb_inter(WsPtrs W, Pools<Real> P, int par, int pair, int cap)
     const int ia = zeroA ? 0 : 1;  // index of A's share
     const Real fa = pick<Real>(Dd.ci_frac[pair][ia], Dd.ci_frac_f[pair][ia]);
     const Real fb = pick<Real>(Dd.ci_frac[pair][1 - ia], Dd.ci_frac_f[pair][1 - ia]);
-    for (unsigned r = threadIdx.x; r < uB; r += COUL_THREADS) {
-        const unsigned j = (unsigned)(((unsigned long long)aB * r + bB) % uB);
+    // indices advanced by additions mod n: j(r) = (aB r + bB) mod nB steps by
+    // aB T mod nB, i(k) = (aA k + bA) mod nA by aA T mod nA over r and by
+    // aA nB mod nA along a chain
+    const unsigned t0 = threadIdx.x;
+    unsigned j = (unsigned)(((unsigned long long)aB * t0 + bB) % uB);
+    unsigned i0 = (unsigned)(((unsigned long long)aA * t0 + bA) % uA);
+    const unsigned stepB = (unsigned)(((unsigned long long)aB * COUL_THREADS) % uB);
+    const unsigned stepA = (unsigned)(((unsigned long long)aA * COUL_THREADS) % uA);
+    const unsigned chainA = (unsigned)(((unsigned long long)aA * uB) % uA);
+    for (unsigned r = t0; r < uB; r += COUL_THREADS) {
         Real vb[3] = {gbx[j], gby[j], gbz[j]};
+        unsigned i = i0;
         for (unsigned k = r; k < uA; k += uB) {
-            const unsigned i = (unsigned)(((unsigned long long)aA * k + bA) % uA);
             const uint4 w = coulomb_rng(seed, disc, sfield, step, c, 1u + (k >> 1));
             Real n0r, n1r;
             CoulMath<Real>::normal2(w.x, w.y, n0r, n1r);
@@ -1348,10 +1356,16 @@ k_coulomb_inter(WsPtrs W, Pools<Real> P, int par, int pair, int cap)
             ax[i] = va[0];
             ay[i] = va[1];
             az[i] = va[2];
+            i += chainA;
+            if (i >= uA) i -= uA;
         }
         gbx[j] = vb[0];
         gby[j] = vb[1];
         gbz[j] = vb[2];
+        j += stepB;
+        if (j >= uB) j -= uB;
+        i0 += stepA;
+        if (i0 >= uA) i0 -= uA;
     }
     if (staged) {
         __syncthreads();
