@@ -21,9 +21,18 @@ constexpr int COLLIDE_THREADS = 256;   // threads per block of the collision ker
 constexpr int TILES_PER_TICKET = O2_TILES_PER_TICKET;  // tiles taken per atomic ticket by a push block
 constexpr int BIRTHS_THREADS = 512;    // block of the birth-append kernel (sub-tiles)
 constexpr int TILE_ALIGN = BIRTHS_THREADS / (1024 / 128);  // tiles per birth-append block
-constexpr int SORT_WARPS = 4;          // warps per sort block
-constexpr int SORT_WARP_SLOTS = 8192;  // slots per sort warp (16-bit counters)
-constexpr int SORT_ILP = 8;            // 32-slot rows loaded per warp before ranking
+#ifndef O2_SORT_WARPS
+#define O2_SORT_WARPS 4
+#endif
+#ifndef O2_SORT_WARP_SLOTS
+#define O2_SORT_WARP_SLOTS 8192
+#endif
+#ifndef O2_SORT_ILP
+#define O2_SORT_ILP 8
+#endif
+constexpr int SORT_WARPS = O2_SORT_WARPS;  // warps per sort block
+constexpr int SORT_WARP_SLOTS = O2_SORT_WARP_SLOTS;  // slots per sort warp (16-bit counters)
+constexpr int SORT_ILP = O2_SORT_ILP;  // 32-slot rows loaded per warp before ranking
 constexpr int SORT_CHUNK = SORT_WARPS * SORT_WARP_SLOTS;
 constexpr int PAIR_BIRTH_CAP = 16;     // births of (19) per cell per pass
 constexpr int MAX_GAS_CH = 16;

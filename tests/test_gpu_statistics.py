@@ -11,7 +11,9 @@ histogram bin holding at least 100 counts on both sides, the mean of z^2 is
 at most 3, at most 10% of the values exceed 3 and none exceeds 6.  Neighbouring
 nodes are strongly correlated, so exceedances come in clusters: two oracle
 ensembles of 12 independent seeds each gave mean z^2 between 1.2 and 2.1, up
-to 4.6% of the values beyond 3 and at most 4.2 (four trials)."""
+to 4.6% of the values beyond 3 and at most 4.2 (four trials).  The same test
+runs with the paper's sequential gas scheme and with intra- and inter-species
+Coulomb collisions."""
 import multiprocessing
 import os
 import sys
@@ -33,11 +35,19 @@ KW = dict(n_op=40000, iedf_bins=2)
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _oracle_run(seed):
+# the discharge as loaded, with the paper's sequential gas scheme instead
+# of the null-collision test, and with intra- and inter-species Coulomb
+# collisions every 10 steps (ln Gamma raised so that they matter)
+VARIANTS = {"null_collision": {}, "sequential_gas": {"gas_scheme": 1},
+            "coulomb": {"n2": 10, "coulomb_log": 1e3, "coulomb_inter": True}}
+
+
+def _oracle_run(args):
+    seed, extra = args
     sys.path.insert(0, ROOT)
     import oracle as orc
     from paper_0705_0495_gb300 import inputs as inp
-    o = orc.Oracle(inp.cfg1(seed=seed, **KW), inp.xs_tables())
+    o = orc.Oracle(inp.cfg1(seed=seed, **KW, **extra), inp.xs_tables())
     o.step(STEPS)
     return _averages(o.diag())
 
@@ -68,17 +78,19 @@ def _z(a, b):
     return diff / np.where(se > 0, se, 1.0)
 
 
-def test_fp32_gpu_ensemble_matches_fp64_oracle_ensemble():
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+def test_fp32_gpu_ensemble_matches_fp64_oracle_ensemble(variant):
     from paper_0705_0495_gb300 import o2pic
     oracle.build()
+    extra = VARIANTS[variant]
     # independent realisations on the oracle side, run in parallel on the
     # host cores (a spawned pool: no process is forked from a CUDA process)
     pool = multiprocessing.get_context("spawn").Pool(min(SEEDS, os.cpu_count() or 1))
-    pending = pool.map_async(_oracle_run, [101 + k for k in range(SEEDS)])
+    pending = pool.map_async(_oracle_run, [(101 + k, extra) for k in range(SEEDS)])
     tabs = inputs.xs_tables()
     gpu = []
     for k in range(SEEDS):
-        sim = o2pic.Simulation([inputs.cfg1(fp64=False, seed=1 + k, **KW)], tabs)
+        sim = o2pic.Simulation([inputs.cfg1(fp64=False, seed=1 + k, **KW, **extra)], tabs)
         sim.step(STEPS)
         gpu.append(_averages(sim.diagnostics(0)))
         sim.close()
