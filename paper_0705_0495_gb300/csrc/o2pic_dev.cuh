@@ -12,7 +12,8 @@ constexpr int CHUNK = 1024;            // slots per push chunk
 constexpr int PUSH_THREADS = 256;      // 4 consecutive slots per thread
 constexpr int SUBTILE = 128;           // slots of one warp in a tile (32 lanes x 4)
 constexpr int SUBTILES = 1024 / SUBTILE;
-constexpr int BIRTH_CAP_W = 32;        // births staged per sub-tile
+constexpr int BIRTH_CAP_W = 32;        // births staged per sub-tile (null-collision scheme)
+constexpr int BIRTH_CAP_SEQ = 128;     // the same with the sequential gas scheme (n1 steps of collisions at once)
 constexpr int QCAP = 160;              // candidate queue of one warp (< 32 left + one sub-tile)
 constexpr int COLLIDE_THREADS = 256;   // threads per block of the collision kernel
 #ifndef O2_TILES_PER_TICKET
@@ -214,7 +215,8 @@ struct WsPtrs {
     Counts *cnt;              // [D*3]
     int *chunk_ds;            // [D*3 + 1] first chunk per (d,s) (prefix), device copy
     int *tile_cnt;            // [max_chunks * SUBTILES * 3] births per sub-tile and product species
-    void *births;             // [max_chunks * SUBTILES * BIRTH_CAP_W] staged birth records
+    void *births;             // [max_chunks * SUBTILES * birth_cap] staged birth records
+    int birth_cap;            // records per sub-tile
     unsigned long long *births_lb;  // [max_chunks * SUBTILES / BIRTHS_THREADS * 3] look-back words
     unsigned long long *acc_fix;  // [3 * total_nodes] fixed-point density accumulators
     double *acc_dbl;          // [3 * total_nodes] FP64 accumulators

@@ -83,6 +83,7 @@ struct Layout {
     size_t cell[2], off[2], vx[2], vy[2], vz[2];
     size_t total;
     int total_nodes, total_cells, max_chunks, total_cap, sort_blocks, n_lut, maxN, eedf_max, fm_max, cand_cap;
+    int birth_cap;
     long long gtab_n;  // elements of the node-major gas tables
     std::vector<int> pbase, capr, gbase, ccell, sort_cbase, sort_gmax, cs_base, eedf_base, iedf_base,
         fm_base;
@@ -311,7 +312,8 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.disc = B.take(sizeof(Disc) * D);
     L.cnt = B.take(sizeof(Counts) * 3 * D);
     L.tile_cnt = B.take(4ull * 3 * SUBTILES * mc);
-    L.births = B.take((size_t)mc * SUBTILES * BIRTH_CAP_W * (fp64 ? 40 : 24));
+    L.birth_cap = c[0].gas_scheme == 1 ? BIRTH_CAP_SEQ : BIRTH_CAP_W;
+    L.births = B.take((size_t)mc * SUBTILES * L.birth_cap * (fp64 ? 40 : 24));
     L.births_lb = B.take(8ull * 3 * (mc / TILE_ALIGN + 1));
     L.acc = B.take(8ull * 3 * tn);
     L.Efield = B.take(8ull * tn);
@@ -699,6 +701,7 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.chunk_ds = nullptr;
     W.tile_cnt = reinterpret_cast<int *>(b + L.tile_cnt);
     W.births = b + L.births;
+    W.birth_cap = L.birth_cap;
     W.births_lb = reinterpret_cast<unsigned long long *>(b + L.births_lb);
     W.acc_fix = reinterpret_cast<unsigned long long *>(b + L.acc);
     W.acc_dbl = reinterpret_cast<double *>(b + L.acc);

@@ -199,9 +199,10 @@ struct BirthRec {
 // order; the tag restores parent order when they are appended.
 template <typename Real>
 struct BirthSink {
-    BirthRec<Real> *rec;  // the sub-tile's BIRTH_CAP_W records
+    BirthRec<Real> *rec;  // the sub-tile's birth_cap records
     int *n;               // the sub-tile's record count
     Ctl *ctl;
+    int cap;
 };
 
 // ask the L2 cache to fetch [p, p + bytes) (16-byte aligned, a multiple of
@@ -216,7 +217,7 @@ __device__ __forceinline__ void stage_birth(const BirthSink<Real> &B, int tag, i
                                             const Real v[3])
 {
     const int pos = atomicAdd(B.n, 1);
-    if (pos >= BIRTH_CAP_W) {
+    if (pos >= B.cap) {
         set_status(B.ctl, ST_BIRTHBUF);
         return;
     }
@@ -892,7 +893,7 @@ k_collide(WsPtrs W, Pools<Real> P, int par)
             Real vx = vxA[i], vy = vyA[i], vz = vzA[i];
             const Real nun = S.nbins > 0 ? pick<Real>(W.nubin[S.bin_off + bin].numax_n, W.nubin[S.bin_off + bin].numax_n_f)
                                          : pick<Real>(S.numax_n, S.numax_n_f);
-            const BirthSink<Real> B{stage + (size_t)sub * BIRTH_CAP_W, W.tile_cnt + (size_t)sub * NSP, ctl};
+            const BirthSink<Real> B{stage + (size_t)sub * W.birth_cap, W.tile_cnt + (size_t)sub * NSP, ctl, W.birth_cap};
             const Outcome o = gas_collide<Real>(W, Dd, s, (unsigned)rel, step, nun, vx, vy, vz, c, off,
                                                 slot << 1, B);
             if (o.alive) {
@@ -919,25 +920,76 @@ k_collide(WsPtrs W, Pools<Real> P, int par)
     }
 }
 
+// Bound on P = n dx sigma u_n n1 of channel j of species S for a particle
+// of speed |v|, over every gas molecule Box-Muller can give (|V| below 10
+// thermal speeds): the prefix maximum of n dx sigma u_n over the table up
+// to the centre-of-mass energy of |v| + 10 v_gas (beyond the table: the last
+// value times that speed), times n1, with a 1e-3 margin for rounding.  A
+// draw at or above it cannot collide, whatever the molecule.
+// (The speed and its place on the species' energy grid are the same for all
+// channels of the species: dsmc_locate once per particle and speed,
+// dsmc_bound per channel.)
+template <typename Real>
+__device__ __forceinline__ void dsmc_locate(const WsPtrs &W, const SpeciesC &S, const Real v[3], Real &umax,
+                                            int &k, int &region)
+{
+    umax = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) + Real(10) * pick<Real>(S.vgas_n, S.vgas_n_f);
+    const XsPoint<Real> pm = xs_locate<Real>(W.tables[S.table_lo], Lut<Real>::E(W), pick<Real>(S.Ek, S.Ek_f) * umax * umax);
+    k = pm.k;
+    region = pm.region;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real dsmc_bound(const WsPtrs &W, const SpeciesC &S, int j, Real umax, int k, int region,
+                                           Real n1)
+{
+    const Real *tb = GasTab<Real>::ptr(W) + S.gtab_off;
+    const Real *pmr = GasTab<Real>::bound(W) + S.gtab_off;
+    Real bnd;
+    if (region == 0) {
+        bnd = tb[j] * umax;
+    } else if (region == 1) {
+        bnd = pmr[(size_t)k * S.gtab_ld + j];
+    } else {
+        const Real last = tb[(size_t)(k + 1) * S.gtab_ld + j] * umax;
+        const Real pmv = pmr[(size_t)k * S.gtab_ld + j];
+        bnd = last > pmv ? last : pmv;
+    }
+    return bnd * n1 * Real(1.001);
+}
+
 // The paper's sequential scheme for the gas channels (Sec. II, Eq. 1),
 // every n1 steps after the sort: part 0 walks the gas channels of the list
 // numbered below (13), part 1 those above (14).  One block per tile of the
-// table rebuilt after the sort, four slots per thread.  A particle meets the
-// channels of its species in list order; channel k takes place with P =
-// n sigma(E) u n1 dt (clamped at 1 and counted) against a gas molecule drawn
-// from the Maxwellian; one that dies in (15), (16) or (17) is replaced by
-// its product, which meets the later channels ("readmitted").  Random
-// numbers: stream 6 of the chain's first particle, sub-stream k, draws 4g,
-// 4g + 1, 4g + 2 in generation g.  Products are recorded in the first
-// particle's sub-tile: (18)'s with product bits 0 (electron) and 1 (O2+),
-// the one that ends a chain with bit 1.
+// table rebuilt after the sort; the tile's particles are held in shared
+// memory and the list is walked channel by channel.  For a channel every
+// particle of its species draws its test number and compares it with a
+// bound on P (dsmc_bound); those below it are queued and the block's threads
+// take the queue one entry each: a gas molecule from the Maxwellian, P = n
+// sigma(E) u n1 dt (clamped at 1 and counted), the test, the kinematics.  A
+// particle that dies in (15), (16) or (17) is replaced by its product, which
+// meets the later channels ("readmitted").  Random numbers: stream 6 of the
+// chain's first particle, sub-stream = the channel's place in the list,
+// draws 4g (molecule), 4g + 1 (test, direction), 4g + 2 (second direction of
+// (18)) in generation g.  Products are recorded in the first particle's
+// sub-tile: (18)'s with product bits 0 (electron) and 1 (O2+), the one that
+// ends a chain with bit 1.  The decisions are those of walking each
+// particle's chain in turn: a particle's channels stay in list order, and
+// particles do not interact.
 template <typename Real>
-__global__ void __launch_bounds__(DSMC_THREADS)
+__global__ void __launch_bounds__(DSMC_THREADS, 3)
 k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
 {
     pdl_wait();
-    using Acc = typename AccT<Real>::T;
     __shared__ unsigned s_ev[C_NCOUNT];
+    __shared__ Real sv[3][CHUNK];        // velocity of the chain's current particle
+    __shared__ signed char ssp[CHUNK];   // its species, -1 for no particle
+    __shared__ unsigned char sgen[CHUNK];
+    __shared__ unsigned short sq[CHUNK]; // queue of one channel
+    __shared__ Real sumax[CHUNK];        // speed bound and grid place of the particle (dsmc_locate)
+    __shared__ unsigned short sk[CHUNK];
+    __shared__ unsigned char sreg[CHUNK];
+    __shared__ unsigned s_qn;
     Ctl *ctl = W.ctl;
     const int chunk = blockIdx.x;
     if (chunk >= ctl->total_chunks) return;
@@ -951,9 +1003,10 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
     if (chunk >= C.chunk0 + C.nchunk) return;  // padding between species
     const int d = ds / NSP, s = ds % NSP;
     const Disc &Dd = W.disc[d];
-    for (int q = threadIdx.x; q < C_NCOUNT; q += DSMC_THREADS) s_ev[q] = 0;
-    if (part == 1 && threadIdx.x < SUBTILES) W.tile_cnt[(size_t)(chunk * SUBTILES + threadIdx.x) * NSP] = 0;
-    __syncthreads();
+    const int tid = threadIdx.x;
+    for (int q = tid; q < C_NCOUNT; q += DSMC_THREADS) s_ev[q] = 0;
+    if (part == 1 && tid < SUBTILES) W.tile_cnt[(size_t)(chunk * SUBTILES + tid) * NSP] = 0;
+    if (tid == 0) s_qn = 0u;
     const unsigned long long step = ctl->step[par];
     const int cur = ctl->cur;
     int *cellA = P.cell[cur];
@@ -961,108 +1014,156 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
     BirthRec<Real> *stage = reinterpret_cast<BirthRec<Real> *>(W.births);
     const Real *lutE = Lut<Real>::E(W);
     const Real n1 = Real(Dd.n1);
-    for (int k4 = 0; k4 < CHUNK / DSMC_THREADS; ++k4) {
-        const int local = threadIdx.x + k4 * DSMC_THREADS;
-        const int rel = (chunk - C.chunk0) * CHUNK + local;
+    const int rel0 = (chunk - C.chunk0) * CHUNK;
+    const int pb = Dd.pbase[s];
+    unsigned nlive = 0;
+    for (int local = tid; local < CHUNK; local += DSMC_THREADS) {
+        const int rel = rel0 + local;
+        signed char sp = -1;
+        if (rel < C.n) {
+            const int i = pb + rel;
+            if (cellA[i] >= 0) {
+                sp = (signed char)s;
+                const Real v[3] = {vxA[i], vyA[i], vzA[i]};
+                sv[0][local] = v[0];
+                sv[1][local] = v[1];
+                sv[2][local] = v[2];
+                Real um;
+                int k, reg;
+                dsmc_locate<Real>(W, Dd.sp[s], v, um, k, reg);
+                sumax[local] = um;
+                sk[local] = (unsigned short)k;
+                sreg[local] = (unsigned char)reg;
+                ++nlive;
+            }
+        }
+        ssp[local] = sp;
+        sgen[local] = 0;
+    }
+    if (nlive) atomicAdd(&s_ev[C_DSMC], nlive);
+    __syncthreads();
+    for (int kk = 0; kk < Dd.ndsmc; ++kk) {
+        const DsmcCh &e = Dd.dsmc[kk];
+        if (part == 0 ? e.reaction > 12 : e.reaction < 15) continue;  // uniform
+        const SpeciesC &S = Dd.sp[e.sp];
+        // the test of every particle of the channel's species against the
+        // bound, the thread's four particles side by side (independent chains)
+        {
+            constexpr int PT = CHUNK / DSMC_THREADS;
+            bool in[PT];
+            unsigned w[PT];
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                const int local = tid + q * DSMC_THREADS;
+                in[q] = ssp[local] == e.sp;
+                w[q] = in[q] ? rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * sgen[local] + 1u, step,
+                                         (unsigned)(rel0 + local)).x
+                             : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                const int local = tid + q * DSMC_THREADS;
+                if (!in[q]) continue;
+                if (unif<Real>(w[q]) < dsmc_bound<Real>(W, S, e.j, sumax[local], sk[local], sreg[local], n1))
+                    sq[atomicAdd(&s_qn, 1u)] = (unsigned short)local;
+            }
+        }
+        __syncthreads();
+        const int nq = (int)s_qn;
+        if (nq > 0) {
+            const GasChan &ch = S.ch[e.j];
+            for (int qi = tid; qi < nq; qi += DSMC_THREADS) {
+                const int local = sq[qi];
+                const int rel = rel0 + local;
+                const unsigned gen = sgen[local];
+                Real v[3] = {sv[0][local], sv[1][local], sv[2][local]};
+                const uint4 b = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen + 1u, step, (unsigned)rel);
+                const uint4 a = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen, step, (unsigned)rel);
+                Real n0, nn1, n2, n3;
+                box_muller<Real>(a.x, a.y, n0, nn1);
+                box_muller<Real>(a.z, a.w, n2, n3);
+                const Real vg = pick<Real>(S.vgas_n, S.vgas_n_f);
+                const Real V[3] = {vg * n0, vg * nn1, vg * n2};
+                const Real g0 = v[0] - V[0], g1 = v[1] - V[1], g2 = v[2] - V[2];
+                const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
+                const Real u = sqrt(u2);
+                const Real E = pick<Real>(S.Ek, S.Ek_f) * u2;
+                // n_j dx sigma_j(E) from the species' node-major table
+                const XsPoint<Real> pt = xs_locate<Real>(W.tables[S.table_lo], lutE, E);
+                const Real *ra = GasTab<Real>::ptr(W) + S.gtab_off + (size_t)pt.k * S.gtab_ld;
+                const Real xa = ra[e.j], xb = ra[S.gtab_ld + e.j];
+                Real xs = pt.region == 2 ? xb : xa + pt.f * (xb - xa);
+                xs = E < pick<Real>(ch.th, ch.th_f) ? Real(0) : xs;
+                Real Pj = xs * u * n1;
+                if (Pj > Real(1)) {
+                    atomicAdd(&s_ev[C_VIOL_PAIR], 1u);
+                    Pj = Real(1);
+                }
+                if (!(unif<Real>(b.x) < Pj)) continue;
+                atomicAdd(&s_ev[C_EVENTS + ch.reaction], 1u);
+                Real nd[3], nd2[3] = {Real(0), Real(0), Real(1)};
+                iso_dir<Real>(unif<Real>(b.y), unif<Real>(b.z), nd);
+                if (ch.reaction == 18) {
+                    const uint4 e2 = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen + 2u, step, (unsigned)rel);
+                    iso_dir<Real>(unif<Real>(e2.x), unif<Real>(e2.y), nd2);
+                }
+                GasProducts<Real> pr;
+                Real vo[3];
+                Real um;
+                int bk, breg;
+                if (gas_event<Real>(W, Dd, S, ch, v, V, E, nd, nd2, vo, pr)) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) sv[q][local] = vo[q];
+                    dsmc_locate<Real>(W, S, vo, um, bk, breg);
+                    if (pr.n > 0) {
+                        const int i = pb + rel;
+                        const int sub = chunk * SUBTILES + local / SUBTILE;
+                        const BirthSink<Real> B{stage + (size_t)sub * W.birth_cap, W.tile_cnt + (size_t)sub * NSP,
+                                                ctl, W.birth_cap};
+                        for (int q = 0; q < pr.n; ++q)
+                            stage_birth<Real>(B, ((local % SUBTILE) << 1) | pr.prod[q], pr.sp[q], cellA[i], offA[i],
+                                              pr.v[q]);
+                    }
+                } else {
+                    ssp[local] = (signed char)pr.sp[0];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) sv[q][local] = pr.v[0][q];
+                    sgen[local] = (unsigned char)(gen + 1u);
+                    dsmc_locate<Real>(W, Dd.sp[pr.sp[0]], pr.v[0], um, bk, breg);
+                }
+                sumax[local] = um;
+                sk[local] = (unsigned short)bk;
+                sreg[local] = (unsigned char)breg;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) s_qn = 0u;
+        __syncthreads();
+    }
+    // write back: the first particle's new velocity, or its removal and the
+    // product that ends its chain
+    for (int local = tid; local < CHUNK; local += DSMC_THREADS) {
+        const int rel = rel0 + local;
         if (rel >= C.n) break;
-        const int i = Dd.pbase[s] + rel;
+        const int i = pb + rel;
         const int c = cellA[i];
         if (c < 0) continue;
-        atomicAdd(&s_ev[C_DSMC], 1u);
-        const Real off = offA[i];
-        Real v[3] = {vxA[i], vyA[i], vzA[i]};
-        int cs = s, gen = 0;
-        const int sub = chunk * SUBTILES + local / SUBTILE;
-        const int tag = (local % SUBTILE) << 1;
-        const BirthSink<Real> B{stage + (size_t)sub * BIRTH_CAP_W, W.tile_cnt + (size_t)sub * NSP, ctl};
-        // bound on a channel's n dx sigma u_n over every gas molecule Box-
-        // Muller can give (|V| < 10 thermal speeds), from the particle's speed;
-        // refreshed when the chain changes species
-        int bsp = -1, bk = 0, breg = 0;
-        Real umax = Real(0);
-        for (int kk = 0; kk < Dd.ndsmc; ++kk) {
-            const DsmcCh &e = Dd.dsmc[kk];
-            if (e.sp != cs || (part == 0 ? e.reaction > 12 : e.reaction < 15)) continue;
-            const SpeciesC &S = Dd.sp[cs];
-            const GasChan &ch = S.ch[e.j];
-            const uint4 b = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen + 1u, step, (unsigned)rel);
-            if (bsp != cs) {
-                umax = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) + Real(10) * pick<Real>(S.vgas_n, S.vgas_n_f);
-                const XsPoint<Real> pm = xs_locate<Real>(W.tables[S.table_lo], lutE, pick<Real>(S.Ek, S.Ek_f) * umax * umax);
-                bk = pm.k;
-                breg = pm.region;
-                bsp = cs;
-            }
-            {
-                // P = n dx sigma u_n n1 <= the bound times n1 (1e-3 margin for rounding):
-                // a draw at or above it cannot collide, whatever the molecule
-                const Real *tb = GasTab<Real>::ptr(W) + S.gtab_off;
-                const Real *pmr = GasTab<Real>::bound(W) + S.gtab_off;
-                Real bnd;
-                if (breg == 0) bnd = tb[e.j] * umax;
-                else if (breg == 1) bnd = pmr[(size_t)bk * S.gtab_ld + e.j];
-                else {
-                    const Real last = tb[(size_t)(bk + 1) * S.gtab_ld + e.j] * umax;
-                    const Real pmv = pmr[(size_t)bk * S.gtab_ld + e.j];
-                    bnd = last > pmv ? last : pmv;
-                }
-                if (unif<Real>(b.x) >= bnd * n1 * Real(1.001)) continue;
-            }
-            const uint4 a = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen, step, (unsigned)rel);
-            Real n0, nn1, n2, n3;
-            box_muller<Real>(a.x, a.y, n0, nn1);
-            box_muller<Real>(a.z, a.w, n2, n3);
-            const Real vg = pick<Real>(S.vgas_n, S.vgas_n_f);
-            const Real V[3] = {vg * n0, vg * nn1, vg * n2};
-            const Real g0 = v[0] - V[0], g1 = v[1] - V[1], g2 = v[2] - V[2];
-            const Real u2 = g0 * g0 + g1 * g1 + g2 * g2;
-            const Real u = sqrt(u2);
-            const Real E = pick<Real>(S.Ek, S.Ek_f) * u2;
-            // n_j dx sigma_j(E) from the species' node-major table
-            const XsPoint<Real> pt = xs_locate<Real>(W.tables[S.table_lo], lutE, E);
-            const Real *ra = GasTab<Real>::ptr(W) + S.gtab_off + (size_t)pt.k * S.gtab_ld;
-            const Real xa = ra[e.j], xb = ra[S.gtab_ld + e.j];
-            Real xs = pt.region == 2 ? xb : xa + pt.f * (xb - xa);
-            xs = E < pick<Real>(ch.th, ch.th_f) ? Real(0) : xs;
-            Real Pj = xs * u * n1;
-            if (Pj > Real(1)) {
-                atomicAdd(&s_ev[C_VIOL_PAIR], 1u);
-                Pj = Real(1);
-            }
-            if (!(unif<Real>(b.x) < Pj)) continue;
-            atomicAdd(&s_ev[C_EVENTS + ch.reaction], 1u);
-            Real nd[3], nd2[3] = {Real(0), Real(0), Real(1)};
-            iso_dir<Real>(unif<Real>(b.y), unif<Real>(b.z), nd);
-            if (ch.reaction == 18) {
-                const uint4 e2 = rng_block(Dd.seed, Dd.discharge, s, 6, kk, 4u * gen + 2u, step, (unsigned)rel);
-                iso_dir<Real>(unif<Real>(e2.x), unif<Real>(e2.y), nd2);
-            }
-            GasProducts<Real> pr;
-            Real vo[3];
-            if (gas_event<Real>(W, Dd, S, ch, v, V, E, nd, nd2, vo, pr)) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) v[q] = vo[q];
-                for (int q = 0; q < pr.n; ++q) stage_birth<Real>(B, tag | pr.prod[q], pr.sp[q], c, off, pr.v[q]);
-            } else {
-                cs = pr.sp[0];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) v[q] = pr.v[0][q];
-                ++gen;
-            }
-            bsp = -1;  // the speed changed: a new bound
-        }
-        if (gen == 0) {
+        const Real v[3] = {sv[0][local], sv[1][local], sv[2][local]};
+        if (sgen[local] == 0) {
             vxA[i] = v[0];
             vyA[i] = v[1];
             vzA[i] = v[2];
         } else {
+            const Real off = offA[i];
             cellA[i] = -1;
             deposit_global(acc_global<Real>(W) + (size_t)s * W.total_nodes + Dd.gbase, c, off, -1);
-            stage_birth<Real>(B, tag | 1, cs, c, off, v);
+            const int sub = chunk * SUBTILES + local / SUBTILE;
+            const BirthSink<Real> B{stage + (size_t)sub * W.birth_cap, W.tile_cnt + (size_t)sub * NSP, ctl, W.birth_cap};
+            stage_birth<Real>(B, ((local % SUBTILE) << 1) | 1, ssp[local], c, off, v);
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < C_NCOUNT; k += DSMC_THREADS)
+    for (int k = tid; k < C_NCOUNT; k += DSMC_THREADS)
         if (s_ev[k]) atomicAdd(&W.counters[(size_t)d * C_NCOUNT + k], (unsigned long long)s_ev[k]);
 }
 
@@ -1115,10 +1216,10 @@ k_births(WsPtrs W, Pools<Real> P, int par, int salt)
     const int T1 = (W.cnt[d * NSP + 2].chunk0 + W.cnt[d * NSP + 2].nchunk) * SUBTILES;
     int mine[NSP] = {0, 0, 0};
     const bool in = t < total && t < T1;
-    const BirthRec<Real> *rec = reinterpret_cast<const BirthRec<Real> *>(W.births) + (size_t)t * BIRTH_CAP_W;
+    const BirthRec<Real> *rec = reinterpret_cast<const BirthRec<Real> *>(W.births) + (size_t)t * W.birth_cap;
     int nrec = 0;  // records of this sub-tile (any order; the tag gives species and parent order)
     if (in) {
-        nrec = min(W.tile_cnt[(size_t)t * NSP], BIRTH_CAP_W);
+        nrec = min(W.tile_cnt[(size_t)t * NSP], W.birth_cap);
         for (int r = 0; r < nrec; ++r) ++mine[rec[r].tag & 3];
     }
     int excl[NSP];
