@@ -110,6 +110,8 @@ def lib():
         l.orc_bin_of.argtypes = [C.c_void_p, C.c_double]
         l.orc_fields.argtypes = [C.c_void_p, dp, dp, dp]
         l.orc_counters.argtypes = [C.c_void_p, lp, lp, lp, lp]
+        l.orc_reset_diag.restype = None
+        l.orc_reset_diag.argtypes = [C.c_void_p]
         l.orc_diag.restype = C.c_longlong
         l.orc_diag.argtypes = [C.c_void_p, dp, dp, lp, lp, lp]
         l.orc_philox.argtypes = [u32p, u32p, u32p]
@@ -288,6 +290,9 @@ class Oracle:
         lp = lambda a: a.ctypes.data_as(C.POINTER(C.c_longlong))
         lib().orc_counters(self.h, lp(ab), lp(ev), lp(vi), lp(bi))
         return {"absorbed": ab.reshape(3, 2), "events": ev, "violations": vi, "births": bi}
+
+    def reset_diag(self):
+        lib().orc_reset_diag(self.h)
 
     def diag(self):
         d, N = self.d, self.N

@@ -1496,6 +1496,17 @@ void orc_counters(const orc_sim *s, long long *absorbed, long long *events,
     if (births) memcpy(births, s->births, sizeof(s->births));
 }
 
+void orc_reset_diag(orc_sim *s)
+{
+    int N = s->c.n_cells;
+    for (int sp = 0; sp < 3; ++sp) memset(s->dens_sum[sp], 0, (N + 1) * sizeof(double));
+    memset(s->phi_sum, 0, (N + 1) * sizeof(double));
+    if (s->c.eedf_bins > 0) memset(s->eedf, 0, s->c.eedf_bins * sizeof(long long));
+    if (s->c.iedf_bins > 0) memset(s->iedf, 0, 2 * s->c.iedf_bins * sizeof(long long));
+    if (s->c.fm_bins > 0) memset(s->fm, 0, (size_t)s->c.fm_xbins * s->c.fm_bins * sizeof(long long));
+    s->nsamp = 0;
+}
+
 long long orc_diag(const orc_sim *s, double *dens_sum, double *phi_sum,
                    long long *eedf, long long *iedf, long long *fm)
 {

@@ -86,6 +86,8 @@ void orc_fields(orc_sim *s, double *rho, double *phi, double *E);
 void orc_counters(const orc_sim *s, long long *absorbed, long long *events,
                   long long *violations, long long *births);
 /* diagnostics: dens_sum[3][N+1], phi_sum[N+1], eedf, iedf[2][bins], fm[xbins][bins] */
+/* clear the diagnostic sums and histograms (a new averaging window) */
+void orc_reset_diag(orc_sim *s);
 long long orc_diag(const orc_sim *s, double *dens_sum, double *phi_sum,
                    long long *eedf, long long *iedf, long long *fm);
 
