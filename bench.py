@@ -48,6 +48,8 @@ def _args():
                    help="gas targets: 0 null-collision test (default), 1 the sequential scheme every n1 steps")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the workload's sort interval instead of timing the candidates first")
+    p.add_argument("--clocks-dir", default=None,
+                   help="keep the raw nvidia-smi clock samples of the timed region in this directory")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the FP64, batched-sweep, Coulomb and sequential-gas figures beside the main one")
     return p.parse_args()
@@ -103,10 +105,13 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    out_dir = None  # where the raw samples go (default: the system's temporary directory)
+
     def __init__(self, index):
+        import tempfile
         self.index = index
         self.proc = None
-        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.out = os.path.join(Clocks.out_dir or tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -516,6 +521,7 @@ def run_ours(a, rank, world, local_rank):
 
 def main():
     a = _args()
+    Clocks.out_dir = a.clocks_dir
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

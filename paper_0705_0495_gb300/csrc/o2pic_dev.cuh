@@ -37,7 +37,10 @@ constexpr int SORT_ILP = O2_SORT_ILP;  // 32-slot rows loaded per warp before ra
 constexpr int SORT_CHUNK = SORT_WARPS * SORT_WARP_SLOTS;
 constexpr int PAIR_BIRTH_CAP = 16;     // births of (19) per cell per pass
 constexpr int MAX_GAS_CH = 16;
-constexpr int FIELD_THREADS = 1024;
+#ifndef O2_FIELD_THREADS
+#define O2_FIELD_THREADS 1024
+#endif
+constexpr int FIELD_THREADS = O2_FIELD_THREADS;
 constexpr int FIX_BITS = 24;           // fixed-point deposit: weight * 2^24
 constexpr int MAX_DISCHARGES = 1024;
 constexpr long long SPIN_LIMIT = 1LL << 22;  // polls of a bounded wait
