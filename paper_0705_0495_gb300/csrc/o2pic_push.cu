@@ -438,22 +438,25 @@ __host__ __device__ __forceinline__ unsigned long long split_value(unsigned long
     return (unsigned long long)(hi * (1LL << SPLIT_BITS) + lo);
 }
 
-__device__ __forceinline__ unsigned long long acc_value(unsigned long long node) { return split_value(node); }
-__device__ __forceinline__ double acc_value(double node) { return node; }
+// The FP64 path's shared grid holds exact 64-bit integer sums of the
+// weights in units of 2^-FIX_BITS_64 (a particle's two weights add up to
+// exactly 2^FIX_BITS_64); they become doubles once per node and flush.  A
+// block adds at most FLUSH_TICKETS tickets of weights before a flush, far
+// below the 2^63 / 2^FIX_BITS_64 particles a node could hold.  (Shared-memory
+// double atomics took nine tenths of the FP64 push.)
+constexpr int FIX_BITS_64 = 40;
+static_assert((long long)FLUSH_TICKETS * TILES_PER_TICKET * CHUNK < (1LL << (63 - FIX_BITS_64)),
+              "FP64 shared sums must stay within int64");
 
-// removal of one particle deposited in phase A (it died in a collision):
-// the same fixed-point weights, so the node value returns exactly
-__device__ __forceinline__ void deposit_shared_remove(unsigned long long *sAcc, int c, float off)
+// the block's sum of a node in the global accumulators' type
+template <typename Real> __device__ __forceinline__ typename AccT<Real>::T sacc_value(unsigned long long node);
+template <> __device__ __forceinline__ unsigned long long sacc_value<float>(unsigned long long node)
 {
-    const unsigned w1 = __float2uint_rn(off * (float)(1 << FIX_BITS));
-    const unsigned w0 = (1u << FIX_BITS) - w1;
-    split_sub(&sAcc[c], w0);
-    split_sub(&sAcc[c + 1], w1);
+    return split_value(node);
 }
-__device__ __forceinline__ void deposit_shared_remove(double *sAcc, int c, double off)
+template <> __device__ __forceinline__ double sacc_value<double>(unsigned long long node)
 {
-    atomicAdd(&sAcc[c], -(1.0 - off));
-    atomicAdd(&sAcc[c + 1], -off);
+    return (double)(long long)node * (1.0 / (double)(1ull << FIX_BITS_64));
 }
 
 // charge of one particle added to (sign > 0) or removed from the global
@@ -517,13 +520,44 @@ __device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep
         split_add(&sAcc[ck + 1], w1[k]);
     }
 }
-__device__ __forceinline__ void deposit4(double *sAcc, const int dep[4], const double off[4])
+__device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep[4], const double off[4])
 {
+    constexpr double SC = (double)(1ull << FIX_BITS_64);
+    unsigned long long w0[4], w1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        w1[k] = dep[k] >= 0 ? (unsigned long long)__double2ll_rn(off[k] * SC) : 0ull;
+        w0[k] = dep[k] >= 0 ? (1ull << FIX_BITS_64) - w1[k] : 0ull;
+    }
+    // as in the FP32 path: a warp whose 128 slots sit in one cell adds its
+    // sums once, a lane whose four slots share a cell adds them once
+    const int lane = threadIdx.x & 31;
+    const bool same = dep[0] >= 0 && dep[1] == dep[0] && dep[2] == dep[0] && dep[3] == dep[0];
+    unsigned long long a = w0[0] + w0[1] + w0[2] + w0[3];
+    unsigned long long b = w1[0] + w1[1] + w1[2] + w1[3];
+    const int c0 = __shfl_sync(0xffffffffu, dep[0], 0);
+    if (__all_sync(0xffffffffu, same && dep[0] == c0)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&sAcc[c0], a);
+            atomicAdd(&sAcc[c0 + 1], b);
+        }
+        return;
+    }
+    if (same) {
+        atomicAdd(&sAcc[dep[0]], a);
+        atomicAdd(&sAcc[dep[0] + 1], b);
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (dep[k] >= 0) {
-            atomicAdd(&sAcc[dep[k]], 1.0 - off[k]);
-            atomicAdd(&sAcc[dep[k] + 1], off[k]);
+            atomicAdd(&sAcc[dep[k]], w0[k]);
+            atomicAdd(&sAcc[dep[k] + 1], w1[k]);
         }
     }
 }
@@ -542,7 +576,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     using Acc = typename AccT<Real>::T;
     constexpr int NW = PUSH_THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    Acc *sAcc = reinterpret_cast<Acc *>(smem);
+    unsigned long long *sAcc = reinterpret_cast<unsigned long long *>(smem);  // integer sums (both paths)
     Real *sE = reinterpret_cast<Real *>(sAcc + (Nmax + 2));
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     // per-warp list of collision candidates (slot, energy bin) before it is
@@ -574,7 +608,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         __syncthreads();
         Acc *g = accG + (size_t)fs * W.total_nodes + Dd.gbase;
         for (int i = tid; i <= Dd.N; i += PUSH_THREADS) {
-            const Acc v = acc_value(sAcc[i]);
+            const Acc v = sacc_value<Real>(sAcc[i]);
             if (v != Acc(0)) acc_add(&g[i], v);
         }
         for (int q = tid; q < C_NCOUNT; q += PUSH_THREADS) {
@@ -630,8 +664,8 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 W.tile_cnt[((size_t)tbeg * SUBTILES + q) * NSP] = 0;
             continue;
         }
-        // a new (d, s), or the FP32 split sums at their bound: flush
-        if (nx != ds || (sizeof(Real) == 4 && run_tk >= FLUSH_TICKETS)) {
+        // a new (d, s), or the block's integer sums at their bound: flush
+        if (nx != ds || run_tk >= FLUSH_TICKETS) {
             if (qn > 0) list_out();
             if (ds >= 0) flush(ds);
             const int nd = nx / NSP;
@@ -641,7 +675,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 for (int i = tid; i <= Dn.N; i += PUSH_THREADS) sE[i] = Eg[i];
                 d = nd;
             }
-            for (int i = tid; i <= Dn.N + 1; i += PUSH_THREADS) sAcc[i] = Acc(0);
+            for (int i = tid; i <= Dn.N + 1; i += PUSH_THREADS) sAcc[i] = 0ull;
             {
                 const SpeciesC &Sn = Dn.sp[nx % NSP];
                 for (int b = tid; b < Sn.nbins; b += PUSH_THREADS) {
@@ -1337,9 +1371,8 @@ k_births(WsPtrs W, Pools<Real> P, int par, int salt)
 template <typename Real>
 static size_t push_smem_bytes(int Nmax, int eedf_max, int fm_max)
 {
-    using Acc = typename AccT<Real>::T;
     constexpr int NW = PUSH_THREADS / 32;
-    size_t b = sizeof(Acc) * (Nmax + 2) + sizeof(Real) * (Nmax + 2);
+    size_t b = sizeof(unsigned long long) * (Nmax + 2) + sizeof(Real) * (Nmax + 2);
     b += sizeof(int) * NW * QCAP;  // candidate slots
     b += sizeof(unsigned) * (eedf_max + fm_max);
     b += (size_t)NW * QCAP;        // candidate energy bins
