@@ -96,3 +96,9 @@ def test_oracle_binding_config_layout_matches_its_header(tmp_path):
     c = _c_layout(tmp_path, "orc_cfg", names, "o2pic_oracle.h", os.path.join(ROOT, "oracle"))
     py = [getattr(cls, n).offset for n in names] + [C.sizeof(cls)]
     assert c == py, list(zip(names + ["sizeof"], c, py))
+
+
+def test_kernel_kinds_of_the_binding_match_the_header():
+    src = open(os.path.join(ROOT, "include", "o2pic.h")).read()
+    kinds = dict((k.lower(), int(v)) for k, v in re.findall(r"PIC_KERNEL_([A-Z_]+)\s*=\s*(\d+)", src))
+    assert kinds == o2pic.KERNELS
