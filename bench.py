@@ -501,6 +501,15 @@ def run_ours(a, rank, world, local_rank):
                 "precision": ("FP64 throughout" if d.fp64 else
                               "FP32 particles, push and collisions; exact fixed-point charge "
                               "accumulation; FP64 Poisson, field and diagnostics"),
+                # error against the FP64 oracle, as the parity tests establish it
+                "accuracy": ("FP64 path: step by step within 1e-9 of the gap and of the thermal "
+                             "speed with identical event counts; FP32 path: each step from the "
+                             "oracle's state within 1e-5, at most 1e-4 of particle-steps with a "
+                             "flipped decision (one full-size step of this workload included); "
+                             "time-averaged densities, potential, EEDF and IEDF of FP32 and FP64 "
+                             "seed ensembles within 3 standard errors of the oracle's "
+                             "(tests/test_gpu_parity.py, test_gpu_statistics.py, "
+                             "test_gpu_long_horizon.py)"),
                 "l2": ("inputs larger than L2: the particle state touched per time step "
                        f"({state_bytes / 1e6:.0f} MB) exceeds the 129 MB L2"
                        if not flush else "L2 flushed between timed iterations"),
