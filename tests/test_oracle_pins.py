@@ -1,7 +1,7 @@
 """Pins of the FP64 CPU oracle against what the paper and mathematics fix.
 
-Each test checks the oracle against something other than itself: published
-known-answer vectors, closed forms printed in the paper (Eqs. 4, 8, 9),
+Each test checks the oracle against something other than itself: a second
+Philox4x32-10 implementation, closed forms printed in the paper (Eqs. 4, 8, 9),
 exact solutions of the discrete field equations, leapfrog trajectories,
 the cold-plasma dispersion relation, conservation laws of each reaction of
 Table I, the collision-rate algebra of the null-collision method and of
@@ -89,6 +89,63 @@ def test_philox_uniformity_and_independence():
     chi2, p = stats.chisquare(counts)
     assert p > 1e-4
     assert abs(np.corrcoef(u[:-1], u[1:])[0, 1]) < 0.03
+
+
+# A second, independent Philox4x32-10: PyTorch's header-only engine
+# (ATen/core/PhiloxRNGEngine.h).  Its key is the 64-bit seed (words 0, 1),
+# its counter words 2, 3 the 64-bit subsequence and words 0, 1 the 64-bit
+# offset; four calls return the four words of one block.
+_PHILOX_REF_SRC = r"""
+#include <ATen/core/PhiloxRNGEngine.h>
+#include <cstdio>
+int main() {
+    unsigned c0, c1, c2, c3, k0, k1;
+    while (std::scanf("%u %u %u %u %u %u", &c0, &c1, &c2, &c3, &k0, &k1) == 6) {
+        const uint64_t seed = (uint64_t)k0 | ((uint64_t)k1 << 32);
+        const uint64_t sub = (uint64_t)c2 | ((uint64_t)c3 << 32);
+        const uint64_t off = (uint64_t)c0 | ((uint64_t)c1 << 32);
+        at::philox_engine e(seed, sub, off);
+        const unsigned w0 = e(), w1 = e(), w2 = e(), w3 = e();
+        std::printf("%u %u %u %u\n", w0, w1, w2, w3);
+    }
+    return 0;
+}
+"""
+
+
+def test_philox_matches_an_independent_implementation(tmp_path):
+    """The oracle's generator is Philox4x32-10 bit for bit: its blocks equal
+    those of PyTorch's own engine (written from the same SC'11 definition,
+    not from this repository) for random counters and keys, all-zero and
+    all-one words and carries across the 32-bit halves."""
+    import shutil
+    import subprocess
+
+    import torch
+    inc = os.path.join(os.path.dirname(torch.__file__), "include")
+    if not os.path.exists(os.path.join(inc, "ATen", "core", "PhiloxRNGEngine.h")):
+        pytest.skip("PyTorch headers not installed")
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    src = tmp_path / "philox_ref.cpp"
+    exe = tmp_path / "philox_ref"
+    src.write_text(_PHILOX_REF_SRC)
+    subprocess.run([cxx, "-O1", "-std=c++17", "-I", inc, str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    rng = np.random.default_rng(5)
+    M = 2**32 - 1
+    cases = [([0, 0, 0, 0], [0, 0]), ([M, M, M, M], [M, M]), ([M, 0, M, 0], [0, M]),
+             ([0, 0, 0, 0], [M, 0]), ([1, 2, 3, 4], [5, 6])]
+    for _ in range(300):
+        cases.append(([int(x) for x in rng.integers(0, 2**32, size=4, dtype=np.uint64)],
+                      [int(x) for x in rng.integers(0, 2**32, size=2, dtype=np.uint64)]))
+    stdin = "".join(" ".join(str(v) for v in c + k) + "\n" for c, k in cases)
+    out = subprocess.run([str(exe)], input=stdin, capture_output=True, text=True, check=True).stdout
+    ref = [[int(v) for v in line.split()] for line in out.strip().splitlines()]
+    assert len(ref) == len(cases)
+    for (c, k), r in zip(cases, ref):
+        assert list(oracle.philox(c, k)) == r, (c, k)
 
 
 # ------------------------------------------------------- cross sections
