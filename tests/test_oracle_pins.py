@@ -624,6 +624,40 @@ def test_neutralisation_rate_matches_eq1(weight):
     assert abs(ev - expect) < 4 * math.sqrt(expect) + 0.02 * expect
 
 
+@pytest.mark.parametrize("reaction,target", [(13, 2), (19, 1)])
+def test_electron_target_rate_matches_eq1(reaction, target):
+    """Recombination (13) on O2+ and detachment (19) on O- with a cross
+    section linear in the pair energy (exact under the tables' linear
+    interpolation): every electron, at speed u on resting targets, reacts
+    with P = n_T sigma(E) u tau of Eq. 1, E = mu u^2 / 2 with the pair's
+    reduced mass; the projectiles are thinned (bound below 1).  A wrong mass,
+    target density, speed or tau changes the count by far more than its
+    binomial spread."""
+    L, N = 0.064, 64
+    dx = L / N
+    ne, nt, w, dt, u = 20000, 4000, 1e6, 1e-12, 1e6
+    E = inputs.geometric_grid(0.01, 10.0, 64)
+    a = 4.4e-9  # m^2 per eV
+    tab = dict(reaction=reaction, sub=0, E_eV=E, sigma_m2=a * E, threshold_eV=0.0)
+    d = _disch(L=L, n_cells=N, n1=1, dt_override=dt, weight_override=w)
+    o = oracle.Oracle(d, [tab])
+    rs = np.random.default_rng(41 + reaction)
+    x = rs.uniform(10.3 * dx, 10.7 * dx, ne)
+    n = rs.normal(size=(ne, 3))
+    v = u * n / np.linalg.norm(n, axis=1)[:, None]
+    o.set(0, x, v[:, 0], v[:, 1], v[:, 2])
+    o.set(target, x[:nt], np.zeros(nt), np.zeros(nt), np.zeros(nt))
+    o.set(3 - target, [], [], [], [])
+    o.step(1)
+    ev = o.counters()["events"][reaction]
+    mu = ME * MASS[target] / (ME + MASS[target])
+    Ep = 0.5 * mu * u * u / QE
+    P = nt * w / dx * a * Ep * u * dt
+    assert 0.03 < P < 0.07
+    expect = ne * P
+    assert abs(ev - expect) < 4 * math.sqrt(expect * (1 - P))
+
+
 def test_pair_pass_exhausts_targets_with_clamped_probability():
     L, N = 0.064, 64
     dx = L / N
