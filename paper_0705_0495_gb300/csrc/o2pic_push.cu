@@ -769,6 +769,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             // each slot is pushed without branches; absorptions are noted in
             // a mask and handled after the four slots
             unsigned nslots = 0, nlive = 0, outm = 0, wallm = 0;
+            bool cchg = false;  // a cell index of the lane's slots changed
             int dep[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -794,7 +795,9 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 wallm |= cn >= N ? 1u << k : 0u;
                 vx[k] = was ? v : vx[k];
                 off[k] = live ? o : off[k];
-                c[k] = was ? (out ? -1 : cn) : ck;
+                const int cnew = was ? (out ? -1 : cn) : ck;
+                cchg |= cnew != ck;
+                c[k] = cnew;
                 dep[k] = live ? cn : -1;
                 int bin = 0;
                 unsigned thr = tnull;
@@ -828,26 +831,34 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             }
             if (DIAG) {
                 // distributions after the free flight, before collisions
+                if (s == 0 && Dd.eedf_bins > 0) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int cn = dep[k];
-                    if (cn < 0) continue;
-                    const Real v = vx[k];
-                    if (s == 0 && cn == N / 2 && Dd.eedf_bins > 0) {
-                        const Real vy = vyA[i0 + k], vz = vzA[i0 + k];
+                    for (int k = 0; k < 4; ++k) {
+                        if (dep[k] != N / 2) continue;
+                        const Real v = vx[k], vy = vyA[i0 + k], vz = vzA[i0 + k];
                         const Real Ee = pick<Real>(S.ke_eV, S.ke_eV_f) * (v * v + vy * vy + vz * vz);
                         const Real bb = floor(Ee * pick<Real>(Dd.eedf_scale, Dd.eedf_scale_f));
                         if (bb >= Real(0) && bb < Real(Dd.eedf_bins)) atomicAdd(&sEedf[(int)bb], 1u);
                     }
-                    if (s == 1 && Dd.fm_bins > 0) {
-                        Real Es = pick<Real>(S.ke_eV, S.ke_eV_f) * v * v;
-                        if (v < Real(0)) Es = -Es;
-                        const Real bb = floor((Es + pick<Real>(Dd.fm_emax, Dd.fm_emax_f)) *
-                                              pick<Real>(Dd.fm_scale, Dd.fm_scale_f));
-                        if (bb >= Real(0) && bb < Real(Dd.fm_bins)) {
-                            const int xb = (int)(((long long)cn * Dd.fm_xbins) / N);
-                            atomicAdd(&sFm[xb * Dd.fm_bins + (int)bb], 1u);
+                }
+                if (s == 1 && Dd.fm_bins > 0) {
+                    // cold, sorted O- of a warp fall into a few bins: the lanes
+                    // of one bin add their count once (no 32-way conflicts)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int cn = dep[k];
+                        int fb = -1;
+                        if (cn >= 0) {
+                            const Real v = vx[k];
+                            Real Es = pick<Real>(S.ke_eV, S.ke_eV_f) * v * v;
+                            if (v < Real(0)) Es = -Es;
+                            const Real bb = floor((Es + pick<Real>(Dd.fm_emax, Dd.fm_emax_f)) *
+                                                  pick<Real>(Dd.fm_scale, Dd.fm_scale_f));
+                            if (bb >= Real(0) && bb < Real(Dd.fm_bins))
+                                fb = (int)(((long long)cn * Dd.fm_xbins) / N) * Dd.fm_bins + (int)bb;
                         }
+                        const unsigned peers = __match_any_sync(0xffffffffu, fb);
+                        if (fb >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sFm[fb], (unsigned)__popc(peers));
                     }
                 }
             }
@@ -862,9 +873,14 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 }
             }
             if (full) {
-                st4(cellA + i0, c);
-                st4(offA + i0, off);
-                st4(vxA + i0, vx);
+                // an unchanged value is not written back: slow ions keep
+                // their cells for many steps, and a lane of dead slots
+                // changes nothing (its DRAM sectors then stay clean)
+                if (cchg) st4(cellA + i0, c);
+                if (nlive) {
+                    st4(offA + i0, off);
+                    st4(vxA + i0, vx);
+                }
             } else {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
