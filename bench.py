@@ -47,7 +47,8 @@ def _args():
     p.add_argument("--gas-scheme", type=int, default=None, choices=[0, 1],
                    help="gas targets: 0 null-collision test (default), 1 the sequential scheme every n1 steps")
     p.add_argument("--no-autotune", action="store_true",
-                   help="keep the workload's sort interval instead of timing the candidates first")
+                   help="keep the workload's sort interval and the push grid's blocks per SM "
+                        "instead of timing the candidates first")
     p.add_argument("--clocks-dir", default=None,
                    help="keep the raw nvidia-smi clock samples of the timed region in this directory")
     p.add_argument("--no-variants", action="store_true",
@@ -306,6 +307,13 @@ def run_ours(a, rank, world, local_rank):
         d.sort_interval = best
         tune = {"chosen": best, "ms_per_time_step": {str(k): v for k, v in ms.items()}}
     sim = o2pic.Simulation([d], tabs)
+    push_tune = None
+    if not a.no_autotune:
+        # the push grid: every blocks-per-SM count timed on this simulation
+        # (results do not depend on it)
+        pb, pms = autotune.tune_push_blocks(sim)
+        push_tune = {"chosen": pb, "max": sim.launch("push")[1],
+                     "ms_per_time_step": {str(k): v for k, v in pms.items()}}
     spc = d.steps_per_cycle
     state_bytes = sum(d.n_init) * (12 + (16 if not d.fp64 else 32))
     flush = state_bytes < 4 * L2_BYTES
@@ -515,6 +523,7 @@ def run_ours(a, rank, world, local_rank):
                        if not flush else "L2 flushed between timed iterations"),
                 "parallelism": f"{world} GPU(s), one independent discharge per GPU",
                 "sort_interval_autotune": tune,
+                "push_blocks_per_sm_autotune": push_tune,
             },
             "roofline": roof,
             "e2e": e2e,

@@ -293,6 +293,27 @@ pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, long long *l
                              double *bytes, int reset);
 
 /*
+ * Launch shape of a kernel kind, for autotuning.  Only PIC_KERNEL_PUSH has
+ * one: the particle push (steps 3 and 4 above, the charge assignment of
+ * step 1 and the null-collision test of step 5) is a persistent grid of
+ * blocks_per_sm blocks of 256 threads on every SM, each block taking tickets
+ * of tiles until none are left.  pic_init sets the largest count that fits on
+ * an SM (registers and shared memory); pic_set_launch may lower it to any
+ * count in 1 .. that maximum.  Results do not depend on it: the charge sums
+ * are exact integers and births are appended in parent order (FP32 mixed
+ * state is bit for bit the same; the FP64 path adds each block's charge to
+ * double accumulators, whose rounding can differ in the last bits).  The
+ * call waits for the handle's stream and drops the captured graph of one
+ * period, which the next pic_step records again.
+ *   pic_get_launch  current and largest blocks per SM (either pointer may
+ *                   be NULL)
+ *   pic_set_launch  PIC_EINVAL for another kind or a count out of range, and
+ *                   the shape is left unchanged
+ */
+pic_status pic_get_launch(pic_handle *h, int kernel, int *blocks_per_sm, int *max_blocks_per_sm);
+pic_status pic_set_launch(pic_handle *h, int kernel, int blocks_per_sm);
+
+/*
  * pic_field_solve_static -- charge deposit, Poisson solve and field of ONE
  * discharge from particle arrays that the caller owns, without allocating
  * any memory.  The paper has no counterpart: this entry point serves callers

@@ -1,4 +1,4 @@
-"""Runtime autotuner of the cell-sort interval.
+"""Runtime autotuners of the cell-sort interval and of the push grid.
 
 The sort runs on every particle-target step (every n1 steps) and, in
 addition, every `sort_interval` steps: sorting more often keeps the particles
@@ -8,6 +8,13 @@ each candidate interval (the divisors of n1, and 0 = only on particle-target
 steps) on the GPU and returns the fastest.  The choice changes the slot order
 and so the realisation of the random streams, not the method: the oracle
 follows the same interval.
+
+The push is a persistent grid of blocks taking tickets of tiles; how many
+blocks share an SM (1 up to what its registers and shared memory hold) trades
+latency hiding against contention.  Its results do not depend on the count,
+so the push tuner switches it on one running simulation and times the
+candidates in interleaved rounds (each round gives every candidate the next
+stretch of the discharge, so a drift of the plasma favours none).
 """
 import dataclasses
 
@@ -43,4 +50,37 @@ def tune_sort_interval(discharge, tables, warm_steps=100, timed_steps=200, cands
         finally:
             sim.close()
     best = min(ms, key=ms.get)
+    return best, ms
+
+
+def push_candidates(max_per_sm):
+    """Blocks per SM worth timing for the push: every count that fits."""
+    return list(range(1, max(1, int(max_per_sm)) + 1))
+
+
+def tune_push_blocks(sim, steps=200, rounds=2, cands=None):
+    """Time each blocks-per-SM count of the push on the running simulation
+    `sim` (CUDA events on its stream, `steps` time steps per candidate and
+    round after one untimed period for the new grid's graph); leaves the
+    fastest set and returns (best, {count: ms per time step})."""
+    import torch
+    _, mx = sim.launch("push")
+    cands = cands if cands is not None else push_candidates(mx)
+    warm = max(2, min(steps, 64))
+    tot = {k: 0.0 for k in cands}
+    for _ in range(rounds):
+        for k in cands:
+            sim.set_launch(k)
+            sim.step(warm)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(sim.stream)
+            sim.step(steps)
+            e1.record(sim.stream)
+            torch.cuda.synchronize()
+            tot[k] += e0.elapsed_time(e1)
+    ms = {k: v / (rounds * steps) for k, v in tot.items()}
+    best = min(ms, key=ms.get)
+    sim.set_launch(best)
     return best, ms

@@ -1390,6 +1390,33 @@ extern "C" pic_status pic_timing(pic_handle *h, double *push_ms, long long *push
     return PIC_OK;
 }
 
+extern "C" pic_status pic_get_launch(pic_handle *h, int kernel, int *blocks_per_sm, int *max_blocks_per_sm)
+{
+    if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
+    if (kernel != PIC_KERNEL_PUSH) return fail(h, PIC_EINVAL, "only the push has a launch shape");
+    if (blocks_per_sm) *blocks_per_sm = h->L.push_per_sm;
+    if (max_blocks_per_sm) *max_blocks_per_sm = h->L.push_max_per_sm;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_launch(pic_handle *h, int kernel, int blocks_per_sm)
+{
+    if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
+    if (kernel != PIC_KERNEL_PUSH) return fail(h, PIC_EINVAL, "only the push has a launch shape");
+    if (blocks_per_sm < 1 || blocks_per_sm > h->L.push_max_per_sm)
+        return fail(h, PIC_EINVAL, "blocks per SM out of 1 .. " + std::to_string(h->L.push_max_per_sm));
+    if (blocks_per_sm == h->L.push_per_sm) return PIC_OK;
+    // the captured period holds the old grid: wait for it, then drop it
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->gexec) {
+        CK(cudaGraphExecDestroy(h->gexec));
+        h->gexec = nullptr;
+    }
+    h->L.push_per_sm = blocks_per_sm;
+    h->L.push_blocks = h->L.num_sms * blocks_per_sm;
+    return PIC_OK;
+}
+
 extern "C" pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, long long *launches,
                                         double *bytes, int reset)
 {

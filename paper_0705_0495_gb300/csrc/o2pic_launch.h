@@ -30,6 +30,9 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
 
 struct LaunchCfg {
     int push_blocks;      // persistent grid of the push
+    int push_per_sm;      // its blocks per SM
+    int push_max_per_sm;  // the most that fit on an SM
+    int num_sms;
     int collide_blocks;   // grid of the collision kernel (loops over the candidates)
     size_t push_smem;     // dynamic shared memory of the push (non-diag)
     size_t push_smem_diag;

@@ -1424,6 +1424,9 @@ cudaError_t push_configure(bool fp64, LaunchCfg &L, int num_sms)
     }
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
+    L.num_sms = num_sms;
+    L.push_max_per_sm = per_sm;
+    L.push_per_sm = per_sm;
     L.push_blocks = num_sms * per_sm;
     L.collide_blocks = num_sms * 8;
     return cudaSuccess;

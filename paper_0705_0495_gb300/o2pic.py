@@ -51,7 +51,8 @@ class pic_config(C.Structure):
 
 EXPORTS = ["pic_workspace_size", "pic_init", "pic_step", "pic_diagnostics", "pic_get_state",
            "pic_set_state", "pic_set_step", "pic_fields", "pic_numax", "pic_set_timing",
-           "pic_timing", "pic_kernel_timing", "pic_destroy", "pic_last_error",
+           "pic_timing", "pic_kernel_timing", "pic_get_launch", "pic_set_launch", "pic_destroy",
+           "pic_last_error",
            "pic_field_solve_static"]
 KERNELS = {"push": 0, "coulomb": 1, "sequential_gas": 2}
 
@@ -93,6 +94,10 @@ def load(path: str = LIB_PATH):
     l.pic_timing.argtypes = [vp, dp, lp, lp, dp, C.c_int]
     l.pic_kernel_timing.restype = C.c_int
     l.pic_kernel_timing.argtypes = [vp, C.c_int, dp, lp, dp, C.c_int]
+    l.pic_get_launch.restype = C.c_int
+    l.pic_get_launch.argtypes = [vp, C.c_int, ip, ip]
+    l.pic_set_launch.restype = C.c_int
+    l.pic_set_launch.argtypes = [vp, C.c_int, C.c_int]
     l.pic_destroy.restype = None
     l.pic_destroy.argtypes = [vp]
     l.pic_last_error.restype = C.c_char_p
@@ -283,6 +288,16 @@ class Simulation:
         self._check(self.lib.pic_kernel_timing(self.h, KERNELS[kernel], C.byref(ms), C.byref(n),
                                                C.byref(bts), 1 if reset else 0))
         return {"ms": ms.value, "launches": n.value, "bytes": bts.value}
+
+    def launch(self, kernel="push"):
+        """(blocks per SM, largest blocks per SM) of a kernel kind's grid"""
+        cur, mx = C.c_int(), C.c_int()
+        self._check(self.lib.pic_get_launch(self.h, KERNELS[kernel], C.byref(cur), C.byref(mx)))
+        return cur.value, mx.value
+
+    def set_launch(self, blocks_per_sm, kernel="push"):
+        """blocks per SM of a kernel kind's grid (results do not depend on it)"""
+        self._check(self.lib.pic_set_launch(self.h, KERNELS[kernel], int(blocks_per_sm)))
 
 
 def field_solve_static(cfg: pic_config, step: int, cell_ptrs, off_ptrs, counts, rho_ptr, phi_ptr, E_ptr,

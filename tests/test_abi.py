@@ -37,6 +37,15 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(o2pic.EXPORTS) <= set(names)
 
 
+def test_null_handle_calls_fail_cleanly(lib):
+    # argument checks that need no GPU: a NULL handle is PIC_EINVAL
+    assert lib.pic_step(None, 1) == 1
+    assert lib.pic_set_launch(None, 0, 1) == 1
+    assert lib.pic_get_launch(None, 0, None, None) == 1
+    assert lib.pic_kernel_timing(None, 0, None, None, None, 0) == 1
+    assert lib.pic_last_error(None)
+
+
 def test_workspace_size_and_validation(lib):
     d = inputs.cfg1()
     n = o2pic.workspace_size([d], inputs.xs_tables())
