@@ -433,6 +433,31 @@ def run_ours(a, rank, world, local_rank):
                    "sample": f"failed: {ex}"}
 
     variants = None
+    # the error against the FP64 oracle of each variant, with the tests that
+    # establish it (FP32 replay: each step from the oracle's state within
+    # 1e-5, at most 1e-4 of particle-steps with a flipped decision)
+    REPLAY = "FP32 replay within 1e-5"
+    accuracy = {
+        "fp64": "step by step within 1e-9 of the gap and of the thermal speed, identical event counts "
+                "(tests/test_gpu_parity.py); seed ensembles over 60 RF cycles within 3 standard errors "
+                "(tests/test_gpu_long_horizon.py)",
+        "batched": "each discharge of a batched handle equals its own oracle step by step within 1e-9 "
+                   "(FP64, uneven discharges, tests/test_gpu_parity.py); the FP32 kernels are those of "
+                   f"the single discharge ({REPLAY})",
+        "coulomb": "FP64 step by step within 1e-9 (n2 = 1 and 3, ragged and oversized cells); "
+                   f"{REPLAY}, one full-size step of this workload compared per cell; seed ensembles "
+                   "within 3 standard errors (tests/test_gpu_parity.py, test_gpu_statistics.py)",
+        "coulomb_inter": "FP64 step by step within 1e-9 (empty, single and oversized cells); "
+                         f"{REPLAY}; seed ensembles within 3 standard errors "
+                         "(tests/test_gpu_parity.py, test_gpu_statistics.py)",
+        "sweep_13p8": "the seven discharges in one handle each equal their own oracle step by step "
+                      "within 1e-9 (FP64, tests/test_gpu_parity.py)",
+        "ion_subcycle": f"FP64 step by step within 1e-9 for k = 2 and 5; {REPLAY} (tests/test_gpu_parity.py)",
+        "sequential_gas": "FP64 step by step within 1e-9 (chains (15) -> (16)/(17), frequent "
+                          f"particle-target events); {REPLAY}, one full-size step of this workload "
+                          "included; seed ensembles within 3 standard errors "
+                          "(tests/test_gpu_parity.py, test_gpu_statistics.py)",
+    }
     if rank == 0 and world == 1 and not a.no_variants:
         sim.close()
         sim = None
@@ -492,6 +517,9 @@ def run_ours(a, rank, world, local_rank):
                 f"per channel) instead of the null-collision test: {_describe(dq)}", [dq], 200, 400)
         except Exception as ex:
             variants["sequential_gas"] = {"error": str(ex)}
+        for k, v in variants.items():
+            if "error" not in v:
+                v["accuracy"] = accuracy[k]
 
     if rank == 0:
         line = {
