@@ -524,6 +524,44 @@ def test_gas_event_conservation(reaction):
             assert dk == pytest.approx(th * QE, rel=1e-8)
 
 
+@pytest.mark.parametrize("reaction,sp", [(4, 0), (9, 0), (5, 1)])
+def test_scattering_is_isotropic_in_the_cm_frame(reaction, sp):
+    """Sec. III: the scattering of (4)-(12) is isotropic in the centre-of-mass
+    frame.  With uniform random numbers, the cosine of the angle between the
+    relative velocities before and after is uniform on [-1, 1] and the
+    azimuth about the incoming one is uniform on [0, 2 pi); the outgoing
+    speed is that of Eq. 5.  A half-range cosine, a doubled azimuth or a
+    direction tied to the incoming one fails."""
+    tabs = inputs.xs_tables()
+    idx = [i for i, t in enumerate(tabs) if t["reaction"] == reaction][0]
+    th = tabs[idx]["threshold_eV"]
+    o = oracle.Oracle(_disch(), tabs)
+    rs = np.random.default_rng(70 + reaction)
+    m = MASS[sp]
+    mu = m * M_O2 / (m + M_O2)
+    g = np.array([0.3, -0.5, 0.81])
+    g /= np.linalg.norm(g)
+    Ecm = th + 4.0
+    u = math.sqrt(2 * Ecm * QE / mu)
+    V = np.array([120.0, -40.0, 75.0])
+    v = V + u * g
+    # a basis about g for the azimuth
+    e1 = np.cross(g, [1.0, 0.0, 0.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(g, e1)
+    cosx, phi = [], []
+    for _ in range(3000):
+        vo, alive, prods, Vo = o.gas_event(sp, idx, v, V, rs.random(4), rs.random(2))
+        gp = vo - Vo
+        up = np.linalg.norm(gp)
+        assert up == pytest.approx(math.sqrt(max(0.0, u * u - 2 * th * QE / mu)), rel=1e-9)
+        n = gp / up
+        cosx.append(float(np.dot(n, g)))
+        phi.append(math.atan2(float(np.dot(n, e2)), float(np.dot(n, e1))) % (2 * math.pi))
+    assert stats.kstest((np.array(cosx) + 1) / 2, "uniform").pvalue > 1e-3
+    assert stats.kstest(np.array(phi) / (2 * math.pi), "uniform").pvalue > 1e-3
+
+
 def test_charge_exchange_swaps_velocities():
     tabs = inputs.xs_tables()
     idx = [i for i, t in enumerate(tabs) if t["reaction"] == 6][0]
