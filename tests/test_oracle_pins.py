@@ -591,6 +591,35 @@ def test_impact_detachment_event_conservation():
 
 # -------------------------------------------------------- bookkeeping
 
+def test_births_are_appended_after_the_survivors_in_parent_order():
+    """Most electrons ionise (18) in one step (a cross section so large that
+    the null-collision test always passes): the new electrons and O2+ follow
+    the survivors of their species, one per ionising parent, in the parents'
+    order, at the parents' positions.  Without a field the parents that did
+    not collide keep their velocities bit for bit, which tells them apart."""
+    d = _disch(L=0.01, dt_override=1e-11)
+    E = inputs.geometric_grid(0.01, 1e3, 64)
+    tab = dict(reaction=18, sub=0, E_eV=E, sigma_m2=np.full_like(E, 1e-15), threshold_eV=0.1)
+    o = oracle.Oracle(d, [tab])
+    rs = np.random.default_rng(17)
+    n = 50
+    x0 = rs.permutation(np.linspace(0.1, 0.9, n)) * d.L   # parents not sorted by position
+    v = rs.normal(size=(n, 3)) * 1.5e6
+    o.set(0, x0, v[:, 0], v[:, 1], v[:, 2])
+    o.set(2, [0.5 * d.L], [0.0], [0.0], [0.0])           # one O2+ already there
+    o.set(1, [], [], [], [])
+    o.step(1)
+    k = o.counters()["events"][18]
+    e, op = o.get(0), o.get(2)
+    hit = (e["vx"][:n] != v[:, 0]) | (e["vy"][:n] != v[:, 1]) | (e["vz"][:n] != v[:, 2])
+    assert hit.sum() == k and k > n // 2 and k < n          # some parents did not collide
+    assert len(e["x"]) == n + k and len(op["x"]) == 1 + k
+    assert np.array_equal(e["x"][n:], e["x"][:n][hit])       # born where the parent is
+    assert np.array_equal(op["x"][1:], e["x"][:n][hit])
+    assert np.allclose(e["x"][:n], x0 + v[:, 0] * d.dt, rtol=0, atol=1e-12 * d.L)
+    assert e["alive"].all() and op["alive"].all()
+
+
 def test_particle_and_charge_bookkeeping_full_step_loop():
     d = inputs.cfg1(n_op=4000)
     o = oracle.Oracle(d, inputs.xs_tables())
