@@ -110,6 +110,8 @@ def lib():
         l.orc_bin_of.argtypes = [C.c_void_p, C.c_double]
         l.orc_fields.argtypes = [C.c_void_p, dp, dp, dp]
         l.orc_counters.argtypes = [C.c_void_p, lp, lp, lp, lp]
+        l.orc_eq1_evaluations.restype = C.c_longlong
+        l.orc_eq1_evaluations.argtypes = [C.c_void_p]
         l.orc_reset_diag.restype = None
         l.orc_reset_diag.argtypes = [C.c_void_p]
         l.orc_diag.restype = C.c_longlong
@@ -285,11 +287,12 @@ class Oracle:
     def counters(self):
         ab = np.zeros(6, dtype=np.int64)
         ev = np.zeros(20, dtype=np.int64)
-        vi = np.zeros(2, dtype=np.int64)
+        vi = np.zeros(3, dtype=np.int64)
         bi = np.zeros(3, dtype=np.int64)
         lp = lambda a: a.ctypes.data_as(C.POINTER(C.c_longlong))
         lib().orc_counters(self.h, lp(ab), lp(ev), lp(vi), lp(bi))
-        return {"absorbed": ab.reshape(3, 2), "events": ev, "violations": vi, "births": bi}
+        return {"absorbed": ab.reshape(3, 2), "events": ev, "violations": vi, "births": bi,
+                "eq1_evaluations": int(lib().orc_eq1_evaluations(self.h))}
 
     def reset_diag(self):
         lib().orc_reset_diag(self.h)

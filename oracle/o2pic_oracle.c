@@ -103,11 +103,14 @@ struct orc_sim {
     double numax[3];
     double pnull[3];
     double nubin[64];   /* electrons: bound per lab-energy bin */
+    double vmax[3];     /* largest speed per species: at the last sort, raised
+                           by the velocity changes since (particle-target pass) */
     double pbin[64];
     parts_t p[3];
     long long step;
     double *rho, *phi, *E, *dens[3];
-    long long absorbed[3][2], events[20], viol[2], births[3];
+    long long absorbed[3][2], events[20], viol[3], births[3];
+    long long peval;    /* Eq. 1 probabilities evaluated (pair pass, sequential scheme) */
     long long nsamp;
     long long psteps;   /* live particles pushed, summed over steps */
     double *dens_sum[3], *phi_sum;
@@ -257,29 +260,56 @@ static void blist_push(blist_t *l, int sp, double x, const double v[3])
     b->v[2] = v[2];
 }
 
-/* Bound on the total gas collision frequency of a species: the largest
- * sum_j n_j sigma_j(E) sqrt(2E/mu) over every table node up to the cap and the
- * cap itself, times the safety factor. */
-static double compute_numax(const orc_sim *s, int sp)
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Bound on the total gas collision frequency sum_j n_j sigma_j(E) u of
+ * species sp over centre-of-mass energies 0 <= E <= cap, u = sqrt(2E/mu):
+ * [0, cap] is cut at every node and every threshold of the species' gas
+ * channels.  Between neighbouring cut points a < b no channel has a node or
+ * a threshold, so each sigma_j is linear (or zero) there and at most
+ * max(sigma_j(a), sigma_j(b)), and u <= u(b).  The bound is the largest
+ * sum_j n_j max(sigma_j(a), sigma_j(b)) u(b) over the intervals, times the
+ * safety factor: no energy up to the cap exceeds it. */
+static double numax_upto(const orc_sim *s, int sp, double cap)
 {
     double mu = reduced_mass(MASS[sp], M_O2);
-    double cap = s->c.ecap_eV[sp];
-    double best = 0.0;
+    int np = 2;
+    for (int a = 0; a < s->n_gas_ch[sp]; ++a) np += s->t[s->gas_ch[sp][a]].n + 1;
+    double *pt = malloc(np * sizeof(double));
+    int m = 0;
+    pt[m++] = 0.0;
+    pt[m++] = cap;
     for (int a = 0; a < s->n_gas_ch[sp]; ++a) {
         const table_t *ta = &s->t[s->gas_ch[sp][a]];
-        for (int k = 0; k <= ta->n; ++k) {
-            double E = (k < ta->n) ? ta->E[k] : cap;
-            if (E > cap || E <= 0.0) continue;
-            double u = sqrt(2.0 * E * QE / mu);
-            double nu = 0.0;
-            for (int b = 0; b < s->n_gas_ch[sp]; ++b) {
-                const table_t *tb = &s->t[s->gas_ch[sp][b]];
-                nu += tb->ndens * sigma_of(tb, E) * u;
-            }
-            if (nu > best) best = nu;
-        }
+        for (int k = 0; k < ta->n; ++k)
+            if (ta->E[k] > 0.0 && ta->E[k] < cap) pt[m++] = ta->E[k];
+        if (ta->th > 0.0 && ta->th < cap) pt[m++] = ta->th;
     }
+    qsort(pt, m, sizeof(double), cmp_double);
+    double best = 0.0;
+    for (int i = 0; i + 1 < m; ++i) {
+        double a = pt[i], b = pt[i + 1];
+        if (!(b > a)) continue;
+        double u = sqrt(2.0 * b * QE / mu);
+        double nu = 0.0;
+        for (int c = 0; c < s->n_gas_ch[sp]; ++c) {
+            const table_t *tc = &s->t[s->gas_ch[sp][c]];
+            double sa = sigma_of(tc, a), sb = sigma_of(tc, b);
+            nu += tc->ndens * (sa > sb ? sa : sb) * u;
+        }
+        if (nu > best) best = nu;
+    }
+    free(pt);
     return best * s->c.numax_safety;
+}
+
+static double compute_numax(const orc_sim *s, int sp)
+{
+    return numax_upto(s, sp, s->c.ecap_eV[sp]);
 }
 
 /* Electron energy bins: bin b holds lab energies K with
@@ -309,34 +339,25 @@ static double bin_top(int b)
     return ldexp(1.0 + (double)(b % 4 + 1) / 4.0, BIN_LOG2_E0 + b / 4);
 }
 
-/* Bound of bin b (not the last): relative speed at most the bin's top
- * electron speed plus 7 thermal speeds of the gas molecule (a Maxwellian
- * sample beyond that, chance 1e-10, is counted as a violation); the same
- * node scan as compute_numax up to the matching centre-of-mass energy. */
+/* Largest gas-molecule speed a collision can draw, in thermal speeds
+ * sqrt(kT/M): the molecule's velocity is sqrt(kT/M) (n0, n1, n2) from two
+ * Box-Muller pairs, whose radius sqrt(-2 ln r) is largest for the smallest
+ * uniform r = 2^-33 (FP64 uniforms; 2^-24 in FP32), so |(n0, n1)| and |n2|
+ * are at most sqrt(66 ln 2) = 6.77 and the speed at most 9.58 of them. */
+#define GAS_SPEED_MAX 10.0
+
+/* Bound of bin b (not the last): the relative speed of an electron of the
+ * bin and any gas molecule is at most the bin's top electron speed plus
+ * GAS_SPEED_MAX thermal speeds, so the bound up to the matching
+ * centre-of-mass energy covers every candidate of the bin. */
 static double compute_numax_bin(const orc_sim *s, int b)
 {
     const int sp = 0;
     double mu = reduced_mass(MASS[sp], M_O2);
     double vtop = sqrt(2.0 * bin_top(b) * QE / MASS[sp]);
     double vg = sqrt(KB * s->c.T_gas / M_O2);
-    double urel = vtop + 7.0 * vg;
-    double cap = 0.5 * mu * urel * urel / QE;
-    double best = 0.0;
-    for (int a = 0; a < s->n_gas_ch[sp]; ++a) {
-        const table_t *ta = &s->t[s->gas_ch[sp][a]];
-        for (int k = 0; k <= ta->n; ++k) {
-            double E = (k < ta->n) ? ta->E[k] : cap;
-            if (E > cap || E <= 0.0) continue;
-            double u = sqrt(2.0 * E * QE / mu);
-            double nu = 0.0;
-            for (int c = 0; c < s->n_gas_ch[sp]; ++c) {
-                const table_t *tb = &s->t[s->gas_ch[sp][c]];
-                nu += tb->ndens * sigma_of(tb, E) * u;
-            }
-            if (nu > best) best = nu;
-        }
-    }
-    return best * s->c.numax_safety;
+    double urel = vtop + GAS_SPEED_MAX * vg;
+    return numax_upto(s, sp, 0.5 * mu * urel * urel / QE);
 }
 
 static void load_species(orc_sim *s, int sp)
@@ -827,6 +848,7 @@ static int dsmc_channel(orc_sim *s, int root_sp, long long root, int gen, int k,
     double u = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
     double E = 0.5 * reduced_mass(MASS[sp], M_O2) * u * u / QE;
     double P = t->ndens * sigma_of(t, E) * u * (s->c.n1 * s->c.dt);
+    s->peval++;
     if (P > 1.0) {
         s->viol[1]++;
         P = 1.0;
@@ -929,9 +951,12 @@ static void sort_species(orc_sim *s, int sp, long long *start)
     parts_t q = {0};
     parts_reserve(&q, live > 0 ? live : 1);
     q.n = live;
+    s->vmax[sp] = 0.0;
     for (long long i = 0; i < p->n; ++i) {
         if (!p->alive[i]) continue;
         long long d = cnt[cell[i]]++;
+        double spd = sqrt(p->vx[i] * p->vx[i] + p->vy[i] * p->vy[i] + p->vz[i] * p->vz[i]);
+        if (spd > s->vmax[sp]) s->vmax[sp] = spd;
         q.x[d] = p->x[i];
         q.vx[d] = p->vx[i];
         q.vy[d] = p->vy[i];
@@ -948,7 +973,34 @@ static void sort_species(orc_sim *s, int sp, long long *start)
     free(cell);
 }
 
-/* per-cell particle-target pass of one reaction (Eq. 1 with tau = n1 dt) */
+/* the largest speeds after a pass that changed velocities (Coulomb
+ * collisions, the first part of the sequential gas scheme): the recorded
+ * maximum of each species is raised to the largest speed of its live
+ * particles, so it still bounds every speed */
+static void raise_vmax(orc_sim *s)
+{
+    for (int sp = 0; sp < 3; ++sp) {
+        const parts_t *p = &s->p[sp];
+        for (long long i = 0; i < p->n; ++i) {
+            if (!p->alive[i]) continue;
+            double spd = sqrt(p->vx[i] * p->vx[i] + p->vy[i] * p->vy[i] + p->vz[i] * p->vz[i]);
+            if (spd > s->vmax[sp]) s->vmax[sp] = spd;
+        }
+    }
+}
+
+/* u rounded up to 5 significant bits (u = m 2^e, m in [1/2, 1): ceil(32 m)/32
+ * 2^e): the relative-speed cap of the particle-target pass, a few per cent
+ * above the sum of the largest speeds, on a coarse grid that the same sum
+ * computed with other roundings meets with the same result */
+static double round_up_5bits(double u)
+{
+    if (!(u > 0.0)) return 0.0;
+    int e;
+    double m = frexp(u, &e);
+    return ldexp(ceil(m * 32.0) / 32.0, e);
+}
+
 /* Bound on sigma(E) u over a particle-target table for relative speeds up
  * to u_cap (SI): on a segment [E_k, E_k+1] sigma is at most the larger end
  * value and u at most the speed of E_k+1; below the grid sigma is the first
@@ -966,13 +1018,14 @@ static double pair_bound(const table_t *t, double mu, double u_cap)
     return 1.001 * (g > tail ? g : tail);
 }
 
-/* Particle-target reaction in one cell (Eq. 1), by thinning: B bounds
- * P = n_T sigma u tau for every pair below the cap speed (the relative speed
- * of the projectile's cap energy), candidates are drawn among the cell's
- * projectiles with probability B each (geometric gaps, a random stream per
- * cell), and a candidate reacts with probability P/B, so every projectile
- * reacts with probability P; with B >= 1 every projectile is a candidate and
- * reacts with probability min(P, 1). */
+/* Particle-target reaction in one cell (Eq. 1 with tau = n1 dt, P clamped at
+ * 1 and the clamp counted: reading R10), evaluated by thinning.  No pair is
+ * faster than the sum of the two species' largest speeds, so with u_cap that
+ * sum (rounded up), B = n_T max sigma u tau over u <= u_cap bounds P for every
+ * pair of the pass.  Candidates are drawn among the cell's projectiles with
+ * probability min(B, 1) each (geometric gaps, a random stream per cell), and
+ * a candidate reacts with probability min(P, 1)/min(B, 1): every projectile
+ * reacts with probability min(P, 1), as if each were tested. */
 static void pair_channel(orc_sim *s, int reaction, int c, long long **start, blist_t *bl)
 {
     int tab = s->pair_tab[reaction];
@@ -991,9 +1044,10 @@ static void pair_channel(orc_sim *s, int reaction, int c, long long **start, bli
     double tau = s->c.n1 * s->c.dt;
     double mp = MASS[ps], mt = MASS[ts];
     double mu = reduced_mass(mp, mt);
-    double u_cap = sqrt(2.0 * s->c.ecap_eV[ps] * QE / mu);
+    double u_cap = round_up_5bits(s->vmax[ps] + s->vmax[ts]);
     double B = nT * pair_bound(t, mu, u_cap) * tau;
     double lq = B < 1.0 ? log1p(-B) : 0.0;
+    double Bc = B < 1.0 ? B : 1.0;
     long long i = p0 - 1;
     uint32_t draw = 0;
     for (;;) {
@@ -1023,11 +1077,12 @@ static void pair_channel(orc_sim *s, int reaction, int c, long long **start, bli
         double u = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
         double E = 0.5 * reduced_mass(mp, mt) * u * u / QE;
         double P_ = nT * sigma_of(t, E) * u * tau;
-        double Bc = B < 1.0 ? B : 1.0;
-        if (P_ > Bc) {  /* above the cap speed, or beyond 1 */
+        s->peval++;
+        if (P_ > 1.0) {  /* Eq. 1 beyond 1: clamped (R10) and counted */
             s->viol[1]++;
-            P_ = Bc;
+            P_ = 1.0;
         }
+        if (P_ > Bc) s->viol[2]++;  /* the bound failed: cannot happen (u <= u_cap) */
         if (!(unif(d0[1]) * Bc < P_)) continue;
         s->events[reaction]++;
         if (reaction == 13 || reaction == 14) {
@@ -1393,6 +1448,7 @@ static void step_once(orc_sim *s)
              * e-O-, e-O2+, O- - O2+ in turn */
             if (s->c.coulomb_inter)
                 for (int pr = 0; pr < 3; ++pr) coulomb_inter(s, pr, start);
+            raise_vmax(s);
         }
         if (pair && s->c.gas_scheme == 1) {
             /* the sequential scheme: the whole list of Table I in order, gas
@@ -1400,6 +1456,7 @@ static void step_once(orc_sim *s)
              * their products readmitted, a new sort (particles were born and
              * removed), (19) */
             dsmc_pass(s, 0, bl);
+            raise_vmax(s);
             for (int c = 0; c < N; ++c) {
                 pair_channel(s, 13, c, start, bl);
                 pair_channel(s, 14, c, start, bl);
@@ -1433,6 +1490,7 @@ void orc_step(orc_sim *s, long long nsteps)
 
 long long orc_step_index(const orc_sim *s) { return s->step; }
 long long orc_particle_steps(const orc_sim *s) { return s->psteps; }
+long long orc_eq1_evaluations(const orc_sim *s) { return s->peval; }
 void orc_set_step(orc_sim *s, long long step) { s->step = step; }
 long long orc_count(const orc_sim *s, int sp) { return s->p[sp].n; }
 double orc_numax(const orc_sim *s, int sp) { return s->numax[sp]; }
@@ -1492,6 +1550,7 @@ void orc_counters(const orc_sim *s, long long *absorbed, long long *events,
     if (violations) {
         violations[0] = s->viol[0];
         violations[1] = s->viol[1];
+        violations[2] = s->viol[2];
     }
     if (births) memcpy(births, s->births, sizeof(s->births));
 }

@@ -71,6 +71,8 @@ void orc_destroy(orc_sim *s);
 void orc_step(orc_sim *s, long long nsteps);
 long long orc_step_index(const orc_sim *s);
 long long orc_particle_steps(const orc_sim *s);
+/* Eq. 1 probabilities evaluated (particle-target candidates, sequential-scheme tests) */
+long long orc_eq1_evaluations(const orc_sim *s);
 long long orc_count(const orc_sim *s, int sp);
 void orc_get(const orc_sim *s, int sp, double *x, double *vx, double *vy,
              double *vz, int *alive);
@@ -82,7 +84,8 @@ double orc_numax(const orc_sim *s, int sp);
 double orc_numax_bin(const orc_sim *s, int b);
 int orc_bin_of(const orc_sim *s, double K_eV);
 void orc_fields(orc_sim *s, double *rho, double *phi, double *E);
-/* counters: absorbed[3][2], events[20], violations[2] (gas, pair), births[3] */
+/* counters: absorbed[3][2], events[20], violations[3] (gas nu_max exceeded,
+ * Eq. 1 P > 1 clamps, particle-target bound below P: never expected), births[3] */
 void orc_counters(const orc_sim *s, long long *absorbed, long long *events,
                   long long *violations, long long *births);
 /* diagnostics: dens_sum[3][N+1], phi_sum[N+1], eedf, iedf[2][bins], fm[xbins][bins] */

@@ -166,7 +166,7 @@ class Discharge:
     fm_bins: int = 64
     fm_xbins: int = 64
     fm_emax: float = 4.0
-    numax_safety: float = 1.05
+    numax_safety: float = 1.0       # the bound is strict by construction (piecewise over the tables)
     numax_bins: int = 64            # electrons: bounds per quarter octave of lab energy
     n2: int = 0                     # intra-species Coulomb collisions every n2 steps (0: none)
     coulomb_log: float = 10.0       # ln Gamma of Eq. 2 (not given in the paper)

@@ -346,37 +346,91 @@ def test_electron_energy_bin_index():
         assert o.bin_of(K) == b, (K, o.bin_of(K), b)
 
 
+# largest gas-molecule speed a collision can draw, in thermal speeds
+# sqrt(kT/M): two Box-Muller pairs whose radius sqrt(-2 ln r) is largest at
+# the smallest FP64 uniform r = 2^-33, so |(n0, n1)| and |n2| are at most
+# sqrt(66 ln 2) each
+BM_MAX = math.sqrt(2 * 66 * math.log(2.0))
+
+
+def _gas_frequency(o, tabs_idx, ngas, u, Ecm):
+    nu = np.zeros(len(u))
+    for k in tabs_idx:
+        nu += ngas * np.array([o.sigma(k, e) for e in Ecm]) * u
+    return nu
+
+
 def test_electron_bin_bounds_cover_the_collision_frequency():
     # every bin's bound is at least sum_j n_j sigma_j(E_cm) u for electrons of
-    # that bin against gas molecules within 7 thermal speeds, and, the point
-    # of the bins, not much larger than the largest such frequency
+    # that bin against ANY gas molecule Box-Muller can draw (speeds up to
+    # BM_MAX thermal speeds, including the worst case: at the top of the bin,
+    # head on at the largest speed), and, the point of the bins, not much
+    # larger than the largest such frequency
     d = _disch(p_Pa=20.0, ecap_override=1250.0)
     tabs = [t for t in inputs.xs_tables() if t["reaction"] in (4, 7, 8, 9, 10, 11, 12, 15, 18)]
     o = oracle.Oracle(d, tabs)
     ngas = d.p_Pa / (KB * d.T_gas)
     mu = ME * M_O2 / (ME + M_O2)
     vg = math.sqrt(KB * d.T_gas / M_O2)
+    assert 9.5 < BM_MAX < 10.0
     rs = np.random.default_rng(21)
     gas_tabs = list(range(len(tabs)))
     for b in range(0, 63, 3):
         lo = 2.0 ** (-6 + b // 4) * (1 + (b % 4) / 4)
         hi = 2.0 ** (-6 + b // 4) * (1 + (b % 4 + 1) / 4)
-        K = rs.uniform(lo, hi, size=400)
-        dirs = rs.normal(size=(400, 3))
+        K = np.concatenate([rs.uniform(lo, hi, size=400), [hi * (1 - 1e-15)]])
+        dirs = rs.normal(size=(401, 3))
         dirs /= np.linalg.norm(dirs, axis=1)[:, None]
         v = np.sqrt(2 * K * QE / ME)[:, None] * dirs
-        V = rs.normal(size=(400, 3)) * vg
-        V *= np.minimum(1.0, 7.0 / np.linalg.norm(V / vg, axis=1))[:, None]
+        # molecule speeds spread over the whole range Box-Muller can give
+        gd = rs.normal(size=(401, 3))
+        gd /= np.linalg.norm(gd, axis=1)[:, None]
+        V = gd * vg * rs.uniform(0.0, BM_MAX, size=401)[:, None]
+        V[-1] = -dirs[-1] * vg * BM_MAX  # head on, fastest molecule, top of the bin
         u = np.linalg.norm(v - V, axis=1)
         Ecm = 0.5 * mu * u * u / QE
-        nu = np.zeros(400)
-        for k in gas_tabs:
-            nu += ngas * np.array([o.sigma(k, e) for e in Ecm]) * u
+        nu = _gas_frequency(o, gas_tabs, ngas, u, Ecm)
         bound = o.numax_bin(b)
-        assert np.all(nu <= bound), (b, nu.max(), bound)
+        assert np.all(nu <= bound / d.numax_safety), (b, nu.max(), bound)
         assert bound <= o.numax(0) * 1.0000001 or hi > 1000.0
         if nu.max() > 0 and b >= 8:
             assert bound < 2.0 * nu.max(), (b, bound, nu.max())
+
+
+@pytest.mark.parametrize("species", [0, 1, 2])
+def test_numax_bounds_every_energy_up_to_the_cap(species):
+    # nu_max of Sec. II's null-collision bound: no centre-of-mass energy in
+    # [0, E_cap] has sum_j n_j sigma_j(E) sqrt(2E/mu) above it (the tables'
+    # nodes, thresholds, points between them and random energies), and it is
+    # the sup of that frequency within the width of a grid segment
+    d = _disch(p_Pa=20.0, ecap_override=1250.0)
+    tabs = [t for t in inputs.xs_tables() if t["reaction"] not in (13, 14, 19)]
+    o = oracle.Oracle(d, tabs)
+    # projectiles of Table I: O- for (5), (14), (16), (17), O2+ for (6), else the electron
+    proj = {5: 1, 14: 1, 16: 1, 17: 1, 6: 2}
+    idx = [k for k, t in enumerate(tabs) if proj.get(t["reaction"], 0) == species]
+    assert idx
+    ngas = d.p_Pa / (KB * d.T_gas)
+    mu = MASS[species] * M_O2 / (MASS[species] + M_O2)
+    cap = d.ecap_eV[species]
+    pts = [0.0, cap]
+    for k in idx:
+        E = tabs[k]["E_eV"]
+        E = E[E < cap]
+        pts += list(E) + list(0.5 * (E[1:] + E[:-1])) + [tabs[k]["threshold_eV"]]
+    rs = np.random.default_rng(5 + species)
+    pts += list(rs.uniform(0.0, cap, 2000)) + list(np.exp(rs.uniform(math.log(1e-4), math.log(cap), 2000)))
+    E = np.array(sorted(p for p in pts if 0.0 <= p <= cap))
+    u = np.sqrt(2 * E * QE / mu)
+    nu = np.zeros(len(E))
+    for k in idx:
+        s = np.array([o.sigma(k, e) for e in E])
+        # (17) sees O2(a) at C n_O2 (Sec. III C), every other channel n_O2
+        nj = ngas * (d.C_delta if tabs[k]["reaction"] == 17 else 1.0)
+        nu += nj * s * u
+    bound = o.numax(species) / d.numax_safety
+    assert np.all(nu <= bound), (nu.max(), bound)
+    assert bound < 1.15 * nu.max(), (bound, nu.max())
 
 
 def test_binned_null_collision_real_event_fraction():
@@ -745,6 +799,55 @@ def test_pair_pass_exhausts_targets_with_clamped_probability():
     assert c["violations"][1] == nop
     assert o.get(2)["alive"].sum() == 0
     assert o.get(0)["alive"].sum() == ne - nop
+
+
+def test_pair_pass_fast_projectile_reacts_with_eq1_probability():
+    """A projectile far faster than the rest (here far above any energy cap
+    of the discharge) reacts with P = n_T sigma u tau of Eq. 1, not with a
+    bound computed for slower pairs: the thinning bound follows the largest
+    speeds of the two species.  Recombination (13) with a flat cross section
+    in 64 cells, each with 60 slow electrons, one fast electron and 20 O2+ at
+    rest; 12 seeds."""
+    L, N = 0.064, 64
+    dx = L / N
+    w, dt, sig = 1e6, 1e-12, 1.25e-6
+    u_fast, u_slow = 2e7, 1e5
+    fast = slow = 0
+    n_fast = n_slow = 0
+    for seed in range(1, 13):
+        d = _disch(L=L, n_cells=N, n1=1, dt_override=dt, weight_override=w, seed=seed)
+        o = oracle.Oracle(d, [_flat(13, sig)])
+        rs = np.random.default_rng(100 + seed)
+        xs, vs = [], []
+        for c in range(N):
+            x = (c + rs.uniform(0.4, 0.6, 61)) * dx
+            dirs = rs.normal(size=(61, 3))
+            dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+            sp = np.full(61, u_slow)
+            sp[30] = u_fast
+            xs.append(x)
+            vs.append(dirs * sp[:, None])
+        x, v = np.concatenate(xs), np.concatenate(vs)
+        o.set(0, x, v[:, 0], v[:, 1], v[:, 2])
+        xt = np.repeat((np.arange(N) + 0.5) * dx, 20)
+        o.set(2, xt, np.zeros_like(xt), np.zeros_like(xt), np.zeros_like(xt))
+        o.set(1, [], [], [], [])
+        o.step(1)
+        st = o.get(0)
+        spd = np.sqrt(st["vx"] ** 2 + st["vy"] ** 2 + st["vz"] ** 2)
+        isf = spd > 0.5 * u_fast
+        assert isf.sum() == N
+        fast += int((~st["alive"][isf]).sum())
+        slow += int((~st["alive"][~isf]).sum())
+        n_fast += N
+        n_slow += int((~isf).sum())
+        assert o.counters()["violations"][2] == 0
+    nT = 20 * w / dx
+    Pf = nT * sig * u_fast * dt
+    Ps = nT * sig * u_slow * dt
+    assert 0.4 < Pf < 0.6
+    assert abs(fast - n_fast * Pf) < 4 * math.sqrt(n_fast * Pf * (1 - Pf)), (fast, n_fast * Pf)
+    assert abs(slow - n_slow * Ps) < 4 * math.sqrt(n_slow * Ps * (1 - Ps)) + 2, (slow, n_slow * Ps)
 
 
 # ------------------------------------------------------------- loading
