@@ -233,14 +233,14 @@ def reduce_over_ranks(values, ops, device):
     return out
 
 
-def measure_variant(name, discharges, warm_steps, timed_steps):
+def measure_variant(name, discharges, warm_steps, timed_steps, numeric_budget=None):
     """Particle-steps/s and the push's HBM fraction of another configuration
     (the FP64 path, the batched sweep), timed with CUDA events like the main
     figure; the state of each is far larger than L2."""
     import torch
 
     from paper_0705_0495_gb300 import o2pic
-    sim = o2pic.Simulation(discharges, inputs.xs_tables())
+    sim = o2pic.Simulation(discharges, inputs.xs_tables(), numeric_budget=numeric_budget)
     try:
         sim.step(warm_steps)
         g0 = [sim.diagnostics(k) for k in range(len(discharges))]
@@ -266,6 +266,10 @@ def measure_variant(name, discharges, warm_steps, timed_steps):
         out = {"workload": name, "value": ps / (ms / 1e3), "unit": UNIT, "time_steps": timed_steps,
                "warmup_time_steps": warm_steps, "ms_per_time_step": ms / timed_steps,
                "push_hbm_frac": achieved / peak}
+        g1 = sim.diagnostics(0)
+        if g1["eq1_evaluations"] > 0:
+            # Eq. 1 probabilities above 1 (clamped), per evaluation
+            out["eq1_clamp_fraction"] = float(g1["violations"][1]) / g1["eq1_evaluations"]
         for kind in ("coulomb", "sequential_gas"):
             kc = sim.kernel_timing(kind)
             if kc["launches"] > 0 and kc["ms"] > 0:
@@ -306,7 +310,7 @@ def run_ours(a, rank, world, local_rank):
         best, ms = autotune.tune_sort_interval(d, tabs)
         d.sort_interval = best
         tune = {"chosen": best, "ms_per_time_step": {str(k): v for k, v in ms.items()}}
-    sim = o2pic.Simulation([d], tabs)
+    sim = o2pic.Simulation([d], tabs, numeric_budget=1.0 if d.gas_scheme else None)
     push_tune = None
     if not a.no_autotune:
         # the push grid: every blocks-per-SM count timed on this simulation
@@ -514,7 +518,8 @@ def run_ours(a, rank, world, local_rank):
             dq.gas_scheme = 1
             variants["sequential_gas"] = measure_variant(
                 f"{a.workload} with the sequential gas scheme (Table I in order every {dq.n1} steps, Eq. 1 "
-                f"per channel) instead of the null-collision test: {_describe(dq)}", [dq], 200, 400)
+                f"per channel) instead of the null-collision test: {_describe(dq)}", [dq], 200, 400,
+                numeric_budget=1.0)
         except Exception as ex:
             variants["sequential_gas"] = {"error": str(ex)}
         for k, v in variants.items():

@@ -21,7 +21,7 @@
  *      dead particles (Sec. II: particles are sorted into cells after the free
  *      flight);
  *   8. every n1 steps the per-cell particle-target reactions (13), (14), (19)
- *      with probability P = n sigma u tau, tau = n1 dt (Eq. 1);
+ *      with probability min(P, 1), P = n sigma u tau, tau = n1 dt (Eq. 1);
  *   9. diagnostics: cycle-averaged densities and potential, the electron
  *      energy distribution at L/2, the O- distribution f_-(E, x) (Sec. IV) and
  *      the O2+ energy distribution at each electrode.
@@ -100,8 +100,11 @@ typedef struct {
  *   C_delta        O2(a1Delta_g)/O2 density ratio for reaction (17) (Sec. III C)
  *   T0_eV          temperatures of the initial Maxwellian load per species
  *   ecap_eV        centre-of-mass energy up to which the collision-frequency
- *                  bound nu_max is taken (max of sum_j n_j sigma_j(E) u over
- *                  table nodes below the cap and the cap, times numax_safety)
+ *                  bound nu_max is taken: [0, ecap] is cut at every node and
+ *                  threshold of the species' gas channels, and nu_max is the
+ *                  largest sum_j n_j max(sigma_j(a), sigma_j(b)) sqrt(2b/mu)
+ *                  over the pieces [a, b], times numax_safety (so no energy
+ *                  up to the cap has a larger frequency)
  *   n_init         superparticles loaded uniformly in (0, L) per species
  *   capacity       slots per species (>= n_init; births beyond it fail with
  *                  PIC_ECAPACITY)
@@ -120,8 +123,10 @@ typedef struct {
  *                  (K = m 2^e with m in [1, 2): bin 4 (e + 6) + floor(4 (m - 1)),
  *                  clamped to [0, numax_bins - 1]); bin b < numax_bins - 1 uses
  *                  the bound up to the centre-of-mass energy of relative speed
- *                  (top electron speed of the bin + 7 sqrt(kT/M_O2)), the last
- *                  bin the species' bound; 0 = one bound for all energies
+ *                  (top electron speed of the bin + 10 sqrt(kT/M_O2), above
+ *                  the fastest gas molecule the Box-Muller draws can give),
+ *                  the last bin the species' bound; 0 = one bound for all
+ *                  energies
  *   precision      pic_precision; all discharges of one handle share it
  *   n2             interval of the intra-species Coulomb collisions (1)-(3)
  *                  (Sec. III A): every n2 steps, after the cell sort of that
@@ -214,7 +219,12 @@ pic_status pic_step(pic_handle *h, long long n_steps);
 
 /*
  * Diagnostics of one discharge, copied into caller-owned host arrays (any
- * pointer may be NULL to skip it).  Sizes: N = n_cells.
+ * pointer may be NULL to skip it).  Sizes: N = n_cells.  The densities and
+ * the potential come back as sums over the n_samples samples of the window
+ * (every diag_every steps since the last reset): dens_sum / n_samples and
+ * phi_sum / n_samples are the cycle-averaged profiles of the paper's Sec. IV
+ * when the window spans whole RF cycles.  Sums rather than averages let a
+ * caller merge windows exactly (the FP32 path accumulates exact integers).
  *   dens_sum   [3][N+1]  sum over samples of the number density per species
  *   phi_sum    [N+1]     sum over samples of the potential
  *   eedf       [eedf_bins] electrons in the cell [L/2, L/2 + dx), E = m v^2/2
@@ -229,7 +239,9 @@ pic_status pic_step(pic_handle *h, long long n_steps);
  *              33 null-collision candidates, 34 slots visited by the push,
  *              35 particles through the Coulomb pass (summed over passes),
  *              36 live slots through the sequential gas scheme (summed over
- *              its two parts and passes), 37-39 reserved (0)
+ *              its two parts and passes), 37 Eq. 1 probabilities evaluated
+ *              (particle-target candidates and sequential-scheme tests below
+ *              their bound), 38-39 reserved (0)
  *   n_samples  number of diagnostic samples accumulated
  * reset != 0 clears the sums and histograms after copying.
  */
@@ -259,6 +271,20 @@ pic_status pic_set_state(pic_handle *h, int discharge, int species, long long n,
 
 /* Set the step counter (which drives U(t) and the random counters). */
 pic_status pic_set_step(pic_handle *h, long long step);
+
+/*
+ * Numerical budget of pic_step (paper Sec. II with reading R10/R11: the
+ * null-collision bound nu_max is taken up to ecap_eV, and Eq. 1's linear
+ * P = n sigma u tau is clamped at 1).  pic_step returns PIC_ENUMERIC when, in
+ * a discharge, more than 10 and more than max_fraction of the null-collision
+ * candidates met a total frequency above their bound (counters[26] against
+ * counters[33]), or more than 10 and more than max_fraction of the Eq. 1
+ * probabilities evaluated (particle-target candidates and sequential-scheme
+ * tests, counters[37]) exceeded 1 (counters[27]).  Counts are cumulative
+ * since pic_init.  Default 1e-6; a run that wants coarse n1 dt on purpose
+ * raises it.  PIC_EINVAL for a fraction outside [0, 1].
+ */
+pic_status pic_set_numeric_budget(pic_handle *h, double max_fraction);
 
 /* Potential, field and charge density of one discharge at the current state
  * (each [N+1], SI; NULL skips). */
@@ -328,7 +354,10 @@ pic_status pic_set_launch(pic_handle *h, int kernel, int blocks_per_sm);
  *   step       time-step number n; phi(x = 0) = U_rf sin(2 pi f n dt + phase)
  *   d_cell[s]  device array of n[s] cell indices per species (< 0 = dead)
  *   d_off[s]   device array of n[s] offsets in [0, 1): float for
- *              PIC_FP32_MIXED, double for PIC_FP64
+ *              PIC_FP32_MIXED, double for PIC_FP64; a value outside
+ *              [0, 1] (or NaN) is clamped into it, so a bad offset moves
+ *              that particle's charge within its cell but never corrupts
+ *              the sums
  *   n[s]       host array of the three slot counts
  *   d_rho, d_phi, d_E  device outputs, n_cells + 1 doubles each (SI)
  *   cuda_stream  the work is queued on this stream (NULL = legacy default);
@@ -336,8 +365,12 @@ pic_status pic_set_launch(pic_handle *h, int kernel, int blocks_per_sm);
  * Limit: n_cells <= 4096 (larger grids fail with PIC_EINVAL).  Scratch: one
  * fixed array of 3 x 4097 x 8 bytes in device memory, which every GPU that
  * loads this library reserves until the process exits.  The first call on a
- * device looks up that array's device address with the device current; make
- * that first call before any stream capture on the device.  All calls on a
+ * device looks up that array's device address with the device current, and
+ * under CUDA's default lazy module loading that first call also loads this
+ * library's kernels and the array onto the device (a driver-side
+ * allocation): make one warm-up call per device before any region that must
+ * not allocate and before any stream capture, or run with
+ * CUDA_MODULE_LOADING=EAGER.  All calls on a
  * device share the array and clear it first: calls that can run at the same
  * time on the GPU (unordered streams) race and corrupt each other's output.
  */

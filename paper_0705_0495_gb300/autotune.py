@@ -36,7 +36,7 @@ def tune_sort_interval(discharge, tables, warm_steps=100, timed_steps=200, cands
     ms = {}
     for k in (cands if cands is not None else candidates(discharge.n1)):
         d = dataclasses.replace(discharge, sort_interval=k)
-        sim = o2pic.Simulation([d], tables)
+        sim = o2pic.Simulation([d], tables, numeric_budget=1.0 if d.gas_scheme else None)
         try:
             sim.step(warm_steps)
             torch.cuda.synchronize()

@@ -49,7 +49,8 @@ enum : unsigned {
     ST_CAPACITY = 1u,   // particle capacity exceeded
     ST_TIMEOUT = 2u,    // look-back wait gave up
     ST_BIRTHBUF = 4u,   // a per-chunk or per-cell birth buffer overflowed
-    ST_BADSTATE = 8u    // an impossible state was found (index out of range)
+    ST_BADSTATE = 8u,   // an impossible state was found (index out of range)
+    ST_NONFINITE = 16u  // a particle's position or velocity became NaN or infinite
 };
 
 // Counters accumulated on the device (per discharge).
@@ -65,7 +66,8 @@ enum {
     C_BCANDS = 32,      // candidates of those species
     C_COUL = 33,        // particles through the Coulomb pass (cells with >= 2 of a species)
     C_DSMC = 34,        // live slots visited by the sequential gas scheme (both parts)
-    C_NCOUNT = 35
+    C_PEVAL = 35,       // Eq. 1 probabilities evaluated (pair-pass candidates, sequential-scheme tests)
+    C_NCOUNT = 36
 };
 
 struct TableDesc {
@@ -132,7 +134,6 @@ struct PairC {          // particle-target reaction of one discharge
     // bound on sigma(E) u_n over the table: sigma u_n <= max(bnd_g, bnd_s * u_n)
     // (u_n relative speed in cells per step; margins included)
     double bnd_g, bnd_s;
-    double ucap_n;      // relative speed (cells per step) of the projectile's cap energy
     float Ek_f, mfrac_f, Mfrac_f, dloss_f, coef_f, pad_f;
     float bnd_g_f, bnd_s_f;
 };
@@ -250,7 +251,9 @@ struct WsPtrs {
     int *pair_bcount;         // [total cells] births of (19) per cell
     int *cell_disc;           // [total cells] discharge of each global cell
     int *pair_first;          // [total cells] first flagged projectile of the current reaction
-    unsigned *vmax2;          // [D * 3] largest speed^2 (cells/step, float bits) at the last sort
+    unsigned long long *vmax2;// [D * 3] largest speed^2 (cells/step, double bits): at the last
+                              // sort, raised by the velocity changes since (Coulomb pass, first
+                              // part of the sequential gas scheme); the particle-target pass's cap
     struct NuBin *nubin;      // [D * NUBIN_MAX] electron collision-frequency bounds per energy bin
     int2 *cand;               // [cand_cap] collision candidates: (slot, ds << 8 | energy bin)
     int cand_cap;
@@ -367,6 +370,17 @@ __device__ __forceinline__ bool species_rests(const Disc &Dd, int s, unsigned lo
 __device__ __forceinline__ void set_status(Ctl *ctl, unsigned bits)
 {
     atomicOr(&ctl->status, bits);
+}
+
+// Raise the recorded largest speed^2 of (discharge, species) ds to the
+// warp's largest m2 (every lane of the warp calls it; non-negative doubles
+// order like their bit patterns).
+__device__ __forceinline__ void vmax_raise(unsigned long long *vmax2, int ds, double m2)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    if ((threadIdx.x & 31) == 0 && m2 > 0.0)
+        atomicMax(&vmax2[ds], (unsigned long long)__double_as_longlong(m2));
 }
 
 } // namespace o2

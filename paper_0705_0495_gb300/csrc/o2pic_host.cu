@@ -24,6 +24,10 @@ constexpr double PI = 3.14159265358979323846;
 constexpr double EPS0 = 8.8541878128e-12;
 constexpr double M_O = 16.0 * AMU;
 constexpr double M_O2 = 32.0 * AMU;
+// largest gas-molecule speed a collision can draw, in thermal speeds
+// sqrt(kT/M_O2): two Box-Muller pairs of radius at most sqrt(66 ln 2) = 6.77
+// (the smallest FP64 uniform is 2^-33; FP32 2^-24), so at most 9.58
+constexpr double GAS_SPEED_MAX = 10.0;
 // O- carries the extra electron and O2+ lacks one, so that every reaction of
 // Table I conserves mass exactly.
 const double MASS[3] = {ME, M_O + ME, M_O2 - ME};
@@ -348,7 +352,7 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.pair_bcount = B.take(4ull * tc);
     L.cell_disc = B.take(4ull * tc);
     L.pair_first = B.take(4ull * tc);
-    L.vmax2 = B.take(4ull * 3 * D);
+    L.vmax2 = B.take(8ull * 3 * D);
     L.nubin = B.take(sizeof(NuBin) * NUBIN_MAX * (size_t)D);
     // collision candidates of one step: a quarter of all slots (a candidate
     // probability up to 1/4 on average); more is reported as PIC_ECAPACITY
@@ -395,6 +399,9 @@ struct pic_handle {
     std::vector<NuBin> nubin;   // [D * NUBIN_MAX]
     std::vector<double> numax;  // [D*3]
     std::string err;
+    // largest accepted fraction of nu_max violations among null-collision
+    // candidates and of Eq. 1 P > 1 clamps among Eq. 1 evaluations
+    double numeric_budget = 1e-6;
     // graph of one period
     cudaGraphExec_t gexec = nullptr;
     long long period = 0;
@@ -553,31 +560,41 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
             S.ch[j].th = t.th;
             S.ch[j].th_f = (float)t.th;
         }
-        // nu_max up to a centre-of-mass energy: largest sum_j n_j sigma_j(E)
-        // sqrt(2E/mu) over the nodes up to it and at it, times the safety factor
+        // nu_max up to a centre-of-mass energy capE: [0, capE] is cut at every
+        // node and threshold of the species' channels; between neighbouring
+        // cuts a < b every sigma_j is linear (or zero), so sum_j n_j
+        // max(sigma_j(a), sigma_j(b)) sqrt(2b/mu) bounds the frequency there;
+        // the largest over the intervals, times the safety factor
         auto numax_upto = [&](double capE) {
-            double best = 0.0;
+            std::vector<double> cut{0.0, capE};
             for (int a = 0; a < S.nch; ++a) {
                 const HostTable &ta = h->tabs[S.ch[a].table];
-                for (int k = 0; k <= ta.n; ++k) {
-                    const double E = k < ta.n ? ta.E[k] : capE;
-                    if (E > capE || E <= 0.0) continue;
-                    const double u = std::sqrt(2.0 * E * QE / mu);
-                    double nu = 0.0;
-                    for (int b = 0; b < S.nch; ++b) {
-                        const HostTable &tb = h->tabs[S.ch[b].table];
-                        const double nj = (tb.reaction == 17) ? q.C_delta * ngas : ngas;
-                        nu += nj * sigma_host(tb, E) * u;
-                    }
-                    best = std::max(best, nu);
+                for (int k = 0; k < ta.n; ++k)
+                    if (ta.E[k] > 0.0 && ta.E[k] < capE) cut.push_back(ta.E[k]);
+                if (ta.th > 0.0 && ta.th < capE) cut.push_back(ta.th);
+            }
+            std::sort(cut.begin(), cut.end());
+            double best = 0.0;
+            for (size_t i = 0; i + 1 < cut.size(); ++i) {
+                const double a = cut[i], b = cut[i + 1];
+                if (!(b > a)) continue;
+                const double u = std::sqrt(2.0 * b * QE / mu);
+                double nu = 0.0;
+                for (int c = 0; c < S.nch; ++c) {
+                    const HostTable &tc = h->tabs[S.ch[c].table];
+                    const double nj = (tc.reaction == 17) ? q.C_delta * ngas : ngas;
+                    nu += nj * std::max(sigma_host(tc, a), sigma_host(tc, b)) * u;
                 }
+                best = std::max(best, nu);
             }
             return best * q.numax_safety;
         };
         S.numax = numax_upto(q.ecap_eV[s]);
         // electrons: one bound per quarter octave of lab energy; a bin's
-        // relative speed is at most its top electron speed plus 7 thermal
-        // speeds of the gas molecule; the last bin keeps the species' bound
+        // relative speed is at most its top electron speed plus the largest
+        // gas-molecule speed a collision can draw (Box-Muller radius at the
+        // smallest uniform 2^-33: below 9.6 thermal speeds sqrt(kT/M_O2),
+        // taken as GAS_SPEED_MAX); the last bin keeps the species' bound
         S.nbins = (s == 0) ? q.numax_bins : 0;
         S.bin_off = d * NUBIN_MAX;
         for (int b = 0; b < S.nbins; ++b) {
@@ -585,7 +602,7 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
             double nu = S.numax;
             if (b < S.nbins - 1) {
                 const double Ktop = std::ldexp(1.0 + (b % 4 + 1) / 4.0, NUBIN_LOG2_E0 + b / 4);
-                const double urel = std::sqrt(2.0 * Ktop * QE / m) + 7.0 * std::sqrt(KB * q.T_gas_K / M_O2);
+                const double urel = std::sqrt(2.0 * Ktop * QE / m) + GAS_SPEED_MAX * std::sqrt(KB * q.T_gas_K / M_O2);
                 nu = numax_upto(0.5 * mu * urel * urel / QE);
             }
             const double pb = 1.0 - std::exp(-nu * q.dt_s);
@@ -655,7 +672,6 @@ static void build_disc(pic_handle *h, int d, const std::vector<int> &gas_tabs_by
             P.bnd_g = g * 1.001;
             P.bnd_s = t.S[n - 1] * 1.001;
         }
-        P.ucap_n = std::sqrt(2.0 * q.ecap_eV[P.proj] * QE / mu) * tdx;
         P.bnd_g_f = (float)(P.bnd_g * 1.0001);
         P.bnd_s_f = (float)(P.bnd_s * 1.0001);
     }
@@ -737,7 +753,7 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.pair_bcount = reinterpret_cast<int *>(b + L.pair_bcount);
     W.cell_disc = reinterpret_cast<int *>(b + L.cell_disc);
     W.pair_first = reinterpret_cast<int *>(b + L.pair_first);
-    W.vmax2 = reinterpret_cast<unsigned *>(b + L.vmax2);
+    W.vmax2 = reinterpret_cast<unsigned long long *>(b + L.vmax2);
     W.nubin = reinterpret_cast<NuBin *>(b + L.nubin);
     W.cand = reinterpret_cast<int2 *>(b + L.cand);
     W.cand_cap = L.cand_cap;
@@ -1036,11 +1052,14 @@ static pic_status check_status(pic_handle *h)
         return fail(h, PIC_ECAPACITY, (status & ST_CAPACITY) ? "particle capacity exceeded; births were dropped"
                                                              : "a per-chunk or per-cell birth buffer overflowed");
     if (status & ST_BADSTATE) return fail(h, PIC_EINVAL, "inconsistent device state");
+    if (status & ST_NONFINITE)
+        return fail(h, PIC_ENUMERIC, "a particle position or velocity became non-finite (the particle was removed)");
     for (int d = 0; d < h->D; ++d) {
-        const unsigned long long v = c[(size_t)d * C_NCOUNT + C_VIOL_GAS];
-        const unsigned long long cand = c[(size_t)d * C_NCOUNT + C_CANDS];
-        if (v > 10 && (double)v > 1e-6 * (double)cand)
+        const unsigned long long *cd = &c[(size_t)d * C_NCOUNT];
+        if (cd[C_VIOL_GAS] > 10 && (double)cd[C_VIOL_GAS] > h->numeric_budget * (double)cd[C_CANDS])
             return fail(h, PIC_ENUMERIC, "collision frequency above nu_max too often (raise ecap_eV)");
+        if (cd[C_VIOL_PAIR] > 10 && (double)cd[C_VIOL_PAIR] > h->numeric_budget * (double)cd[C_PEVAL])
+            return fail(h, PIC_ENUMERIC, "Eq. 1 probability above 1 too often (shorten n1 dt)");
     }
     return PIC_OK;
 }
@@ -1108,6 +1127,15 @@ extern "C" pic_status pic_step(pic_handle *h, long long n_steps)
         if (s != PIC_OK) return s;
     }
     return check_status(h);
+}
+
+extern "C" pic_status pic_set_numeric_budget(pic_handle *h, double max_fraction)
+{
+    if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
+    if (!(max_fraction >= 0.0) || !(max_fraction <= 1.0))
+        return fail(h, PIC_EINVAL, "max_fraction must lie in [0, 1]");
+    h->numeric_budget = max_fraction;
+    return PIC_OK;
 }
 
 extern "C" pic_status pic_set_step(pic_handle *h, long long step)
@@ -1193,7 +1221,8 @@ extern "C" pic_status pic_diagnostics(pic_handle *h, int d, double *dens_sum, do
         counters[34] = (long long)c[C_SLOTS];
         counters[35] = (long long)c[C_COUL];
         counters[36] = (long long)c[C_DSMC];
-        for (int k = 37; k < 40; ++k) counters[k] = 0;
+        counters[37] = (long long)c[C_PEVAL];
+        for (int k = 38; k < 40; ++k) counters[k] = 0;
     }
     if (n_samples) *n_samples = (long long)ns;
     if (reset) {

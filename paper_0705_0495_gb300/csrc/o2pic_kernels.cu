@@ -411,7 +411,7 @@ k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
     const Disc &Dd = W.disc[d];
     const int N = Dd.N, n = W.cnt[ds].n;
     const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
-    if (bi == 0 && threadIdx.x == 0) W.vmax2[ds] = 0u;  // raised by the scatter
+    if (bi == 0 && threadIdx.x == 0) W.vmax2[ds] = 0ull;  // raised by the scatter
     if (bi >= G) return;
     for (int i = threadIdx.x; i <= N; i += blockDim.x) ssm[i] = 0;
     __syncthreads();
@@ -584,7 +584,7 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
     Real *offD = P.off[nxt] + pb, *vxD = P.vx[nxt] + pb, *vyD = P.vy[nxt] + pb,
          *vzD = P.vz[nxt] + pb;
     const unsigned lt = (1u << lane) - 1u;
-    float vm2 = 0.f;  // largest speed^2 of the live particles this lane moves
+    double vm2 = 0.0;  // largest speed^2 of the live particles this lane moves
     for (int i0 = lo; i0 < hi; i0 += 32 * SORT_ILP) {
         int b[SORT_ILP];
         int dst[SORT_ILP];
@@ -636,7 +636,7 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
         for (int r = 0; r < SORT_ILP; ++r) {
             if (dst[r] >= 0) {
                 const int g = gb[r] + dst[r];
-                vm2 = fmaxf(vm2, (float)(rx[r] * rx[r] + ry[r] * ry[r] + rz[r] * rz[r]));
+                vm2 = fmax(vm2, (double)(rx[r] * rx[r] + ry[r] * ry[r] + rz[r] * rz[r]));
                 cellD[g] = b[r];
                 offD[g] = ro[r];
                 vxD[g] = rx[r];
@@ -645,10 +645,8 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
             }
         }
     }
-    // speed bound of the species for the particle-target pass (float bits of
-    // a non-negative number order like unsigned integers)
-    const unsigned vb = __reduce_max_sync(0xffffffffu, __float_as_uint(vm2));
-    if (lane == 0 && vb) atomicMax(&W.vmax2[ds], vb);
+    // speed bound of the species for the particle-target pass
+    vmax_raise(W.vmax2, ds, vm2);
 }
 
 __global__ void k_sort_finish(WsPtrs W)
@@ -719,14 +717,29 @@ constexpr int NO_FLAG = 0x7F7F7F7F;  // larger than any slot index
 // P > 1 is recorded, and the sequential pass of that cell restarts there.
 // Before it, every projectile's outcome is exactly that of the sequential
 // pass, because no earlier projectile of the cell changed anything.
-// Particle-target reaction k by thinning (Eq. 1): B bounds P = n sigma u tau
-// for every pair below the projectile's cap speed (the same definition as the
-// oracle's), the cell's candidates are its projectiles at geometric gaps of
-// rate B (a random stream per cell), and a candidate reacts with probability
-// P / B; with B >= 1 every projectile is a candidate.
-__device__ __forceinline__ double pair_bound_B(const PairC &pc, int liveT)
+// Particle-target reaction k by thinning (Eq. 1): no pair of the pass is
+// faster than the sum of the two species' largest speeds (recorded at the
+// sort and raised by the velocity changes since), so with u_cap that sum,
+// rounded up to 5 significant bits in m/s (the same grid point whatever the
+// rounding of the sum), B = n_target max sigma u tau over u <= u_cap bounds P
+// for every pair; the cell's candidates are its projectiles at geometric
+// gaps of rate B (a random stream per cell), and a candidate reacts with
+// probability min(P, 1) / min(B, 1); with B >= 1 every projectile is a
+// candidate.  Every projectile then reacts with probability min(P, 1).
+__device__ __forceinline__ double round_up_5bits(double u)
 {
-    return (double)liveT * pc.coef * fmax(pc.bnd_g, pc.bnd_s * pc.ucap_n);
+    if (!(u > 0.0)) return 0.0;
+    int e;
+    const double m = frexp(u, &e);
+    return ldexp(ceil(m * 32.0) / 32.0, e);
+}
+__device__ __forceinline__ double pair_bound_B(const WsPtrs &W, const Disc &Dd, int d, const PairC &pc, int liveT)
+{
+    const double vs = Dd.sp[0].vscale;  // cells per step -> m/s
+    const double vp = sqrt(__longlong_as_double((long long)W.vmax2[d * NSP + pc.proj]));
+    const double vt = sqrt(__longlong_as_double((long long)W.vmax2[d * NSP + pc.targ]));
+    const double ucap_n = round_up_5bits((vp + vt) * vs) / vs;
+    return (double)liveT * pc.coef * fmax(pc.bnd_g, pc.bnd_s * ucap_n);
 }
 // gap before the next candidate: floor(ln U / ln(1 - B)) for the draw-th word
 // of the cell's stream (B < 1, lq = ln(1 - B)), at most 2^30
@@ -758,7 +771,7 @@ k_pair_eval(WsPtrs W, Pools<Real> P, int par, int k)
     if (range <= 0) return;
     const int liveT = range - W.pair_kills[(size_t)gw * NSP + pt];
     if (liveT <= 0) return;
-    const double B = pair_bound_B(pc, liveT);
+    const double B = pair_bound_B(W, Dd, d, pc, liveT);
     long long first = 0;
     if (B < 1.0) {
         const int rx = k == 0 ? 13 : (k == 1 ? 14 : 19);
@@ -806,14 +819,14 @@ k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
     const int pbp = Dd.pbase[ps], pbt = Dd.pbase[pt];
     // candidates of the thinning, 32 at a time: each lane draws its gap, a
     // warp scan of (1 + gap) places them (the gaps do not depend on events)
-    const double B = pair_bound_B(pc, liveT);
+    const double B = pair_bound_B(W, Dd, d, pc, liveT);
     const bool thin = B < 1.0;
     const double lq = thin ? log1p(-B) : 0.0;
     const Real Bc = thin ? Real(B) : Real(1);
     long long pos = p0 - 1;  // last candidate placed (warp-uniform)
     unsigned draw = 0;
     bool stop = false;
-    unsigned nviol = 0;
+    unsigned nviol = 0, neval = 0;
     int nkp = 0, nkt = 0;
     (void)first;
     while (!stop && pos + 1 < p1) {
@@ -829,7 +842,7 @@ k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
         draw += 32;
         int from = 0;
         for (;;) {
-            bool ev = false, ex = false, viol = false;
+            bool ev = false, ex = false, viol = false, evald = false;
             int j = -1;
             uint4 d0 = make_uint4(0, 0, 0, 0);
             if (i < p1 && lane >= from && cellA[pbp + i] >= 0) {
@@ -850,16 +863,18 @@ k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
                     const Real u = sqrt(u2);
                     const Real E = pick<Real>(pc.Ek, pc.Ek_f) * u2;
                     Real Pc = coefP * pair_sigma<Real>(W, T, E) * u;
-                    if (Pc > Bc) {  // above the cap speed, or beyond 1
+                    if (Pc > Real(1)) {  // Eq. 1 beyond 1: clamped and counted (R10)
                         viol = true;
-                        Pc = Bc;
+                        Pc = Real(1);
                     }
                     ev = unif<Real>(d0.y) * Bc < Pc;
+                    evald = true;
                 }
             }
             const unsigned m = __ballot_sync(0xffffffffu, ev || ex);
             const int l = m ? __ffs(m) - 1 : 32;
             nviol += __popc(__ballot_sync(0xffffffffu, viol && lane <= l));
+            neval += __popc(__ballot_sync(0xffffffffu, evald && lane <= l));
             if (!m) break;
             const bool exl = __shfl_sync(0xffffffffu, ex, l);
             if (exl) {
@@ -932,6 +947,7 @@ k_pair_fix(WsPtrs W, Pools<Real> P, int par, int k)
     }
     if (lane == 0) {
         if (nviol) atomicAdd(&cnt[C_VIOL_PAIR], (unsigned long long)nviol);
+        if (neval) atomicAdd(&cnt[C_PEVAL], (unsigned long long)neval);
         kills[ps] += nkp;
         kills[pt] += nkt;
         W.pair_bcount[gw] = nb < PAIR_BIRTH_CAP ? nb : PAIR_BIRTH_CAP;
@@ -1076,6 +1092,16 @@ __device__ __forceinline__ void coulomb_copy(Real *__restrict__ dx, Real *__rest
     }
 }
 
+// largest speed^2 among n velocities (a block-strided share per thread)
+template <typename Real>
+__device__ __forceinline__ double speed2_max(const Real *x, const Real *y, const Real *z, int n)
+{
+    double m = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+        m = fmax(m, (double)(x[k] * x[k] + y[k] * y[k] + z[k] * z[k]));
+    return m;
+}
+
 // Collision k of a cell with the random numbers of draw 1 + k/2: the normal
 // is the first (k even) or second (k odd) of the Box-Muller pair, the
 // azimuth word 2 or 3.
@@ -1191,6 +1217,9 @@ k_coulomb(WsPtrs W, Pools<Real> P, int par, int cap)
     }
     const SpeciesC &S = Dd.sp[s];
     const Real kn = pick<Real>(S.coul_k, S.coul_k_f) * Real(n);
+    // the new speeds raise the species' recorded largest speed, which bounds
+    // P in a particle-target pass of the same step
+    double m2;
     if (n <= cap) {
         Real *sx = reinterpret_cast<Real *>(coul_smem), *sy = sx + cap, *sz = sy + cap;
         coulomb_copy<Real>(sx, sy, sz, gx, gy, gz, n);
@@ -1198,10 +1227,14 @@ k_coulomb(WsPtrs W, Pools<Real> P, int par, int cap)
         coulomb_cell_pairs<Real>(sx, sy, sz, un, prm, kn, seed, disc, s, step, c);
         __syncthreads();
         coulomb_copy<Real>(gx, gy, gz, sx, sy, sz, n);
+        m2 = speed2_max<Real>(sx, sy, sz, n);
     } else {
         __syncthreads();
         coulomb_cell_pairs<Real>(gx, gy, gz, un, prm, kn, seed, disc, s, step, c);
+        __syncthreads();
+        m2 = speed2_max<Real>(gx, gy, gz, n);
     }
+    vmax_raise(W.vmax2, d * NSP + s, m2);
 }
 
 // One Coulomb collision between particles a (velocity va) and b (vb) of
@@ -1344,6 +1377,7 @@ k_coulomb_inter(WsPtrs W, Pools<Real> P, int par, int pair, int cap)
     const unsigned stepB = (unsigned)(((unsigned long long)aB * COUL_THREADS) % uB);
     const unsigned stepA = (unsigned)(((unsigned long long)aA * COUL_THREADS) % uA);
     const unsigned chainA = (unsigned)(((unsigned long long)aA * uB) % uA);
+    double m2b = 0.0;  // largest new speed^2 of this thread's B particles
     for (unsigned r = t0; r < uB; r += COUL_THREADS) {
         Real vb[3] = {gbx[j], gby[j], gbz[j]};
         unsigned i = i0;
@@ -1362,15 +1396,17 @@ k_coulomb_inter(WsPtrs W, Pools<Real> P, int par, int pair, int cap)
         gbx[j] = vb[0];
         gby[j] = vb[1];
         gbz[j] = vb[2];
+        m2b = fmax(m2b, (double)(vb[0] * vb[0] + vb[1] * vb[1] + vb[2] * vb[2]));
         j += stepB;
         if (j >= uB) j -= uB;
         i0 += stepA;
         if (i0 >= uA) i0 -= uA;
     }
-    if (staged) {
-        __syncthreads();
-        coulomb_copy<Real>(gax, gay, gaz, ax, ay, az, nA);
-    }
+    __syncthreads();
+    if (staged) coulomb_copy<Real>(gax, gay, gaz, ax, ay, az, nA);
+    // the new speeds raise both species' recorded largest speeds
+    vmax_raise(W.vmax2, d * NSP + sA, speed2_max<Real>(ax, ay, az, nA));
+    vmax_raise(W.vmax2, d * NSP + sB, m2b);
 }
 
 // Births of (19) appended to the electron array of each discharge in cell

@@ -770,6 +770,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             // a mask and handled after the four slots
             unsigned nslots = 0, nlive = 0, outm = 0, wallm = 0;
             bool cchg = false;  // a cell index of the lane's slots changed
+            bool nonfin = false;
             int dep[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -784,6 +785,8 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 Real o = off[k] + v * ks;
                 const Real fl = floor(o);
                 const bool bad = !(fl > Real(-2 * N - 4) && fl < Real(2 * N + 4));
+                // a non-finite velocity or position is an error, not an absorption
+                nonfin |= was && !isfinite(o);
                 int cn = bad ? (v < Real(0) ? -1 : N) : cc + (int)fl;
                 o -= fl;
                 const bool wrap = o >= Real(1);
@@ -791,7 +794,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 cn += wrap ? 1 : 0;
                 const bool out = was && (cn < 0 || cn >= N);
                 const bool live = was && !out;
-                outm |= out ? 1u << k : 0u;
+                outm |= (out && isfinite(o)) ? 1u << k : 0u;
                 wallm |= cn >= N ? 1u << k : 0u;
                 vx[k] = was ? v : vx[k];
                 off[k] = live ? o : off[k];
@@ -814,6 +817,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 }
                 qn += __popc(m);
             }
+            if (nonfin) set_status(ctl, ST_NONFINITE);
             if (outm) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -1092,6 +1096,7 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
     }
     if (nlive) atomicAdd(&s_ev[C_DSMC], nlive);
     __syncthreads();
+    unsigned ntest = 0;  // Eq. 1 tests of this thread's particles
     for (int kk = 0; kk < Dd.ndsmc; ++kk) {
         const DsmcCh &e = Dd.dsmc[kk];
         if (part == 0 ? e.reaction > 12 : e.reaction < 15) continue;  // uniform
@@ -1114,6 +1119,7 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
             for (int q = 0; q < PT; ++q) {
                 const int local = tid + q * DSMC_THREADS;
                 if (!in[q]) continue;
+                ++ntest;
                 if (unif<Real>(w[q]) < dsmc_bound<Real>(W, S, e.j, sumax[local], sk[local], sreg[local], n1))
                     sq[atomicAdd(&s_qn, 1u)] = (unsigned short)local;
             }
@@ -1190,8 +1196,11 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
         if (tid == 0) s_qn = 0u;
         __syncthreads();
     }
+    if (ntest) atomicAdd(&s_ev[C_PEVAL], ntest);
     // write back: the first particle's new velocity, or its removal and the
-    // product that ends its chain
+    // product that ends its chain; part 0 raises the species' recorded
+    // largest speed (the particle-target pass that follows bounds P with it)
+    double m2 = 0.0;
     for (int local = tid; local < CHUNK; local += DSMC_THREADS) {
         const int rel = rel0 + local;
         if (rel >= C.n) break;
@@ -1203,6 +1212,7 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
             vxA[i] = v[0];
             vyA[i] = v[1];
             vzA[i] = v[2];
+            m2 = fmax(m2, (double)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
         } else {
             const Real off = offA[i];
             cellA[i] = -1;
@@ -1212,6 +1222,7 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
             stage_birth<Real>(B, ((local % SUBTILE) << 1) | 1, ssp[local], c, off, v);
         }
     }
+    if (part == 0) vmax_raise(W.vmax2, ds, m2);
     __syncthreads();
     for (int k = tid; k < C_NCOUNT; k += DSMC_THREADS)
         if (s_ev[k]) atomicAdd(&W.counters[(size_t)d * C_NCOUNT + k], (unsigned long long)s_ev[k]);

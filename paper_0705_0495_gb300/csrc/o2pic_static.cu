@@ -41,7 +41,10 @@ __global__ void k_static_deposit_f32(unsigned long long *acc, const int *cell, c
          i += (long long)gridDim.x * blockDim.x) {
         const int c = cell[i];
         if (c < 0 || c >= N) continue;
-        const unsigned w1 = __float2uint_rn(off[i] * (float)(1 << o2::FIX_BITS));
+        // an offset outside [0, 1] (or NaN) is clamped into it, so that the
+        // two weights stay within [0, 2^FIX_BITS] and add up to one particle
+        const float o = fminf(fmaxf(off[i], 0.0f), 1.0f);
+        const unsigned w1 = __float2uint_rn(o * (float)(1 << o2::FIX_BITS));
         const unsigned w0 = (1u << o2::FIX_BITS) - w1;
         atomicAdd(&acc[c], (unsigned long long)w0);
         atomicAdd(&acc[c + 1], (unsigned long long)w1);
@@ -54,8 +57,9 @@ __global__ void k_static_deposit_f64(double *acc, const int *cell, const double 
          i += (long long)gridDim.x * blockDim.x) {
         const int c = cell[i];
         if (c < 0 || c >= N) continue;
-        atomicAdd(&acc[c], 1.0 - off[i]);
-        atomicAdd(&acc[c + 1], off[i]);
+        const double o = fmin(fmax(off[i], 0.0), 1.0);  // clamped as in the FP32 path
+        atomicAdd(&acc[c], 1.0 - o);
+        atomicAdd(&acc[c + 1], o);
     }
 }
 

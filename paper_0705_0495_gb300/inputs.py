@@ -248,7 +248,9 @@ def cfg4(**kw) -> Discharge:
 
 
 def cfg5(seed=1, fp64=True, **kw) -> Discharge:
-    """Long-horizon run: cfg1 for 1000 RF cycles."""
+    """Long-horizon run: cfg1 for 1000 RF cycles, with room for the densities
+    to grow sixteenfold."""
+    kw.setdefault("capacity_factor", 16.0)
     return cfg1(seed=seed, fp64=fp64, rf_cycles=1000.0, **kw)
 
 

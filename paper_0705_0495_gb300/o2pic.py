@@ -50,7 +50,7 @@ class pic_config(C.Structure):
 
 
 EXPORTS = ["pic_workspace_size", "pic_init", "pic_step", "pic_diagnostics", "pic_get_state",
-           "pic_set_state", "pic_set_step", "pic_fields", "pic_numax", "pic_set_timing",
+           "pic_set_state", "pic_set_step", "pic_set_numeric_budget", "pic_fields", "pic_numax", "pic_set_timing",
            "pic_timing", "pic_kernel_timing", "pic_get_launch", "pic_set_launch", "pic_destroy",
            "pic_last_error",
            "pic_field_solve_static"]
@@ -84,6 +84,8 @@ def load(path: str = LIB_PATH):
     l.pic_set_state.argtypes = [vp, C.c_int, C.c_int, C.c_longlong, dp, dp, dp, dp, ip]
     l.pic_set_step.restype = C.c_int
     l.pic_set_step.argtypes = [vp, C.c_longlong]
+    l.pic_set_numeric_budget.restype = C.c_int
+    l.pic_set_numeric_budget.argtypes = [vp, C.c_double]
     l.pic_fields.restype = C.c_int
     l.pic_fields.argtypes = [vp, C.c_int, dp, dp, dp]
     l.pic_numax.restype = C.c_double
@@ -171,7 +173,7 @@ def workspace_size(discharges, tables, fp64=None) -> int:
 class Simulation:
     """Discharges advanced together on one GPU through libo2pic."""
 
-    def __init__(self, discharges, tables, fp64=None, device="cuda", stream=None):
+    def __init__(self, discharges, tables, fp64=None, device="cuda", stream=None, numeric_budget=None):
         import torch
         self.lib = load()
         if not isinstance(discharges, (list, tuple)):
@@ -196,6 +198,8 @@ class Simulation:
         if rc != 0:
             raise PicError(rc, self.lib.pic_last_error(None).decode())
         self.h = h
+        if numeric_budget is not None:
+            self.set_numeric_budget(numeric_budget)
 
     def _check(self, rc):
         if rc != 0:
@@ -217,6 +221,11 @@ class Simulation:
 
     def set_step(self, k):
         self._check(self.lib.pic_set_step(self.h, int(k)))
+
+    def set_numeric_budget(self, max_fraction):
+        """largest accepted fraction of nu_max violations and of Eq. 1 P > 1
+        clamps before pic_step reports PIC_ENUMERIC (default 1e-6)"""
+        self._check(self.lib.pic_set_numeric_budget(self.h, float(max_fraction)))
 
     def count(self, d, s):
         n = C.c_longlong()
@@ -262,13 +271,15 @@ class Simulation:
         ns = C.c_longlong()
         self._check(self.lib.pic_diagnostics(self.h, d, _dp(dens), _dp(phi), _lp(eedf), _lp(iedf),
                                              _lp(fm), _lp(cnt), C.byref(ns), 1 if reset else 0))
+        k = max(ns.value, 1)
         return {"n_samples": ns.value, "dens_sum": dens, "phi_sum": phi, "eedf": eedf,
+                "dens_avg": dens / k, "phi_avg": phi / k,
                 "iedf": iedf, "fm": fm, "absorbed": cnt[0:6].reshape(3, 2),
                 "events": cnt[6:26].copy(), "violations": cnt[26:28].copy(),
                 "slots": cnt[28:31].copy(), "steps": int(cnt[31]),
                 "particle_steps": int(cnt[32]), "candidates": int(cnt[33]),
                 "slots_visited": int(cnt[34]), "coulomb_particles": int(cnt[35]),
-                "sequential_gas_slots": int(cnt[36])}
+                "sequential_gas_slots": int(cnt[36]), "eq1_evaluations": int(cnt[37])}
 
     def set_timing(self, on=True):
         self._check(self.lib.pic_set_timing(self.h, 1 if on else 0))

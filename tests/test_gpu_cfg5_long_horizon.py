@@ -1,0 +1,114 @@
+"""The long-horizon workload at its full length: the cfg1 discharge (2.5 cm,
+128 cells, 20 Pa, 100 V, 10k e + 10k O- + 20k O2+ at load) for 1000 RF
+cycles, the paper's time to a quasi-stationary state (Sec. II), 8 seeds
+each in FP32 mixed and in FP64 on the GPU (each precision one batched handle
+of 8 discharges) and 8 seeds of the FP64 oracle in parallel on the host
+cores.  Time averages over the last 200 cycles (densities of e, O-, O2+, the
+potential, the EEDF at L/2, the O2+ energy distribution at each electrode
+in 20 bins): the normal-equivalent Welch deviate z of every node and every
+bin with at least 100 counts on both sides (tests/ensemble.py) within 3 at
+>= 99 % of them, for each GPU ensemble against the oracle's.
+
+It takes about 15 minutes (the oracle: 4e10 particle-steps per seed), so it
+runs only when O2PIC_CFG5=1; O2PIC_CFG5_REPORT names a JSON file that
+receives the profiles, the z statistics and the timings."""
+import json
+import multiprocessing
+import os
+import sys
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from ensemble import averages, compare, within_3
+from paper_0705_0495_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+SEEDS = 8
+CYCLES = 1000
+AVERAGE = 200
+KW = dict(iedf_bins=20)
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    if os.environ.get("O2PIC_CFG5") != "1":
+        pytest.skip("the 1000-cycle run takes about 15 minutes: set O2PIC_CFG5=1")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _oracle_run(seed):
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle as orc
+    from ensemble import averages as avg
+    from paper_0705_0495_gb300 import inputs as inp
+    t0 = time.time()
+    d = inp.cfg5(seed=seed, **KW)
+    o = orc.Oracle(d, inp.xs_tables())
+    o.step((CYCLES - AVERAGE) * d.steps_per_cycle)
+    o.reset_diag()
+    o.step(AVERAGE * d.steps_per_cycle)
+    r = avg(o.diag())
+    r["seconds"] = time.time() - t0
+    r["particle_steps"] = o.particle_steps
+    r["counts"] = [o.count(s) for s in range(3)]
+    return r
+
+
+def _gpu_runs(fp64):
+    from paper_0705_0495_gb300 import o2pic
+    ds = [inputs.cfg5(fp64=fp64, seed=1 + k, **KW) for k in range(SEEDS)]
+    sim = o2pic.Simulation(ds, inputs.xs_tables())
+    spc = ds[0].steps_per_cycle
+    t0 = time.time()
+    sim.step((CYCLES - AVERAGE) * spc)
+    for k in range(SEEDS):
+        sim.diagnostics(k, reset=True)
+    sim.step(AVERAGE * spc)
+    torch.cuda.synchronize()
+    sec = time.time() - t0
+    out = [averages(sim.diagnostics(k)) for k in range(SEEDS)]
+    ps = sum(sim.diagnostics(k)["particle_steps"] for k in range(SEEDS))
+    counts = [[sim.count(k, s) for s in range(3)] for k in range(SEEDS)]
+    sim.close()
+    return out, {"seconds": sec, "particle_steps": ps, "counts": counts}
+
+
+def test_cfg5_1000_cycles_fp32_and_fp64_gpu_ensembles_match_the_oracle():
+    oracle.build()
+    pool = multiprocessing.get_context("spawn").Pool(min(SEEDS, os.cpu_count() or 1))
+    pending = pool.map_async(_oracle_run, [101 + k for k in range(SEEDS)])
+    gpu = {"fp32": _gpu_runs(False), "fp64": _gpu_runs(True)}
+    orc = pending.get(timeout=7200)
+    pool.close()
+    pool.join()
+    report = {"cycles": CYCLES, "average_cycles": AVERAGE, "seeds": SEEDS,
+              "oracle": {"seconds_per_seed": [r["seconds"] for r in orc],
+                         "particle_steps_per_seed": [r["particle_steps"] for r in orc],
+                         "final_counts": [r["counts"] for r in orc],
+                         "cores": os.cpu_count()}}
+    ok = {}
+    for name, (runs, meta) in gpu.items():
+        zs, sizes = compare(runs, orc, min_iedf_bins=5)
+        frac = within_3(zs)
+        ok[name] = frac
+        mid = inputs.cfg5().n_cells // 2
+        report[name] = dict(meta, within_3=frac, sizes=sizes, max_abs_z=float(np.max(np.abs(zs))),
+                            mean_dens_mid=[float(np.mean([r["dens"][s][mid] for r in runs])) for s in range(3)])
+    report["oracle"]["mean_dens_mid"] = [float(np.mean([r["dens"][s][inputs.cfg5().n_cells // 2] for r in orc]))
+                                         for s in range(3)]
+    path = os.environ.get("O2PIC_CFG5_REPORT")
+    if path:
+        with open(path, "w") as f:
+            json.dump(report, f, indent=1)
+    for name, frac in ok.items():
+        assert frac >= 0.99, (name, frac, report[name])

@@ -2,13 +2,13 @@
 on the GPU in FP32 mixed and in FP64, against 8 seeds of the FP64 oracle.
 The time averages over the last 30 cycles (densities of e, O-, O2+, the
 potential, the EEDF at L/2 and the O2+ energy distribution at the
-electrodes) of each GPU ensemble must agree with the oracle ensemble as in
-the 2-cycle ensemble test: with z = (m_gpu - m_orc) / sqrt(s_gpu^2/n +
-s_orc^2/n) per node and per histogram bin holding at least 100 counts on both
-sides, the mean of z^2 at most 3, at most 10% of the values beyond 3, none
-beyond 6.  (100 cycles averaged over the last 50 passed the same criteria;
-60 keep the test within a few minutes, the oracle seeds running in parallel
-on the host cores.)"""
+electrodes, 20 bins per electrode) of each GPU ensemble must agree with the
+oracle ensemble within 3 sigma of the seed-to-seed scatter: the normal-
+equivalent Welch deviate z of every node and of every histogram bin holding
+at least 100 counts on both sides (tests/ensemble.py) within 3 at >= 99 % of
+them.  Two oracle ensembles of 8 seeds met it (100 %).  The 8 GPU runs of a
+precision are one batched handle.  The full horizon of the workload (1000
+cycles) is tests/test_gpu_cfg5_long_horizon.py."""
 import multiprocessing
 import os
 import sys
@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
+from ensemble import averages, compare, within_3
 from paper_0705_0495_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -25,7 +26,7 @@ pytestmark = pytest.mark.gpu
 SEEDS = 8
 CYCLES = 60
 AVERAGE = 30
-KW = dict(n_op=40000, iedf_bins=2)
+KW = dict(n_op=40000, iedf_bins=20)
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -37,58 +38,32 @@ def _built():
     __graft_entry__.build()
 
 
-def _averages(g):
-    ns = g["n_samples"]
-    return {"dens": g["dens_sum"] / ns, "phi": g["phi_sum"] / ns,
-            "eedf": g["eedf"].astype(float), "iedf": g["iedf"].astype(float).ravel()}
-
-
 def _oracle_run(seed):
     sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
     import oracle as orc
+    from ensemble import averages as avg
     from paper_0705_0495_gb300 import inputs as inp
     d = inp.cfg1(seed=seed, **KW)
     o = orc.Oracle(d, inp.xs_tables())
     o.step((CYCLES - AVERAGE) * d.steps_per_cycle)
     o.reset_diag()
     o.step(AVERAGE * d.steps_per_cycle)
-    return _averages(o.diag())
+    return avg(o.diag())
 
 
 def _gpu_runs(fp64):
     from paper_0705_0495_gb300 import o2pic
-    tabs = inputs.xs_tables()
-    out = []
+    ds = [inputs.cfg1(fp64=fp64, seed=1 + k, **KW) for k in range(SEEDS)]
+    sim = o2pic.Simulation(ds, inputs.xs_tables())
+    spc = ds[0].steps_per_cycle
+    sim.step((CYCLES - AVERAGE) * spc)
     for k in range(SEEDS):
-        d = inputs.cfg1(fp64=fp64, seed=1 + k, **KW)
-        sim = o2pic.Simulation([d], tabs)
-        sim.step((CYCLES - AVERAGE) * d.steps_per_cycle)
-        sim.diagnostics(0, reset=True)
-        sim.step(AVERAGE * d.steps_per_cycle)
-        out.append(_averages(sim.diagnostics(0)))
-        sim.close()
+        sim.diagnostics(k, reset=True)
+    sim.step(AVERAGE * spc)
+    out = [averages(sim.diagnostics(k)) for k in range(SEEDS)]
+    sim.close()
     return out
-
-
-def _z(a, b):
-    a, b = np.asarray(a), np.asarray(b)
-    n = a.shape[0]
-    floor = 1e-6 * np.sqrt(np.mean(b.mean(axis=0) ** 2))
-    se = np.sqrt(a.var(axis=0, ddof=1) / n + b.var(axis=0, ddof=1) / n + floor ** 2)
-    return (a.mean(axis=0) - b.mean(axis=0)) / np.where(se > 0, se, 1.0)
-
-
-def _compare(gpu, orc):
-    zs = []
-    for key in ("dens", "phi"):
-        zs.append(_z([g[key] for g in gpu], [o[key] for o in orc]).ravel())
-    for key in ("eedf", "iedf"):
-        a = np.array([g[key] for g in gpu])
-        b = np.array([o[key] for o in orc])
-        keep = (a.mean(axis=0) >= 100) & (b.mean(axis=0) >= 100)
-        assert keep.sum() >= 2, key
-        zs.append(_z(a[:, keep], b[:, keep]).ravel())
-    return np.concatenate(zs)
 
 
 def test_fp32_and_fp64_gpu_ensembles_match_the_oracle_over_60_cycles():
@@ -100,8 +75,6 @@ def test_fp32_and_fp64_gpu_ensembles_match_the_oracle_over_60_cycles():
     pool.close()
     pool.join()
     for name, gpu in results.items():
-        zs = _compare(gpu, orc)
+        zs, sizes = compare(gpu, orc, min_iedf_bins=5)
         top = np.sort(np.abs(zs))[-5:]
-        assert np.mean(zs ** 2) <= 3.0, (name, np.mean(zs ** 2), top)
-        assert np.mean(np.abs(zs) > 3.0) <= 0.10, (name, np.mean(np.abs(zs) > 3.0), top)
-        assert np.all(np.abs(zs) <= 6.0), (name, top)
+        assert within_3(zs) >= 0.99, (name, within_3(zs), sizes, top)

@@ -3,8 +3,11 @@ on the same seeded inputs.
 
 FP64 path: step by step, slot by slot (same order, same random streams),
 within 1e-9 of the gap / of the thermal speed.  FP32 path: each step started
-from the oracle's state ("replay"), matched by position, within 1e-5 with
-decision flips counted (at most 1e-4 of particle-steps).
+from the oracle's state ("replay") and compared particle by particle
+(tests/replay.py): every particle whose decisions agree within 1e-5 (of the
+gap, of its speed or the thermal speed), the particles whose discrete
+decision differs ("flips": absorption, null-collision test, channel,
+partner) at most 1e-4 of the particles compared.
 """
 import math
 
@@ -13,6 +16,7 @@ import pytest
 
 import oracle
 from paper_0705_0495_gb300 import inputs
+from replay import StepResult, compare_step
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -33,10 +37,18 @@ def _built():
     __graft_entry__.build()
 
 
-def _sim(ds, tabs=None, fp64=None):
+# Cases that make Eq. 1's P exceed 1 on purpose (cross sections scaled up,
+# or the sequential gas scheme's n1 dt for fast electrons) accept any
+# number of P > 1 clamps; everything else runs with the library's default
+# budget, so an unexpected clamp fails the test.
+LOOSE = 1.0
+
+
+def _sim(ds, tabs=None, fp64=None, budget=None):
     from paper_0705_0495_gb300 import o2pic
     return o2pic.Simulation(ds if isinstance(ds, list) else [ds],
-                            inputs.xs_tables() if tabs is None else tabs, fp64=fp64)
+                            inputs.xs_tables() if tabs is None else tabs, fp64=fp64,
+                            numeric_budget=budget)
 
 
 def _vth(d, s):
@@ -54,77 +66,6 @@ def _cmp_slots(d, g, o, s):
     vt = _vth(d, s)
     ev = max(np.max(np.abs(g[c][m] - o[c][m])) for c in ("vx", "vy", "vz")) / vt
     return ex, ev
-
-
-def _slotwise(d, g, o, s, tol):
-    """slot by slot (valid while both sides keep the same order)"""
-    if len(g["x"]) != len(o["x"]):
-        return None
-    vt = _vth(d, s)
-    err = np.abs(g["x"] - o["x"]) / d.L
-    for c in ("vx", "vy", "vz"):
-        err = np.maximum(err, np.abs(g[c] - o[c]) / vt)
-    both = g["alive"] & o["alive"]
-    bad = (g["alive"] != o["alive"]) | (both & (err > tol))
-    rest = float(np.max(err[both & ~bad], initial=0.0))
-    return int(both.sum()), int(bad.sum()), rest
-
-
-def _matched(d, g, o, s, tol):
-    """Decision flips under the better of two pairings: slot by slot, and by
-    sorted position (a sort can reorder a cell after one flipped particle).
-    Returns (n_compared, n_flips, max error of the non-flipped)."""
-    best = _slotwise(d, g, o, s, tol)
-    if best is not None and best[1] == 0:
-        return best
-    gm, om = g["alive"], o["alive"]
-    gi = np.argsort(g["x"][gm], kind="stable")
-    oi = np.argsort(o["x"][om], kind="stable")
-    gx = {c: g[c][gm][gi] for c in ("x", "vx", "vy", "vz")}
-    ox = {c: o[c][om][oi] for c in ("x", "vx", "vy", "vz")}
-    n = min(len(gx["x"]), len(ox["x"]))
-    extra = abs(len(gx["x"]) - len(ox["x"]))
-    vt = _vth(d, s)
-    err = np.abs(gx["x"][:n] - ox["x"][:n]) / d.L
-    for c in ("vx", "vy", "vz"):
-        err = np.maximum(err, np.abs(gx[c][:n] - ox[c][:n]) / vt)
-    bad = err > tol
-    rest = float(np.max(err[~bad], initial=0.0))
-    byx = (n, int(bad.sum()) + extra, rest)
-    if best is None or byx[1] < best[1]:
-        best = byx
-    return best
-
-
-def _matched_by_cell(d, g, o, s, tol):
-    """After a Coulomb pass: a decision that changes the number of particles
-    of a species in a cell (a birth, a death or a cell crossing decided
-    differently in FP32) changes that cell's random pairing, so all of its
-    particles scatter with other partners.  Cells whose counts agree are
-    compared slot by slot; the others are counted.  Returns (particles
-    compared, bad particles, cells with different counts, worst error of the
-    good ones)."""
-    N = d.n_cells
-    dx = d.L / N
-    side = []
-    for st in (g, o):
-        m = st["alive"]
-        c = np.clip(np.floor(st["x"][m] / dx).astype(np.int64), 0, N - 1)
-        order = np.argsort(c, kind="stable")
-        side.append(({k: st[k][m][order] for k in ("x", "vx", "vy", "vz")},
-                     np.bincount(c, minlength=N)))
-    (ga, gc), (oa, oc) = side
-    gs = np.concatenate([[0], np.cumsum(gc)])
-    os_ = np.concatenate([[0], np.cumsum(oc)])
-    same = gc == oc
-    gi = np.concatenate([np.arange(gs[k], gs[k + 1]) for k in np.flatnonzero(same)] + [np.zeros(0, int)])
-    oi = np.concatenate([np.arange(os_[k], os_[k + 1]) for k in np.flatnonzero(same)] + [np.zeros(0, int)])
-    vt = _vth(d, s)
-    err = np.abs(ga["x"][gi] - oa["x"][oi]) / d.L
-    for k in ("vx", "vy", "vz"):
-        err = np.maximum(err, np.abs(ga[k][gi] - oa[k][oi]) / vt)
-    bad = err > tol
-    return len(gi), int(bad.sum()), int((~same).sum()), float(np.max(err[~bad], initial=0.0))
 
 
 # ------------------------------------------------------------------ load
@@ -155,9 +96,9 @@ def test_initial_fields_match_oracle():
 
 # --------------------------------------------------------- FP64 parity
 
-def _run_pair(d, steps_list, tabs=None):
+def _run_pair(d, steps_list, tabs=None, budget=None):
     tabs = inputs.xs_tables() if tabs is None else tabs
-    sim = _sim(d, tabs)
+    sim = _sim(d, tabs, budget=budget)
     orc = oracle.Oracle(d, tabs)
     done = 0
     worst = (0.0, 0.0)
@@ -190,8 +131,11 @@ def test_fp64_diagnostics_match_oracle():
     assert g["n_samples"] == o["n_samples"] == 20
     assert np.max(np.abs(g["dens_sum"] - o["dens_sum"])) <= 1e-9 * np.max(o["dens_sum"])
     assert np.max(np.abs(g["phi_sum"] - o["phi_sum"])) <= 1e-9 * np.max(np.abs(o["phi_sum"]))
+    # the histograms bin the same particles by the same energies: FP64
+    # rounding could only move a sample that lies within about 1e-13 of a
+    # bin edge (or a cell edge, for the EEDF cell and the f_- regions)
     for k in ("eedf", "iedf", "fm"):
-        assert np.abs(g[k] - o[k]).sum() <= 2, k
+        assert np.array_equal(g[k], o[k]), (k, np.flatnonzero(g[k] != o[k]))
     assert o["eedf"].sum() > 0 and o["fm"].sum() > 0
 
 
@@ -243,34 +187,68 @@ def test_fp64_pair_pass_with_frequent_events():
     # oracle, which evaluates every projectile
     d = inputs.cfg1(n_op=6000)
     tabs = _scaled_pair_tables(3e6)
-    sim, orc, (ex, ev) = _run_pair(d, [10, 11, 20, 30], tabs)
+    sim, orc, (ex, ev) = _run_pair(d, [10, 11, 20, 30], tabs, budget=LOOSE)
     assert ex < TOL64 and ev < TOL64, (ex, ev)
     g, o = sim.diagnostics(0), orc.counters()
     assert np.array_equal(g["events"], o["events"])
+    assert np.array_equal(g["violations"], o["violations"][:2])
     assert g["events"][13] > 0 and g["events"][14] > 0 and g["events"][19] > 0, g["events"]
 
 
 def test_fp32_pair_pass_with_frequent_events():
+    # as above in FP32, replayed over two particle-target steps
     d = inputs.cfg1(fp64=False, n_op=6000)
     tabs = _scaled_pair_tables(3e6)
+    sim, r = _replay(d, 12, start=9, tabs=tabs, budget=LOOSE)
+    _check_replay(r)
+    assert sim.diagnostics(0)["events"][[13, 14, 19]].sum() > 0
+
+
+def test_fp64_pair_pass_fast_projectiles_react_as_the_oracle():
+    # one electron far faster than the rest in each of 64 cells (far above
+    # any energy cap of the discharge): the thinning bound of the pass comes
+    # from the species' largest speeds, so the fast projectiles react with
+    # Eq. 1's probability on both sides, with identical events
+    L, N = 0.064, 64
+    dx = L / N
+    d = inputs.Discharge(L=L, n_cells=N, p_Pa=20.0, U_rf=0.0, n_op=0, n0_m3=0.0, weight_override=1e6,
+                         n1=1, sort_interval=0, diag_every=0, T0_eV=(0.0, 0.0, 0.0), dt_override=1e-12,
+                         capacity_extra=8192, iedf_emax=100.0)
+    E = inputs.geometric_grid(*inputs.E_GRID_E)
+    tabs = [dict(reaction=13, sub=0, E_eV=E, sigma_m2=np.full_like(E, 1.25e-6), threshold_eV=0.0)]
     sim = _sim(d, tabs)
     orc = oracle.Oracle(d, tabs)
-    orc.step(9)
-    compared = flips = 0
-    worst = 0.0
-    for n in range(9, 21):
-        for s in range(3):
-            st = orc.get(s)
-            sim.set_state(0, s, st["x"], st["vx"], st["vy"], st["vz"], st["alive"])
-        sim.set_step(n)
-        sim.step(1)
-        orc.step(1)
-        for s in range(3):
-            c, f, w = _matched(d, sim.get_state(0, s), orc.get(s), s, TOL32)
-            compared, flips, worst = compared + c, flips + f, max(worst, w)
-    assert worst < TOL32
-    assert flips <= 1e-3 * compared, (flips, compared)
-    assert sim.diagnostics(0)["events"][[13, 14, 19]].sum() > 0
+    rs = np.random.default_rng(7)
+    x = np.concatenate([(c + rs.uniform(0.4, 0.6, 61)) * dx for c in range(N)])
+    dirs = rs.normal(size=(len(x), 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    sp = np.full(len(x), 1e5)
+    sp[30::61] = 2e7
+    v = dirs * sp[:, None]
+    xt = np.repeat((np.arange(N) + 0.5) * dx, 20)
+    zt = np.zeros_like(xt)
+    for side in (sim, orc):
+        if side is sim:
+            side.set_state(0, 0, x, v[:, 0], v[:, 1], v[:, 2])
+            side.set_state(0, 2, xt, zt, zt, zt)
+            side.set_state(0, 1, np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0))
+        else:
+            side.set(0, x, v[:, 0], v[:, 1], v[:, 2])
+            side.set(2, xt, zt, zt, zt)
+            side.set(1, [], [], [], [])
+    sim.step(1)
+    orc.step(1)
+    for s in (0, 2):
+        ex, ev = _cmp_slots(d, sim.get_state(0, s), orc.get(s), s)
+        assert ex < TOL64 and ev < TOL64, (s, ex, ev)
+    g, o = sim.diagnostics(0), orc.counters()
+    assert np.array_equal(g["events"], o["events"])
+    assert o["violations"][2] == 0
+    st = orc.get(0)
+    fast = np.sqrt(st["vx"] ** 2 + st["vy"] ** 2 + st["vz"] ** 2) > 1e7
+    # about half of the fast electrons react (P = 0.5), far more than the
+    # cap-energy bound of the discharge would have let through
+    assert 16 <= int((~st["alive"][fast]).sum()) <= 48
 
 
 # ------------------------------------------------ Coulomb collisions (1)-(3)
@@ -305,7 +283,7 @@ def test_fp64_coulomb_ragged_cells_with_pair_pass():
         # frequent particle-target events, except in the large cells (whose
         # per-cell birth buffers they would overflow)
         tabs = _scaled_pair_tables(3e6 if n_cells > 3 else 1.0)
-        sim, orc, (ex, ev) = _run_pair(d, [1, 2, 5, 6, 12, 18], tabs)
+        sim, orc, (ex, ev) = _run_pair(d, [1, 2, 5, 6, 12, 18], tabs, budget=LOOSE)
         assert ex < TOL64 and ev < TOL64, (n_cells, n_op, ex, ev)
         assert np.array_equal(sim.diagnostics(0)["events"], orc.counters()["events"])
         assert sim.diagnostics(0)["coulomb_particles"] > 0
@@ -324,16 +302,14 @@ def test_fp64_coulomb_inter_species_step_by_step(n_cells, n_op):
 
 def test_fp32_coulomb_inter_species_replay():
     d = inputs.cfg1(fp64=False, n2=1, coulomb_log=1e4, coulomb_inter=True)
-    compared, flips, worst = _replay(d, 20)
-    assert worst < TOL32, worst
-    assert flips <= 1e-4 * compared, (flips, compared)
+    _, r = _replay(d, 20)
+    _check_replay(r, n=sum(d.n_init) * 20)
 
 
 def test_fp32_coulomb_replay():
     d = inputs.cfg1(fp64=False, n2=1, coulomb_log=1e4)
-    compared, flips, worst = _replay(d, 30)
-    assert worst < TOL32, worst
-    assert flips <= 1e-4 * compared, (flips, compared)
+    _, r = _replay(d, 30)
+    _check_replay(r, n=sum(d.n_init) * 30)
 
 
 # ------------------------------------- the sequential gas scheme (R22)
@@ -348,7 +324,7 @@ def _scaled_tables(factors):
 
 def test_fp64_sequential_scheme_step_by_step():
     d = inputs.cfg1(gas_scheme=1)
-    sim, orc, (ex, ev) = _run_pair(d, [1, 9, 10, 11, 20, 30, 60, 100])
+    sim, orc, (ex, ev) = _run_pair(d, [1, 9, 10, 11, 20, 30, 60, 100], budget=LOOSE)
     assert ex < TOL64 and ev < TOL64, (ex, ev)
     g, o = sim.diagnostics(0), orc.counters()
     assert np.array_equal(g["events"], o["events"])
@@ -361,7 +337,7 @@ def test_fp64_sequential_scheme_chains_and_pair_events():
     # scaled up so that (19) meets the re-sorted cells with new particles
     d = inputs.cfg1(n_op=6000, gas_scheme=1, U_rf=300.0)
     tabs = _scaled_tables({15: 1e3, 16: 3e3, 17: 300.0, 13: 3e6, 14: 3e6, 19: 3e6})
-    sim, orc, (ex, ev) = _run_pair(d, [10, 20, 30, 40], tabs)
+    sim, orc, (ex, ev) = _run_pair(d, [10, 20, 30, 40], tabs, budget=LOOSE)
     assert ex < TOL64 and ev < TOL64, (ex, ev)
     g, o = sim.diagnostics(0), orc.counters()
     assert np.array_equal(g["events"], o["events"])
@@ -370,9 +346,8 @@ def test_fp64_sequential_scheme_chains_and_pair_events():
 
 def test_fp32_sequential_scheme_replay():
     d = inputs.cfg1(fp64=False, gas_scheme=1)
-    compared, flips, worst = _replay(d, 30)
-    assert worst < TOL32, worst
-    assert flips <= 1e-4 * compared, (flips, compared)
+    _, r = _replay(d, 30, budget=LOOSE)
+    _check_replay(r)
 
 
 def test_fp64_empty_discharge():
@@ -413,9 +388,8 @@ def test_fp64_ion_subcycling_step_by_step(k):
 
 def test_fp32_ion_subcycling_replay():
     d = inputs.cfg1(fp64=False, ion_subcycle=5)
-    compared, flips, worst = _replay(d, 30)
-    assert worst < TOL32, worst
-    assert flips <= 1e-4 * compared, (flips, compared)
+    _, r = _replay(d, 30)
+    _check_replay(r)
 
 
 def test_fp64_sweep_13p8_batched_matches_oracles():
@@ -439,45 +413,60 @@ def test_fp64_sweep_13p8_batched_matches_oracles():
 
 # ----------------------------------------------------- FP32 replay parity
 
-def _replay(d, steps, start=0, orc=None):
-    tabs = inputs.xs_tables()
-    sim = _sim(d, tabs)
+def _replay(d, steps, start=0, orc=None, tabs=None, budget=None):
+    """FP32 replay: every step starts on both sides from the oracle's state;
+    the states after the step are compared particle by particle
+    (tests/replay.py).  Returns the simulation and the summed result."""
+    tabs = inputs.xs_tables() if tabs is None else tabs
+    sim = _sim(d, tabs, budget=budget)
     if orc is None:
         orc = oracle.Oracle(d, tabs)
         if start:
             orc.step(start)
-    compared = flips = 0
-    worst = 0.0
+    coul = d.n2 > 0
+    total = StepResult()
     for n in range(start, start + steps):
+        pre_o = [orc.get(s) for s in range(3)]
         for s in range(3):
-            st = orc.get(s)
+            st = pre_o[s]
             sim.set_state(0, s, st["x"], st["vx"], st["vy"], st["vz"], st["alive"])
+        pre_g = [sim.get_state(0, s) for s in range(3)]
         sim.set_step(n)
         sim.step(1)
         orc.step(1)
+        coul_step = coul and (n + 1) % d.n2 == 0
         for s in range(3):
-            c, f, w = _matched(d, sim.get_state(0, s), orc.get(s), s, TOL32)
-            compared += c
-            flips += f
-            worst = max(worst, w)
-    return compared, flips, worst
+            total = total.add(compare_step(d, s, pre_o[s], pre_g[s], sim.get_state(0, s), orc.get(s),
+                                           TOL32, coulomb=coul_step))
+    return sim, total
+
+
+def _check_replay(r, n=None, flip_budget=1e-4):
+    """the bar of the FP32 path: every particle whose decisions agree within
+    TOL32, flipped decisions at most flip_budget of the compared particles;
+    with Coulomb passes, cells re-paired by a count-changing decision at
+    most 10 + 1e-6 of the particle-steps n, holding under 2% of them"""
+    assert r.compared > 0
+    assert r.worst < TOL32, r
+    assert r.flips <= flip_budget * r.compared, r
+    if n is not None:
+        assert r.recount_cells <= 10 + 1e-6 * n, r
+        assert r.excluded <= 0.02 * n, r
 
 
 def test_fp32_replay_cfg1_100_steps():
     d = inputs.cfg1(fp64=False)
-    compared, flips, worst = _replay(d, 100)
-    assert compared > 3_000_000
-    assert worst < TOL32, worst
-    assert flips <= 1e-4 * compared, (flips, compared)
+    _, r = _replay(d, 100)
+    assert r.compared > 3_000_000
+    _check_replay(r)
 
 
 def test_fp32_replay_ragged_multi_tile_cfg2_geometry():
     # cfg2's gap, grid, pressure and voltage with 3e5 superparticles: many
     # chunks and sort blocks, a ragged tail, steps across a sort and a pair pass
     d = inputs.cfg2(n_op=150_001 * 2 - 1)
-    compared, flips, worst = _replay(d, 4, start=7)
-    assert worst < TOL32
-    assert flips <= 1e-4 * compared, (flips, compared)
+    _, r = _replay(d, 4, start=7)
+    _check_replay(r)
 
 
 # ------------------------------------------------- full-size, one step
@@ -491,37 +480,112 @@ def test_full_size_one_step_replay(name, n2, gas):
     import dataclasses
     d = dataclasses.replace(inputs.WORKLOADS[name](), n2=n2, gas_scheme=gas)
     tabs = inputs.xs_tables()
-    sim = _sim(d, tabs)
+    sim = _sim(d, tabs, budget=LOOSE if gas else None)
     orc = oracle.Oracle(d, tabs, load=False)
+    pre_g = []
     for s in range(3):
         st = sim.get_state(0, s)
         orc.set(s, st["x"], st["vx"], st["vy"], st["vz"], st["alive"])
-        del st
+        pre_g.append(st)
     if gas:
         sim.set_step(d.n1 - 1)
         orc.set_step(d.n1 - 1)
+    pre_o = [orc.get(s) for s in range(3)]
     sim.step(1)
     orc.step(1)
-    compared = flips = cells = 0
-    worst = 0.0
+    total = StepResult()
     for s in range(3):
-        if n2:
-            c, f, nc, w = _matched_by_cell(d, sim.get_state(0, s), orc.get(s), s, TOL32)
-            cells += nc
-        else:
-            c, f, w = _matched(d, sim.get_state(0, s), orc.get(s), s, TOL32)
-        compared, flips, worst = compared + c, flips + f, max(worst, w)
-    # a count-changing FP32 decision re-pairs a whole cell: at most one such
-    # decision in 1e6 particles, and the cells left out hold under 2% of them;
-    # any other flipped particle drags its Coulomb partner along, which
-    # doubles the decision-flip budget
-    assert cells <= 10 + 1e-6 * sum(d.n_init), cells
-    assert compared > (0.98 if n2 else 0.99) * sum(d.n_init), compared
-    assert worst < TOL32
-    assert flips <= (2e-4 if n2 else 1e-4) * compared, (flips, compared)
+        total = total.add(compare_step(d, s, pre_o[s], pre_g[s], sim.get_state(0, s), orc.get(s), TOL32,
+                                       coulomb=n2 > 0))
+    _check_replay(total, n=sum(d.n_init) if n2 else None)
+    assert total.compared > (0.98 if n2 else 0.99) * sum(d.n_init), total
     g, o = sim.diagnostics(0), orc.counters()
     # reaction counts: equal up to flipped decisions
-    assert np.abs(g["events"] - o["events"]).sum() <= max(10, 1e-4 * compared)
+    assert np.abs(g["events"] - o["events"]).sum() <= max(10, 1e-4 * total.compared)
+
+
+def test_fp64_cfg2_full_size_100_steps():
+    # cfg2 at its full size (4e6 superparticles at load) in FP64 for 100 steps
+    # with sorts and particle-target passes: slot by slot within 1e-9, with
+    # identical event and absorption counts
+    d = inputs.cfg2(fp64=True)
+    sim, orc, (ex, ev) = _run_pair(d, [1, 10, 50, 100])
+    assert ex < TOL64 and ev < TOL64, (ex, ev)
+    g, o = sim.diagnostics(0), orc.counters()
+    assert np.array_equal(g["events"], o["events"])
+    assert np.array_equal(g["absorbed"], o["absorbed"])
+    assert g["events"][4] > 0 and g["events"][18] > 0
+
+
+def test_fp32_free_running_divergence_curve():
+    """The FP32 path left to run on its own from the oracle's initial state
+    (no replay): the fraction of particles still on the oracle's trajectory
+    within 1e-5, and the largest potential difference, against the step.
+    A flipped decision re-routes a particle, and through the field and the
+    sorts the others follow; the curve says how fast.  Recorded in the test
+    output (and in O2PIC_CURVE_REPORT when set); the first ten steps must
+    keep 99.9 % of the particles."""
+    import json
+    import os
+    from replay import align, _err
+    d = inputs.cfg1(fp64=False)
+    tabs = inputs.xs_tables()
+    sim = _sim(d, tabs)
+    orc = oracle.Oracle(d, tabs)
+    for s in range(3):
+        st = orc.get(s)
+        sim.set_state(0, s, st["x"], st["vx"], st["vy"], st["vz"], st["alive"])
+    curve = []
+    done = 0
+    dx = d.L / d.n_cells
+    for k in (1, 2, 5, 10, 20, 50, 100, 200, 500, 1000, 2000):
+        sim.step(k - done)
+        orc.step(k - done)
+        done = k
+        on, tot = 0, 0
+        for s in range(3):
+            g, o = sim.get_state(0, s), orc.get(s)
+            gi, oi = np.flatnonzero(g["alive"]), np.flatnonzero(o["alive"])
+            pg, po, _, _ = align(g["x"][gi], o["x"][oi], 1e-5 * d.L)
+            e = _err(d, s, g, gi[pg], o, oi[po])
+            on += int(np.sum(e <= TOL32))
+            tot += len(oi)
+        _, pg_, _ = sim.fields(0)
+        _, po_, _ = orc.fields()
+        dphi = float(np.max(np.abs(pg_ - po_)) / np.max(np.abs(po_)))
+        curve.append({"step": k, "on_trajectory": on / max(tot, 1), "phi_rel_diff": dphi})
+    print("FP32 free-running divergence:", json.dumps(curve))
+    path = os.environ.get("O2PIC_CURVE_REPORT")
+    if path:
+        with open(path, "w") as f:
+            json.dump(curve, f, indent=1)
+    assert all(c["on_trajectory"] >= 0.999 for c in curve if c["step"] <= 10), curve
+
+
+def test_cfg3_batched_full_size_one_step_replay():
+    # the 64-discharge sweep at its full size (3e7 superparticles, one launch
+    # per kernel for all discharges): the GPU's loaded state of every
+    # discharge is handed to its own oracle and all take one step
+    ds = inputs.cfg3_sweep()
+    tabs = inputs.xs_tables()
+    sim = _sim(ds, tabs)
+    total = StepResult()
+    for k, d in enumerate(ds):
+        orc = oracle.Oracle(d, tabs, discharge=k, load=False)
+        for s in range(3):
+            st = sim.get_state(k, s)
+            orc.set(s, st["x"], st["vx"], st["vy"], st["vz"], st["alive"])
+        ds[k] = (d, orc, [sim.get_state(k, s) for s in range(3)])
+    sim.step(1)
+    for k, (d, orc, pre_g) in enumerate(ds):
+        pre_o = [orc.get(s) for s in range(3)]
+        orc.step(1)
+        for s in range(3):
+            total = total.add(compare_step(d, s, pre_o[s], pre_g[s], sim.get_state(k, s), orc.get(s), TOL32))
+        g, o = sim.diagnostics(k), orc.counters()
+        assert np.abs(g["events"] - o["events"]).sum() <= max(10, 1e-4 * sum(d.n_init)), k
+    _check_replay(total)
+    assert total.compared > 0.99 * sum(sum(d.n_init) for d, _, _ in ds), total
 
 
 def test_capacity_overflow_is_reported():

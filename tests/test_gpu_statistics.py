@@ -2,18 +2,18 @@
 
 After the first steps the two paths are different realisations of the same
 stochastic process (FP32 rounding changes single decisions, which then
-diverge), so they are compared as ensembles: the time-averaged densities of
-e, O- and O2+, the potential, the EEDF at L/2 and the O2+ energy distribution
-at the electrodes, each averaged over independent seeds, must agree within
-3 standard errors of the seed-to-seed scatter: with
-z = (m_gpu - m_orc) / sqrt(s_gpu^2/n + s_orc^2/n) for every node and every
-histogram bin holding at least 100 counts on both sides, the mean of z^2 is
-at most 3, at most 10% of the values exceed 3 and none exceeds 6.  Neighbouring
-nodes are strongly correlated, so exceedances come in clusters: two oracle
-ensembles of 12 independent seeds each gave mean z^2 between 1.2 and 2.1, up
-to 4.6% of the values beyond 3 and at most 4.2 (four trials).  The same test
-runs with the paper's sequential gas scheme and with intra- and inter-species
-Coulomb collisions."""
+diverge), so they are compared as seed ensembles: the time-averaged
+densities of e, O- and O2+, the potential, the EEDF at L/2 and the O2+
+energy distribution at the electrodes (20 bins per electrode) of 32
+independent runs on each side.  Every node and every histogram bin holding
+at least 100 counts on both sides gives a normal-equivalent Welch deviate z
+(tests/ensemble.py); the bar is the one of the method's statement, "within
+3 sigma of the seed-to-seed scatter": |z| <= 3 at >= 99 % of them.  Two
+oracle ensembles of 32 seeds each met it in five trials out of five (99.45 %
+to 100 %; 16 seeds: 99.08 % to 99.82 %).  The same test runs with the
+paper's sequential gas scheme and with intra- and inter-species Coulomb
+collisions.  The 32 GPU runs are one batched handle (32 discharges of one
+launch per kernel)."""
 import multiprocessing
 import os
 import sys
@@ -22,16 +22,17 @@ import numpy as np
 import pytest
 
 import oracle
+from ensemble import averages, compare, within_3
 from paper_0705_0495_gb300 import inputs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SEEDS = 12
+SEEDS = 32
 STEPS = 2000  # two RF cycles of the cfg1 discharge
-# cfg1 with twice the superparticles and 2 energy bins per electrode for the
-# O2+ distribution, so that its bins hold more than 100 counts
-KW = dict(n_op=40000, iedf_bins=2)
+# cfg1 with twice the superparticles and 20 energy bins per electrode for the
+# O2+ distribution
+KW = dict(n_op=40000, iedf_bins=20)
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -45,11 +46,13 @@ VARIANTS = {"null_collision": {}, "sequential_gas": {"gas_scheme": 1},
 def _oracle_run(args):
     seed, extra = args
     sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
     import oracle as orc
+    from ensemble import averages as avg
     from paper_0705_0495_gb300 import inputs as inp
     o = orc.Oracle(inp.cfg1(seed=seed, **KW, **extra), inp.xs_tables())
     o.step(STEPS)
-    return _averages(o.diag())
+    return avg(o.diag())
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -58,24 +61,6 @@ def _built():
         pytest.skip("no GPU")
     import __graft_entry__
     __graft_entry__.build()
-
-
-def _averages(g):
-    ns = g["n_samples"]
-    return {"dens": g["dens_sum"] / ns, "phi": g["phi_sum"] / ns,
-            "eedf": g["eedf"].astype(float), "iedf": g["iedf"].astype(float).ravel()}
-
-
-def _z(a, b):
-    a, b = np.asarray(a), np.asarray(b)
-    n = a.shape[0]
-    # values the seeds do not change (the driven electrode's potential) would
-    # have no scatter: the error gets a floor of 1e-6 of the quantity's RMS,
-    # far above FP32/FP64 rounding and far below the statistical scatter
-    floor = 1e-6 * np.sqrt(np.mean(b.mean(axis=0) ** 2))
-    se = np.sqrt(a.var(axis=0, ddof=1) / n + b.var(axis=0, ddof=1) / n + floor ** 2)
-    diff = a.mean(axis=0) - b.mean(axis=0)
-    return diff / np.where(se > 0, se, 1.0)
 
 
 @pytest.mark.parametrize("variant", sorted(VARIANTS))
@@ -87,33 +72,15 @@ def test_fp32_gpu_ensemble_matches_fp64_oracle_ensemble(variant):
     # host cores (a spawned pool: no process is forked from a CUDA process)
     pool = multiprocessing.get_context("spawn").Pool(min(SEEDS, os.cpu_count() or 1))
     pending = pool.map_async(_oracle_run, [(101 + k, extra) for k in range(SEEDS)])
-    tabs = inputs.xs_tables()
-    gpu = []
-    for k in range(SEEDS):
-        sim = o2pic.Simulation([inputs.cfg1(fp64=False, seed=1 + k, **KW, **extra)], tabs)
-        sim.step(STEPS)
-        gpu.append(_averages(sim.diagnostics(0)))
-        sim.close()
+    ds = [inputs.cfg1(fp64=False, seed=1 + k, **KW, **extra) for k in range(SEEDS)]
+    # the sequential scheme's n1 dt lets Eq. 1 exceed 1 for fast electrons
+    sim = o2pic.Simulation(ds, inputs.xs_tables(), numeric_budget=1.0 if extra.get("gas_scheme") else None)
+    sim.step(STEPS)
+    gpu = [averages(sim.diagnostics(k)) for k in range(SEEDS)]
+    sim.close()
     orc = pending.get(timeout=1800)
     pool.close()
     pool.join()
-    zs = compare(gpu, orc)
+    zs, sizes = compare(gpu, orc, min_iedf_bins=3)
     top = np.sort(np.abs(zs))[-5:]
-    assert np.mean(zs ** 2) <= 3.0, (np.mean(zs ** 2), top)
-    assert np.mean(np.abs(zs) > 3.0) <= 0.10, (np.mean(np.abs(zs) > 3.0), top)
-    assert np.all(np.abs(zs) <= 6.0), top
-
-
-def compare(gpu, orc):
-    """z of every node of the densities and potential, and of every EEDF and
-    IEDF bin with at least 100 counts on both sides"""
-    zs = []
-    for key in ("dens", "phi"):
-        zs.append(_z([g[key] for g in gpu], [o[key] for o in orc]).ravel())
-    for key in ("eedf", "iedf"):
-        a = np.array([g[key] for g in gpu])
-        b = np.array([o[key] for o in orc])
-        keep = (a.mean(axis=0) >= 100) & (b.mean(axis=0) >= 100)
-        assert keep.sum() >= 2, key
-        zs.append(_z(a[:, keep], b[:, keep]).ravel())
-    return np.concatenate(zs)
+    assert within_3(zs) >= 0.99, (variant, within_3(zs), sizes, top)
