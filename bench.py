@@ -83,16 +83,18 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic(push_slots_per_launch):
+def _traffic(push_slots_per_launch, shape):
     """DRAM bytes per push launch from a committed ncu capture, scaled by the
-    slots a launch processes; null when the kernel source changed since."""
+    slots a launch processes; null when the kernel source changed since the
+    capture or the launch shape (threads, slots per thread, blocks per SM)
+    differs from the captured one."""
     path = os.path.join(ROOT, "profiles", "k_push_traffic.json")
     src = os.path.join(ROOT, "paper_0705_0495_gb300", "csrc", "o2pic_push.cu")
     try:
         with open(path) as f:
             rec = json.load(f)
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("source_sha256") != sha:
+        if rec.get("source_sha256") != sha or list(rec.get("launch_shape", [])) != list(shape):
             return None
         return rec["dram_bytes_per_slot"] * push_slots_per_launch
     except Exception:
@@ -171,10 +173,10 @@ class OracleSample:
     `target` (same plasma density), loaded once; each call advances `steps`
     time steps and returns (particle-steps, seconds)."""
 
-    def __init__(self, name, target=5_000_000, steps=10):
+    def __init__(self, name, target=5_000_000, steps=10, seed_offset=0):
         import oracle
         oracle.build()
-        d = _workload(name)
+        d = _workload(name, rank=seed_offset)
         total = sum(d.n_init)
         if total > target:
             d = _workload(name, scale=target / total)
@@ -192,27 +194,80 @@ class OracleSample:
         return self.o.particle_steps - p0, dt
 
 
+def _oracle_worker(args):
+    """one host core's share of the parallel CPU baseline: its own sample of
+    the workload (another seed), `steps` time steps; (particle-steps, s)"""
+    name, target, steps, k = args
+    sys.path.insert(0, ROOT)
+    smp = OracleSample(name, target=target, steps=steps, seed_offset=k)
+    return smp.run()
+
+
+def cpu_baseline_all_cores(name, target, steps):
+    """The oracle on every host core at once: one independent sample per core
+    (a spawned pool), the throughput summed over the cores and divided by
+    the slowest core's time.  Returns (value, cores, text)."""
+    import multiprocessing
+    cores = os.cpu_count() or 1
+    with multiprocessing.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(name, target, steps, k) for k in range(cores)])
+    ps = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return ps / dt, cores, (f"{cores} independent samples in parallel, one per host core, each a "
+                            f"{name} discharge with about {target:.3g} superparticles (same plasma "
+                            f"density, its own seed), {steps} time steps")
+
+
+_REF = None
+
+
+def _ref_init(name, target, steps, counter):
+    """a reference-arm worker: its own sample of the workload (its own seed)"""
+    global _REF
+    sys.path.insert(0, ROOT)
+    with counter.get_lock():
+        k = counter.value
+        counter.value += 1
+    _REF = OracleSample(name, target=target, steps=steps, seed_offset=k)
+
+
+def _ref_step(_):
+    return _REF.run()
+
+
 def run_reference(a, rank, world):
+    """The reference arm: the FP64 oracle (the paper publishes no code) on the
+    host cores, one independent bounded sample of the workload per core; a
+    step advances every core's sample by 10 time steps, and the value is the
+    particle-steps of all cores over the wall time."""
     if rank != 0:
         return
+    import multiprocessing
     d = _workload(a.workload, scale=a.scale)
-    smp = OracleSample(a.workload, target=min(5_000_000, sum(d.n_init)))
+    cores = os.cpu_count() or 1
+    target = min(2_000_000, sum(d.n_init))
+    ctx = multiprocessing.get_context("spawn")
+    counter = ctx.Value("i", 0)
     total_ps, total_t = 0, 0.0
-    for k in range(a.warmup + a.steps):
-        ps, dt = smp.run()
-        if k >= a.warmup:
-            total_ps += ps
-            total_t += dt
+    with ctx.Pool(cores, initializer=_ref_init, initargs=(a.workload, target, 10, counter)) as pool:
+        for k in range(a.warmup + a.steps):
+            t0 = time.perf_counter()
+            res = pool.map(_ref_step, range(cores), chunksize=1)
+            dt = time.perf_counter() - t0
+            if k >= a.warmup:
+                total_ps += sum(r[0] for r in res)
+                total_t += dt
     value = total_ps / total_t
+    text = (f"{cores} independent samples in parallel, one per host core, each a {a.workload} discharge "
+            f"with about {target:.3g} superparticles (same plasma density, its own seed), 10 time "
+            f"steps per bench step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total_t / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{a.workload}: {_describe(d)}",
-                   "step": "bounded sample: " + smp.text},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": smp.text},
+        "config": {"workload": f"{a.workload}: {_describe(d)}", "step": "bounded sample: " + text},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -258,11 +313,20 @@ def measure_variant(name, discharges, warm_steps, timed_steps, numeric_budget=No
         sim.timing(reset=True)
         sim.kernel_timing("coulomb", reset=True)
         sim.kernel_timing("sequential_gas", reset=True)
+        r0 = [sim.diagnostics(k) for k in range(len(discharges))]
         sim.step(min(timed_steps, 200))
+        kp = sim.kernel_timing("push")
         tm = sim.timing()
+        r1 = [sim.diagnostics(k) for k in range(len(discharges))]
         peak, _ = _peaks()
         launches = max(1, tm["push_launches"])
-        achieved = tm["push_bytes"] / launches / (tm["push_ms"] / 1e3 / launches) / 1e9 if tm["push_ms"] > 0 else 0.0
+        # the push of steps without diagnostics, against the method's bytes
+        # (24 or 40 B per particle-step, 16 or 32 B per candidate)
+        R = 8.0 if discharges[0].fp64 else 4.0
+        live = sum(r1[k]["particle_steps"] - r0[k]["particle_steps"] for k in range(len(discharges))) / launches
+        cands = sum(r1[k]["candidates"] - r0[k]["candidates"] for k in range(len(discharges))) / launches
+        dur = kp["ms"] / 1e3 / max(1, kp["launches"])
+        achieved = (live * (4.0 + 4.0 * R) + cands * 4.0 * R) / dur / 1e9 if dur > 0 else 0.0
         out = {"workload": name, "value": ps / (ms / 1e3), "unit": UNIT, "time_steps": timed_steps,
                "warmup_time_steps": warm_steps, "ms_per_time_step": ms / timed_steps,
                "push_hbm_frac": achieved / peak}
@@ -313,11 +377,13 @@ def run_ours(a, rank, world, local_rank):
     sim = o2pic.Simulation([d], tabs, numeric_budget=1.0 if d.gas_scheme else None)
     push_tune = None
     if not a.no_autotune:
-        # the push grid: every blocks-per-SM count timed on this simulation
-        # (results do not depend on it)
-        pb, pms = autotune.tune_push_blocks(sim)
-        push_tune = {"chosen": pb, "max": sim.launch("push")[1],
-                     "ms_per_time_step": {str(k): v for k, v in pms.items()}}
+        # the push's launch shape: every (threads per block, slots per thread,
+        # blocks per SM) timed on this simulation (results do not depend on it)
+        best, pms = autotune.tune_push_shape(sim)
+        push_tune = {"threads_per_block": best[0], "slots_per_thread": best[1], "blocks_per_sm": best[2],
+                     "ms_per_time_step": pms}
+    k_shape, b_shape = sim.launch_shape()
+    shape_now = list(sim.launch_shapes()[k_shape][:2]) + [b_shape]
     spc = d.steps_per_cycle
     state_bytes = sum(d.n_init) * (12 + (16 if not d.fp64 else 32))
     flush = state_bytes < 4 * L2_BYTES
@@ -371,21 +437,40 @@ def run_ours(a, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     cycle_ms_timed = e0.elapsed_time(e1)
+    kp = sim.kernel_timing("push")        # the push of steps without diagnostics
+    kd = sim.kernel_timing("push_diag")   # the push that also samples them
     tm = sim.timing()
     r1 = sim.diagnostics(0)
     sim.set_timing(False)
     launches = max(1, tm["push_launches"])
-    dur_s = tm["push_ms"] / 1e3 / launches
-    bytes_per_launch = tm["push_bytes"] / launches
-    achieved = bytes_per_launch / dur_s / 1e9 if dur_s > 0 else 0.0
+    live_per_launch = (r1["particle_steps"] - r0["particle_steps"]) / launches
+    cands_per_launch = (r1["candidates"] - r0["candidates"]) / launches
+    # algorithmic bytes of a push launch as the method needs them: cell,
+    # offset and vx read and written per live particle (24 B in FP32, 40 B in
+    # FP64), vy and vz read and written per null-collision candidate (16 or
+    # 32 B); and the design's own count (every slot, the electrons' vy and vz
+    # read for the energy-binned bound, the candidate list)
+    R = 8.0 if d.fp64 else 4.0
+    alg = live_per_launch * (4.0 + 4.0 * R) + cands_per_launch * 4.0 * R
+    design = tm["push_bytes"] / launches
+    dur_s = kp["ms"] / 1e3 / max(1, kp["launches"])
+    achieved = alg / dur_s / 1e9 if dur_s > 0 else 0.0
     slots_per_launch = (r1["slots_visited"] - r0["slots_visited"]) / launches
-    traffic = _traffic(slots_per_launch)
+    traffic = _traffic(slots_per_launch, shape_now)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": f"{peak_kind} HBM copy bandwidth",
-            "push_launches_timed": tm["push_launches"],
+            "kernel": "k_push (FP32, steps without diagnostics: 9 of 10 push launches)",
+            "us_per_launch": dur_s * 1e6,
+            "bytes_per_particle_step": alg / max(1.0, live_per_launch),
+            "bytes_count": "24 B per particle-step (cell, offset, vx read and written) + 16 B per "
+                           "null-collision candidate (vy, vz read and written)",
+            "design_bytes_per_particle_step": design / max(1.0, live_per_launch),
+            "design_frac": design / dur_s / 1e9 / peak if dur_s > 0 else 0.0,
+            "diag_push_us_per_launch": 1e3 * kd["ms"] / max(1, kd["launches"]),
             "push_share_of_step_time": tm["push_ms"] / cycle_ms_timed if cycle_ms_timed > 0 else None,
-            "bytes_per_particle_step": bytes_per_launch / max(1.0, (r1["particle_steps"] - r0["particle_steps"]) / launches)}
+            "launch_shape": {"threads_per_block": shape_now[0], "slots_per_thread": shape_now[1],
+                             "blocks_per_sm": shape_now[2]}}
 
     e2e = None
     if not a.no_e2e:
@@ -428,12 +513,12 @@ def run_ours(a, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         try:
-            smp = OracleSample(a.workload, target=min(5_000_000, sum(d.n_init)), steps=30)
-            ps, dt = smp.run()
-            cpu = {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": smp.text.replace("per sample", "")}
+            target = min(2_000_000, sum(d.n_init))
+            val, cores, text = cpu_baseline_all_cores(a.workload, target, 30)
+            cpu = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text,
+                   "host_cores": os.cpu_count()}
         except Exception as ex:  # the baseline is reported, not required
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {ex}"}
 
     variants = None
@@ -555,16 +640,34 @@ def run_ours(a, rank, world, local_rank):
                        f"({state_bytes / 1e6:.0f} MB) exceeds the 129 MB L2"
                        if not flush else "L2 flushed between timed iterations"),
                 "parallelism": f"{world} GPU(s), one independent discharge per GPU",
-                "sort_interval_autotune": tune,
-                "push_blocks_per_sm_autotune": push_tune,
+                # the four tuned knobs: sort interval, threads per block, slots
+                # per thread and blocks per SM of the push
+                "autotune": {"sort_interval": d.sort_interval,
+                             "push_threads_per_block": shape_now[0],
+                             "push_slots_per_thread": shape_now[1],
+                             "push_blocks_per_sm": shape_now[2],
+                             "sort_interval_ms_per_time_step": (tune or {}).get("ms_per_time_step"),
+                             "push_shape_ms_per_time_step": (push_tune or {}).get("ms_per_time_step")},
             },
             "roofline": roof,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches_timed,
-            "variants": variants,
+            # one RF cycle is one CUDA graph: graph launches per bench step
+            "cuda_graph": {"time_steps_per_graph": g1["graph_cycle_steps"],
+                           "graph_launches_per_step": (g1["graph_launch_calls"] - g0["graph_launch_calls"]) / a.steps},
         }
+        if variants:
+            # the variants' workloads and accuracy first, their figures last
+            # (FP64 and the batched sweep at the very end of the line)
+            order = ["coulomb", "coulomb_inter", "sweep_13p8", "ion_subcycle", "sequential_gas", "batched", "fp64"]
+            line["variant_workloads"] = {k: {"workload": v.get("workload"), "accuracy": v.get("accuracy")}
+                                         for k, v in variants.items() if "error" not in v}
+            keep = ("value", "ms_per_time_step", "push_hbm_frac", "coulomb_ms_per_launch", "coulomb_hbm_frac",
+                    "sequential_gas_ms_per_launch", "sequential_gas_hbm_frac", "eq1_clamp_fraction", "error")
+            line["variants"] = {k: {f: variants[k][f] for f in keep if f in variants[k]}
+                                for k in order if k in variants}
         print(json.dumps(line), flush=True)
     if sim is not None:
         sim.close()

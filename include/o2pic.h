@@ -210,10 +210,16 @@ pic_status pic_init(const pic_config *cfgs, int n_discharges,
 
 /*
  * Advance every discharge by n_steps time steps (each of length dt_s).
- * Work is queued on the handle's stream (replaying a captured CUDA graph of
- * whole sort/diagnostic periods where possible); the call then synchronises
- * and checks the device status word, returning PIC_ECAPACITY, PIC_ETIMEOUT or
- * PIC_ENUMERIC if the device reported one.
+ * Work is queued on the handle's stream.  When one RF cycle, 1 / (f_rf dt),
+ * is a whole number of time steps and of periods of the step schedule (the
+ * least common multiple of 2, n1, n2, sort_interval and diag_every; taken
+ * from the first discharge) and at most 8192 steps, the first full cycle a
+ * call covers is captured as one CUDA graph and every full cycle from a
+ * period-aligned step is one cudaGraphLaunch; what is left is replayed as
+ * graphs of one period, then step by step.  (Timing mode launches step by
+ * step.)  The call then synchronises and checks the device status word,
+ * returning PIC_ECAPACITY, PIC_ETIMEOUT, PIC_ENUMERIC or PIC_EINVAL if the
+ * device reported one.
  */
 pic_status pic_step(pic_handle *h, long long n_steps);
 
@@ -241,7 +247,9 @@ pic_status pic_step(pic_handle *h, long long n_steps);
  *              36 live slots through the sequential gas scheme (summed over
  *              its two parts and passes), 37 Eq. 1 probabilities evaluated
  *              (particle-target candidates and sequential-scheme tests below
- *              their bound), 38-39 reserved (0)
+ *              their bound), 38 time steps of the captured RF-cycle graph
+ *              (0 when the cycle is not captured), 39 CUDA graph launches
+ *              since pic_init (cycle and period graphs)
  *   n_samples  number of diagnostic samples accumulated
  * reset != 0 clears the sums and histograms after copying.
  */
@@ -306,15 +314,23 @@ pic_status pic_timing(pic_handle *h, double *push_ms, long long *push_launches,
                       long long *launches, double *push_bytes, int reset);
 
 /*
- * The same for one kernel kind (timing mode on): PIC_KERNEL_PUSH gives what
- * pic_timing gives; PIC_KERNEL_COULOMB the Coulomb pass of collisions
+ * The same for one kernel kind (timing mode on): PIC_KERNEL_PUSH the push
+ * launches of steps without diagnostics, PIC_KERNEL_PUSH_DIAG those of
+ * diagnostics steps (pic_timing gives both together; their algorithmic
+ * bytes are shared out by launches, reset clears both);
+ * PIC_KERNEL_COULOMB the Coulomb pass of collisions
  * (1)-(3): device ms, launches and algorithmic bytes (vx, vy, vz read and
  * written for every particle of a cell holding at least two of its species)
  * since its last reset; PIC_KERNEL_SEQUENTIAL_GAS the two parts of the
  * sequential gas scheme (cell, offset, vx, vy, vz read and vx, vy, vz written
  * per live slot and part).  Unknown kinds return PIC_EINVAL.
  */
-typedef enum { PIC_KERNEL_PUSH = 0, PIC_KERNEL_COULOMB = 1, PIC_KERNEL_SEQUENTIAL_GAS = 2 } pic_kernel;
+typedef enum {
+    PIC_KERNEL_PUSH = 0,            /* push launches of steps without diagnostics */
+    PIC_KERNEL_COULOMB = 1,
+    PIC_KERNEL_SEQUENTIAL_GAS = 2,
+    PIC_KERNEL_PUSH_DIAG = 3        /* push launches that also sample the diagnostics */
+} pic_kernel;
 pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, long long *launches,
                              double *bytes, int reset);
 
@@ -322,8 +338,9 @@ pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, long long *l
  * Launch shape of a kernel kind, for autotuning.  Only PIC_KERNEL_PUSH has
  * one: the particle push (steps 3 and 4 above, the charge assignment of
  * step 1 and the null-collision test of step 5) is a persistent grid of
- * blocks_per_sm blocks of 256 threads on every SM, each block taking tickets
- * of tiles until none are left.  pic_init sets the largest count that fits on
+ * blocks_per_sm blocks on every SM (of the current shape's threads, see
+ * pic_launch_shapes below), each block taking tickets of tiles until none
+ * are left.  pic_init sets the largest count that fits on
  * an SM (registers and shared memory); pic_set_launch may lower it to any
  * count in 1 .. that maximum.  Results do not depend on it: the charge sums
  * are exact integers and births are appended in parent order (FP32 mixed
@@ -338,6 +355,29 @@ pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, long long *l
  */
 pic_status pic_get_launch(pic_handle *h, int kernel, int *blocks_per_sm, int *max_blocks_per_sm);
 pic_status pic_set_launch(pic_handle *h, int kernel, int blocks_per_sm);
+
+/*
+ * Launch shapes of the push (the same kernel work as above, for autotuning).
+ * The push is compiled for a few shapes: threads per block and slots per
+ * thread (each warp takes slots_per_thread / 4 consecutive sub-tiles of 128
+ * slots at a time, each lane four consecutive slots of each: one 16-byte
+ * vector per array and one Philox block).  The FP32 mixed path has several,
+ * the FP64 path one.  Results do not depend on the shape (as for the blocks
+ * per SM above).
+ *   pic_launch_shapes     writes up to `capacity` shapes (threads per block,
+ *                         slots per thread, largest blocks per SM; any
+ *                         pointer may be NULL) and returns how many there
+ *                         are; -1 for a NULL handle or another kind
+ *   pic_get_launch_shape  the current shape index and blocks per SM
+ *   pic_set_launch_shape  select a shape index and blocks per SM (1 .. that
+ *                         shape's largest); PIC_EINVAL otherwise, leaving the
+ *                         shape unchanged.  Waits for the stream and drops
+ *                         the captured graph like pic_set_launch.
+ */
+int pic_launch_shapes(pic_handle *h, int kernel, int *threads, int *slots_per_thread,
+                      int *max_blocks_per_sm, int capacity);
+pic_status pic_get_launch_shape(pic_handle *h, int kernel, int *shape, int *blocks_per_sm);
+pic_status pic_set_launch_shape(pic_handle *h, int kernel, int shape, int blocks_per_sm);
 
 /*
  * pic_field_solve_static -- charge deposit, Poisson solve and field of ONE

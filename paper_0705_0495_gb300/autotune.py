@@ -1,4 +1,5 @@
-"""Runtime autotuners of the cell-sort interval and of the push grid.
+"""Runtime autotuners of the cell-sort interval and of the push's launch
+shape (threads per block, slots per thread, blocks per SM).
 
 The sort runs on every particle-target step (every n1 steps) and, in
 addition, every `sort_interval` steps: sorting more often keeps the particles
@@ -11,10 +12,13 @@ follows the same interval.
 
 The push is a persistent grid of blocks taking tickets of tiles; how many
 blocks share an SM (1 up to what its registers and shared memory hold) trades
-latency hiding against contention.  Its results do not depend on the count,
-so the push tuner switches it on one running simulation and times the
-candidates in interleaved rounds (each round gives every candidate the next
-stretch of the discharge, so a drift of the plasma favours none).
+latency hiding against contention, and the shapes it is compiled for trade
+threads per block (the per-block charge grid is shared by more or fewer
+warps) against slots per thread (more independent work per thread, more
+registers).  Its results depend on none of these, so the push tuner switches
+them on one running simulation and times the candidates in interleaved
+rounds (each round gives every candidate the next stretch of the discharge,
+so a drift of the plasma favours none).
 """
 import dataclasses
 
@@ -84,3 +88,38 @@ def tune_push_blocks(sim, steps=200, rounds=2, cands=None):
     best = min(ms, key=ms.get)
     sim.set_launch(best)
     return best, ms
+
+
+def shape_candidates(shapes):
+    """(shape index, blocks per SM) pairs worth timing: every count that fits
+    for every compiled shape; shapes as given by Simulation.launch_shapes()"""
+    return [(k, b) for k, (_, _, mx) in enumerate(shapes) for b in push_candidates(mx)]
+
+
+def tune_push_shape(sim, steps=200, rounds=2):
+    """Time every (shape, blocks per SM) of the push on the running simulation
+    `sim` as tune_push_blocks does; leaves the fastest set and returns
+    ((threads, slots per thread, blocks per SM), {"threads x spt @ blocks":
+    ms per time step})."""
+    import torch
+    shapes = sim.launch_shapes()
+    cands = shape_candidates(shapes)
+    warm = max(2, min(steps, 64))
+    tot = {c: 0.0 for c in cands}
+    for _ in range(rounds):
+        for c in cands:
+            sim.set_launch_shape(*c)
+            sim.step(warm)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(sim.stream)
+            sim.step(steps)
+            e1.record(sim.stream)
+            torch.cuda.synchronize()
+            tot[c] += e0.elapsed_time(e1)
+    ms = {c: v / (rounds * steps) for c, v in tot.items()}
+    best = min(ms, key=ms.get)
+    sim.set_launch_shape(*best)
+    nt, spt, _ = shapes[best[0]]
+    return (nt, spt, best[1]), {f"{shapes[k][0]}x{shapes[k][1]}@{b}": v for (k, b), v in ms.items()}

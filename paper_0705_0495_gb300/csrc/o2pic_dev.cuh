@@ -9,12 +9,10 @@ namespace o2 {
 
 constexpr int NSP = 3;                 // 0 e, 1 O-, 2 O2+
 constexpr int CHUNK = 1024;            // slots per push chunk
-constexpr int PUSH_THREADS = 256;      // 4 consecutive slots per thread
 constexpr int SUBTILE = 128;           // slots of one warp in a tile (32 lanes x 4)
 constexpr int SUBTILES = 1024 / SUBTILE;
 constexpr int BIRTH_CAP_W = 32;        // births staged per sub-tile (null-collision scheme)
 constexpr int BIRTH_CAP_SEQ = 128;     // the same with the sequential gas scheme (n1 steps of collisions at once)
-constexpr int QCAP = 160;              // candidate queue of one warp (< 32 left + one sub-tile)
 constexpr int COLLIDE_THREADS = 256;   // threads per block of the collision kernel
 #ifndef O2_TILES_PER_TICKET
 #define O2_TILES_PER_TICKET 8

@@ -402,15 +402,23 @@ struct pic_handle {
     // largest accepted fraction of nu_max violations among null-collision
     // candidates and of Eq. 1 P > 1 clamps among Eq. 1 evaluations
     double numeric_budget = 1e-6;
-    // graph of one period
-    cudaGraphExec_t gexec = nullptr;
+    // captured graphs: one RF cycle (the whole cycle's kernels; cycle_steps
+    // time steps, a multiple of the schedule's period) and one period of the
+    // step schedule (for what is left of a call)
+    cudaGraphExec_t gexec = nullptr;        // one period
+    cudaGraphExec_t gexec_cycle = nullptr;  // one RF cycle
     long long period = 0;
-    long long graph_launches = 0;
+    long long cycle_steps = 0;              // 0: the cycle is not captured
+    long long graph_launches = 0;           // kernels in the period graph
+    long long cycle_graph_launches = 0;     // kernels in the cycle graph
+    long long graph_calls = 0;              // cudaGraphLaunch calls since pic_init
     bool graph_failed = false;
     // timing
     bool timing = false;
-    double kms[3] = {0.0, 0.0, 0.0};   // device ms per timed kernel kind (push, Coulomb, sequential gas)
-    long long kl[3] = {0, 0, 0};       // timed launches per kind
+    // device ms and timed launches per kernel kind (push, Coulomb, sequential
+    // gas, push with diagnostics)
+    double kms[4] = {0.0, 0.0, 0.0, 0.0};
+    long long kl[4] = {0, 0, 0, 0};
     long long launches = 0;
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kind;          // kind of each event pair
@@ -970,7 +978,7 @@ static cudaError_t enqueue_step(pic_handle *h, long long n, int &nk, bool timed)
     e = launch_push(h->fp64, diag, h->W, h->pools(), par, h->L, st);
     if (e) return e;
     ++nk;
-    if ((e = time_close(h, timed, st, 0))) return e;
+    if ((e = time_close(h, timed, st, diag ? PIC_KERNEL_PUSH_DIAG : PIC_KERNEL_PUSH))) return e;
     e = launch_collide(h->fp64, h->W, h->pools(), par, h->L.collide_blocks, st);
     if (e) return e;
     ++nk;
@@ -1064,6 +1072,37 @@ static pic_status check_status(pic_handle *h)
     return PIC_OK;
 }
 
+// Capture `nsteps` time steps from the current step as one CUDA graph (on a
+// private stream, thread-local capture); false if capture or instantiation
+// failed.
+static bool capture_steps(pic_handle *h, long long nsteps, cudaGraphExec_t *out, long long *kernels)
+{
+    cudaGraph_t g = nullptr;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int nk = 0;
+    cudaStream_t keep = h->stream;
+    h->stream = cs;
+    for (long long k = 0; ok && k < nsteps; ++k) ok = enqueue_step(h, h->step + k, nk, false) == cudaSuccess;
+    h->stream = keep;
+    cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    ok = ok && ee == cudaSuccess && g;
+    if (ok) ok = cudaGraphInstantiate(out, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    if (!ok) *out = nullptr;
+    *kernels = nk;
+    return ok;
+}
+
+// the longest stretch captured as one graph
+constexpr long long MAX_GRAPH_STEPS = 8192;
+
 extern "C" pic_status pic_step(pic_handle *h, long long n_steps)
 {
     if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
@@ -1076,36 +1115,43 @@ extern "C" pic_status pic_step(pic_handle *h, long long n_steps)
         if (q.sort_interval > 0) P = lcm_ll(P, q.sort_interval);
         if (q.diag_every > 0) P = lcm_ll(P, q.diag_every);
         h->period = P;
+        // one RF cycle as the graph unit when it is a whole number of time
+        // steps and of schedule periods (the drive phase is read on the
+        // device from the step counter, so any period-aligned start replays
+        // the same work)
+        const double spc = 1.0 / (q.f_rf_Hz * q.dt_s);
+        const long long c = std::llround(spc);
+        h->cycle_steps = 0;
+        if (c >= P && std::fabs(spc - (double)c) <= 1e-6 * spc && c % P == 0 && c <= MAX_GRAPH_STEPS)
+            h->cycle_steps = c;
     }
     long long left = n_steps;
     while (left > 0) {
         const bool aligned = (h->step % h->period) == 0;
-        if (!h->timing && !h->graph_failed && aligned && left >= h->period && h->period <= 4096) {
-            if (!h->gexec) {
-                cudaGraph_t g = nullptr;
-                cudaStream_t cs = nullptr;
-                CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-                bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-                int nk = 0;
-                cudaStream_t keep = h->stream;
-                h->stream = cs;
-                for (long long k = 0; ok && k < h->period; ++k)
-                    ok = enqueue_step(h, h->step + k, nk, false) == cudaSuccess;
-                h->stream = keep;
-                cudaError_t ee = cudaStreamEndCapture(cs, &g);
-                ok = ok && ee == cudaSuccess && g;
-                if (ok) ok = cudaGraphInstantiate(&h->gexec, g, 0) == cudaSuccess;
-                if (g) cudaGraphDestroy(g);
-                cudaStreamDestroy(cs);
-                cudaGetLastError();
-                if (!ok) {
-                    h->gexec = nullptr;
+        const bool graphs = !h->timing && !h->graph_failed && aligned;
+        if (graphs && h->cycle_steps > 0 && left >= h->cycle_steps) {
+            if (!h->gexec_cycle) {
+                if (!capture_steps(h, h->cycle_steps, &h->gexec_cycle, &h->cycle_graph_launches)) {
                     h->graph_failed = true;
                     continue;
                 }
-                h->graph_launches = nk;
+            }
+            CK(cudaGraphLaunch(h->gexec_cycle, h->stream));
+            ++h->graph_calls;
+            h->launches += h->cycle_graph_launches;
+            h->step += h->cycle_steps;
+            left -= h->cycle_steps;
+            continue;
+        }
+        if (graphs && left >= h->period && h->period <= MAX_GRAPH_STEPS) {
+            if (!h->gexec) {
+                if (!capture_steps(h, h->period, &h->gexec, &h->graph_launches)) {
+                    h->graph_failed = true;
+                    continue;
+                }
             }
             CK(cudaGraphLaunch(h->gexec, h->stream));
+            ++h->graph_calls;
             h->launches += h->graph_launches;
             h->step += h->period;
             left -= h->period;
@@ -1222,7 +1268,8 @@ extern "C" pic_status pic_diagnostics(pic_handle *h, int d, double *dens_sum, do
         counters[35] = (long long)c[C_COUL];
         counters[36] = (long long)c[C_DSMC];
         counters[37] = (long long)c[C_PEVAL];
-        for (int k = 38; k < 40; ++k) counters[k] = 0;
+        counters[38] = h->cycle_steps;
+        counters[39] = h->graph_calls;
     }
     if (n_samples) *n_samples = (long long)ns;
     if (reset) {
@@ -1403,13 +1450,13 @@ extern "C" pic_status pic_timing(pic_handle *h, double *push_ms, long long *push
     const double R = h->fp64 ? 8.0 : 4.0;
     const double bytes = (double)(slots - h->slots0) * 2.0 * (4.0 + 2.0 * R) +
                          (double)(bslots - h->bslots0) * 2.0 * R + (double)(cands - h->cands0) * 8.0;
-    if (push_ms) *push_ms = h->kms[0];
-    if (push_launches) *push_launches = h->kl[0];
+    if (push_ms) *push_ms = h->kms[PIC_KERNEL_PUSH] + h->kms[PIC_KERNEL_PUSH_DIAG];
+    if (push_launches) *push_launches = h->kl[PIC_KERNEL_PUSH] + h->kl[PIC_KERNEL_PUSH_DIAG];
     if (launches) *launches = h->launches;
     if (push_bytes) *push_bytes = bytes;
     if (reset) {
-        h->kms[0] = 0.0;
-        h->kl[0] = 0;
+        h->kms[PIC_KERNEL_PUSH] = h->kms[PIC_KERNEL_PUSH_DIAG] = 0.0;
+        h->kl[PIC_KERNEL_PUSH] = h->kl[PIC_KERNEL_PUSH_DIAG] = 0;
         h->launches = 0;
         h->slots0 = slots;
         h->cands0 = cands;
@@ -1441,6 +1488,68 @@ extern "C" pic_status pic_set_launch(pic_handle *h, int kernel, int blocks_per_s
         CK(cudaGraphExecDestroy(h->gexec));
         h->gexec = nullptr;
     }
+    if (h->gexec_cycle) {
+        CK(cudaGraphExecDestroy(h->gexec_cycle));
+        h->gexec_cycle = nullptr;
+    }
+    h->L.push_per_sm = blocks_per_sm;
+    h->L.push_blocks = h->L.num_sms * blocks_per_sm;
+    return PIC_OK;
+}
+
+extern "C" int pic_launch_shapes(pic_handle *h, int kernel, int *threads, int *slots_per_thread,
+                                 int *max_blocks_per_sm, int capacity)
+{
+    if (!h) {
+        fail(nullptr, PIC_EINVAL, "NULL handle");
+        return -1;
+    }
+    if (kernel != PIC_KERNEL_PUSH) {
+        fail(h, PIC_EINVAL, "only the push has a launch shape");
+        return -1;
+    }
+    const int n = h->L.push_nshapes;
+    for (int k = 0; k < n && k < capacity; ++k) {
+        if (threads) threads[k] = h->L.shape_threads[k];
+        if (slots_per_thread) slots_per_thread[k] = h->L.shape_spt[k];
+        if (max_blocks_per_sm) max_blocks_per_sm[k] = h->L.shape_max_per_sm[k];
+    }
+    return n;
+}
+
+extern "C" pic_status pic_get_launch_shape(pic_handle *h, int kernel, int *shape, int *blocks_per_sm)
+{
+    if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
+    if (kernel != PIC_KERNEL_PUSH) return fail(h, PIC_EINVAL, "only the push has a launch shape");
+    if (shape) *shape = h->L.push_shape;
+    if (blocks_per_sm) *blocks_per_sm = h->L.push_per_sm;
+    return PIC_OK;
+}
+
+extern "C" pic_status pic_set_launch_shape(pic_handle *h, int kernel, int shape, int blocks_per_sm)
+{
+    if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
+    if (kernel != PIC_KERNEL_PUSH) return fail(h, PIC_EINVAL, "only the push has a launch shape");
+    if (shape < 0 || shape >= h->L.push_nshapes)
+        return fail(h, PIC_EINVAL, "shape out of 0 .. " + std::to_string(h->L.push_nshapes - 1));
+    const int mx = h->L.shape_max_per_sm[shape];
+    if (blocks_per_sm < 1 || blocks_per_sm > mx)
+        return fail(h, PIC_EINVAL, "blocks per SM out of 1 .. " + std::to_string(mx));
+    if (shape == h->L.push_shape && blocks_per_sm == h->L.push_per_sm) return PIC_OK;
+    // the captured graph holds the old grid: wait for it, then drop it
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->gexec) {
+        CK(cudaGraphExecDestroy(h->gexec));
+        h->gexec = nullptr;
+    }
+    if (h->gexec_cycle) {
+        CK(cudaGraphExecDestroy(h->gexec_cycle));
+        h->gexec_cycle = nullptr;
+    }
+    h->L.push_shape = shape;
+    h->L.push_max_per_sm = mx;
+    h->L.push_smem = h->L.shape_smem[shape];
+    h->L.push_smem_diag = h->L.shape_smem_diag[shape];
     h->L.push_per_sm = blocks_per_sm;
     h->L.push_blocks = h->L.num_sms * blocks_per_sm;
     return PIC_OK;
@@ -1450,9 +1559,24 @@ extern "C" pic_status pic_kernel_timing(pic_handle *h, int kernel, double *ms, l
                                         double *bytes, int reset)
 {
     if (!h) return fail(nullptr, PIC_EINVAL, "NULL handle");
-    if (kernel == PIC_KERNEL_PUSH) {
-        long long all = 0;
-        return pic_timing(h, ms, launches, &all, bytes, reset);
+    if (kernel == PIC_KERNEL_PUSH || kernel == PIC_KERNEL_PUSH_DIAG) {
+        // the push launches of one kind; the algorithmic bytes are shared out
+        // by launches (every launch of a step moves the same particle data)
+        const double kms = h->kms[kernel];
+        const long long kl = h->kl[kernel];
+        long long all = 0, pl = 0;
+        double pms = 0.0, pbytes = 0.0;
+        const pic_status st = pic_timing(h, &pms, &pl, &all, &pbytes, 0);
+        if (st != PIC_OK) return st;
+        if (ms) *ms = kms;
+        if (launches) *launches = kl;
+        if (bytes) *bytes = pl > 0 ? pbytes * (double)kl / (double)pl : 0.0;
+        if (reset) {
+            long long a2 = 0, l2 = 0;
+            double m2 = 0.0, b2 = 0.0;
+            return pic_timing(h, &m2, &l2, &a2, &b2, 1);
+        }
+        return PIC_OK;
     }
     if (kernel != PIC_KERNEL_COULOMB && kernel != PIC_KERNEL_SEQUENTIAL_GAS)
         return fail(h, PIC_EINVAL, "unknown kernel kind");
@@ -1484,6 +1608,7 @@ extern "C" void pic_destroy(pic_handle *h)
 {
     if (!h) return;
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->gexec_cycle) cudaGraphExecDestroy(h->gexec_cycle);
     for (auto &e : h->ev) cudaEventDestroy(e);
     delete h;
 }

@@ -28,10 +28,16 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+constexpr int MAX_PUSH_SHAPES = 8;
+
 struct LaunchCfg {
     int push_blocks;      // persistent grid of the push
     int push_per_sm;      // its blocks per SM
-    int push_max_per_sm;  // the most that fit on an SM
+    int push_max_per_sm;  // the most that fit on an SM (current shape)
+    int push_shape;       // index of the push's launch shape
+    int push_nshapes;     // shapes compiled for this precision
+    int shape_threads[MAX_PUSH_SHAPES], shape_spt[MAX_PUSH_SHAPES], shape_max_per_sm[MAX_PUSH_SHAPES];
+    size_t shape_smem[MAX_PUSH_SHAPES], shape_smem_diag[MAX_PUSH_SHAPES];
     int num_sms;
     int collide_blocks;   // grid of the collision kernel (loops over the candidates)
     size_t push_smem;     // dynamic shared memory of the push (non-diag)

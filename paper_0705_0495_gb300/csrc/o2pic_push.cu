@@ -36,12 +36,6 @@ namespace o2 {
 #define O2_PUSH_L2_AHEAD 2
 #endif
 
-#ifndef O2_PUSH_BLOCKS_F32
-#define O2_PUSH_BLOCKS_F32 3
-#endif
-template <typename Real> struct PushOcc {
-    static constexpr int blocks = sizeof(Real) == 4 ? O2_PUSH_BLOCKS_F32 : 2;
-};
 
 template <typename Real> struct AccT;
 template <> struct AccT<float> { using T = unsigned long long; };
@@ -108,6 +102,11 @@ __device__ __forceinline__ void st4(double *p, const double v[4])
     reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
+
+// the largest value below 1 (an offset that rounded up to 1 is held there)
+template <typename Real> __device__ __forceinline__ Real below_one();
+template <> __device__ __forceinline__ float below_one<float>() { return 0x1.fffffep-1f; }
+template <> __device__ __forceinline__ double below_one<double>() { return 0x1.fffffffffffffp-1; }
 
 // Interpolation of the gas-channel cross sections of one projectile at the
 // centre-of-mass energy E [eV]: piecewise linear in E on the shared geometric
@@ -232,14 +231,14 @@ __device__ __forceinline__ void stage_birth(const BirthSink<Real> &B, int tag, i
 
 // Energy bin of an electron's lab energy K [eV] for the collision-frequency
 // bound: with K = m 2^e, m in [1, 2), bin 4 (e + 6) + floor(4 (m - 1)) (the
-// exponent and the top two mantissa bits), clamped to [0, nb - 1]; K <= 0
-// or NaN gives bin 0.
+// exponent and the top two mantissa bits), clamped to [0, nb - 1].  K is a
+// sum of squares times a positive factor: for K >= 0 the exponent and the
+// top two mantissa bits are the bits above the lower 21 (FP32), and +0 falls
+// below bin 0.  (FP64: K <= 0 or NaN gives bin 0.)
 __device__ __forceinline__ int energy_bin(float K, int nb)
 {
-    if (!(K > 0.f)) return 0;
-    const unsigned u = __float_as_uint(K);
-    const int b = 4 * ((int)((u >> 23) & 0xFFu) - 127 - NUBIN_LOG2_E0) + (int)((u >> 21) & 3u);
-    return b < 0 ? 0 : (b > nb - 1 ? nb - 1 : b);
+    const int b = (int)(__float_as_uint(K) >> 21) - 4 * (127 + NUBIN_LOG2_E0);
+    return min(max(b, 0), nb - 1);
 }
 __device__ __forceinline__ int energy_bin(double K, int nb)
 {
@@ -485,13 +484,24 @@ template <> __device__ __forceinline__ double *acc_global<double>(const WsPtrs &
 // are summed over the warp and one lane adds them; otherwise every lane adds
 // its own (its four weights summed first when they share a cell, and
 // 4 * 32 * 2^FIX_BITS < 2^32).  No lane-matching: it runs on a narrow pipe.
-__device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep[4], const float off[4])
+__device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep[4], const float off[4],
+                                         bool spread)
 {
     unsigned w0[4], w1[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         w1[k] = dep[k] >= 0 ? __float2uint_rn(off[k] * (float)(1 << FIX_BITS)) : 0u;
         w0[k] = dep[k] >= 0 ? (1u << FIX_BITS) - w1[k] : 0u;
+    }
+    if (spread) {
+        // a species whose slots rarely share a cell (electrons): every slot adds its own
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (dep[k] < 0) continue;
+            split_add(&sAcc[dep[k]], w0[k]);
+            split_add(&sAcc[dep[k] + 1], w1[k]);
+        }
+        return;
     }
     const int lane = threadIdx.x & 31;
     const bool same = dep[0] >= 0 && dep[1] == dep[0] && dep[2] == dep[0] && dep[3] == dep[0];
@@ -520,7 +530,8 @@ __device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep
         split_add(&sAcc[ck + 1], w1[k]);
     }
 }
-__device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep[4], const double off[4])
+__device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep[4], const double off[4],
+                                         bool /*spread*/)
 {
     constexpr double SC = (double)(1ull << FIX_BITS_64);
     unsigned long long w0[4], w1[4];
@@ -568,13 +579,30 @@ __device__ __forceinline__ bool Dd_binned(const WsPtrs &W, int ds)
     return W.disc[ds / NSP].sp[ds % NSP].nbins > 0;
 }
 
-template <typename Real, bool DIAG>
-__global__ void __launch_bounds__(PUSH_THREADS, PushOcc<Real>::blocks)
+// Launch shape of the push: NT threads per block, SPT slots per thread.  A
+// warp takes SPT/4 consecutive sub-tiles of 128 slots per pass and lane l the
+// four consecutive slots 4l .. 4l+3 of each (16-byte vectors, one Philox
+// block); a block's pass covers NT SPT / 128 sub-tiles.  MINB is the blocks
+// per SM the register allocation is sized for.
+template <int NT, int SPT, int MINB>
+struct PushShape {
+    static constexpr int threads = NT;
+    static constexpr int spt = SPT;
+    static constexpr int minb = MINB;
+    static constexpr int nw = NT / 32;
+    static constexpr int groups = SPT / 4;                 // sub-tiles per warp and pass
+    static constexpr int qcap = 32 + 32 * SPT;             // candidate queue: < 32 left + one pass
+    static_assert(SPT % 4 == 0 && NT % 32 == 0, "shape");
+    static_assert((TILES_PER_TICKET * SUBTILES) % (nw * groups) == 0, "a ticket holds whole passes");
+};
+
+template <typename Real, bool DIAG, typename SH>
+__global__ void __launch_bounds__(SH::threads, SH::minb)
 k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
 {
     pdl_wait();
     using Acc = typename AccT<Real>::T;
-    constexpr int NW = PUSH_THREADS / 32;
+    constexpr int PUSH_THREADS = SH::threads, NW = SH::nw, G = SH::groups, QCAP = SH::qcap;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *sAcc = reinterpret_cast<unsigned long long *>(smem);  // integer sums (both paths)
     Real *sE = reinterpret_cast<Real *>(sAcc + (Nmax + 2));
@@ -708,28 +736,35 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         const int nbins = S.nbins;
         const bool binned = nbins > 0;  // electrons: bound per lab-energy bin
         const Real ke = pick<Real>(S.ke_eV, S.ke_eV_f);
-        const int wbase0 = pb + (tbeg - C.chunk0) * CHUNK + w * SUBTILE;  // warp's first sub-tile
-        for (int t = tbeg; t < tend; ++t) {
-            const int sbase = wbase0 + (t - tbeg) * CHUNK;
-            const int i0 = sbase + 4 * lane;
-            const int sub = t * SUBTILES + w;
-            if (lane == 0) W.tile_cnt[(size_t)sub * NSP] = 0;  // births recorded by the collision kernel
+        // the ticket's sub-tiles in rows of NW G: warp w takes sub-tiles
+        // w G .. w G + G - 1 of every row
+        constexpr int ROW = NW * G;
+        const int st_beg = tbeg * SUBTILES, st_end = tend * SUBTILES;
+        // the warp's first slot in the ticket
+        const int wbase0 = pb + (tbeg - C.chunk0) * CHUNK + w * G * SUBTILE;
+        unsigned tslots = 0, tlive = 0;  // the ticket's slot counts of this thread
+        for (int r0 = st_beg; r0 < st_end; r0 += ROW) {
             if (O2_PUSH_L2_AHEAD > 0 && tid == 0) {
-                // the tile O2_PUSH_L2_AHEAD ahead in this ticket: its cell,
-                // offset and vx (and vy, vz for a binned species) into L2
-                const int ta = (t == tbeg) ? tbeg + 1 : t + O2_PUSH_L2_AHEAD;
-                const int tb = (t == tbeg) ? min(tbeg + O2_PUSH_L2_AHEAD, tend - 1) : ta;
-                for (int tp = ta; tp <= tb && tp < tend; ++tp) {
-                    const size_t sl = (size_t)pb + (size_t)(tp - C.chunk0) * CHUNK;
-                    l2_prefetch(cellA + sl, CHUNK * sizeof(int));
-                    l2_prefetch(offA + sl, CHUNK * sizeof(Real));
-                    l2_prefetch(vxA + sl, CHUNK * sizeof(Real));
-                    if (binned) {
-                        l2_prefetch(vyA + sl, CHUNK * sizeof(Real));
-                        l2_prefetch(vzA + sl, CHUNK * sizeof(Real));
-                    }
+                // the row O2_PUSH_L2_AHEAD ahead in this ticket (on the first
+                // row also those between): cell, offset and vx into L2
+                const int ra = (r0 == st_beg) ? r0 + ROW : r0 + O2_PUSH_L2_AHEAD * ROW;
+                const int rb = (r0 == st_beg) ? min(r0 + O2_PUSH_L2_AHEAD * ROW, st_end - ROW) : ra;
+                for (int rp = ra; rp <= rb && rp < st_end; rp += ROW) {
+                    const size_t sl = (size_t)pb + (size_t)(rp - C.chunk0 * SUBTILES) * SUBTILE;
+                    const unsigned n = (unsigned)min(ROW, st_end - rp) * SUBTILE;
+                    l2_prefetch(cellA + sl, n * sizeof(int));
+                    l2_prefetch(offA + sl, n * sizeof(Real));
+                    l2_prefetch(vxA + sl, n * sizeof(Real));
                 }
             }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+            const int sub = r0 + w * G + g;
+            // a row of at most one tile fits the ticket's whole tiles; a
+            // longer one can overhang its tail
+            if (ROW > SUBTILES && sub >= st_end) break;
+            const int i0 = wbase0 + (r0 - st_beg) * SUBTILE + g * SUBTILE + 4 * lane;
+            if (lane == 0) W.tile_cnt[(size_t)sub * NSP] = 0;  // births recorded by the collision kernel
 
             // ---- phase A: push, absorb, null test, deposit, candidate queue
             int c[4];
@@ -771,6 +806,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             unsigned nslots = 0, nlive = 0, outm = 0, wallm = 0;
             bool cchg = false;  // a cell index of the lane's slots changed
             bool nonfin = false;
+            unsigned candm = 0u, bins = 0u;
             int dep[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -809,13 +845,22 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                     thr = s_btn[bin];
                 }
                 const bool cand = live && wk[k] < thr;
-                const unsigned m = __ballot_sync(0xffffffffu, cand);
-                if (cand) {
-                    const int pos = qn + __popc(m & lt_mask);
-                    qIdx[pos] = i0 + k;
-                    qBin[pos] = (unsigned char)bin;
+                candm |= cand ? 1u << k : 0u;
+                bins |= (unsigned)bin << (8 * k);
+            }
+            // candidates are rare: one vote, and the queue only when a lane has one
+            if (__any_sync(0xffffffffu, candm != 0u)) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const bool cand = (candm >> k) & 1u;
+                    const unsigned m = __ballot_sync(0xffffffffu, cand);
+                    if (cand) {
+                        const int pos = qn + __popc(m & lt_mask);
+                        qIdx[pos] = i0 + k;
+                        qBin[pos] = (unsigned char)(bins >> (8 * k));
+                    }
+                    qn += __popc(m);
                 }
-                qn += __popc(m);
             }
             if (nonfin) set_status(ctl, ST_NONFINITE);
             if (outm) {
@@ -866,16 +911,9 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                     }
                 }
             }
-            deposit4(sAcc, dep, off);
-            {
-                const unsigned ws = __reduce_add_sync(0xffffffffu, nslots);
-                const unsigned wl = __reduce_add_sync(0xffffffffu, nlive);
-                if (lane == 0) {
-                    if (ws) atomicAdd(&s_cnt[C_SLOTS], ws);
-                    if (ws && binned) atomicAdd(&s_cnt[C_BSLOTS], ws);
-                    if (wl) atomicAdd(&s_cnt[C_LIVE], wl);
-                }
-            }
+            deposit4(sAcc, dep, off, false);
+            tslots += nslots;
+            tlive += nlive;
             if (full) {
                 // an unchanged value is not written back: slow ions keep
                 // their cells for many steps, and a lane of dead slots
@@ -895,8 +933,18 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                     }
                 }
             }
+            }
             __syncwarp();
             if (qn >= 32) list_out();
+        }
+        {
+            const unsigned ws = __reduce_add_sync(0xffffffffu, tslots);
+            const unsigned wl = __reduce_add_sync(0xffffffffu, tlive);
+            if (lane == 0) {
+                if (ws) atomicAdd(&s_cnt[C_SLOTS], ws);
+                if (ws && binned) atomicAdd(&s_cnt[C_BSLOTS], ws);
+                if (wl) atomicAdd(&s_cnt[C_LIVE], wl);
+            }
         }
     }
     if (qn > 0) list_out();
@@ -1396,70 +1444,97 @@ k_births(WsPtrs W, Pools<Real> P, int par, int salt)
 }
 
 template <typename Real>
-static size_t push_smem_bytes(int Nmax, int eedf_max, int fm_max)
+static size_t push_smem_bytes(int Nmax, int eedf_max, int fm_max, int nw, int qcap)
 {
-    constexpr int NW = PUSH_THREADS / 32;
     size_t b = sizeof(unsigned long long) * (Nmax + 2) + sizeof(Real) * (Nmax + 2);
-    b += sizeof(int) * NW * QCAP;  // candidate slots
+    b += sizeof(int) * nw * qcap;  // candidate slots
     b += sizeof(unsigned) * (eedf_max + fm_max);
-    b += (size_t)NW * QCAP;        // candidate energy bins
+    b += (size_t)nw * qcap;        // candidate energy bins
     return (b + 15) & ~size_t(15);
+}
+
+// The push's launch shapes (threads per block, slots per thread, blocks per
+// SM the registers are sized for): the FP32 path has several for the
+// autotuner, the FP64 path one.  Results do not depend on the shape (exact
+// integer charge sums, births in parent order).
+using PushF0 = PushShape<256, 4, 3>;
+using PushF1 = PushShape<128, 4, 6>;
+using PushF2 = PushShape<512, 4, 1>;
+using PushF3 = PushShape<128, 8, 4>;
+using PushF4 = PushShape<256, 8, 2>;
+using PushD0 = PushShape<256, 4, 2>;
+
+template <typename Real, typename SH>
+static cudaError_t push_shape_setup(LaunchCfg &L, int k)
+{
+    const size_t sm = push_smem_bytes<Real>(L.maxN, 0, 0, SH::nw, SH::qcap);
+    const size_t smd = push_smem_bytes<Real>(L.maxN, L.eedf_max, L.fm_max, SH::nw, SH::qcap);
+    cudaError_t e = cudaFuncSetAttribute(k_push<Real, false, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_push<Real, true, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<Real, false, SH>, SH::threads, sm);
+    if (e != cudaSuccess) return e;
+    L.shape_threads[k] = SH::threads;
+    L.shape_spt[k] = SH::spt;
+    L.shape_max_per_sm[k] = per_sm < 1 ? 1 : per_sm;
+    L.shape_smem[k] = sm;
+    L.shape_smem_diag[k] = smd;
+    return cudaSuccess;
 }
 
 cudaError_t push_configure(bool fp64, LaunchCfg &L, int num_sms)
 {
     cudaError_t e;
-    int per_sm = 1;
     if (fp64) {
-        L.push_smem = push_smem_bytes<double>(L.maxN, 0, 0);
-        L.push_smem_diag = push_smem_bytes<double>(L.maxN, L.eedf_max, L.fm_max);
-        e = cudaFuncSetAttribute(k_push<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.push_smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_push<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.push_smem_diag);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<double, false>, PUSH_THREADS,
-                                                          L.push_smem);
+        L.push_nshapes = 1;
+        if ((e = push_shape_setup<double, PushD0>(L, 0))) return e;
     } else {
-        L.push_smem = push_smem_bytes<float>(L.maxN, 0, 0);
-        L.push_smem_diag = push_smem_bytes<float>(L.maxN, L.eedf_max, L.fm_max);
-        e = cudaFuncSetAttribute(k_push<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.push_smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_push<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.push_smem_diag);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<float, false>, PUSH_THREADS,
-                                                          L.push_smem);
+        L.push_nshapes = 5;
+        if ((e = push_shape_setup<float, PushF0>(L, 0))) return e;
+        if ((e = push_shape_setup<float, PushF1>(L, 1))) return e;
+        if ((e = push_shape_setup<float, PushF2>(L, 2))) return e;
+        if ((e = push_shape_setup<float, PushF3>(L, 3))) return e;
+        if ((e = push_shape_setup<float, PushF4>(L, 4))) return e;
     }
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     L.num_sms = num_sms;
-    L.push_max_per_sm = per_sm;
-    L.push_per_sm = per_sm;
-    L.push_blocks = num_sms * per_sm;
+    L.push_shape = 0;
+    L.push_max_per_sm = L.shape_max_per_sm[0];
+    L.push_per_sm = L.push_max_per_sm;
+    L.push_blocks = num_sms * L.push_per_sm;
+    L.push_smem = L.shape_smem[0];
+    L.push_smem_diag = L.shape_smem_diag[0];
     L.collide_blocks = num_sms * 8;
     return cudaSuccess;
+}
+
+template <typename Real, typename SH>
+static void launch_push_shape(bool diag, const WsPtrs &W, const Pools<Real> &P, int par, const LaunchCfg &L,
+                              cudaStream_t st)
+{
+    const int em = diag ? L.eedf_max : 0, fm = diag ? L.fm_max : 0;
+    const size_t sm = diag ? L.push_smem_diag : L.push_smem;
+    if (diag)
+        launch_k(k_push<Real, true, SH>, L.push_blocks, SH::threads, sm, st, W, P, par, L.maxN, em, fm);
+    else
+        launch_k(k_push<Real, false, SH>, L.push_blocks, SH::threads, sm, st, W, P, par, L.maxN, em, fm);
 }
 
 cudaError_t launch_push(bool fp64, bool diag, const WsPtrs &W, const void *pools, int par,
                         const LaunchCfg &L, cudaStream_t st)
 {
-    const int em = diag ? L.eedf_max : 0, fm = diag ? L.fm_max : 0;
-    const size_t sm = diag ? L.push_smem_diag : L.push_smem;
     if (fp64) {
-        const Pools<double> &P = *static_cast<const Pools<double> *>(pools);
-        if (diag)
-            launch_k(k_push<double, true>, L.push_blocks, PUSH_THREADS, sm, st, W, P, par, L.maxN, em, fm);
-        else
-            launch_k(k_push<double, false>, L.push_blocks, PUSH_THREADS, sm, st, W, P, par, L.maxN, em, fm);
+        launch_push_shape<double, PushD0>(diag, W, *static_cast<const Pools<double> *>(pools), par, L, st);
     } else {
         const Pools<float> &P = *static_cast<const Pools<float> *>(pools);
-        if (diag)
-            launch_k(k_push<float, true>, L.push_blocks, PUSH_THREADS, sm, st, W, P, par, L.maxN, em, fm);
-        else
-            launch_k(k_push<float, false>, L.push_blocks, PUSH_THREADS, sm, st, W, P, par, L.maxN, em, fm);
+        switch (L.push_shape) {
+        case 1: launch_push_shape<float, PushF1>(diag, W, P, par, L, st); break;
+        case 2: launch_push_shape<float, PushF2>(diag, W, P, par, L, st); break;
+        case 3: launch_push_shape<float, PushF3>(diag, W, P, par, L, st); break;
+        case 4: launch_push_shape<float, PushF4>(diag, W, P, par, L, st); break;
+        default: launch_push_shape<float, PushF0>(diag, W, P, par, L, st); break;
+        }
     }
     return cudaGetLastError();
 }

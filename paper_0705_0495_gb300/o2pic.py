@@ -51,10 +51,11 @@ class pic_config(C.Structure):
 
 EXPORTS = ["pic_workspace_size", "pic_init", "pic_step", "pic_diagnostics", "pic_get_state",
            "pic_set_state", "pic_set_step", "pic_set_numeric_budget", "pic_fields", "pic_numax", "pic_set_timing",
-           "pic_timing", "pic_kernel_timing", "pic_get_launch", "pic_set_launch", "pic_destroy",
+           "pic_timing", "pic_kernel_timing", "pic_get_launch", "pic_set_launch", "pic_launch_shapes",
+           "pic_get_launch_shape", "pic_set_launch_shape", "pic_destroy",
            "pic_last_error",
            "pic_field_solve_static"]
-KERNELS = {"push": 0, "coulomb": 1, "sequential_gas": 2}
+KERNELS = {"push": 0, "coulomb": 1, "sequential_gas": 2, "push_diag": 3}
 
 _lib = None
 
@@ -100,6 +101,12 @@ def load(path: str = LIB_PATH):
     l.pic_get_launch.argtypes = [vp, C.c_int, ip, ip]
     l.pic_set_launch.restype = C.c_int
     l.pic_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    l.pic_launch_shapes.restype = C.c_int
+    l.pic_launch_shapes.argtypes = [vp, C.c_int, ip, ip, ip, C.c_int]
+    l.pic_get_launch_shape.restype = C.c_int
+    l.pic_get_launch_shape.argtypes = [vp, C.c_int, ip, ip]
+    l.pic_set_launch_shape.restype = C.c_int
+    l.pic_set_launch_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     l.pic_destroy.restype = None
     l.pic_destroy.argtypes = [vp]
     l.pic_last_error.restype = C.c_char_p
@@ -279,7 +286,8 @@ class Simulation:
                 "slots": cnt[28:31].copy(), "steps": int(cnt[31]),
                 "particle_steps": int(cnt[32]), "candidates": int(cnt[33]),
                 "slots_visited": int(cnt[34]), "coulomb_particles": int(cnt[35]),
-                "sequential_gas_slots": int(cnt[36]), "eq1_evaluations": int(cnt[37])}
+                "sequential_gas_slots": int(cnt[36]), "eq1_evaluations": int(cnt[37]),
+                "graph_cycle_steps": int(cnt[38]), "graph_launch_calls": int(cnt[39])}
 
     def set_timing(self, on=True):
         self._check(self.lib.pic_set_timing(self.h, 1 if on else 0))
@@ -305,6 +313,27 @@ class Simulation:
         cur, mx = C.c_int(), C.c_int()
         self._check(self.lib.pic_get_launch(self.h, KERNELS[kernel], C.byref(cur), C.byref(mx)))
         return cur.value, mx.value
+
+    def launch_shapes(self, kernel="push"):
+        """[(threads per block, slots per thread, largest blocks per SM)] of
+        the shapes a kernel kind is compiled for"""
+        cap = 16
+        t, p, m = ((C.c_int * cap)() for _ in range(3))
+        n = self.lib.pic_launch_shapes(self.h, KERNELS[kernel], t, p, m, cap)
+        if n < 0:
+            raise PicError(1, self.lib.pic_last_error(self.h).decode())
+        return [(t[k], p[k], m[k]) for k in range(n)]
+
+    def launch_shape(self, kernel="push"):
+        """(shape index, blocks per SM) of a kernel kind's grid"""
+        sh, b = C.c_int(), C.c_int()
+        self._check(self.lib.pic_get_launch_shape(self.h, KERNELS[kernel], C.byref(sh), C.byref(b)))
+        return sh.value, b.value
+
+    def set_launch_shape(self, shape, blocks_per_sm, kernel="push"):
+        """launch shape (index into launch_shapes()) and blocks per SM
+        (results do not depend on them)"""
+        self._check(self.lib.pic_set_launch_shape(self.h, KERNELS[kernel], int(shape), int(blocks_per_sm)))
 
     def set_launch(self, blocks_per_sm, kernel="push"):
         """blocks per SM of a kernel kind's grid (results do not depend on it)"""

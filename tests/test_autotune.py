@@ -18,6 +18,11 @@ def test_push_candidates_are_every_count_that_fits():
     assert autotune.push_candidates(0) == [1]
 
 
+def test_shape_candidates_cover_every_shape_and_count():
+    shapes = [(256, 4, 3), (128, 8, 2), (512, 4, 1)]
+    assert autotune.shape_candidates(shapes) == [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (2, 1)]
+
+
 def _gpu():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
@@ -102,4 +107,65 @@ def test_push_tuner_times_every_count_and_keeps_the_fastest():
     assert set(ms) == set(range(1, mx + 1))
     assert ms[best] == min(ms.values()) and all(v > 0 for v in ms.values())
     assert sim.launch()[0] == best
+    sim.close()
+
+
+@pytest.mark.gpu
+def test_push_launch_shapes_do_not_change_fp32_results():
+    """The FP32 state after 250 steps is bit for bit the same for every
+    compiled launch shape of the push (threads per block, slots per thread)
+    at its largest and at one block per SM, and with the shape switched in
+    the middle of a run."""
+    _gpu()
+    from paper_0705_0495_gb300 import o2pic
+    d = inputs.cfg1(fp64=False, n_op=40000)
+    tabs = inputs.xs_tables()
+    ref_sim = o2pic.Simulation([d], tabs)
+    shapes = ref_sim.launch_shapes()
+    assert len(shapes) >= 3 and {spt for _, spt, _ in shapes} >= {4, 8}
+    assert len({nt for nt, _, _ in shapes}) >= 2
+    ref_sim.step(250)
+    ref = [ref_sim.get_state(0, s) for s in range(3)]
+    gref = ref_sim.diagnostics(0)
+    ref_sim.close()
+    runs = [[(k, mx)] for k, (_, _, mx) in enumerate(shapes)] + [[(k, 1)] for k in range(len(shapes))]
+    runs.append([(len(shapes) - 1, 1), (0, shapes[0][2])])
+    for plan in runs:
+        sim = o2pic.Simulation([d], tabs)
+        per = 250 // len(plan)
+        done = 0
+        for i, (k, b) in enumerate(plan):
+            sim.set_launch_shape(k, b)
+            assert sim.launch_shape() == (k, b)
+            n = per if i < len(plan) - 1 else 250 - done
+            sim.step(n)
+            done += n
+        for s in range(3):
+            st = sim.get_state(0, s)
+            for key in ("x", "vx", "vy", "vz", "alive"):
+                assert np.array_equal(st[key], ref[s][key]), (plan, s, key)
+        g = sim.diagnostics(0)
+        for key in ("events", "absorbed", "eedf", "iedf", "fm"):
+            assert np.array_equal(g[key], gref[key]), (plan, key)
+        assert np.array_equal(g["dens_sum"], gref["dens_sum"])
+        sim.close()
+
+
+@pytest.mark.gpu
+def test_push_shape_tuner_times_every_shape_and_keeps_the_fastest():
+    _gpu()
+    from paper_0705_0495_gb300 import o2pic
+    sim = o2pic.Simulation([inputs.cfg1(fp64=False, n_op=40000)], inputs.xs_tables())
+    best, ms = autotune.tune_push_shape(sim, steps=20, rounds=1)
+    shapes = sim.launch_shapes()
+    assert len(ms) == sum(mx for _, _, mx in shapes)
+    key = f"{best[0]}x{best[1]}@{best[2]}"
+    assert ms[key] == min(ms.values())
+    k, b = sim.launch_shape()
+    assert (shapes[k][0], shapes[k][1], b) == best
+    with pytest.raises(o2pic.PicError):
+        sim.set_launch_shape(len(shapes), 1)
+    with pytest.raises(o2pic.PicError):
+        sim.set_launch_shape(0, shapes[0][2] + 1)
+    assert sim.launch_shape() == (k, b)
     sim.close()
