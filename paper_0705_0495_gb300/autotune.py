@@ -18,7 +18,8 @@ warps) against slots per thread (more independent work per thread, more
 registers).  Its results depend on none of these, so the push tuner switches
 them on one running simulation and times the candidates in interleaved
 rounds (each round gives every candidate the next stretch of the discharge,
-so a drift of the plasma favours none).
+so a drift of the plasma favours none).  Both push tuners end on a whole RF
+cycle, so that whole-cycle steps after them replay the captured cycle graph.
 """
 import dataclasses
 
@@ -87,6 +88,7 @@ def tune_push_blocks(sim, steps=200, rounds=2, cands=None):
     ms = {k: v / (rounds * steps) for k, v in tot.items()}
     best = min(ms, key=ms.get)
     sim.set_launch(best)
+    sim.align_to_cycle()
     return best, ms
 
 
@@ -121,5 +123,6 @@ def tune_push_shape(sim, steps=200, rounds=2):
     ms = {c: v / (rounds * steps) for c, v in tot.items()}
     best = min(ms, key=ms.get)
     sim.set_launch_shape(*best)
+    sim.align_to_cycle()
     nt, spt, _ = shapes[best[0]]
     return (nt, spt, best[1]), {f"{shapes[k][0]}x{shapes[k][1]}@{b}": v for (k, b), v in ms.items()}

@@ -289,6 +289,18 @@ class Simulation:
                 "sequential_gas_slots": int(cnt[36]), "eq1_evaluations": int(cnt[37]),
                 "graph_cycle_steps": int(cnt[38]), "graph_launch_calls": int(cnt[39])}
 
+    def align_to_cycle(self):
+        """step to the next whole RF cycle when one cycle runs as a captured
+        CUDA graph, so that whole-cycle step() calls from here on replay that
+        graph (a start off the schedule's period runs single steps); returns
+        the number of time steps taken"""
+        g = self.diagnostics(0)
+        c = g["graph_cycle_steps"]
+        n = (-g["steps"]) % c if c > 0 else 0
+        if n:
+            self.step(n)
+        return n
+
     def set_timing(self, on=True):
         self._check(self.lib.pic_set_timing(self.h, 1 if on else 0))
 

@@ -48,15 +48,16 @@ def welch_z(a, b):
     return z
 
 
-def compare(ens_a, ens_b, min_iedf_bins=1):
+def compare_labeled(ens_a, ens_b, min_iedf_bins=1):
     """z of every node of the densities and potential and of every EEDF and
     IEDF bin with at least MIN_COUNTS counts on both sides; returns
-    (z array, {part: number of quantities})"""
-    zs, sizes = [], {}
+    (z array, {part: number of quantities}, [(part, index) of each z])"""
+    zs, sizes, labels = [], {}, []
     for key in ("dens", "phi"):
         z = welch_z([g[key].ravel() for g in ens_a], [o[key].ravel() for o in ens_b])
         zs.append(z)
         sizes[key] = len(z)
+        labels += [(key, i) for i in range(len(z))]
     for key in ("eedf", "iedf"):
         a = np.array([g[key] for g in ens_a])
         b = np.array([o[key] for o in ens_b])
@@ -66,7 +67,28 @@ def compare(ens_a, ens_b, min_iedf_bins=1):
         z = welch_z(a[:, keep], b[:, keep])
         zs.append(z)
         sizes[key] = len(z)
-    return np.concatenate(zs), sizes
+        labels += [(key, int(i)) for i in np.flatnonzero(keep)]
+    return np.concatenate(zs), sizes, labels
+
+
+def compare(ens_a, ens_b, min_iedf_bins=1):
+    """compare_labeled without the labels"""
+    z, sizes, _ = compare_labeled(ens_a, ens_b, min_iedf_bins)
+    return z, sizes
+
+
+def worst(ens_a, ens_b, n=5, min_iedf_bins=1):
+    """the n quantities of largest |z|: part, flat index, z and each
+    ensemble's mean and standard deviation there"""
+    z, _, labels = compare_labeled(ens_a, ens_b, min_iedf_bins)
+    out = []
+    for j in np.argsort(-np.abs(z))[:n]:
+        key, i = labels[j]
+        a = np.array([np.asarray(g[key], dtype=float).ravel()[i] for g in ens_a])
+        b = np.array([np.asarray(o[key], dtype=float).ravel()[i] for o in ens_b])
+        out.append({"part": key, "index": i, "z": float(z[j]), "mean_a": float(a.mean()),
+                    "sd_a": float(a.std(ddof=1)), "mean_b": float(b.mean()), "sd_b": float(b.std(ddof=1))})
+    return out
 
 
 def within_3(zs):

@@ -168,4 +168,14 @@ def test_push_shape_tuner_times_every_shape_and_keeps_the_fastest():
     with pytest.raises(o2pic.PicError):
         sim.set_launch_shape(0, shapes[0][2] + 1)
     assert sim.launch_shape() == (k, b)
+    # the tuner ends on a whole RF cycle: a cycle's steps are one graph launch
+    g0 = sim.diagnostics(0)
+    c = g0["graph_cycle_steps"]
+    assert c > 0 and g0["steps"] % c == 0
+    sim.step(2 * c)
+    g1 = sim.diagnostics(0)
+    assert g1["graph_launch_calls"] - g0["graph_launch_calls"] == 2
+    assert sim.align_to_cycle() == 0
+    sim.step(3)
+    assert sim.align_to_cycle() == c - 3
     sim.close()

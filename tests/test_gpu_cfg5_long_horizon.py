@@ -22,7 +22,7 @@ import numpy as np
 import pytest
 
 import oracle
-from ensemble import averages, compare, within_3
+from ensemble import averages, compare, within_3, worst
 from paper_0705_0495_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -103,6 +103,7 @@ def test_cfg5_1000_cycles_fp32_and_fp64_gpu_ensembles_match_the_oracle():
         ok[name] = frac
         mid = inputs.cfg5().n_cells // 2
         report[name] = dict(meta, within_3=frac, sizes=sizes, max_abs_z=float(np.max(np.abs(zs))),
+                            worst=worst(runs, orc, 5, min_iedf_bins=5),
                             mean_dens_mid=[float(np.mean([r["dens"][s][mid] for r in runs])) for s in range(3)])
     report["oracle"]["mean_dens_mid"] = [float(np.mean([r["dens"][s][inputs.cfg5().n_cells // 2] for r in orc]))
                                          for s in range(3)]
