@@ -28,9 +28,10 @@ def averages(g):
 
 def welch_z(a, b):
     """normal-equivalent deviate of Welch's t for every column of a and b
-    (runs along axis 0); a column with no scatter on either side (the driven
-    electrode's potential) gives 0 when the means agree to 1e-9 of the
-    quantity's scale"""
+    (runs along axis 0); a column with no scatter on either side beyond
+    rounding (standard error below 1e-12 of the quantity's scale: the driven
+    electrode's potential, a time average of the drive alone) gives 0 when
+    the means agree to 1e-9 of the scale"""
     a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
     na, nb = a.shape[0], b.shape[0]
     va, vb = a.var(axis=0, ddof=1) / na, b.var(axis=0, ddof=1) / nb
@@ -38,7 +39,7 @@ def welch_z(a, b):
     se2 = va + vb
     scale = np.sqrt(np.mean(b.mean(axis=0) ** 2)) + 1e-300
     z = np.zeros_like(diff)
-    ok = se2 > 0
+    ok = se2 > (1e-12 * scale) ** 2
     t = diff[ok] / np.sqrt(se2[ok])
     dof = se2[ok] ** 2 / (va[ok] ** 2 / (na - 1) + vb[ok] ** 2 / (nb - 1))
     # the same two-sided tail probability under a standard normal
