@@ -584,7 +584,10 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
     Real *offD = P.off[nxt] + pb, *vxD = P.vx[nxt] + pb, *vyD = P.vy[nxt] + pb,
          *vzD = P.vz[nxt] + pb;
     const unsigned lt = (1u << lane) - 1u;
-    double vm2 = 0.0;  // largest speed^2 of the live particles this lane moves
+    // largest speed^2 of the live particles this lane moves, in the
+    // particles' own precision (one conversion at the end: FP64 arithmetic
+    // per particle is slow on this part)
+    Real vm2 = Real(0);
     for (int i0 = lo; i0 < hi; i0 += 32 * SORT_ILP) {
         int b[SORT_ILP];
         int dst[SORT_ILP];
@@ -636,7 +639,7 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
         for (int r = 0; r < SORT_ILP; ++r) {
             if (dst[r] >= 0) {
                 const int g = gb[r] + dst[r];
-                vm2 = fmax(vm2, (double)(rx[r] * rx[r] + ry[r] * ry[r] + rz[r] * rz[r]));
+                vm2 = fmax(vm2, Real(rx[r] * rx[r] + ry[r] * ry[r] + rz[r] * rz[r]));
                 cellD[g] = b[r];
                 offD[g] = ro[r];
                 vxD[g] = rx[r];
@@ -646,7 +649,7 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
         }
     }
     // speed bound of the species for the particle-target pass
-    vmax_raise(W.vmax2, ds, vm2);
+    vmax_raise(W.vmax2, ds, (double)vm2);
 }
 
 __global__ void k_sort_finish(WsPtrs W)
@@ -1096,10 +1099,10 @@ __device__ __forceinline__ void coulomb_copy(Real *__restrict__ dx, Real *__rest
 template <typename Real>
 __device__ __forceinline__ double speed2_max(const Real *x, const Real *y, const Real *z, int n)
 {
-    double m = 0.0;
+    Real m = Real(0);
     for (int k = threadIdx.x; k < n; k += blockDim.x)
-        m = fmax(m, (double)(x[k] * x[k] + y[k] * y[k] + z[k] * z[k]));
-    return m;
+        m = fmax(m, Real(x[k] * x[k] + y[k] * y[k] + z[k] * z[k]));
+    return (double)m;
 }
 
 // Collision k of a cell with the random numbers of draw 1 + k/2: the normal
@@ -1377,7 +1380,7 @@ k_coulomb_inter(WsPtrs W, Pools<Real> P, int par, int pair, int cap)
     const unsigned stepB = (unsigned)(((unsigned long long)aB * COUL_THREADS) % uB);
     const unsigned stepA = (unsigned)(((unsigned long long)aA * COUL_THREADS) % uA);
     const unsigned chainA = (unsigned)(((unsigned long long)aA * uB) % uA);
-    double m2b = 0.0;  // largest new speed^2 of this thread's B particles
+    Real m2b = Real(0);  // largest new speed^2 of this thread's B particles
     for (unsigned r = t0; r < uB; r += COUL_THREADS) {
         Real vb[3] = {gbx[j], gby[j], gbz[j]};
         unsigned i = i0;
@@ -1396,7 +1399,7 @@ k_coulomb_inter(WsPtrs W, Pools<Real> P, int par, int pair, int cap)
         gbx[j] = vb[0];
         gby[j] = vb[1];
         gbz[j] = vb[2];
-        m2b = fmax(m2b, (double)(vb[0] * vb[0] + vb[1] * vb[1] + vb[2] * vb[2]));
+        m2b = fmax(m2b, Real(vb[0] * vb[0] + vb[1] * vb[1] + vb[2] * vb[2]));
         j += stepB;
         if (j >= uB) j -= uB;
         i0 += stepA;
@@ -1406,7 +1409,7 @@ k_coulomb_inter(WsPtrs W, Pools<Real> P, int par, int pair, int cap)
     if (staged) coulomb_copy<Real>(gax, gay, gaz, ax, ay, az, nA);
     // the new speeds raise both species' recorded largest speeds
     vmax_raise(W.vmax2, d * NSP + sA, speed2_max<Real>(ax, ay, az, nA));
-    vmax_raise(W.vmax2, d * NSP + sB, m2b);
+    vmax_raise(W.vmax2, d * NSP + sB, (double)m2b);
 }
 
 // Births of (19) appended to the electron array of each discharge in cell

@@ -1248,7 +1248,7 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
     // write back: the first particle's new velocity, or its removal and the
     // product that ends its chain; part 0 raises the species' recorded
     // largest speed (the particle-target pass that follows bounds P with it)
-    double m2 = 0.0;
+    Real m2 = Real(0);
     for (int local = tid; local < CHUNK; local += DSMC_THREADS) {
         const int rel = rel0 + local;
         if (rel >= C.n) break;
@@ -1260,7 +1260,7 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
             vxA[i] = v[0];
             vyA[i] = v[1];
             vzA[i] = v[2];
-            m2 = fmax(m2, (double)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+            m2 = fmax(m2, Real(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
         } else {
             const Real off = offA[i];
             cellA[i] = -1;
@@ -1270,7 +1270,7 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
             stage_birth<Real>(B, ((local % SUBTILE) << 1) | 1, ssp[local], c, off, v);
         }
     }
-    if (part == 0) vmax_raise(W.vmax2, ds, m2);
+    if (part == 0) vmax_raise(W.vmax2, ds, (double)m2);
     __syncthreads();
     for (int k = tid; k < C_NCOUNT; k += DSMC_THREADS)
         if (s_ev[k]) atomicAdd(&W.counters[(size_t)d * C_NCOUNT + k], (unsigned long long)s_ev[k]);
