@@ -406,14 +406,14 @@ template <> __device__ __forceinline__ void acc_add(unsigned long long *a, unsig
 }
 template <> __device__ __forceinline__ void acc_add(double *a, double v) { atomicAdd(a, v); }
 
-// Shared charge grid of the FP32 path: the 8 bytes of a node hold two
-// signed 32-bit sums, of the low SPLIT_BITS bits of the fixed-point weights
-// (word 0) and of the rest (word 1); the node's value is
-// word1 * 2^SPLIT_BITS + word0.  Adds are plain 32-bit atomics whose result
-// is not needed (no carry), and both sums stay exact while a block adds at
-// most FLUSH_TICKETS tickets of weights before it flushes (each weight is
-// below 2^FIX_BITS, so word 1 stays below 2^(FIX_BITS - SPLIT_BITS) per
-// particle and word 0 below 2^SPLIT_BITS per add).
+// Split 64-bit shared sums of the FP32 path: the 8 bytes hold two signed
+// 32-bit sums, of the low SPLIT_BITS bits of each added weight (word 0) and
+// of the rest (word 1); the value is word1 * 2^SPLIT_BITS + word0.  Adds are
+// plain 32-bit atomics whose result is not needed (no carry), and both sums
+// stay exact while a block adds at most FLUSH_TICKETS tickets of weights
+// before it flushes (each particle's weight is at most 2^FIX_BITS, so word 1
+// grows by at most 2^(FIX_BITS - SPLIT_BITS) per particle and word 0 by less
+// than 2^SPLIT_BITS per add).
 constexpr int SPLIT_BITS = 12;
 constexpr int FLUSH_TICKETS = 256 / TILES_PER_TICKET;  // 256 tiles of weights at most
 static_assert((long long)FLUSH_TICKETS * TILES_PER_TICKET * CHUNK * (1LL << (FIX_BITS - SPLIT_BITS)) < (1LL << 31),
@@ -423,12 +423,6 @@ __device__ __forceinline__ void split_add(unsigned long long *node, unsigned v)
     unsigned *w = reinterpret_cast<unsigned *>(node);  // w[0] low part, w[1] high part
     atomicAdd(&w[0], v & ((1u << SPLIT_BITS) - 1u));
     atomicAdd(&w[1], v >> SPLIT_BITS);
-}
-__device__ __forceinline__ void split_sub(unsigned long long *node, unsigned v)
-{
-    unsigned *w = reinterpret_cast<unsigned *>(node);
-    atomicSub(&w[0], v & ((1u << SPLIT_BITS) - 1u));
-    atomicSub(&w[1], v >> SPLIT_BITS);
 }
 __host__ __device__ __forceinline__ unsigned long long split_value(unsigned long long node)
 {
@@ -458,6 +452,22 @@ template <> __device__ __forceinline__ double sacc_value<double>(unsigned long l
     return (double)(long long)node * (1.0 / (double)(1ull << FIX_BITS_64));
 }
 
+// a node's sum in the global accumulators' type from the block's shared sums
+template <typename Real>
+__device__ __forceinline__ typename AccT<Real>::T sacc_node(const unsigned long long *sAcc, const unsigned *sCnt, int i);
+template <>
+__device__ __forceinline__ unsigned long long sacc_node<float>(const unsigned long long *sAcc, const unsigned *sCnt,
+                                                               int i)
+{
+    const unsigned long long lw = i > 0 ? split_value(sAcc[i - 1]) : 0ull;
+    return ((unsigned long long)sCnt[i] << FIX_BITS) - split_value(sAcc[i]) + lw;
+}
+template <>
+__device__ __forceinline__ double sacc_node<double>(const unsigned long long *sAcc, const unsigned *, int i)
+{
+    return sacc_value<double>(sAcc[i]);
+}
+
 // charge of one particle added to (sign > 0) or removed from the global
 // accumulator of its species (births, pair-pass kills)
 __device__ __forceinline__ void deposit_global(unsigned long long *acc, int c, float off, int sign)
@@ -479,29 +489,60 @@ template <typename Real> __device__ __forceinline__ typename AccT<Real>::T *acc_
 template <> __device__ __forceinline__ unsigned long long *acc_global<float>(const WsPtrs &W) { return W.acc_fix; }
 template <> __device__ __forceinline__ double *acc_global<double>(const WsPtrs &W) { return W.acc_dbl; }
 
-// Charge of the four slots of a thread into the shared grid.  When the
-// whole warp's slots sit in one cell (sorted, slow particles), the weights
-// are summed over the warp and one lane adds them; otherwise every lane adds
-// its own (its four weights summed first when they share a cell, and
-// 4 * 32 * 2^FIX_BITS < 2^32).  No lane-matching: it runs on a narrow pipe.
-__device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep[4], const float off[4],
-                                         bool spread)
+// Charge of the four slots of a thread into the block's shared sums.  The
+// FP32 sums are kept per CELL: the particles that land in it (sCnt, one
+// 32-bit add) and the sum of their upper CIC weights w1 = rn(offset
+// 2^FIX_BITS) (sAcc, split words); node i is then
+// count_i 2^FIX_BITS - W1_i + W1_(i-1), the same integer as the sum of the
+// particles' two node weights, with three shared atomics per particle
+// instead of four.  When the whole warp's slots sit in one cell (sorted,
+// slow particles) the weights are summed over the warp and one lane adds
+// them; otherwise every lane adds its own (its four summed first when they
+// share a cell; 4 * 32 * 2^FIX_BITS < 2^32).  No lane matching: it runs on a
+// narrow pipe.
+__device__ __forceinline__ void deposit4(unsigned long long *sAcc, unsigned *sCnt, const int dep[4],
+                                         const float off[4])
+{
+    unsigned w1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w1[k] = dep[k] >= 0 ? __float2uint_rn(off[k] * (float)(1 << FIX_BITS)) : 0u;
+    const int lane = threadIdx.x & 31;
+    const bool same = dep[0] >= 0 && dep[1] == dep[0] && dep[2] == dep[0] && dep[3] == dep[0];
+    const unsigned a = w1[0] + w1[1] + w1[2] + w1[3];
+    const int c0 = __shfl_sync(0xffffffffu, dep[0], 0);
+    if (__all_sync(0xffffffffu, same && dep[0] == c0)) {
+        const unsigned sa = __reduce_add_sync(0xffffffffu, a);
+        if (lane == 0) {
+            atomicAdd(&sCnt[c0], 128u);
+            split_add(&sAcc[c0], sa);
+        }
+        return;
+    }
+    if (same) {
+        atomicAdd(&sCnt[dep[0]], 4u);
+        split_add(&sAcc[dep[0]], a);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        // an empty slot adds nothing to cell 0
+        const int ck = dep[k] >= 0 ? dep[k] : 0;
+        atomicAdd(&sCnt[ck], dep[k] >= 0 ? 1u : 0u);
+        split_add(&sAcc[ck], w1[k]);
+    }
+}
+
+// The push that also samples the diagnostics keeps its FP32 sums per NODE
+// (both CIC weights of a particle, split words, four shared atomics per
+// particle): its shared memory holds the histograms, and per-cell counts on
+// top of them would leave room for fewer blocks per SM.
+__device__ __forceinline__ void deposit4_nodes(unsigned long long *sAcc, const int dep[4], const float off[4])
 {
     unsigned w0[4], w1[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         w1[k] = dep[k] >= 0 ? __float2uint_rn(off[k] * (float)(1 << FIX_BITS)) : 0u;
         w0[k] = dep[k] >= 0 ? (1u << FIX_BITS) - w1[k] : 0u;
-    }
-    if (spread) {
-        // a species whose slots rarely share a cell (electrons): every slot adds its own
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (dep[k] < 0) continue;
-            split_add(&sAcc[dep[k]], w0[k]);
-            split_add(&sAcc[dep[k] + 1], w1[k]);
-        }
-        return;
     }
     const int lane = threadIdx.x & 31;
     const bool same = dep[0] >= 0 && dep[1] == dep[0] && dep[2] == dep[0] && dep[3] == dep[0];
@@ -530,8 +571,7 @@ __device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep
         split_add(&sAcc[ck + 1], w1[k]);
     }
 }
-__device__ __forceinline__ void deposit4(unsigned long long *sAcc, const int dep[4], const double off[4],
-                                         bool /*spread*/)
+__device__ __forceinline__ void deposit4_nodes(unsigned long long *sAcc, const int dep[4], const double off[4])
 {
     constexpr double SC = (double)(1ull << FIX_BITS_64);
     unsigned long long w0[4], w1[4];
@@ -603,6 +643,8 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     pdl_wait();
     using Acc = typename AccT<Real>::T;
     constexpr int PUSH_THREADS = SH::threads, NW = SH::nw, G = SH::groups, QCAP = SH::qcap;
+    // FP32 without diagnostics: per-cell sums (counts + upper weights)
+    constexpr bool CELLS = sizeof(Real) == 4 && !DIAG;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *sAcc = reinterpret_cast<unsigned long long *>(smem);  // integer sums (both paths)
     Real *sE = reinterpret_cast<Real *>(sAcc + (Nmax + 2));
@@ -613,6 +655,9 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
     unsigned *sEedf = reinterpret_cast<unsigned *>(sE + (Nmax + 2)) + NW * QCAP;
     unsigned *sFm = sEedf + eedf_max;
     unsigned char *qBin = reinterpret_cast<unsigned char *>(sFm + fm_max) + w * QCAP;
+    // FP32: particles per cell of the block's sums, after the queues' bins
+    unsigned *sCnt = reinterpret_cast<unsigned *>(
+        (reinterpret_cast<size_t>(reinterpret_cast<unsigned char *>(sFm + fm_max) + NW * QCAP) + 15) & ~size_t(15));
 
     __shared__ int s_ticket[2];
     __shared__ unsigned s_cnt[C_NCOUNT];
@@ -636,7 +681,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         __syncthreads();
         Acc *g = accG + (size_t)fs * W.total_nodes + Dd.gbase;
         for (int i = tid; i <= Dd.N; i += PUSH_THREADS) {
-            const Acc v = sacc_value<Real>(sAcc[i]);
+            const Acc v = CELLS ? sacc_node<Real>(sAcc, sCnt, i) : sacc_value<Real>(sAcc[i]);
             if (v != Acc(0)) acc_add(&g[i], v);
         }
         for (int q = tid; q < C_NCOUNT; q += PUSH_THREADS) {
@@ -703,7 +748,10 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 for (int i = tid; i <= Dn.N; i += PUSH_THREADS) sE[i] = Eg[i];
                 d = nd;
             }
-            for (int i = tid; i <= Dn.N + 1; i += PUSH_THREADS) sAcc[i] = 0ull;
+            for (int i = tid; i <= Dn.N + 1; i += PUSH_THREADS) {
+                sAcc[i] = 0ull;
+                if (CELLS) sCnt[i] = 0u;
+            }
             {
                 const SpeciesC &Sn = Dn.sp[nx % NSP];
                 for (int b = tid; b < Sn.nbins; b += PUSH_THREADS) {
@@ -911,7 +959,10 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                     }
                 }
             }
-            deposit4(sAcc, dep, off, false);
+            if constexpr (CELLS)
+                deposit4(sAcc, sCnt, dep, off);
+            else
+                deposit4_nodes(sAcc, dep, off);
             tslots += nslots;
             tlive += nlive;
             if (full) {
@@ -1444,12 +1495,14 @@ k_births(WsPtrs W, Pools<Real> P, int par, int salt)
 }
 
 template <typename Real>
-static size_t push_smem_bytes(int Nmax, int eedf_max, int fm_max, int nw, int qcap)
+static size_t push_smem_bytes(int Nmax, int eedf_max, int fm_max, int nw, int qcap, bool cells)
 {
     size_t b = sizeof(unsigned long long) * (Nmax + 2) + sizeof(Real) * (Nmax + 2);
     b += sizeof(int) * nw * qcap;  // candidate slots
     b += sizeof(unsigned) * (eedf_max + fm_max);
     b += (size_t)nw * qcap;        // candidate energy bins
+    b = (b + 15) & ~size_t(15);
+    if (cells) b += sizeof(unsigned) * (Nmax + 2);  // particles per cell
     return (b + 15) & ~size_t(15);
 }
 
@@ -1467,8 +1520,8 @@ using PushD0 = PushShape<256, 4, 2>;
 template <typename Real, typename SH>
 static cudaError_t push_shape_setup(LaunchCfg &L, int k)
 {
-    const size_t sm = push_smem_bytes<Real>(L.maxN, 0, 0, SH::nw, SH::qcap);
-    const size_t smd = push_smem_bytes<Real>(L.maxN, L.eedf_max, L.fm_max, SH::nw, SH::qcap);
+    const size_t sm = push_smem_bytes<Real>(L.maxN, 0, 0, SH::nw, SH::qcap, sizeof(Real) == 4);
+    const size_t smd = push_smem_bytes<Real>(L.maxN, L.eedf_max, L.fm_max, SH::nw, SH::qcap, false);
     cudaError_t e = cudaFuncSetAttribute(k_push<Real, false, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_push<Real, true, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
