@@ -619,6 +619,70 @@ __device__ __forceinline__ bool Dd_binned(const WsPtrs &W, int ds)
     return W.disc[ds / NSP].sp[ds % NSP].nbins > 0;
 }
 
+// Push arithmetic of a lane's four slots: E at the particle by linear
+// interpolation, v + (q/m) E dt, offset + v dt / dx.  FP32: two slots per
+// packed instruction (the same roundings as the scalar fused multiply-adds).
+template <typename Real>
+__device__ __forceinline__ void push_arith(const Real *sE, const int c[4], const Real off[4], const Real vx[4],
+                                           Real qm, Real ks, Real vn[4], Real on[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int cc = c[k] >= 0 ? c[k] : 0;
+        const Real e0 = sE[cc], e1 = sE[cc + 1];
+        const Real ep = e0 + off[k] * (e1 - e0);
+        vn[k] = vx[k] + qm * ep;
+        on[k] = off[k] + vn[k] * ks;
+    }
+}
+template <>
+__device__ __forceinline__ void push_arith<float>(const float *sE, const int c[4], const float off[4],
+                                                  const float vx[4], float qm, float ks, float vn[4], float on[4])
+{
+    const float2 qm2 = make_float2(qm, qm), ks2 = make_float2(ks, ks);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int ca = c[2 * p] >= 0 ? c[2 * p] : 0, cb = c[2 * p + 1] >= 0 ? c[2 * p + 1] : 0;
+        const float2 e0 = make_float2(sE[ca], sE[cb]);
+        const float2 e1 = make_float2(sE[ca + 1], sE[cb + 1]);
+        const float2 of = make_float2(off[2 * p], off[2 * p + 1]);
+        const float2 v0 = make_float2(vx[2 * p], vx[2 * p + 1]);
+        const float2 de = __fadd2_rn(e1, make_float2(-e0.x, -e0.y));
+        const float2 ep = __ffma2_rn(of, de, e0);
+        const float2 v = __ffma2_rn(qm2, ep, v0);
+        const float2 o = __ffma2_rn(v, ks2, of);
+        vn[2 * p] = v.x;
+        vn[2 * p + 1] = v.y;
+        on[2 * p] = o.x;
+        on[2 * p + 1] = o.y;
+    }
+}
+// lab kinetic energy factor ke (v^2 + vy^2 + vz^2) of four slots
+template <typename Real>
+__device__ __forceinline__ void energy2(Real ke, const Real v[4], const Real vy[4], const Real vz[4], Real K[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) K[k] = ke * (v[k] * v[k] + vy[k] * vy[k] + vz[k] * vz[k]);
+}
+template <>
+__device__ __forceinline__ void energy2<float>(float ke, const float v[4], const float vy[4], const float vz[4],
+                                               float K[4])
+{
+    const float2 ke2 = make_float2(ke, ke);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const float2 a = make_float2(v[2 * p], v[2 * p + 1]);
+        const float2 y = make_float2(vy[2 * p], vy[2 * p + 1]);
+        const float2 z = make_float2(vz[2 * p], vz[2 * p + 1]);
+        float2 t = __fmul2_rn(a, a);
+        t = __ffma2_rn(y, y, t);
+        t = __ffma2_rn(z, z, t);
+        t = __fmul2_rn(ke2, t);
+        K[2 * p] = t.x;
+        K[2 * p + 1] = t.y;
+    }
+}
+
 // Launch shape of the push: NT threads per block, SPT slots per thread.  A
 // warp takes SPT/4 consecutive sub-tiles of 128 slots per pass and lane l the
 // four consecutive slots 4l .. 4l+3 of each (16-byte vectors, one Philox
@@ -856,6 +920,11 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
             bool nonfin = false;
             unsigned candm = 0u, bins = 0u;
             int dep[4];
+            // the field at the particle, the new velocity and position (the
+            // FP32 path takes two slots per packed instruction)
+            Real vn[4], on[4], Kn[4];
+            push_arith<Real>(sE, c, off, vx, qm, ks, vn, on);
+            if (binned) energy2<Real>(ke, vn, vyl, vzl, Kn);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int ck = c[k];
@@ -863,10 +932,8 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 nslots += ck >= -1 ? 1u : 0u;
                 nlive += was ? 1u : 0u;
                 const int cc = was ? ck : 0;
-                const Real e0 = sE[cc], e1 = sE[cc + 1];
-                const Real ep = e0 + off[k] * (e1 - e0);
-                const Real v = vx[k] + qm * ep;
-                Real o = off[k] + v * ks;
+                const Real v = vn[k];
+                Real o = on[k];
                 const Real fl = floor(o);
                 const bool bad = !(fl > Real(-2 * N - 4) && fl < Real(2 * N + 4));
                 // a non-finite velocity or position is an error, not an absorption
@@ -889,7 +956,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                 int bin = 0;
                 unsigned thr = tnull;
                 if (binned) {
-                    bin = energy_bin(ke * (v * v + vyl[k] * vyl[k] + vzl[k] * vzl[k]), nbins);
+                    bin = energy_bin(Kn[k], nbins);
                     thr = s_btn[bin];
                 }
                 const bool cand = live && wk[k] < thr;
