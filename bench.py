@@ -531,8 +531,8 @@ def run_ours(a, rank, world, local_rank):
     REPLAY = "FP32 replay within 1e-5"
     accuracy = {
         "fp64": "step by step within 1e-9 of the gap and of the thermal speed, identical event counts "
-                "(tests/test_gpu_parity.py); seed ensembles over 60 RF cycles within 3 standard errors "
-                "(tests/test_gpu_long_horizon.py)",
+                "(tests/test_gpu_parity.py); seed ensembles over 60 and over 1000 RF cycles within 3 standard "
+                "errors (tests/test_gpu_long_horizon.py, tests/test_gpu_cfg5_long_horizon.py)",
         "batched": "each discharge of a batched handle equals its own oracle step by step within 1e-9 "
                    "(FP64, uneven discharges, tests/test_gpu_parity.py); the FP32 kernels are those of "
                    f"the single discharge ({REPLAY})",
@@ -638,7 +638,7 @@ def run_ours(a, rank, world, local_rank):
                              "time-averaged densities, potential, EEDF and IEDF of FP32 and FP64 "
                              "seed ensembles within 3 standard errors of the oracle's "
                              "(tests/test_gpu_parity.py, test_gpu_statistics.py, "
-                             "test_gpu_long_horizon.py)"),
+                             "test_gpu_long_horizon.py, test_gpu_cfg5_long_horizon.py)"),
                 "l2": ("inputs larger than L2: the particle state touched per time step "
                        f"({state_bytes / 1e6:.0f} MB) exceeds the 129 MB L2"
                        if not flush else "L2 flushed between timed iterations"),
