@@ -39,6 +39,7 @@ constexpr int MAX_GAS_CH = 16;
 #define O2_FIELD_THREADS 1024
 #endif
 constexpr int FIELD_THREADS = O2_FIELD_THREADS;
+constexpr int FIELD_ILP = 4;  // nodes per thread whose accumulators the field kernel loads at once
 constexpr int FIX_BITS = 24;           // fixed-point deposit: weight * 2^24
 constexpr int MAX_DISCHARGES = 1024;
 constexpr long long SPIN_LIMIT = 1LL << 22;  // polls of a bounded wait

@@ -165,24 +165,41 @@ k_field(WsPtrs W, int par, int diag, int mode)
         __shared__ int s_intE;
         const double K = Dd.Kfix;  // e w 2^-FIX_BITS / eps0
         const bool full = diag || mode != 0;
-        for (int i = tid; i <= N; i += FIELD_THREADS) {
-            long long a[NSP];
+        // the accumulators of FIELD_ILP nodes per thread are all loaded before
+        // any is cleared, so that their loads are in flight together (a store
+        // to one could otherwise alias the next load, one latency each)
+        bool clear[NSP];
 #pragma unroll
-            for (int s = 0; s < NSP; ++s) {
-                const size_t k = (size_t)s * tn + g + i;
-                a[s] = (long long)acc[k];
-                if (mode == 0 && !species_rests(Dd, s, step)) acc[k] = Acc(0);
-                if (diag) W.dens_sum_fix[k] += a[s];  // exact sums; scaled at read-out
+        for (int s = 0; s < NSP; ++s) clear[s] = mode == 0 && !species_rests(Dd, s, step);
+        for (int i0 = tid; i0 <= N; i0 += FIELD_THREADS * FIELD_ILP) {
+            long long aa[FIELD_ILP][NSP];
+#pragma unroll
+            for (int j = 0; j < FIELD_ILP; ++j) {
+                const int i = i0 + j * FIELD_THREADS;
+#pragma unroll
+                for (int s = 0; s < NSP; ++s) aa[j][s] = i <= N ? (long long)acc[(size_t)s * tn + g + i] : 0;
             }
-            const long long q = a[2] - a[0] - a[1];
-            S1[i] = (i == 0 || i == N) ? 0 : q;
-            if (i == 0) s_q0 = q;
-            if (i == N) s_qN = q;
-            if (full) {
-                const double sc = (i == 0 || i == N) ? Dd.dens_fix_wall : Dd.dens_fix;
 #pragma unroll
-                for (int s = 0; s < NSP; ++s) W.dens[(size_t)s * tn + g + i] = (double)a[s] * sc;
-                W.rho[g + i] = QE_ * (double)q * sc;
+            for (int j = 0; j < FIELD_ILP; ++j) {
+                const int i = i0 + j * FIELD_THREADS;
+                if (i > N) break;
+                const long long *a = aa[j];
+#pragma unroll
+                for (int s = 0; s < NSP; ++s) {
+                    const size_t k = (size_t)s * tn + g + i;
+                    if (clear[s]) acc[k] = Acc(0);
+                    if (diag) W.dens_sum_fix[k] += a[s];  // exact sums; scaled at read-out
+                }
+                const long long q = a[2] - a[0] - a[1];
+                S1[i] = (i == 0 || i == N) ? 0 : q;
+                if (i == 0) s_q0 = q;
+                if (i == N) s_qN = q;
+                if (full) {
+                    const double sc = (i == 0 || i == N) ? Dd.dens_fix_wall : Dd.dens_fix;
+#pragma unroll
+                    for (int s = 0; s < NSP; ++s) W.dens[(size_t)s * tn + g + i] = (double)a[s] * sc;
+                    W.rho[g + i] = QE_ * (double)q * sc;
+                }
             }
         }
         __syncthreads();

@@ -249,7 +249,9 @@ __device__ __forceinline__ int energy_bin(double K, int nb)
 }
 
 // One gas-target candidate (null-collision method).  Returns false if the
-// particle died.  v is updated in place; products are staged.
+// particle died.  v is updated in place; products are staged.  The cell and
+// offset are read from cP, offP (into c, off) only when the collision has
+// products or kills the particle.
 struct Outcome {
     bool alive;     // the particle survives
     bool viol;      // sum_j n_j sigma_j u exceeded the bound
@@ -335,7 +337,8 @@ __device__ __forceinline__ bool gas_event(const WsPtrs &W, const Disc &Dd, const
 template <typename Real>
 __device__ __forceinline__ Outcome gas_collide(const WsPtrs &W, const Disc &Dd, int s, unsigned idx,
                                             unsigned long long step, Real numax_n, Real &vx, Real &vy,
-                                            Real &vz, int c, Real off, int tag, const BirthSink<Real> &B)
+                                            Real &vz, const int *cP, const Real *offP, int &c, Real &off,
+                                            int tag, const BirthSink<Real> &B)
 {
     const SpeciesC &S = Dd.sp[s];
     const Real *lutE = Lut<Real>::E(W);
@@ -392,6 +395,11 @@ __device__ __forceinline__ Outcome gas_collide(const WsPtrs &W, const Disc &Dd, 
     GasProducts<Real> pr;
     Real vo[3];
     const bool alive = gas_event<Real>(W, Dd, S, ch, v, V, E, nd, nd2, vo, pr);
+    // the position is needed only by products and by a dying particle
+    if (pr.n > 0 || !alive) {
+        c = *cP;
+        off = *offP;
+    }
     for (int q = 0; q < pr.n; ++q) stage_birth<Real>(B, tag | pr.prod[q], pr.sp[q], c, off, pr.v[q]);
     if (alive) {
         vx = vo[0]; vy = vo[1]; vz = vo[2];
@@ -1072,7 +1080,10 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
 
 // Collisions of the step's candidates (null-collision method, Sec. III
 // kinematics): one thread per candidate, in list order; a dying particle's
-// charge leaves the global grid, births go to its sub-tile's records.  Event
+// charge leaves the global grid, births go to its sub-tile's records.  A
+// candidate's cell and offset are read only when its collision has products
+// or kills it, and its velocity is written back only after an event (a
+// null event changes nothing): each field is a scattered access.  Event
 // counts are summed per block for the discharge of the block's first
 // candidate (the list holds runs of one discharge), others go straight to
 // the global counters.
@@ -1108,18 +1119,21 @@ k_collide(WsPtrs W, Pools<Real> P, int par)
             const int rel = i - Dd.pbase[s];
             const int sub = (W.cnt[ds].chunk0 + rel / CHUNK) * SUBTILES + (rel % CHUNK) / SUBTILE;
             const int slot = rel % SUBTILE;
-            const int c = cellA[i];
-            const Real off = offA[i];
+            int c = 0;
+            Real off = Real(0);
             Real vx = vxA[i], vy = vyA[i], vz = vzA[i];
             const Real nun = S.nbins > 0 ? pick<Real>(W.nubin[S.bin_off + bin].numax_n, W.nubin[S.bin_off + bin].numax_n_f)
                                          : pick<Real>(S.numax_n, S.numax_n_f);
             const BirthSink<Real> B{stage + (size_t)sub * W.birth_cap, W.tile_cnt + (size_t)sub * NSP, ctl, W.birth_cap};
-            const Outcome o = gas_collide<Real>(W, Dd, s, (unsigned)rel, step, nun, vx, vy, vz, c, off,
-                                                slot << 1, B);
+            const Outcome o = gas_collide<Real>(W, Dd, s, (unsigned)rel, step, nun, vx, vy, vz, cellA + i,
+                                                offA + i, c, off, slot << 1, B);
+            // a null event leaves the particle as it was: nothing to write
             if (o.alive) {
-                vxA[i] = vx;
-                vyA[i] = vy;
-                vzA[i] = vz;
+                if (o.reaction >= 0) {
+                    vxA[i] = vx;
+                    vyA[i] = vy;
+                    vzA[i] = vz;
+                }
             } else {
                 cellA[i] = -1;
                 deposit_global(accG + (size_t)s * W.total_nodes + Dd.gbase, c, off, -1);
