@@ -33,6 +33,7 @@ constexpr int SORT_WARPS = O2_SORT_WARPS;  // warps per sort block
 constexpr int SORT_WARP_SLOTS = O2_SORT_WARP_SLOTS;  // slots per sort warp (16-bit counters)
 constexpr int SORT_ILP = O2_SORT_ILP;  // 32-slot rows loaded per warp before ranking
 constexpr int SORT_CHUNK = SORT_WARPS * SORT_WARP_SLOTS;
+constexpr int COLSCAN_SEG = 32;  // rows of the sort's count matrix per column-scan warp
 constexpr int PAIR_BIRTH_CAP = 16;     // births of (19) per cell per pass
 constexpr int MAX_GAS_CH = 16;
 #ifndef O2_FIELD_THREADS
@@ -195,6 +196,8 @@ struct Ctl {
     int D;                        // discharges
     unsigned int births_ticket;   // block order of the birth-append kernel
     unsigned int cand_n;          // collision candidates listed by the push this step
+    unsigned int colscan_ticket;  // warp order of the sort's column scan
+    unsigned int sort_epoch;      // sorts so far (tags the column scan's words)
 };
 
 // Per (discharge, species) dynamic counts.
@@ -220,6 +223,7 @@ struct WsPtrs {
     int *tile_cnt;            // [max_chunks * SUBTILES * 3] births per sub-tile and product species
     void *births;             // [max_chunks * SUBTILES * birth_cap] staged birth records
     int birth_cap;            // records per sub-tile
+    unsigned long long *colscan_agg;  // column totals of the sort's row segments, tagged with the sort
     unsigned long long *births_lb;  // [max_chunks * SUBTILES / BIRTHS_THREADS * 3] look-back words
     unsigned long long *acc_fix;  // [3 * total_nodes] fixed-point density accumulators
     double *acc_dbl;          // [3 * total_nodes] FP64 accumulators

@@ -81,13 +81,14 @@ struct Bump {
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, gpm, gpmf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, nubin, cand, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
+    size_t colscan_agg, ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, gpm, gpmf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, nubin, cand, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
         counters, eedf, iedf, fm, tables, lutE, lutS, lutEf, lutSf, sort_counts, cell_start,
         sort_live, pair_bcount, cell_disc, pair_births, sort_tab, ninit, vt;
     size_t cell[2], off[2], vx[2], vy[2], vz[2];
     size_t total;
     int total_nodes, total_cells, max_chunks, total_cap, sort_blocks, n_lut, maxN, eedf_max, fm_max, cand_cap;
     int birth_cap;
+    long long colscan_units;  // warps of the sort's column scan
     long long gtab_n;  // elements of the node-major gas tables
     std::vector<int> pbase, capr, gbase, ccell, sort_cbase, sort_gmax, cs_base, eedf_base, iedf_base,
         fm_base;
@@ -280,6 +281,7 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
             mc += cr / CHUNK;
             const int g = (cr + SORT_CHUNK - 1) / SORT_CHUNK;
             L.sort_gmax[3 * d + s] = g;
+            L.colscan_units += (long long)((N + 1 + 31) / 32) * ((g + COLSCAN_SEG - 1) / COLSCAN_SEG);
             L.sort_cbase[3 * d + s] = (int)sortc;
             sortc += (long long)g * (N + 1);
             sb += g;
@@ -349,6 +351,7 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.sort_live = B.take(4ull * 3 * D);
     L.sort_tot = B.take(4ull * csb);
     L.warp_base = B.take(4ull * (3 * D + 1));
+    L.colscan_agg = B.take(8ull * 32 * (size_t)std::max(1LL, L.colscan_units));
     L.pair_bcount = B.take(4ull * tc);
     L.cell_disc = B.take(4ull * tc);
     L.pair_first = B.take(4ull * tc);
@@ -727,6 +730,7 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.births = b + L.births;
     W.birth_cap = L.birth_cap;
     W.births_lb = reinterpret_cast<unsigned long long *>(b + L.births_lb);
+    W.colscan_agg = reinterpret_cast<unsigned long long *>(b + L.colscan_agg);
     W.acc_fix = reinterpret_cast<unsigned long long *>(b + L.acc);
     W.acc_dbl = reinterpret_cast<double *>(b + L.acc);
     W.Efield = reinterpret_cast<double *>(b + L.Efield);
@@ -870,7 +874,12 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     h->L.sort_warp_base = reinterpret_cast<const int *>(b + L.warp_base);
     std::vector<int> wbase(3 * n_discharges + 1, 0);
     for (int d = 0; d < n_discharges; ++d)
-        for (int s = 0; s < 3; ++s) wbase[3 * d + s + 1] = wbase[3 * d + s] + cfgs[d].n_cells + 1;
+        for (int s = 0; s < 3; ++s) {
+            // column-scan warps of (d, s): groups of 32 buckets x segments of rows
+            const int g = L.sort_gmax[3 * d + s];
+            wbase[3 * d + s + 1] = wbase[3 * d + s] +
+                                   ((cfgs[d].n_cells + 1 + 31) / 32) * ((g + COLSCAN_SEG - 1) / COLSCAN_SEG);
+        }
     h->L.sort_col_warps = wbase[3 * n_discharges];
     CK(configure_kernels(h->fp64, h->L));
     CK(push_configure(h->fp64, h->L, nsm));

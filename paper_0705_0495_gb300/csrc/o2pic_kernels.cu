@@ -422,6 +422,11 @@ k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
 {
     pdl_wait();
     extern __shared__ __align__(16) unsigned ssm[];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the column scan that follows: its warp order and the tag of its words
+        W.ctl->colscan_ticket = 0u;
+        W.ctl->sort_epoch += 1u;
+    }
     int ds, bi;
     sort_block(tab, ds, bi);
     const int d = ds / NSP, s = ds % NSP;
@@ -464,45 +469,96 @@ k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
     for (int i = threadIdx.x; i <= N; i += blockDim.x) row[i] = (int)ssm[i];
 }
 
-// One warp per (d, s, bucket): running sums down the sort blocks, so each
-// (block, bucket) entry becomes that block's first slot inside the bucket;
-// the bucket total goes to sort_tot.
+// Column scan of the (block x bucket) count matrix: running sums down the
+// sort blocks, so that each (block, bucket) entry becomes that block's first
+// slot inside the bucket, and the bucket totals in sort_tot.  One warp per
+// (d, s, 32 consecutive buckets, COLSCAN_SEG consecutive rows), in the order
+// of a ticket: the warp loads its rows (each row's 32 buckets in one 128-byte
+// load), publishes their column totals tagged with the sort, adds those of
+// the earlier row segments of its buckets (warps with smaller tickets, so
+// running or done, which publish before they wait) and writes each entry's
+// exclusive prefix; the segment holding the last row writes the totals.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __global__ void __launch_bounds__(256)
-k_sort_colscan(WsPtrs W, const int *warp_base)
+k_sort_colscan(WsPtrs W, const int *unit_base)
 {
     pdl_wait();
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    // warp -> (ds, bucket): the buckets of all (d, s) laid end to end
+    Ctl *ctl = W.ctl;
+    int u = 0;
+    if (lane == 0) u = (int)atomicAdd(&ctl->colscan_ticket, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
     const int nds = W.D * NSP;
-    if (gw >= warp_base[nds]) return;
+    if (u >= unit_base[nds]) return;
     int lo = 0, hi = nds;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (warp_base[mid] <= gw) lo = mid; else hi = mid;
+        if (unit_base[mid] <= u) lo = mid; else hi = mid;
     }
     const int ds = lo;
-    const int c = gw - warp_base[ds];
     const int d = ds / NSP, s = ds % NSP;
     const Disc &Dd = W.disc[d];
     const int N = Dd.N;
     const int n = W.cnt[ds].n;
     const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
+    const int nseg = (Dd.sort_gmax[s] + COLSCAN_SEG - 1) / COLSCAN_SEG;
+    const int local = u - unit_base[ds];
+    const int grp = local / nseg, sg = local % nseg;
+    const int c = grp * 32 + lane;
+    const bool valid = c <= N;
     int *cnt = W.sort_counts + Dd.sort_cbase[s];
-    int carry = 0;
-    for (int b0 = 0; b0 < G; b0 += 32) {
-        const int b = b0 + lane;
-        const int v = b < G ? cnt[(size_t)b * (N + 1) + c] : 0;
-        int x = v;
+    const int r0 = sg * COLSCAN_SEG;
+    int v[COLSCAN_SEG];
+    unsigned tot = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (b < G) cnt[(size_t)b * (N + 1) + c] = carry + x - v;
-        carry += __shfl_sync(0xffffffffu, x, 31);
+    for (int k = 0; k < COLSCAN_SEG; ++k) {
+        const int r = r0 + k;
+        v[k] = (valid && r < G) ? cnt[(size_t)r * (N + 1) + c] : 0;
+        tot += (unsigned)v[k];
     }
-    if (lane == 0) W.sort_tot[Dd.cs_base + s * (N + 2) + c] = carry;
+    const unsigned long long epoch = ctl->sort_epoch;
+    // the words of segments 0 .. nseg-1 of this bucket group, 32 per segment
+    unsigned long long *agg = W.colscan_agg + (size_t)(u - sg) * 32;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(agg + (size_t)sg * 32 + lane),
+                 "l"((epoch << 32) | tot) : "memory");
+    unsigned pre = 0;
+    long long spins = 0;
+    bool late = false;
+    for (int k0 = 0; k0 < sg && !late; k0 += 8) {
+        unsigned long long w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = k0 + k < sg ? ld_relaxed_u64(agg + (size_t)(k0 + k) * 32 + lane) : 0ull;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k0 + k >= sg) break;
+            while ((w[k] >> 32) != (epoch & 0xFFFFFFFFull) && spins <= SPIN_LIMIT) {
+                ++spins;
+                __nanosleep(64);
+                w[k] = ld_relaxed_u64(agg + (size_t)(k0 + k) * 32 + lane);
+            }
+            if ((w[k] >> 32) != (epoch & 0xFFFFFFFFull)) {
+                set_status(ctl, ST_TIMEOUT);
+                late = true;
+                break;
+            }
+            pre += (unsigned)(w[k] & 0xFFFFFFFFull);
+        }
+    }
+    unsigned run = pre;
+#pragma unroll
+    for (int k = 0; k < COLSCAN_SEG; ++k) {
+        const int r = r0 + k;
+        if (valid && r < G) cnt[(size_t)r * (N + 1) + c] = (int)run;
+        run += (unsigned)v[k];
+    }
+    const int last = G > 0 ? (G - 1) / COLSCAN_SEG : 0;
+    if (valid && sg == last) W.sort_tot[Dd.cs_base + s * (N + 2) + c] = (int)run;
 }
 
 // Per (d, s): bucket starts (cell_start) by a scan over the bucket totals.

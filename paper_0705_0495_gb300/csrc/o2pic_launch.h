@@ -45,7 +45,7 @@ struct LaunchCfg {
     int sort_blocks;      // sum over (d, s) of sort blocks
     size_t sort_smem;     // count kernel
     size_t scatter_smem;  // scatter kernel
-    int sort_col_warps;   // warps of the column scan (sum over (d, s) of N+1)
+    int sort_col_warps;   // warps of the column scan (sum over (d, s) of bucket groups x row segments)
     const int *sort_warp_base;  // device [D*3+1]: first column-scan warp per (d, s)
     int pair_blocks_sp[NSP];          // evaluation blocks per projectile species
     const int *pair_tab_sp[NSP];      // device [(d, tile)] tables per species

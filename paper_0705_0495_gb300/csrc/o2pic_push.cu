@@ -1412,9 +1412,9 @@ k_dsmc(WsPtrs W, Pools<Real> P, int par, int part)
 // product species in tile order (tiles are numbered in (parent species,
 // slot) order), i.e. in parent order; their charge is deposited.  Each block
 // takes BIRTHS_THREADS consecutive tiles (one per thread, coalesced counts)
-// in ticket order; its place among the blocks of its discharge comes from a
-// look-back over the blocks before it, which only publish sums, so the chain
-// resolves within a few block latencies (waits are bounded).
+// in ticket order; its place among the blocks of its discharge is the sum of
+// the per-species totals that every earlier block publishes before it reads
+// (all read at once by the block's threads; waits are bounded).
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
 {
     unsigned long long v;
@@ -1434,6 +1434,7 @@ k_births(WsPtrs W, Pools<Real> P, int par, int salt)
     using Acc = typename AccT<Real>::T;
     __shared__ int wsum[NSP][BIRTHS_THREADS / 32];
     __shared__ int s_blk, s_excl[NSP], s_tot[NSP];
+    __shared__ unsigned s_part[NSP][BIRTHS_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Ctl *ctl = W.ctl;
     if (tid == 0) s_blk = (int)atomicAdd(&ctl->births_ticket, 1u);
@@ -1492,50 +1493,46 @@ k_births(WsPtrs W, Pools<Real> P, int par, int salt)
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < NSP; ++q) excl[q] += warp > 0 ? wsum[q][warp - 1] : 0;
-    // look-back over the earlier blocks of this discharge, one warp per
-    // species, 32 predecessors per round: the nearest one that has published
-    // its inclusive prefix ends the walk (a ballot finds it, a warp sum adds
-    // the aggregates of the blocks in between)
-    if (warp < NSP) {
-        const int q = warp;
-        // look-back words carry the step and which append of the step wrote
-        // them (0 after the collisions, 1 after the sequential gas scheme)
+    // this block's exclusive prefix within its discharge: the sum of the
+    // aggregates that the discharge's earlier blocks publish.  Every earlier
+    // block took its ticket first, so it is running or done, and it publishes
+    // before it reads; all threads read the predecessors' words at once.
+    // The words carry the step and which append of the step wrote them (0
+    // after the collisions, 1 after the sequential gas scheme).
+    {
         const unsigned long long epoch = (((ctl->step[par] + 1ull) << 1) | (unsigned)salt) & 0xFFFFFFFFull;
         const int first_blk = W.cnt[d * NSP].chunk0 * SUBTILES / BIRTHS_THREADS;
-        unsigned long long *lb = W.births_lb + (size_t)blk * NSP + q;
-        const unsigned own = (unsigned)s_tot[q];
-        unsigned ex = 0;
-        if (blk > first_blk) {
-            if (lane == 0) st_release_u64(lb, (epoch << 32) | own);
-            int jhi = blk - 1;
-            long long spins = 0;
-            for (;;) {
-                const int j = jhi - lane;
-                bool ready = true, incl = true;  // before the first block: an empty prefix
-                unsigned val = 0;
-                if (j >= first_blk) {
-                    const unsigned long long v = ld_acquire_u64(W.births_lb + (size_t)j * NSP + q);
-                    ready = (v >> 32) == epoch;
-                    incl = ready && (v & 0x80000000ull);
-                    val = (unsigned)(v & 0x7FFFFFFFull);
-                }
-                const unsigned im = __ballot_sync(0xffffffffu, incl);
-                const int k = im ? __ffs(im) - 1 : 31;  // lanes 0..k are needed
-                if (__ballot_sync(0xffffffffu, !ready && lane <= k)) {
-                    if (++spins > SPIN_LIMIT) {
-                        if (lane == 0) set_status(ctl, ST_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(64);
-                    continue;
-                }
-                ex += __reduce_add_sync(0xffffffffu, lane <= k ? val : 0u);
-                if (im) break;
-                jhi -= 32;
+        if (tid < NSP) st_release_u64(W.births_lb + (size_t)blk * NSP + tid, (epoch << 32) | (unsigned)s_tot[tid]);
+        unsigned part[NSP] = {0u, 0u, 0u};
+        const int npred = (blk - first_blk) * NSP;
+        long long spins = 0;
+        for (int k = tid; k < npred; k += BIRTHS_THREADS) {
+            const int j = first_blk + k / NSP, q = k % NSP;
+            unsigned long long v = ld_acquire_u64(W.births_lb + (size_t)j * NSP + q);
+            while ((v >> 32) != epoch && spins <= SPIN_LIMIT) {
+                ++spins;
+                __nanosleep(64);
+                v = ld_acquire_u64(W.births_lb + (size_t)j * NSP + q);
             }
+            if ((v >> 32) != epoch) {
+                set_status(ctl, ST_TIMEOUT);
+                break;
+            }
+            const unsigned a = (unsigned)(v & 0xFFFFFFFFull);
+#pragma unroll
+            for (int r = 0; r < NSP; ++r) part[r] += r == q ? a : 0u;
         }
-        if (lane == 0) {
-            st_release_u64(lb, (epoch << 32) | 0x80000000ull | (unsigned long long)(ex + own));
+#pragma unroll
+        for (int q = 0; q < NSP; ++q) {
+            const unsigned v = __reduce_add_sync(0xffffffffu, part[q]);
+            if (lane == 0) s_part[q][warp] = v;
+        }
+        __syncthreads();
+        if (tid < NSP) {
+            const int q = tid;
+            unsigned ex = 0;
+            for (int w = 0; w < BIRTHS_THREADS / 32; ++w) ex += s_part[q][w];
+            const unsigned own = (unsigned)s_tot[q];
             s_excl[q] = (int)ex;
             // the block holding the last tile of the discharge sets the counts
             if (tfirst_blk <= T1 - 1 && T1 - 1 < tfirst_blk + BIRTHS_THREADS) {
