@@ -139,12 +139,12 @@ k_field(WsPtrs W, int par, int diag, int mode)
     const unsigned long long step = ctl->step[par];
     const int tn = W.total_nodes;
     const double dx = Dd.dx;
-    // FP64 scalars once per block: GB300 runs FP64 on few units, and 1024
-    // threads each evaluating sin() would cost more than the whole solve
+    // the drive's potential, once per block by one thread: GB300 runs FP64 on
+    // few units, and 1024 threads each evaluating sin() would cost more than
+    // the whole solve
     __shared__ double s_phi0;
-    if (tid == 0) s_phi0 = Dd.U_rf * sin(Dd.omega * ((double)step * Dd.dt) + Dd.phase);
-    __syncthreads();
-    const double phi0 = s_phi0;
+    auto drive = [&]() { return Dd.U_rf * sin(Dd.omega * ((double)step * Dd.dt) + Dd.phase); };
+    double phi0;
     Real *Er = reinterpret_cast<Real *>(W.Ereal) + g;
     Acc *acc = AccK<Real>::ptr(W);
     if constexpr (sizeof(Real) == 4) {
@@ -179,6 +179,8 @@ k_field(WsPtrs W, int par, int diag, int mode)
 #pragma unroll
                 for (int s = 0; s < NSP; ++s) aa[j][s] = i <= N ? (long long)acc[(size_t)s * tn + g + i] : 0;
             }
+            // thread 0 evaluates the drive while its loads are in flight
+            if (tid == 0 && i0 == 0) s_phi0 = drive();
 #pragma unroll
             for (int j = 0; j < FIELD_ILP; ++j) {
                 const int i = i0 + j * FIELD_THREADS;
@@ -203,6 +205,7 @@ k_field(WsPtrs W, int par, int diag, int mode)
             }
         }
         __syncthreads();
+        phi0 = s_phi0;
         // inclusive int64 scan of S1[1..N-1] and the int128 sum of the result
         const int M = N - 1, lane = tid & 31, warp = tid >> 5;
         const int per = (M + FIELD_THREADS - 1) / FIELD_THREADS;
@@ -296,6 +299,9 @@ k_field(WsPtrs W, int par, int diag, int mode)
             if (tid == 0) W.phi[g + N] = 0.0;
         }
     } else {
+        if (tid == 0) s_phi0 = drive();
+        __syncthreads();
+        phi0 = s_phi0;
         double *x = fsm;  // N+1 entries
         for (int i = tid; i <= N; i += FIELD_THREADS) {
             const double vol = (i == 0 || i == N) ? 0.5 * dx : dx;

@@ -856,6 +856,7 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
         const int nbins = S.nbins;
         const bool binned = nbins > 0;  // electrons: bound per lab-energy bin
         const Real ke = pick<Real>(S.ke_eV, S.ke_eV_f);
+        const float rN = 1.0f / (float)N;  // the diagnostics' x bins
         // the ticket's sub-tiles in rows of NW G: warp w takes sub-tiles
         // w G .. w G + G - 1 of every row
         constexpr int ROW = NW * G;
@@ -1026,8 +1027,16 @@ k_push(WsPtrs W, Pools<Real> P, int par, int Nmax, int eedf_max, int fm_max)
                             if (v < Real(0)) Es = -Es;
                             const Real bb = floor((Es + pick<Real>(Dd.fm_emax, Dd.fm_emax_f)) *
                                                   pick<Real>(Dd.fm_scale, Dd.fm_scale_f));
-                            if (bb >= Real(0) && bb < Real(Dd.fm_bins))
-                                fb = (int)(((long long)cn * Dd.fm_xbins) / N) * Dd.fm_bins + (int)bb;
+                            if (bb >= Real(0) && bb < Real(Dd.fm_bins)) {
+                                // x bin floor(cn X / N) without an integer division: an
+                                // estimate through 1/N in FP32 (off by at most one, as
+                                // cn X <= 2^26), then corrected
+                                const int pr = cn * Dd.fm_xbins;
+                                int xb = (int)((float)pr * rN);
+                                xb += (xb + 1) * N <= pr ? 1 : 0;
+                                xb -= xb * N > pr ? 1 : 0;
+                                fb = xb * Dd.fm_bins + (int)bb;
+                            }
                         }
                         const unsigned peers = __match_any_sync(0xffffffffu, fb);
                         if (fb >= 0 && lane == __ffs(peers) - 1) atomicAdd(&sFm[fb], (unsigned)__popc(peers));
