@@ -248,6 +248,7 @@ struct WsPtrs {
     double *gpm;              // same layout: bound on n_j dx sigma_j(E) u_n for E up to E_{k+1}
     float *gpmf;
     int *sort_counts;         // count matrix
+    unsigned short *sort_whist;  // per-warp bucket counts of each sort block: [(block, warp), bucket]
     int *cell_start;          // [sum over d of 3*(N+2)]
     int *sort_live;           // [D*3]
     int *sort_tot;            // [sum over d of 3*(N+2)] slots per bucket

@@ -81,7 +81,7 @@ struct Bump {
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t colscan_agg, ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, gpm, gpmf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, nubin, cand, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
+    size_t colscan_agg, sort_whist, ctl, disc, cnt, phi_s2_sum, phi0_sum, D0_sum, gtab, gtabf, gpm, gpmf, tile_cnt, births, births_lb, sort_tot, warp_base, pair_first, vmax2, nubin, cand, pair_kills, pair_tab[3], acc, Efield, Ereal, phi, rho, dens, dens_sum, phi_sum, nsamp,
         counters, eedf, iedf, fm, tables, lutE, lutS, lutEf, lutSf, sort_counts, cell_start,
         sort_live, pair_bcount, cell_disc, pair_births, sort_tab, ninit, vt;
     size_t cell[2], off[2], vx[2], vy[2], vz[2];
@@ -347,6 +347,7 @@ Layout make_layout(const pic_config *c, int D, const pic_xs_table *xs, int n_xs,
     L.gpm = B.take(8ull * std::max(1LL, gn));
     L.gpmf = B.take(4ull * std::max(1LL, gn));
     L.sort_counts = B.take(4ull * std::max(1LL, sortc));
+    L.sort_whist = B.take(2ull * SORT_WARPS * std::max(1LL, sortc));
     L.cell_start = B.take(4ull * csb);
     L.sort_live = B.take(4ull * 3 * D);
     L.sort_tot = B.take(4ull * csb);
@@ -759,6 +760,7 @@ extern "C" pic_status pic_init(const pic_config *cfgs, int n_discharges, const p
     W.gpm = reinterpret_cast<double *>(b + L.gpm);
     W.gpmf = reinterpret_cast<float *>(b + L.gpmf);
     W.sort_counts = reinterpret_cast<int *>(b + L.sort_counts);
+    W.sort_whist = reinterpret_cast<unsigned short *>(b + L.sort_whist);
     W.cell_start = reinterpret_cast<int *>(b + L.cell_start);
     W.sort_live = reinterpret_cast<int *>(b + L.sort_live);
     W.sort_tot = reinterpret_cast<int *>(b + L.sort_tot);

@@ -420,14 +420,16 @@ __device__ __forceinline__ void sort_block(const int *tab, int &ds, int &bi)
 }
 
 // Histogram of cells (dead slots in bucket N) of one block of SORT_CHUNK
-// slots; written as row bi of the (block x bucket) count matrix of ds.  Each
-// warp reads SORT_ILP slots per lane before counting, to keep loads in flight.
+// slots, one per warp (SORT_WARP_SLOTS slots, 16-bit counts): the warps'
+// rows go to sort_whist for the scatter, their sum to row bi of the
+// (block x bucket) count matrix of ds.  Each warp reads SORT_ILP slots per
+// lane before counting, to keep loads in flight.
 template <typename Real>
 __global__ void __launch_bounds__(SORT_WARPS * 32)
 k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
 {
     pdl_wait();
-    extern __shared__ __align__(16) unsigned ssm[];
+    extern __shared__ __align__(16) unsigned short wsm[];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // the column scan that follows: its warp order and the tag of its words
         W.ctl->colscan_ticket = 0u;
@@ -441,10 +443,12 @@ k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
     const int G = (n + SORT_CHUNK - 1) / SORT_CHUNK;
     if (bi == 0 && threadIdx.x == 0) W.vmax2[ds] = 0ull;  // raised by the scatter
     if (bi >= G) return;
-    for (int i = threadIdx.x; i <= N; i += blockDim.x) ssm[i] = 0;
+    const int stride = (N + 2) & ~1;
+    for (int i = threadIdx.x; i < SORT_WARPS * stride; i += blockDim.x) wsm[i] = 0;
     __syncthreads();
     const int *cell = P.cell[W.ctl->cur] + Dd.pbase[s];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned short *hw = wsm + (size_t)w * stride;
     const int lo = bi * SORT_CHUNK + w * SORT_WARP_SLOTS;
     const int hi = min(n, lo + SORT_WARP_SLOTS);
     for (int i0 = lo; i0 < hi; i0 += 32 * SORT_ILP) {
@@ -463,16 +467,28 @@ k_sort_count(WsPtrs W, Pools<Real> P, const int *tab)
             // sorted runs: a whole row in one bucket needs no match
             const int b0 = __shfl_sync(0xffffffffu, b[r], 0);
             if (__all_sync(0xffffffffu, b[r] == b0)) {
-                if (lane == 0 && b0 >= 0) atomicAdd(&ssm[b0], 32u);
+                if (lane == 0 && b0 >= 0) hw[b0] += (unsigned short)32;
+                __syncwarp();
                 continue;
             }
             const unsigned peers = __match_any_sync(0xffffffffu, b[r]);
-            if (b[r] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&ssm[b[r]], (unsigned)__popc(peers));
+            if (b[r] >= 0 && lane == __ffs(peers) - 1) hw[b[r]] += (unsigned short)__popc(peers);
+            __syncwarp();
         }
     }
     __syncthreads();
     int *row = W.sort_counts + Dd.sort_cbase[s] + (size_t)bi * (N + 1);
-    for (int i = threadIdx.x; i <= N; i += blockDim.x) row[i] = (int)ssm[i];
+    unsigned short *wrow = W.sort_whist + ((size_t)Dd.sort_cbase[s] + (size_t)bi * (N + 1)) * SORT_WARPS;
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) {
+        int t = 0;
+#pragma unroll
+        for (int q = 0; q < SORT_WARPS; ++q) {
+            const unsigned short h = wsm[(size_t)q * stride + i];
+            wrow[(size_t)q * (N + 1) + i] = h;
+            t += h;
+        }
+        row[i] = t;
+    }
 }
 
 // Column scan of the (block x bucket) count matrix: running sums down the
@@ -592,9 +608,10 @@ k_sort_cellscan(WsPtrs W)
 }
 
 // Stable scatter: warp w of block bi owns slots [lo + w*SORT_WARP_SLOTS, ...);
-// a per-warp bucket count (16-bit) gives each warp its first slot per bucket
-// relative to the block's, then each warp walks its slots in order, ranking
-// equal buckets inside a 32-slot row by lane.  Dead slots (bucket N) are
+// the per-warp bucket counts (16-bit) that the count kernel kept give each
+// warp its first slot per bucket relative to the block's, then each warp
+// walks its slots in order, ranking equal buckets inside a 32-slot row by
+// lane.  Dead slots (bucket N) are
 // dropped.  SORT_ILP rows are loaded before they are ranked.
 template <typename Real>
 __global__ void __launch_bounds__(SORT_WARPS * 32)
@@ -612,44 +629,19 @@ k_sort_scatter(WsPtrs W, Pools<Real> P, const int *tab)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int stride = (N + 2) & ~1;
     unsigned short *hw = hsm + (size_t)w * stride;
-    for (int i = threadIdx.x; i < SORT_WARPS * stride; i += blockDim.x) hsm[i] = 0;
-    __syncthreads();
     const int cur = W.ctl->cur, nxt = cur ^ 1;
     const int pb = Dd.pbase[s];
     const int *cell = P.cell[cur] + pb;
     const int lo = bi * SORT_CHUNK + w * SORT_WARP_SLOTS;
     const int hi = min(n, lo + SORT_WARP_SLOTS);
-    for (int i0 = lo; i0 < hi; i0 += 32 * SORT_ILP) {
-        int b[SORT_ILP];
-#pragma unroll
-        for (int r = 0; r < SORT_ILP; ++r) {
-            const int i = i0 + r * 32 + lane;
-            b[r] = -1;
-            if (i < hi) {
-                const int c = cell[i];
-                b[r] = c < 0 ? N : c;
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < SORT_ILP; ++r) {
-            const int b0 = __shfl_sync(0xffffffffu, b[r], 0);
-            if (__all_sync(0xffffffffu, b[r] == b0)) {
-                if (lane == 0 && b0 >= 0) hw[b0] += (unsigned short)32;
-                __syncwarp();
-                continue;
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, b[r]);
-            if (b[r] >= 0 && lane == __ffs(peers) - 1) hw[b[r]] += (unsigned short)__popc(peers);
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    // per bucket: warp offsets relative to the block's first slot in it
+    // per bucket: warp offsets relative to the block's first slot in it, from
+    // the warps' counts that the count kernel kept
+    const unsigned short *wrow = W.sort_whist + ((size_t)Dd.sort_cbase[s] + (size_t)bi * (N + 1)) * SORT_WARPS;
     for (int c = threadIdx.x; c <= N; c += blockDim.x) {
         unsigned run = 0;
 #pragma unroll
         for (int q = 0; q < SORT_WARPS; ++q) {
-            const unsigned t = hsm[(size_t)q * stride + c];
+            const unsigned t = wrow[(size_t)q * (N + 1) + c];
             hsm[(size_t)q * stride + c] = (unsigned short)run;
             run += t;
         }
@@ -1607,7 +1599,7 @@ cudaError_t configure_kernels(bool fp64, LaunchCfg &L)
 {
     cudaError_t e;
     L.field_smem = sizeof(double) * (L.maxN + 2) + 16 * (L.maxN + 2) + 16;
-    L.sort_smem = sizeof(unsigned) * (L.maxN + 1);
+    L.sort_smem = sizeof(unsigned short) * SORT_WARPS * ((L.maxN + 2) & ~1);
     L.scatter_smem = sizeof(unsigned short) * SORT_WARPS * ((L.maxN + 2) & ~1);
     if (fp64) {
         e = cudaFuncSetAttribute(k_field<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.field_smem);
